@@ -1,0 +1,206 @@
+/*
+ * opf.h -- C ABI of the GB300 ADMM solver for the decomposed linearized
+ * (LinDist3Flow) multi-phase OPF of Ryu, Byeon and Kim, "A GPU-based
+ * Distributed Algorithm for Linearized Optimal Power Flow in Distribution
+ * Systems" (PSCC 2024).
+ *
+ * The library builds the LP of Sec. II-A (Eq. LP_model) from feeder arrays,
+ * splits it into bus, line and merged-leaf subsystems (Sec. V-A) to obtain the
+ * consensus form of Eq. OurModel, computes each subsystem's closed-form
+ * projector once (Eq. closed_2, Algorithm 1 precomputation) and runs the ADMM
+ * iteration of Algorithm 1 on one CUDA device: global update (Eq. closed_1),
+ * local update (Eq. closed_2), dual update (Eq. ADMM-3) and the residuals and
+ * stopping test of Sec. III-C.
+ *
+ * Conventions
+ *  - Every function returns an int status: OPF_OK (0), OPF_NOT_CONVERGED (1)
+ *    or a negative OPF_E_* code; opf_strerror() names it.
+ *  - Input arrays are host memory owned by the caller and are copied during
+ *    the call; nothing is retained.  Output arrays are caller-allocated host
+ *    memory with the stated lengths (checked where a length is passed).
+ *  - The library allocates and owns all device memory of a handle.
+ *  - A handle is not thread safe; use one handle per host thread.  All device
+ *    work of a handle runs on its stream (opf_options.stream, or a stream the
+ *    library creates); calls return after that work has finished.
+ *  - Variable order ("canonical order") of x, the global vector of
+ *    Eq. OurModel:  generators (for each gen, each phase a<b<c: p^g, q^g),
+ *    buses (each bus, each phase: w), loads (each load, each phase:
+ *    p^b, q^b, p^d, q^d), lines (each line, each phase: p_eij, q_eij, p_eji,
+ *    q_eji).  Subsystem order: every non-leaf bus in bus order, then every
+ *    line in line order (a line whose to-bus is a leaf also holds that bus).
+ *    Local slots of a subsystem: ascending global index.  Stacked local
+ *    vectors (x_s, lambda_s) are the subsystems' slots concatenated in
+ *    subsystem order.
+ */
+#ifndef OPF_H
+#define OPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OPF_OK                  0
+#define OPF_NOT_CONVERGED       1   /* max_iter reached; results are readable */
+#define OPF_E_INVALID          -1   /* malformed input (message: opf_last_error) */
+#define OPF_E_INFEASIBLE_LOCAL -2   /* a local system A_s x_s = b_s is inconsistent */
+#define OPF_E_STATE            -3   /* call out of order (e.g. solve before precompute) */
+#define OPF_E_OOM              -4   /* device or host allocation failed */
+#define OPF_E_NUMERIC          -5   /* NaN or Inf in the residual reductions */
+#define OPF_E_TIMEOUT          -6   /* a bounded device wait gave up */
+#define OPF_E_CUDA             -7   /* CUDA runtime error */
+#define OPF_E_CAPACITY         -8   /* size beyond a documented limit */
+
+/* Precision of the iterations (Sec. IV runs the GPU in single precision). */
+#define OPF_PREC_FP64   0   /* plain FP64 iterations */
+#define OPF_PREC_FP32   1   /* FP32 iterations, FP64 reductions, no refinement */
+#define OPF_PREC_MIXED  2   /* FP32 iterations re-centred in FP64, then FP64 polish */
+
+/* Largest subsystem size n_s the iteration kernels accept. */
+#define OPF_MAX_NS 256
+
+/* Radial three-phase feeder (Table I nomenclature).  Phase sets are bit masks
+ * (bit 0 = a, 1 = b, 2 = c).  Per-phase arrays have 3 entries per component
+ * (index = phase), entries of absent phases are ignored.  Bus 0 is the
+ * substation; every other bus has exactly one incoming line (line_to), its
+ * phases equal that line's, and a line's phases are a subset of its from-bus
+ * phases.  Units: powers in p.u., impedances in p.u., voltage squared in p.u.
+ * Infinite bounds are IEEE +-INFINITY. */
+typedef struct opf_feeder {
+    int32_t n_bus;
+    const uint8_t *bus_phases;      /* [n_bus] */
+    const double *bus_wmin;         /* [n_bus*3] bounds on w (Eq. operational) */
+    const double *bus_wmax;         /* [n_bus*3] */
+    const double *bus_gsh;          /* [n_bus*3] shunt conductance g^sh (Eq. balance_eqns) */
+    const double *bus_bsh;          /* [n_bus*3] shunt susceptance b^sh */
+
+    int32_t n_line;                 /* must be n_bus - 1 */
+    const int32_t *line_from;       /* [n_line] from bus i (towards the substation) */
+    const int32_t *line_to;         /* [n_line] to bus j */
+    const uint8_t *line_phases;     /* [n_line] */
+    const double *line_r;           /* [n_line*9] 3x3 resistance, row-major */
+    const double *line_x;           /* [n_line*9] 3x3 reactance, row-major */
+    const double *line_gs_from;     /* [n_line*3] g^s_eij (Eq. power_flow_eqns) */
+    const double *line_bs_from;     /* [n_line*3] b^s_eij */
+    const double *line_gs_to;       /* [n_line*3] g^s_eji */
+    const double *line_bs_to;       /* [n_line*3] b^s_eji */
+    const double *line_tap;         /* [n_line*3] tap ratio tau */
+
+    int32_t n_load;
+    const int32_t *load_bus;        /* [n_load] */
+    const uint8_t *load_phases;     /* [n_load] equal to its bus's phases */
+    const uint8_t *load_delta;      /* [n_load] 0 = wye, 1 = delta (three-phase only) */
+    const double *load_a;           /* [n_load*3] a (Eq. VDLM-1) */
+    const double *load_b;           /* [n_load*3] b (Eq. VDLM-2) */
+    const double *load_alpha;       /* [n_load*3] alpha >= 0 */
+    const double *load_beta;        /* [n_load*3] beta >= 0 */
+
+    int32_t n_gen;
+    const int32_t *gen_bus;         /* [n_gen] */
+    const uint8_t *gen_phases;      /* [n_gen] subset of its bus's phases */
+    const double *gen_pmin;         /* [n_gen*3] */
+    const double *gen_pmax;
+    const double *gen_qmin;
+    const double *gen_qmax;
+    const double *gen_cost;         /* [n_gen] linear cost on every phase's p^g */
+} opf_feeder;
+
+typedef struct opf_options {
+    int32_t device;                 /* CUDA device ordinal */
+    void *stream;                   /* cudaStream_t to run on, or NULL */
+} opf_options;
+
+typedef struct opf_solve_opts {
+    double rho;                     /* penalty (the paper's default is 100) */
+    double eps_rel;                 /* epsilon_rel of the Sec. III-C test */
+    double eps_abs_pres;            /* absolute gate: also require pres <= this */
+    int32_t max_iter;               /* iteration cap (counts every iteration) */
+    int32_t check_every;            /* iterations between tests; even, >= 2 */
+    int32_t precision;              /* OPF_PREC_* */
+    int32_t recenter_every;         /* OPF_PREC_MIXED: iterations between FP64 re-centrings (0 = default) */
+    int32_t engine;                 /* 0 = automatic, 1 = whole-grid kernels, 2 = one-CTA resident */
+} opf_solve_opts;
+
+typedef struct opf_sizes {
+    int64_t n_global;               /* n: length of x */
+    int64_t n_sub;                  /* S */
+    int64_t n_slots;                /* L = sum n_s */
+    int64_t n_rows;                 /* sum m_s */
+    int64_t sum_nf;                 /* sum n_s * f_s of the stored factors (after precompute) */
+    int64_t max_ns;
+} opf_sizes;
+
+typedef struct opf_handle opf_handle;
+
+/* Build the LP of Eq. LP_model from a feeder, decompose it (Sec. V-A) and
+ * upload the subsystems.  Errors: OPF_E_INVALID (malformed feeder),
+ * OPF_E_CAPACITY (a subsystem larger than OPF_MAX_NS), OPF_E_CUDA, OPF_E_OOM. */
+int opf_create(const opf_feeder *f, const opf_options *o, opf_handle **out);
+
+/* Consensus form of Eq. OurModel given directly: n globals with cost c,
+ * bounds lb/ub and an optional is_voltage flag (start value 1, Sec. V-A);
+ * S subsystems with m_s rows and n_s slots; A (row-major m_s x n_s blocks
+ * concatenated), b (m_s entries each) and idx (n_s distinct global indices
+ * each, in the subsystem's slot order) concatenated over s.  Every global
+ * must appear in some subsystem. */
+int opf_create_generic(int32_t n, const double *c, const double *lb, const double *ub,
+                       const uint8_t *is_voltage, int32_t S, const int32_t *m_s,
+                       const int32_t *n_s, const double *A, const double *b,
+                       const int32_t *idx, const opf_options *o, opf_handle **out);
+
+/* Algorithm 1 precomputation (Sec. III-B) on the device in FP64: for each
+ * subsystem an orthonormal basis of row(A_s) by Gram-Schmidt with
+ * re-orthogonalisation (dependent rows dropped after a consistency check),
+ * the projector -Abar_s kept as the smaller of Q Q^T-complement or a null-space
+ * basis, and bbar_s = A_s^+ b_s.  Resets the iterate to the Sec. V-A start.
+ * Idempotent.  Errors: OPF_E_INFEASIBLE_LOCAL, OPF_E_CUDA. */
+int opf_precompute(opf_handle *h);
+
+/* Run Algorithm 1 from the current state until the Sec. III-C test holds with
+ * epsilon_rel = eps and pres <= 1e-4, or max_iter iterations (FP64).
+ * Returns OPF_OK, OPF_NOT_CONVERGED, OPF_E_STATE, OPF_E_NUMERIC, OPF_E_CUDA. */
+int opf_solve(opf_handle *h, double rho, double eps, int32_t max_iter);
+
+/* Same with every option (NULL = defaults: rho 100, eps_rel 1e-8,
+ * eps_abs_pres 1e-4, max_iter 1e6, check_every 50, FP64). */
+int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts);
+
+/* Exactly n_iters FP64 iterations with penalty rho, no stopping test. */
+int opf_step(opf_handle *h, double rho, int32_t n_iters);
+
+/* Reset the iterate to the Sec. V-A start (lambda = 0). */
+int opf_reset(opf_handle *h);
+
+/* Global solution x (n entries, canonical order) and c^T x of the last
+ * iteration.  x may be NULL. */
+int opf_get_solution(opf_handle *h, double *x, size_t n, double *objective);
+
+/* Residuals of the last tested iteration (Sec. III-C); eps_prim and eps_dual
+ * are given for epsilon_rel = 1, i.e. the two norms the test scales.  Any
+ * pointer may be NULL. */
+int opf_get_residuals(opf_handle *h, double *pres, double *dres, double *eps_prim,
+                      double *eps_dual, int64_t *iters);
+
+/* Stacked local copies x_s and duals lambda_s (L entries each, canonical
+ * order); either may be NULL.  opf_set_locals restores them (warm start or
+ * checkpoint); the global x is recomputed by the next iteration. */
+int opf_get_locals(opf_handle *h, double *xs, double *lam, size_t L);
+int opf_set_locals(opf_handle *h, const double *xs, const double *lam, size_t L);
+
+int opf_get_sizes(opf_handle *h, opf_sizes *out);
+
+/* Per-phase device time of the last solve/step in milliseconds (CUDA events
+ * on the handle's stream): [0] precompute, [1] iterations, [2] polish. */
+int opf_get_timing(opf_handle *h, double *ms, int n);
+
+void opf_destroy(opf_handle *h);
+const char *opf_strerror(int code);
+/* Message of the last OPF_E_INVALID / OPF_E_CUDA on this thread. */
+const char *opf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OPF_H */

@@ -1,0 +1,846 @@
+// C ABI of the ADMM library: handle life cycle, device layout, and the
+// drivers that run Algorithm 1 on the device (see include/opf.h).
+//
+// Device layout
+//   Subsystems are reordered by size class (lanes per subsystem W = 8, 16, 32;
+//   R rows per lane for n_s > 32) and packed into warp tasks.  Local slots
+//   follow that order.  The buffer u = rho x_s - lambda is stored in
+//   "global-major" order: the copies of each global i are one contiguous
+//   segment (in canonical slot order), so the global update of Eq. closed_1
+//   is a fixed-order segment sum and needs no atomics.
+//
+// Solve loop
+//   One CUDA graph per solve: a conditional WHILE node whose body runs a
+//   chunk of iterations ending with the Sec. III-C test; the test kernel sets
+//   the loop condition on the device, so a solve is one graph launch and one
+//   final status read.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "opf_internal.h"
+
+namespace opf {
+
+
+
+
+void launch_precompute(const PreArgs &a, cudaStream_t st);
+template <typename T>
+void launch_iterate(const IterArgs<T> &a, const T *u_in, T *u_out, int vstride, double *partials,
+                    const DevStatus *st, bool check, cudaStream_t s);
+void launch_check(const double *partials, int nblk, DevStatus *st, double rho, int add,
+                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
+void launch_copy_if_running(long long n, const double *src, double *dst, const DevStatus *st,
+                            cudaStream_t s);
+void launch_add_iters(DevStatus *st, long long n, cudaStream_t s);
+template <typename T> int prepare_cta_engine(unsigned bytes);
+template <typename T>
+void launch_cta_engine(const IterArgs<T> &g, const CtaLayout &lay, T *u_glob, int n_iters,
+                       int check_every, DevStatus *st, double rho, cudaGraphConditionalHandle cond,
+                       int use_cond, cudaStream_t s);
+template <typename T>
+void launch_make_u(int L, const int *pk, const T *ds, const T *mu, T rho, T *u, const DevStatus *st,
+                   cudaStream_t s);
+template <typename T>
+int launch_global_x(int G, const int2 *gseg, const T *u, const T *ct, const T *lbt, const T *ubt,
+                    const double *xr, const double *c64, T rho, double *x, double *obj_part,
+                    const DevStatus *st, cudaStream_t s);
+template <typename T>
+void launch_init_state(int L, const int *gk, const double *x0, T *ds, T *mu, cudaStream_t s);
+template <typename T>
+void launch_unshift(int L, const int *gk, const double *xr, const double *lamr, const T *ds,
+                    const T *mu, double *ds64, double *mu64, cudaStream_t s);
+template <typename A, typename B>
+void launch_cast(long long n, const A *src, B *dst, cudaStream_t s);
+template <typename T>
+void launch_recenter(int L, int G, int S, const int *gk, const double *xr_old, const double *xr_new,
+                     T *ds, T *mu, double *lamr, const int2 *gseg, const int *uslot,
+                     const double *c64, const double *lb, const double *ub, T *ct, T *lbt, T *ubt,
+                     const int *soff, const int *sn, const int *sf, const int *smode,
+                     const long long *sfoff, const double *F64, const double *bbar, double rho,
+                     T *bt, const DevStatus *st, cudaStream_t s);
+void launch_enter_shift(int L, const int *gk, const double *xr, const double *ds64,
+                        const double *mu64, float *ds32, float *mu32, double *lamr, cudaStream_t s);
+
+}  // namespace opf
+
+using namespace opf;
+
+static thread_local std::string g_last_error;
+
+#define CUDA_TRY(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            g_last_error = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+            return e_ == cudaErrorMemoryAllocation ? OPF_E_OOM : OPF_E_CUDA;             \
+        }                                                                                \
+    } while (0)
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    double rho = 0;
+    int k = 0, R = 0, kind = -1;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        kind = -1;
+    }
+};
+
+struct opf_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    HostModel model;
+    int S = 0, L = 0, G = 0, vstride = 32, n_tasks = 0, iter_blocks = 0;
+    long long nA = 0, nB = 0, nP = 0, nF = 0, sum_nf = 0, n_rows = 0;
+    int max_ns = 0;
+    std::vector<int> canon_slot_to_dev;     // canonical slot -> device slot
+    std::vector<int> h_sn, h_sf;
+    std::vector<void *> allocs;
+    // per subsystem
+    int *d_soff = nullptr, *d_sn = nullptr, *d_sm = nullptr, *d_sf = nullptr, *d_smode = nullptr;
+    int *d_boff = nullptr, *d_pstatus = nullptr;
+    long long *d_aoff = nullptr, *d_poff = nullptr, *d_foff = nullptr;
+    int4 *d_tasks = nullptr;
+    // per slot
+    int *d_gk = nullptr, *d_pk = nullptr, *d_uslot = nullptr;
+    int2 *d_seg = nullptr, *d_gseg = nullptr;
+    double *d_A = nullptr, *d_b = nullptr, *d_W = nullptr, *d_Bw = nullptr, *d_P = nullptr;
+    double *d_F64 = nullptr, *d_bbar64 = nullptr;
+    float *d_F32 = nullptr;
+    // per global
+    double *d_c64 = nullptr, *d_lb64 = nullptr, *d_ub64 = nullptr, *d_x0 = nullptr;
+    double *d_xr = nullptr, *d_xr2 = nullptr, *d_zeroG = nullptr, *d_x = nullptr, *d_objpart = nullptr;
+    float *d_ct32 = nullptr, *d_lbt32 = nullptr, *d_ubt32 = nullptr;
+    // state
+    double *d_ds64 = nullptr, *d_mu64 = nullptr, *d_u64 = nullptr, *d_lamr = nullptr, *d_zeroL = nullptr;
+    float *d_ds32 = nullptr, *d_mu32 = nullptr, *d_u32 = nullptr, *d_bt32 = nullptr;
+    double *d_partials = nullptr;
+    DevStatus *d_st = nullptr;
+    DevStatus *h_st = nullptr;
+    // bookkeeping
+    bool precomputed = false;
+    bool have_prev_u = false;    // d_u64 + L holds the u that produced the last global update
+    double last_rho = 100.0;
+    long long total_iters = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double timing[3] = {0, 0, 0};
+    GraphCache g64, gmix;
+    CtaLayout lay32{}, lay64{};
+    bool cta32_ok = false, cta64_ok = false;
+};
+
+template <typename T>
+static int dalloc(opf_handle *h, T **p, size_t n) {
+    if (n == 0) n = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+    if (e != cudaSuccess) {
+        g_last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return OPF_E_OOM;
+    }
+    h->allocs.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return OPF_OK;
+}
+
+template <typename T>
+static int upload(opf_handle *h, T **p, const std::vector<T> &v) {
+    int rc = dalloc(h, p, v.size());
+    if (rc) return rc;
+    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    return OPF_OK;
+}
+
+#define TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+
+static void size_class(int n, int *W, int *R) {
+    if (n <= 8) { *W = 8; *R = 1; }
+    else if (n <= 16) { *W = 16; *R = 1; }
+    else if (n <= 32) { *W = 32; *R = 1; }
+    else { *W = 32; *R = (n + 31) / 32; }
+}
+
+static unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
+
+template <typename T>
+static bool make_cta_layout(opf_handle *h, CtaLayout *lay, size_t limit) {
+    CtaLayout &c = *lay;
+    c = CtaLayout{};
+    c.S = h->S; c.L = h->L; c.G = h->G; c.n_tasks = h->n_tasks; c.vstride = h->vstride;
+    c.nF = h->nF;
+    size_t off = 0;
+    auto take = [&](unsigned *o, size_t bytes) { *o = (unsigned)off; off = align16((unsigned)(off + bytes)); };
+    take(&c.off_F, (size_t)h->nF * sizeof(T));
+    take(&c.off_bt, (size_t)h->L * sizeof(T));
+    take(&c.off_mu, (size_t)h->L * sizeof(T));
+    take(&c.off_ds, (size_t)h->L * sizeof(T));
+    take(&c.off_u0, (size_t)h->L * sizeof(T));
+    take(&c.off_u1, (size_t)h->L * sizeof(T));
+    take(&c.off_ct, (size_t)h->G * sizeof(T));
+    take(&c.off_lbt, (size_t)h->G * sizeof(T));
+    take(&c.off_ubt, (size_t)h->G * sizeof(T));
+    take(&c.off_seg, (size_t)h->L * sizeof(int2));
+    take(&c.off_gk, (size_t)h->L * sizeof(int));
+    take(&c.off_pk, (size_t)h->L * sizeof(int));
+    take(&c.off_soff, (size_t)h->S * sizeof(int));
+    take(&c.off_sn, (size_t)h->S * sizeof(int));
+    take(&c.off_sf, (size_t)h->S * sizeof(int));
+    take(&c.off_smode, (size_t)h->S * sizeof(int));
+    take(&c.off_sfoff, (size_t)h->S * sizeof(long long));
+    take(&c.off_tasks, (size_t)h->n_tasks * sizeof(int4));
+    take(&c.off_sv, (size_t)32 * 2 * h->vstride * sizeof(T));
+    c.bytes = (unsigned)off;
+    return off <= limit;
+}
+
+static int build_layout(opf_handle *h) {
+    HostModel &M = h->model;
+    h->S = (int)M.subs.size();
+    h->G = M.n;
+    // device order: larger classes first, then larger n
+    std::vector<int> order(h->S);
+    std::iota(order.begin(), order.end(), 0);
+    auto key = [&](int s) {
+        int W, R;
+        size_class(M.subs[s].n, &W, &R);
+        return std::make_pair(-(W * R), -M.subs[s].n);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
+    // canonical slot offsets
+    std::vector<int> csoff(h->S + 1, 0);
+    for (int s = 0; s < h->S; ++s) csoff[s + 1] = csoff[s] + M.subs[s].n;
+    h->L = csoff[h->S];
+    std::vector<int> soff(h->S), sn(h->S), sm(h->S), boff(h->S);
+    std::vector<long long> aoff(h->S), poff(h->S), foff(h->S);
+    std::vector<double> A, b;
+    h->canon_slot_to_dev.assign(h->L, 0);
+    std::vector<int> gk(h->L);
+    long long ao = 0, po = 0, fo = 0;
+    int so = 0, bo = 0, Rmax = 1;
+    h->max_ns = 0;
+    h->n_rows = 0;
+    for (int d = 0; d < h->S; ++d) {
+        const HostSub &s = M.subs[order[d]];
+        soff[d] = so; sn[d] = s.n; sm[d] = s.m; boff[d] = bo;
+        aoff[d] = ao; poff[d] = po; foff[d] = fo;
+        for (int r = 0; r < s.n; ++r) {
+            h->canon_slot_to_dev[csoff[order[d]] + r] = so + r;
+            gk[so + r] = s.vars[r];
+        }
+        A.insert(A.end(), s.A.begin(), s.A.end());
+        b.insert(b.end(), s.b.begin(), s.b.end());
+        so += s.n; bo += s.m;
+        ao += (long long)s.m * s.n;
+        po += (long long)s.n * s.n;
+        fo += (long long)s.n * std::max(0, std::min(s.m, s.n / 2));
+        int W, R;
+        size_class(s.n, &W, &R);
+        Rmax = std::max(Rmax, R);
+        h->max_ns = std::max(h->max_ns, s.n);
+        h->n_rows += s.m;
+    }
+    h->nA = ao; h->nB = bo; h->nP = po; h->nF = fo;
+    h->vstride = 32 * Rmax;
+    // warp tasks
+    std::vector<int4> tasks;
+    for (int d = 0; d < h->S;) {
+        int W, R;
+        size_class(sn[d], &W, &R);
+        int per = 32 / W, cnt = 0;
+        while (d + cnt < h->S && cnt < per) {
+            int W2, R2;
+            size_class(sn[d + cnt], &W2, &R2);
+            if (W2 != W || R2 != R) break;
+            ++cnt;
+        }
+        tasks.push_back(make_int4(d, cnt, W, R));
+        d += cnt;
+    }
+    h->n_tasks = (int)tasks.size();
+    h->iter_blocks = (h->n_tasks + 7) / 8;
+    // u segments: copies of each global contiguous, canonical slot order inside
+    std::vector<int> cnt(h->G, 0);
+    for (int k = 0; k < h->L; ++k) cnt[gk[k]]++;
+    std::vector<int> gstart(h->G + 1, 0);
+    for (int i = 0; i < h->G; ++i) gstart[i + 1] = gstart[i] + cnt[i];
+    std::vector<int> fill(gstart.begin(), gstart.end() - 1);
+    std::vector<int> pk(h->L), uslot(h->L);
+    for (int cs = 0; cs < h->L; ++cs) {            // canonical order
+        int k = h->canon_slot_to_dev[cs];
+        int g = gk[k];
+        pk[k] = fill[g]++;
+        uslot[pk[k]] = k;
+    }
+    std::vector<int2> seg(h->L), gseg(h->G);
+    for (int i = 0; i < h->G; ++i) gseg[i] = make_int2(gstart[i], cnt[i]);
+    for (int k = 0; k < h->L; ++k) seg[k] = gseg[gk[k]];
+    // start point of Sec. V-A
+    std::vector<double> x0(h->G, 0.0);
+    for (int i = 0; i < h->G; ++i) {
+        double lo = M.lb[i], hi = M.ub[i];
+        if (M.volt[i]) x0[i] = 1.0;
+        else if (std::isfinite(lo) && std::isfinite(hi)) x0[i] = 0.5 * (lo + hi);
+        else if (std::isfinite(lo)) x0[i] = lo;
+        else if (std::isfinite(hi)) x0[i] = hi;
+    }
+    h->h_sn = sn;
+    // ---- uploads
+    TRY(upload(h, &h->d_soff, soff));
+    TRY(upload(h, &h->d_sn, sn));
+    TRY(upload(h, &h->d_sm, sm));
+    TRY(upload(h, &h->d_boff, boff));
+    TRY(upload(h, &h->d_aoff, aoff));
+    TRY(upload(h, &h->d_poff, poff));
+    TRY(upload(h, &h->d_foff, foff));
+    TRY(upload(h, &h->d_tasks, tasks));
+    TRY(upload(h, &h->d_gk, gk));
+    TRY(upload(h, &h->d_pk, pk));
+    TRY(upload(h, &h->d_uslot, uslot));
+    TRY(upload(h, &h->d_seg, seg));
+    TRY(upload(h, &h->d_gseg, gseg));
+    TRY(upload(h, &h->d_A, A));
+    TRY(upload(h, &h->d_b, b));
+    TRY(upload(h, &h->d_c64, M.c));
+    TRY(upload(h, &h->d_lb64, M.lb));
+    TRY(upload(h, &h->d_ub64, M.ub));
+    TRY(upload(h, &h->d_x0, x0));
+    const size_t L = h->L, G = h->G;
+    TRY(dalloc(h, &h->d_sf, h->S));
+    TRY(dalloc(h, &h->d_smode, h->S));
+    TRY(dalloc(h, &h->d_pstatus, h->S));
+    TRY(dalloc(h, &h->d_W, h->nA));
+    TRY(dalloc(h, &h->d_Bw, h->nB));
+    TRY(dalloc(h, &h->d_P, h->nP));
+    TRY(dalloc(h, &h->d_F64, h->nF));
+    TRY(dalloc(h, &h->d_F32, h->nF));
+    TRY(dalloc(h, &h->d_bbar64, L));
+    TRY(dalloc(h, &h->d_xr, G));
+    TRY(dalloc(h, &h->d_xr2, G));
+    TRY(dalloc(h, &h->d_zeroG, G));
+    TRY(dalloc(h, &h->d_x, G));
+    TRY(dalloc(h, &h->d_objpart, 4096));
+    TRY(dalloc(h, &h->d_ct32, G));
+    TRY(dalloc(h, &h->d_lbt32, G));
+    TRY(dalloc(h, &h->d_ubt32, G));
+    TRY(dalloc(h, &h->d_ds64, L));
+    TRY(dalloc(h, &h->d_mu64, L));
+    TRY(dalloc(h, &h->d_u64, 2 * L));
+    TRY(dalloc(h, &h->d_lamr, L));
+    TRY(dalloc(h, &h->d_zeroL, L));
+    TRY(dalloc(h, &h->d_ds32, L));
+    TRY(dalloc(h, &h->d_mu32, L));
+    TRY(dalloc(h, &h->d_u32, 2 * L));
+    TRY(dalloc(h, &h->d_bt32, L));
+    TRY(dalloc(h, &h->d_partials, (size_t)6 * std::max(h->iter_blocks, 1)));
+    TRY(dalloc(h, &h->d_st, 1));
+    CUDA_TRY(cudaMemsetAsync(h->d_zeroG, 0, G * sizeof(double), h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->d_zeroL, 0, L * sizeof(double), h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->d_st, 0, sizeof(DevStatus), h->stream));
+    CUDA_TRY(cudaMallocHost(&h->h_st, sizeof(DevStatus)));
+    memset(h->h_st, 0, sizeof(DevStatus));
+    for (auto &e : h->ev) CUDA_TRY(cudaEventCreate(&e));
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    const size_t limit = optin > 4096 ? (size_t)optin - 4096 : 0;
+    h->cta32_ok = make_cta_layout<float>(h, &h->lay32, limit);
+    h->cta64_ok = make_cta_layout<double>(h, &h->lay64, limit);
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return OPF_OK;
+}
+
+static int common_create(opf_handle *h, const opf_options *o) {
+    h->device = o ? o->device : 0;
+    CUDA_TRY(cudaSetDevice(h->device));
+    if (o && o->stream) {
+        h->stream = (cudaStream_t)o->stream;
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    return build_layout(h);
+}
+
+extern "C" int opf_create(const opf_feeder *f, const opf_options *o, opf_handle **out) {
+    if (!out) return OPF_E_INVALID;
+    *out = nullptr;
+    opf_handle *h = new opf_handle();
+    int rc = build_feeder_model(f, &h->model, &g_last_error);
+    if (rc == OPF_OK) rc = common_create(h, o);
+    if (rc != OPF_OK) { opf_destroy(h); return rc; }
+    *out = h;
+    return OPF_OK;
+}
+
+extern "C" int opf_create_generic(int32_t n, const double *c, const double *lb, const double *ub,
+                                  const uint8_t *is_voltage, int32_t S, const int32_t *m_s,
+                                  const int32_t *n_s, const double *A, const double *b,
+                                  const int32_t *idx, const opf_options *o, opf_handle **out) {
+    if (!out) return OPF_E_INVALID;
+    *out = nullptr;
+    opf_handle *h = new opf_handle();
+    int rc = build_generic_model(n, c, lb, ub, is_voltage, S, m_s, n_s, A, b, idx, &h->model, &g_last_error);
+    if (rc == OPF_OK) rc = common_create(h, o);
+    if (rc != OPF_OK) { opf_destroy(h); return rc; }
+    *out = h;
+    return OPF_OK;
+}
+
+static int reset_state(opf_handle *h) {
+    launch_init_state<double>(h->L, h->d_gk, h->d_x0, h->d_ds64, h->d_mu64, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    h->have_prev_u = false;
+    h->total_iters = 0;
+    memset(h->h_st, 0, sizeof(DevStatus));
+    CUDA_TRY(cudaMemsetAsync(h->d_st, 0, sizeof(DevStatus), h->stream));
+    return OPF_OK;
+}
+
+extern "C" int opf_precompute(opf_handle *h) {
+    if (!h) return OPF_E_INVALID;
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_W, h->d_A, std::max<long long>(h->nA, 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_Bw, h->d_b, std::max<long long>(h->nB, 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->d_F64, 0, std::max<long long>(h->nF, 1) * sizeof(double), h->stream));
+    PreArgs a;
+    a.S = h->S; a.sm = h->d_sm; a.sn = h->d_sn; a.soff = h->d_soff;
+    a.aoff = h->d_aoff; a.poff = h->d_poff; a.foff = h->d_foff; a.boff = h->d_boff;
+    a.W = h->d_W; a.Bw = h->d_Bw; a.P = h->d_P; a.F = h->d_F64;
+    a.sf = h->d_sf; a.smode = h->d_smode; a.bbar = h->d_bbar64; a.status = h->d_pstatus;
+    launch_precompute(a, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    launch_cast<double, float>(std::max<long long>(h->nF, 1), h->d_F64, h->d_F32, h->stream);
+    CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
+    std::vector<int> status(h->S);
+    h->h_sf.resize(h->S);
+    CUDA_TRY(cudaMemcpyAsync(status.data(), h->d_pstatus, h->S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->h_sf.data(), h->d_sf, h->S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->timing[0] = ms;
+    for (int s = 0; s < h->S; ++s)
+        if (status[s]) {
+            g_last_error = "inconsistent local system A_s x_s = b_s";
+            h->precomputed = false;
+            return OPF_E_INFEASIBLE_LOCAL;
+        }
+    h->sum_nf = 0;
+    for (int s = 0; s < h->S; ++s) h->sum_nf += (long long)h->h_sn[s] * h->h_sf[s];
+    h->precomputed = true;
+    return reset_state(h);
+}
+
+extern "C" int opf_reset(opf_handle *h) {
+    if (!h) return OPF_E_INVALID;
+    if (!h->precomputed) return OPF_E_STATE;
+    CUDA_TRY(cudaSetDevice(h->device));
+    int rc = reset_state(h);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return OPF_OK;
+}
+
+template <typename T>
+static IterArgs<T> iter_args(opf_handle *h, double rho);
+
+template <>
+IterArgs<double> iter_args<double>(opf_handle *h, double rho) {
+    IterArgs<double> a;
+    a.soff = h->d_soff; a.sn = h->d_sn; a.sf = h->d_sf; a.smode = h->d_smode; a.sfoff = h->d_foff;
+    a.F = h->d_F64; a.seg = h->d_seg; a.gk = h->d_gk; a.pk = h->d_pk;
+    a.bt = h->d_bbar64; a.mu = h->d_mu64; a.ds = h->d_ds64;
+    a.ct = h->d_c64; a.lbt = h->d_lb64; a.ubt = h->d_ub64;
+    a.xr = h->d_zeroG; a.lamr = h->d_zeroL; a.c64 = h->d_c64;
+    a.tasks = h->d_tasks; a.n_tasks = h->n_tasks;
+    a.rho = rho; a.inv_rho = 1.0 / rho;
+    return a;
+}
+
+template <>
+IterArgs<float> iter_args<float>(opf_handle *h, double rho) {
+    IterArgs<float> a;
+    a.soff = h->d_soff; a.sn = h->d_sn; a.sf = h->d_sf; a.smode = h->d_smode; a.sfoff = h->d_foff;
+    a.F = h->d_F32; a.seg = h->d_seg; a.gk = h->d_gk; a.pk = h->d_pk;
+    a.bt = h->d_bt32; a.mu = h->d_mu32; a.ds = h->d_ds32;
+    a.ct = h->d_ct32; a.lbt = h->d_lbt32; a.ubt = h->d_ubt32;
+    a.xr = h->d_xr; a.lamr = h->d_lamr; a.c64 = h->d_c64;
+    a.tasks = h->d_tasks; a.n_tasks = h->n_tasks;
+    a.rho = (float)rho; a.inv_rho = (float)(1.0 / rho);
+    return a;
+}
+
+// Enqueue one chunk of k grid iterations (the last one tested) and the test.
+template <typename T>
+static void enqueue_grid_chunk(opf_handle *h, const IterArgs<T> &a, T *u, int k, double rho,
+                               cudaGraphConditionalHandle cond, int use_cond) {
+    for (int i = 0; i < k; ++i) {
+        const T *uin = u + (size_t)(i & 1) * h->L;
+        T *uout = u + (size_t)((i + 1) & 1) * h->L;
+        launch_iterate<T>(a, uin, uout, h->vstride, h->d_partials, h->d_st, i == k - 1, h->stream);
+    }
+    launch_check(h->d_partials, h->iter_blocks, h->d_st, rho, k, cond, use_cond, h->stream);
+}
+
+// Build a graph "while (!done) body" where body is enqueued by fn(cond).
+template <typename Fn>
+static int build_while_graph(opf_handle *h, GraphCache *gc, Fn fn) {
+    gc->reset();
+    CUDA_TRY(cudaGraphCreate(&gc->graph, 0));
+    cudaGraphConditionalHandle cond;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, gc->graph, 1, cudaGraphCondAssignDefault));
+    // the parameter union has no default constructor in C++: zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams *cp = reinterpret_cast<cudaGraphNodeParams *>(raw);
+    cp->type = cudaGraphNodeTypeConditional;
+    cp->conditional.handle = cond;
+    cp->conditional.type = cudaGraphCondTypeWhile;
+    cp->conditional.size = 1;
+    cudaGraphNode_t node;
+    CUDA_TRY(cudaGraphAddNode(&node, gc->graph, nullptr, nullptr, 0, cp));
+    cudaGraph_t body = cp->conditional.phGraph_out[0];
+    CUDA_TRY(cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    fn(cond);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(h->stream, &captured);
+    if (ec != cudaSuccess) {
+        g_last_error = std::string("stream capture: ") + cudaGetErrorString(ec);
+        gc->reset();
+        return OPF_E_CUDA;
+    }
+    CUDA_TRY(cudaGraphInstantiate(&gc->exec, gc->graph, 0));
+    return OPF_OK;
+}
+
+static int set_status(opf_handle *h, const opf_solve_opts &o, bool keep_iter) {
+    DevStatus st{};
+    st.iter = keep_iter ? h->h_st->iter : 0;
+    st.max_iter = o.max_iter;
+    st.eps_rel = o.eps_rel;
+    st.eps_abs_pres = o.eps_abs_pres;
+    *h->h_st = st;
+    CUDA_TRY(cudaMemcpyAsync(h->d_st, h->h_st, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return OPF_OK;
+}
+
+static int read_status(opf_handle *h) {
+    CUDA_TRY(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return OPF_OK;
+}
+
+// FP64 iterations on the whole grid until the test or max_iter.
+static int run_grid64(opf_handle *h, const opf_solve_opts &o) {
+    const double rho = o.rho;
+    launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    if (h->g64.kind != 0 || h->g64.rho != rho || h->g64.k != o.check_every) {
+        IterArgs<double> a = iter_args<double>(h, rho);
+        TRY(build_while_graph(h, &h->g64, [&](cudaGraphConditionalHandle c) {
+            enqueue_grid_chunk<double>(h, a, h->d_u64, o.check_every, rho, c, 1);
+        }));
+        h->g64.kind = 0; h->g64.rho = rho; h->g64.k = o.check_every;
+    }
+    CUDA_TRY(cudaGraphLaunch(h->g64.exec, h->stream));
+    TRY(read_status(h));
+    h->have_prev_u = h->h_st->iter > 0;
+    return OPF_OK;
+}
+
+// FP64 iterations by the one-CTA engine (testing aid: same arithmetic).
+static int run_cta64(opf_handle *h, const opf_solve_opts &o) {
+    const double rho = o.rho;
+    if (prepare_cta_engine<double>(h->lay64.bytes)) { g_last_error = "cannot size CTA engine"; return OPF_E_CUDA; }
+    launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
+    IterArgs<double> a = iter_args<double>(h, rho);
+    cudaGraphConditionalHandle none{};
+    launch_cta_engine<double>(a, h->lay64, h->d_u64, o.max_iter, o.check_every, h->d_st, rho, none, 0, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    TRY(read_status(h));
+    h->have_prev_u = h->h_st->iter > 0;
+    return OPF_OK;
+}
+
+// FP32 iterations in the shifted frame, re-centred in FP64 every R iterations.
+static int run_mixed(opf_handle *h, const opf_solve_opts &o, bool use_cta, bool recenter) {
+    const double rho = o.rho;
+    const int L = h->L, G = h->G, S = h->S;
+    const int k = o.check_every;
+    int R = o.recenter_every > 0 ? o.recenter_every : 1000;
+    R = std::max(k, (R / k) * k);
+    if (!recenter) R = std::max(k, (std::min(o.max_iter, 1 << 30) / k + 1) * k);
+    // reference = next global update of the current FP64 state; lambda_ref = lambda
+    launch_make_u<double>(L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
+    launch_global_x<double>(G, h->d_gseg, h->d_u64, h->d_c64, h->d_lb64, h->d_ub64, h->d_zeroG, h->d_c64,
+                            rho, h->d_xr, h->d_objpart, nullptr, h->stream);
+    launch_enter_shift(L, h->d_gk, h->d_xr, h->d_ds64, h->d_mu64, h->d_ds32, h->d_mu32, h->d_lamr, h->stream);
+    launch_recenter<float>(L, G, S, h->d_gk, h->d_xr, h->d_xr, h->d_ds32, h->d_mu32, h->d_lamr,
+                           h->d_gseg, h->d_uslot, h->d_c64, h->d_lb64, h->d_ub64, h->d_ct32, h->d_lbt32,
+                           h->d_ubt32, h->d_soff, h->d_sn, h->d_sf, h->d_smode, h->d_foff, h->d_F64,
+                           h->d_bbar64, rho, h->d_bt32, nullptr, h->stream);
+    launch_make_u<float>(L, h->d_pk, h->d_ds32, h->d_mu32, (float)rho, h->d_u32, nullptr, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    if (use_cta && prepare_cta_engine<float>(h->lay32.bytes)) { g_last_error = "cannot size CTA engine"; return OPF_E_CUDA; }
+    const int kind = (use_cta ? 2 : 1) + (recenter ? 0 : 2);
+    if (h->gmix.kind != kind || h->gmix.rho != rho || h->gmix.k != k || h->gmix.R != R) {
+        IterArgs<float> a = iter_args<float>(h, rho);
+        TRY(build_while_graph(h, &h->gmix, [&](cudaGraphConditionalHandle c) {
+            if (use_cta) {
+                launch_cta_engine<float>(a, h->lay32, h->d_u32, R, k, h->d_st, rho, c, 1, h->stream);
+            } else {
+                const int chunks = recenter ? R / k : 1;
+                for (int i = 0; i < chunks; ++i) enqueue_grid_chunk<float>(h, a, h->d_u32, k, rho, c, 1);
+            }
+            if (!recenter) return;
+            // re-centre on the next global update (u of the last iteration is in buffer 0)
+            launch_global_x<float>(G, h->d_gseg, h->d_u32, h->d_ct32, h->d_lbt32, h->d_ubt32, h->d_xr,
+                                   h->d_c64, (float)rho, h->d_xr2, h->d_objpart, h->d_st, h->stream);
+            launch_recenter<float>(L, G, S, h->d_gk, h->d_xr, h->d_xr2, h->d_ds32, h->d_mu32, h->d_lamr,
+                                   h->d_gseg, h->d_uslot, h->d_c64, h->d_lb64, h->d_ub64, h->d_ct32,
+                                   h->d_lbt32, h->d_ubt32, h->d_soff, h->d_sn, h->d_sf, h->d_smode,
+                                   h->d_foff, h->d_F64, h->d_bbar64, rho, h->d_bt32, h->d_st, h->stream);
+            launch_copy_if_running(G, h->d_xr2, h->d_xr, h->d_st, h->stream);
+            launch_make_u<float>(L, h->d_pk, h->d_ds32, h->d_mu32, (float)rho, h->d_u32, h->d_st, h->stream);
+        }));
+        h->gmix.kind = kind; h->gmix.rho = rho; h->gmix.k = k; h->gmix.R = R;
+    }
+    CUDA_TRY(cudaGraphLaunch(h->gmix.exec, h->stream));
+    // back to the unshifted FP64 state
+    launch_unshift<float>(L, h->d_gk, h->d_xr, h->d_lamr, h->d_ds32, h->d_mu32, h->d_ds64, h->d_mu64, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    TRY(read_status(h));
+    h->have_prev_u = false;
+    return OPF_OK;
+}
+
+static opf_solve_opts default_opts() {
+    opf_solve_opts o;
+    memset(&o, 0, sizeof(o));
+    o.rho = 100.0;
+    o.eps_rel = 1e-8;
+    o.eps_abs_pres = 1e-4;
+    o.max_iter = 1000000;
+    o.check_every = 50;
+    o.precision = OPF_PREC_FP64;
+    return o;
+}
+
+extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
+    if (!h) return OPF_E_INVALID;
+    if (!h->precomputed) return OPF_E_STATE;
+    opf_solve_opts o = opts ? *opts : default_opts();
+    if (!(o.rho > 0) || o.max_iter < 1 || o.check_every < 2 || (o.check_every & 1) ||
+        o.precision < 0 || o.precision > 2 || o.engine < 0 || o.engine > 2 || std::isnan(o.eps_rel) ||
+        std::isnan(o.eps_abs_pres)) {
+        g_last_error = "solve options: need rho > 0, max_iter >= 1, even check_every >= 2";
+        return OPF_E_INVALID;
+    }
+    CUDA_TRY(cudaSetDevice(h->device));
+    h->last_rho = o.rho;
+    TRY(set_status(h, o, false));
+    CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
+    if (o.precision == OPF_PREC_FP64) {
+        if (o.engine == 2) {
+            if (!h->cta64_ok) { g_last_error = "instance does not fit one CTA in FP64"; return OPF_E_CAPACITY; }
+            TRY(run_cta64(h, o));
+        } else {
+            TRY(run_grid64(h, o));
+        }
+        CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
+        CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
+    } else {
+        bool cta = o.engine == 2 || (o.engine == 0 && h->cta32_ok);
+        if (cta && !h->cta32_ok) { g_last_error = "instance does not fit one CTA"; return OPF_E_CAPACITY; }
+        TRY(run_mixed(h, o, cta, o.precision == OPF_PREC_MIXED));
+        CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
+        if (o.precision == OPF_PREC_FP32) {
+            // global x of the last FP32 state, evaluated in FP64
+            launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, o.rho, h->d_u64 + h->L, nullptr, h->stream);
+            CUDA_TRY(cudaGetLastError());
+            h->have_prev_u = true;
+        }
+        if (o.precision == OPF_PREC_MIXED && !h->h_st->numeric) {
+            // FP64 polish: continue in FP64 until the test holds there too
+            long long it = h->h_st->iter;
+            h->h_st->done = 0;
+            DevStatus st = *h->h_st;
+            st.done = 0; st.converged = 0; st.iter = it;
+            st.max_iter = std::max<long long>(o.max_iter, it + o.check_every);
+            *h->h_st = st;
+            CUDA_TRY(cudaMemcpyAsync(h->d_st, h->h_st, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
+            TRY(run_grid64(h, o));
+        }
+        CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
+    }
+    CUDA_TRY(cudaEventSynchronize(h->ev[3]));
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&b, h->ev[2], h->ev[3]);
+    h->timing[1] = a;
+    h->timing[2] = b;
+    h->total_iters = h->h_st->iter;
+    if (h->h_st->numeric) { g_last_error = "NaN or Inf in the residuals"; return OPF_E_NUMERIC; }
+    return h->h_st->converged ? OPF_OK : OPF_NOT_CONVERGED;
+}
+
+extern "C" int opf_solve(opf_handle *h, double rho, double eps, int32_t max_iter) {
+    opf_solve_opts o = default_opts();
+    o.rho = rho;
+    o.eps_rel = eps;
+    o.max_iter = max_iter;
+    return opf_solve_ex(h, &o);
+}
+
+extern "C" int opf_step(opf_handle *h, double rho, int32_t n_iters) {
+    if (!h) return OPF_E_INVALID;
+    if (!h->precomputed) return OPF_E_STATE;
+    if (!(rho > 0) || n_iters < 0) return OPF_E_INVALID;
+    CUDA_TRY(cudaSetDevice(h->device));
+    if (n_iters == 0) return OPF_OK;
+    h->last_rho = rho;
+    opf_solve_opts o = default_opts();
+    o.max_iter = 0x7fffffff;
+    TRY(set_status(h, o, false));
+    launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
+    IterArgs<double> a = iter_args<double>(h, rho);
+    for (int i = 0; i < n_iters; ++i) {
+        const double *uin = h->d_u64 + (size_t)(i & 1) * h->L;
+        double *uout = h->d_u64 + (size_t)((i + 1) & 1) * h->L;
+        launch_iterate<double>(a, uin, uout, h->vstride, h->d_partials, h->d_st, i == n_iters - 1, h->stream);
+    }
+    launch_check(h->d_partials, h->iter_blocks, h->d_st, rho, n_iters, cudaGraphConditionalHandle{}, 0, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    TRY(read_status(h));
+    // make the previous-u buffer be the one at offset L
+    if (n_iters & 1) {
+        CUDA_TRY(cudaMemcpyAsync(h->d_u64 + h->L, h->d_u64, h->L * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->have_prev_u = true;
+    h->total_iters = h->h_st->iter;
+    return OPF_OK;
+}
+
+extern "C" int opf_get_solution(opf_handle *h, double *x, size_t n, double *objective) {
+    if (!h) return OPF_E_INVALID;
+    if (!h->have_prev_u) return OPF_E_STATE;
+    if (x && n < (size_t)h->G) return OPF_E_INVALID;
+    CUDA_TRY(cudaSetDevice(h->device));
+    int nb = launch_global_x<double>(h->G, h->d_gseg, h->d_u64 + h->L, h->d_c64, h->d_lb64, h->d_ub64,
+                                     h->d_zeroG, h->d_c64, h->last_rho, h->d_x, h->d_objpart, nullptr,
+                                     h->stream);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<double> part(nb);
+    CUDA_TRY(cudaMemcpyAsync(part.data(), h->d_objpart, nb * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (x) CUDA_TRY(cudaMemcpyAsync(x, h->d_x, h->G * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    double o = 0.0;
+    for (double p : part) o += p;
+    if (objective) *objective = o;
+    return OPF_OK;
+}
+
+extern "C" int opf_get_residuals(opf_handle *h, double *pres, double *dres, double *eps_prim,
+                                 double *eps_dual, int64_t *iters) {
+    if (!h) return OPF_E_INVALID;
+    if (pres) *pres = h->h_st->pres;
+    if (dres) *dres = h->h_st->dres;
+    if (eps_prim) *eps_prim = h->h_st->eprim;
+    if (eps_dual) *eps_dual = h->h_st->edual;
+    if (iters) *iters = h->total_iters;
+    return OPF_OK;
+}
+
+extern "C" int opf_get_locals(opf_handle *h, double *xs, double *lam, size_t L) {
+    if (!h) return OPF_E_INVALID;
+    if (!h->precomputed) return OPF_E_STATE;
+    if (L < (size_t)h->L) return OPF_E_INVALID;
+    CUDA_TRY(cudaSetDevice(h->device));
+    std::vector<double> a(h->L), b(h->L);
+    CUDA_TRY(cudaMemcpyAsync(a.data(), h->d_ds64, h->L * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(b.data(), h->d_mu64, h->L * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < h->L; ++c) {
+        if (xs) xs[c] = a[h->canon_slot_to_dev[c]];
+        if (lam) lam[c] = b[h->canon_slot_to_dev[c]];
+    }
+    return OPF_OK;
+}
+
+extern "C" int opf_set_locals(opf_handle *h, const double *xs, const double *lam, size_t L) {
+    if (!h || !xs || !lam) return OPF_E_INVALID;
+    if (!h->precomputed) return OPF_E_STATE;
+    if (L < (size_t)h->L) return OPF_E_INVALID;
+    CUDA_TRY(cudaSetDevice(h->device));
+    std::vector<double> a(h->L), b(h->L);
+    for (int c = 0; c < h->L; ++c) {
+        a[h->canon_slot_to_dev[c]] = xs[c];
+        b[h->canon_slot_to_dev[c]] = lam[c];
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->d_ds64, a.data(), h->L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_mu64, b.data(), h->L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->have_prev_u = false;
+    return OPF_OK;
+}
+
+extern "C" int opf_get_sizes(opf_handle *h, opf_sizes *out) {
+    if (!h || !out) return OPF_E_INVALID;
+    out->n_global = h->G;
+    out->n_sub = h->S;
+    out->n_slots = h->L;
+    out->n_rows = h->n_rows;
+    out->sum_nf = h->sum_nf;
+    out->max_ns = h->max_ns;
+    return OPF_OK;
+}
+
+extern "C" int opf_get_timing(opf_handle *h, double *ms, int n) {
+    if (!h || !ms) return OPF_E_INVALID;
+    for (int i = 0; i < n && i < 3; ++i) ms[i] = h->timing[i];
+    return OPF_OK;
+}
+
+extern "C" void opf_destroy(opf_handle *h) {
+    if (!h) return;
+    if (h->device >= 0) cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->g64.reset();
+    h->gmix.reset();
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->h_st) cudaFreeHost(h->h_st);
+    for (auto &e : h->ev) if (e) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+extern "C" const char *opf_strerror(int code) {
+    switch (code) {
+        case OPF_OK: return "ok";
+        case OPF_NOT_CONVERGED: return "iteration limit reached before the stopping test held";
+        case OPF_E_INVALID: return "invalid argument or malformed input";
+        case OPF_E_INFEASIBLE_LOCAL: return "inconsistent local system A_s x_s = b_s";
+        case OPF_E_STATE: return "call out of order";
+        case OPF_E_OOM: return "out of memory";
+        case OPF_E_NUMERIC: return "NaN or Inf in the residuals";
+        case OPF_E_TIMEOUT: return "bounded device wait gave up";
+        case OPF_E_CUDA: return "CUDA runtime error";
+        case OPF_E_CAPACITY: return "size beyond a documented limit";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char *opf_last_error(void) { return g_last_error.c_str(); }

@@ -1,0 +1,280 @@
+"""Thin Python binding of the C ABI in ``include/opf.h`` (argument marshalling only).
+
+Every computation runs inside ``libopf.so``; this module only converts numpy
+arrays to pointers.  There is no fallback: if the library is missing or cannot
+be loaded, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libopf.so")
+
+OPF_OK = 0
+OPF_NOT_CONVERGED = 1
+OPF_E_INVALID = -1
+OPF_E_INFEASIBLE_LOCAL = -2
+OPF_E_STATE = -3
+OPF_E_OOM = -4
+OPF_E_NUMERIC = -5
+OPF_E_TIMEOUT = -6
+OPF_E_CUDA = -7
+OPF_E_CAPACITY = -8
+
+PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
+ENGINE_AUTO, ENGINE_GRID, ENGINE_CTA = 0, 1, 2
+
+_P = C.c_void_p
+
+
+class Feeder(C.Structure):
+    _fields_ = [
+        ("n_bus", C.c_int32), ("bus_phases", _P), ("bus_wmin", _P), ("bus_wmax", _P),
+        ("bus_gsh", _P), ("bus_bsh", _P),
+        ("n_line", C.c_int32), ("line_from", _P), ("line_to", _P), ("line_phases", _P),
+        ("line_r", _P), ("line_x", _P), ("line_gs_from", _P), ("line_bs_from", _P),
+        ("line_gs_to", _P), ("line_bs_to", _P), ("line_tap", _P),
+        ("n_load", C.c_int32), ("load_bus", _P), ("load_phases", _P), ("load_delta", _P),
+        ("load_a", _P), ("load_b", _P), ("load_alpha", _P), ("load_beta", _P),
+        ("n_gen", C.c_int32), ("gen_bus", _P), ("gen_phases", _P), ("gen_pmin", _P),
+        ("gen_pmax", _P), ("gen_qmin", _P), ("gen_qmax", _P), ("gen_cost", _P),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [("device", C.c_int32), ("stream", _P)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("rho", C.c_double), ("eps_rel", C.c_double), ("eps_abs_pres", C.c_double),
+                ("max_iter", C.c_int32), ("check_every", C.c_int32), ("precision", C.c_int32),
+                ("recenter_every", C.c_int32), ("engine", C.c_int32)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("n_global", C.c_int64), ("n_sub", C.c_int64), ("n_slots", C.c_int64),
+                ("n_rows", C.c_int64), ("sum_nf", C.c_int64), ("max_ns", C.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libopf.so (built by ``paper_2310_09410_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libopf.so not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    lib.opf_create.argtypes = [C.POINTER(Feeder), C.POINTER(Options), C.POINTER(H)]
+    lib.opf_create_generic.argtypes = [C.c_int32, _P, _P, _P, _P, C.c_int32, _P, _P, _P, _P, _P,
+                                       C.POINTER(Options), C.POINTER(H)]
+    lib.opf_precompute.argtypes = [H]
+    lib.opf_solve.argtypes = [H, C.c_double, C.c_double, C.c_int32]
+    lib.opf_solve_ex.argtypes = [H, C.POINTER(SolveOpts)]
+    lib.opf_step.argtypes = [H, C.c_double, C.c_int32]
+    lib.opf_reset.argtypes = [H]
+    lib.opf_get_solution.argtypes = [H, _P, C.c_size_t, C.POINTER(C.c_double)]
+    lib.opf_get_residuals.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    lib.opf_get_locals.argtypes = [H, _P, _P, C.c_size_t]
+    lib.opf_set_locals.argtypes = [H, _P, _P, C.c_size_t]
+    lib.opf_get_sizes.argtypes = [H, C.POINTER(Sizes)]
+    lib.opf_get_timing.argtypes = [H, _P, C.c_int]
+    lib.opf_destroy.argtypes = [H]
+    lib.opf_destroy.restype = None
+    lib.opf_strerror.argtypes = [C.c_int]
+    lib.opf_strerror.restype = C.c_char_p
+    lib.opf_last_error.argtypes = []
+    lib.opf_last_error.restype = C.c_char_p
+    for name in ("opf_create", "opf_create_generic", "opf_precompute", "opf_solve", "opf_solve_ex",
+                 "opf_step", "opf_reset", "opf_get_solution", "opf_get_residuals", "opf_get_locals",
+                 "opf_set_locals", "opf_get_sizes", "opf_get_timing"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class OPFError(RuntimeError):
+    def __init__(self, code, where):
+        lib = load()
+        msg = lib.opf_strerror(code).decode()
+        detail = lib.opf_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code}) {detail}")
+        self.code = code
+
+
+def _check(code, where, ok=(OPF_OK,)):
+    if code not in ok:
+        raise OPFError(code, where)
+    return code
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class Solver:
+    """One problem instance on one device (wraps an ``opf_handle``)."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    # ---------------------------------------------------------- creation
+    @classmethod
+    def from_feeder(cls, f, device=0, stream=None):
+        lib = load()
+        keep = {}
+
+        def arr(name, dtype, shape=None):
+            a = np.ascontiguousarray(f[name], dtype=dtype)
+            if shape is not None:
+                a = a.reshape(shape)
+            keep[name] = a
+            return _ptr(a)
+
+        nb, nl, nd, ng = int(f["n_bus"]), len(f["line_from"]), len(f["load_bus"]), len(f["gen_bus"])
+        fd = Feeder()
+        fd.n_bus = nb
+        fd.bus_phases = arr("bus_phases", np.uint8)
+        fd.bus_wmin = arr("bus_wmin", np.float64, (nb * 3,))
+        fd.bus_wmax = arr("bus_wmax", np.float64, (nb * 3,))
+        fd.bus_gsh = arr("bus_gsh", np.float64, (nb * 3,))
+        fd.bus_bsh = arr("bus_bsh", np.float64, (nb * 3,))
+        fd.n_line = nl
+        fd.line_from = arr("line_from", np.int32)
+        fd.line_to = arr("line_to", np.int32)
+        fd.line_phases = arr("line_phases", np.uint8)
+        fd.line_r = arr("line_r", np.float64, (nl * 9,))
+        fd.line_x = arr("line_x", np.float64, (nl * 9,))
+        fd.line_gs_from = arr("line_gs_from", np.float64, (nl * 3,))
+        fd.line_bs_from = arr("line_bs_from", np.float64, (nl * 3,))
+        fd.line_gs_to = arr("line_gs_to", np.float64, (nl * 3,))
+        fd.line_bs_to = arr("line_bs_to", np.float64, (nl * 3,))
+        fd.line_tap = arr("line_tap", np.float64, (nl * 3,))
+        fd.n_load = nd
+        fd.load_bus = arr("load_bus", np.int32)
+        fd.load_phases = arr("load_phases", np.uint8)
+        fd.load_delta = arr("load_delta", np.uint8)
+        fd.load_a = arr("load_a", np.float64, (nd * 3,))
+        fd.load_b = arr("load_b", np.float64, (nd * 3,))
+        fd.load_alpha = arr("load_alpha", np.float64, (nd * 3,))
+        fd.load_beta = arr("load_beta", np.float64, (nd * 3,))
+        fd.n_gen = ng
+        fd.gen_bus = arr("gen_bus", np.int32)
+        fd.gen_phases = arr("gen_phases", np.uint8)
+        fd.gen_pmin = arr("gen_pmin", np.float64, (ng * 3,))
+        fd.gen_pmax = arr("gen_pmax", np.float64, (ng * 3,))
+        fd.gen_qmin = arr("gen_qmin", np.float64, (ng * 3,))
+        fd.gen_qmax = arr("gen_qmax", np.float64, (ng * 3,))
+        fd.gen_cost = arr("gen_cost", np.float64)
+        opts = Options(int(device), C.c_void_p(stream) if stream else None)
+        h = C.c_void_p()
+        _check(lib.opf_create(C.byref(fd), C.byref(opts), C.byref(h)), "opf_create")
+        return cls(h, keep)
+
+    @classmethod
+    def from_generic(cls, c, lb, ub, subs, is_voltage=None, device=0, stream=None):
+        """subs: list of dicts with "idx", "A" (m x n) and "b"."""
+        lib = load()
+        c = np.ascontiguousarray(c, np.float64)
+        lb = np.ascontiguousarray(lb, np.float64)
+        ub = np.ascontiguousarray(ub, np.float64)
+        volt = None if is_voltage is None else np.ascontiguousarray(is_voltage, np.uint8)
+        m_s = np.array([np.asarray(s["A"]).reshape(-1, len(s["idx"])).shape[0] for s in subs], np.int32)
+        n_s = np.array([len(s["idx"]) for s in subs], np.int32)
+        A = np.ascontiguousarray(np.concatenate([np.asarray(s["A"], np.float64).ravel() for s in subs]
+                                                + [np.zeros(0)]))
+        b = np.ascontiguousarray(np.concatenate([np.asarray(s["b"], np.float64).ravel() for s in subs]
+                                                + [np.zeros(0)]))
+        idx = np.ascontiguousarray(np.concatenate([np.asarray(s["idx"], np.int64) for s in subs]).astype(np.int32))
+        keep = dict(c=c, lb=lb, ub=ub, volt=volt, m_s=m_s, n_s=n_s, A=A, b=b, idx=idx)
+        opts = Options(int(device), C.c_void_p(stream) if stream else None)
+        h = C.c_void_p()
+        _check(lib.opf_create_generic(len(c), _ptr(c), _ptr(lb), _ptr(ub), _ptr(volt), len(subs),
+                                      _ptr(m_s), _ptr(n_s), _ptr(A), _ptr(b), _ptr(idx),
+                                      C.byref(opts), C.byref(h)), "opf_create_generic")
+        return cls(h, keep)
+
+    # ---------------------------------------------------------- calls
+    def precompute(self):
+        _check(load().opf_precompute(self._h), "opf_precompute")
+
+    def solve(self, rho=100.0, eps_rel=1e-8, eps_abs_pres=1e-4, max_iter=1_000_000, check_every=50,
+              precision=PREC_FP64, recenter_every=0, engine=ENGINE_AUTO):
+        o = SolveOpts(rho, eps_rel, eps_abs_pres, int(max_iter), int(check_every), int(precision),
+                      int(recenter_every), int(engine))
+        rc = load().opf_solve_ex(self._h, C.byref(o))
+        _check(rc, "opf_solve_ex", ok=(OPF_OK, OPF_NOT_CONVERGED))
+        return rc == OPF_OK
+
+    def solve_simple(self, rho=100.0, eps=1e-8, max_iter=1_000_000):
+        rc = load().opf_solve(self._h, rho, eps, int(max_iter))
+        _check(rc, "opf_solve", ok=(OPF_OK, OPF_NOT_CONVERGED))
+        return rc == OPF_OK
+
+    def step(self, n_iters, rho=100.0):
+        _check(load().opf_step(self._h, rho, int(n_iters)), "opf_step")
+
+    def reset(self):
+        _check(load().opf_reset(self._h), "opf_reset")
+
+    def sizes(self):
+        s = Sizes()
+        _check(load().opf_get_sizes(self._h, C.byref(s)), "opf_get_sizes")
+        return {k: int(getattr(s, k)) for k, _ in Sizes._fields_}
+
+    def solution(self):
+        n = self.sizes()["n_global"]
+        x = np.zeros(n)
+        obj = C.c_double()
+        _check(load().opf_get_solution(self._h, _ptr(x), n, C.byref(obj)), "opf_get_solution")
+        return x, obj.value
+
+    def residuals(self):
+        p, d, ep, ed = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        it = C.c_int64()
+        _check(load().opf_get_residuals(self._h, C.byref(p), C.byref(d), C.byref(ep), C.byref(ed),
+                                        C.byref(it)), "opf_get_residuals")
+        return {"pres": p.value, "dres": d.value, "eps_prim": ep.value, "eps_dual": ed.value,
+                "iters": it.value}
+
+    def locals(self):
+        L = self.sizes()["n_slots"]
+        xs, lam = np.zeros(L), np.zeros(L)
+        _check(load().opf_get_locals(self._h, _ptr(xs), _ptr(lam), L), "opf_get_locals")
+        return xs, lam
+
+    def set_locals(self, xs, lam):
+        xs = np.ascontiguousarray(xs, np.float64)
+        lam = np.ascontiguousarray(lam, np.float64)
+        _check(load().opf_set_locals(self._h, _ptr(xs), _ptr(lam), len(xs)), "opf_set_locals")
+
+    def timing(self):
+        t = np.zeros(3)
+        _check(load().opf_get_timing(self._h, _ptr(t), 3), "opf_get_timing")
+        return {"precompute_ms": t[0], "iterate_ms": t[1], "polish_ms": t[2]}
+
+    def close(self):
+        if self._h:
+            load().opf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,80 @@
+"""C ABI: the library builds, loads, exports every declared entry point, and
+rejects malformed input on the host before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2310_09410_gb300 import build, opf, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return opf.load()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(opf_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 15
+    raw = ctypes.CDLL(opf.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+
+
+def test_strerror_names_every_code(lib):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert lib.opf_strerror(code).decode() != "unknown status"
+    assert lib.opf_strerror(42).decode() == "unknown status"
+
+
+def _bad(f, **changes):
+    g = dict(f)
+    g.update(changes)
+    return g
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda f: _bad(f, line_to=np.array([2] + list(f["line_to"][1:]), dtype=np.int32)),  # bus with two feeders
+    lambda f: _bad(f, line_from=np.array([1] + list(f["line_from"][1:]), dtype=np.int32)),   # self loop
+    lambda f: _bad(f, bus_phases=np.array([7] + [1] * (f["n_bus"] - 1), dtype=np.uint8)),
+    lambda f: _bad(f, load_bus=np.array([f["n_bus"] + 3] + list(f["load_bus"][1:]), dtype=np.int32)),
+    lambda f: _bad(f, gen_pmin=np.full_like(f["gen_pmin"], 1.0), gen_pmax=np.zeros_like(f["gen_pmax"])),
+    lambda f: _bad(f, load_delta=np.ones(len(f["load_bus"]), dtype=np.uint8)),   # delta on 1-phase bus
+])
+def test_malformed_feeder_rejected_on_host(lib, mutate):
+    f = synth.preset_feeder("13", 1001)
+    with pytest.raises(opf.OPFError) as e:
+        opf.Solver.from_feeder(mutate(f))
+    assert e.value.code == opf.OPF_E_INVALID
+
+
+def test_generic_validation_on_host(lib):
+    g = synth.random_generic(1)
+    subs = [dict(s) for s in g["subs"]]
+    subs[0] = dict(subs[0], idx=np.array([0, 0] + list(subs[0]["idx"][2:]), dtype=np.int32))
+    with pytest.raises(opf.OPFError) as e:
+        opf.Solver.from_generic(g["c"], g["lb"], g["ub"], subs)
+    assert e.value.code == opf.OPF_E_INVALID
+    big = [{"idx": np.arange(300), "A": np.ones((1, 300)), "b": np.ones(1)}]
+    with pytest.raises(opf.OPFError) as e:
+        opf.Solver.from_generic(np.zeros(300), -np.ones(300), np.ones(300), big)
+    assert e.value.code == opf.OPF_E_CAPACITY
+    uncovered = [{"idx": np.arange(5), "A": np.ones((1, 5)), "b": np.ones(1)}]
+    with pytest.raises(opf.OPFError) as e:
+        opf.Solver.from_generic(np.zeros(6), -np.ones(6), np.ones(6), uncovered)
+    assert e.value.code == opf.OPF_E_INVALID

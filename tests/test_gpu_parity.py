@@ -1,0 +1,153 @@
+"""GPU parity: the CUDA path against the CPU oracle through the C ABI.
+
+* FP64 iterates (x, x_s, lambda) after 100 iterations within 1e-10 relative
+  (both engines), on synthetic feeders of every size and on random
+  consensus instances (rank-deficient blocks, blocks wider than 64);
+* converged solves (FP64 and mixed precision) reach the LP optimum of the
+  oracle within 1e-6 relative with pres <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+from oracle import admm as oracle_admm, lindist
+from paper_2310_09410_gb300 import opf, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_ITER = 1e-10   # relative, FP64 iterates over the first 100 iterations
+TOL_OBJ = 1e-6     # relative objective at convergence
+TOL_PRES = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
+
+
+def oracle_iterates(M, iters, rho=100.0):
+    P = oracle_admm.Prepared(M)
+    return oracle_admm.admm(P, rho=rho, max_iter=iters, check_every=0)
+
+
+FEEDERS = [("13", 1001), ("13", 1002), ("34", 5034), ("123", 2001), ("8500", 3001)]
+
+
+@pytest.mark.parametrize("name,seed", FEEDERS)
+def test_fp64_iterates_match_oracle(name, seed):
+    f = synth.preset_feeder(name, seed)
+    M = lindist.build(f)
+    ref = oracle_iterates(M, 100)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        s.step(100)
+        xs, lam = s.locals()
+        x, obj = s.solution()
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
+    assert abs(obj - ref.objective) <= TOL_ITER * max(1.0, abs(ref.objective))
+
+
+@pytest.mark.parametrize("name,seed", [("13", 1001), ("34", 5034)])
+def test_cta_engine_fp64_matches_oracle(name, seed):
+    f = synth.preset_feeder(name, seed)
+    M = lindist.build(f)
+    ref = oracle_iterates(M, 100)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64, engine=opf.ENGINE_CTA)
+        xs, lam = s.locals()
+        x, _ = s.solution()
+        assert s.residuals()["iters"] == 100
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
+
+
+def generic_model(seed, **kw):
+    g = synth.random_generic(seed, **kw)
+    return g, lindist.from_generic(g)
+
+
+@pytest.mark.parametrize("seed,kw", [(1, {}), (7, {}), (4, {"max_n": 40, "n_global": 120}),
+                                     (9, {"max_n": 100, "n_global": 160, "n_sub": 5}),
+                                     (11, {"p_free": 0.3})])
+def test_generic_iterates_match_oracle(seed, kw):
+    g, M = generic_model(seed, **kw)
+    rho = 3.0
+    ref = oracle_iterates(M, 100, rho=rho)
+    with opf.Solver.from_generic(g["c"], g["lb"], g["ub"], g["subs"]) as s:
+        s.precompute()
+        s.step(100, rho=rho)
+        xs, lam = s.locals()
+        x, _ = s.solution()
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
+
+
+def test_zip_delta_loads_match_oracle():
+    f = synth.with_zip_delta(synth.preset_feeder("34", 5034), seed=3)
+    assert f["load_delta"].sum() > 0
+    M = lindist.build(f)
+    ref = oracle_iterates(M, 100)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        s.step(100)
+        xs, lam = s.locals()
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+
+
+@pytest.mark.parametrize("precision", [opf.PREC_FP64, opf.PREC_MIXED])
+@pytest.mark.parametrize("name,seed", [("13", 1003), ("123", 2002)])
+def test_converged_objective(name, seed, precision):
+    f = synth.preset_feeder(name, seed)
+    M = lindist.build(f)
+    obj_star, _ = oracle_admm.lp_optimum(M)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        ok = s.solve(precision=precision)
+        _, obj = s.solution()
+        r = s.residuals()
+    assert ok
+    assert r["pres"] <= TOL_PRES
+    assert abs(obj - obj_star) <= TOL_OBJ * abs(obj_star), (obj, obj_star, r)
+
+
+def test_step_then_getters_and_errors():
+    f = synth.preset_feeder("13", 1001)
+    with opf.Solver.from_feeder(f) as s:
+        with pytest.raises(opf.OPFError) as e:
+            s.solve()
+        assert e.value.code == opf.OPF_E_STATE
+        s.precompute()
+        s.step(0)
+        with pytest.raises(opf.OPFError):
+            s.solution()                       # no iteration yet
+        s.step(3)                              # odd count
+        xs, lam = s.locals()
+        s.step(2)
+        xs5, lam5 = s.locals()
+        s.set_locals(xs, lam)                  # checkpoint restore
+        s.step(2)
+        xs5b, lam5b = s.locals()
+        assert np.array_equal(xs5, xs5b) and np.array_equal(lam5, lam5b)
+        ok = s.solve(max_iter=100)
+        assert not ok                          # iteration cap, results readable
+        x, obj = s.solution()
+        assert np.all(np.isfinite(x))
+
+
+def test_inconsistent_local_system():
+    subs = [{"idx": np.array([0, 1]), "A": np.array([[1.0, 1.0], [2.0, 2.0]]), "b": np.array([1.0, 3.0])},
+            {"idx": np.array([1, 2]), "A": np.array([[1.0, -1.0]]), "b": np.array([0.0])}]
+    with opf.Solver.from_generic(np.zeros(3), -np.ones(3), np.ones(3), subs) as s:
+        with pytest.raises(opf.OPFError) as e:
+            s.precompute()
+        assert e.value.code == opf.OPF_E_INFEASIBLE_LOCAL
