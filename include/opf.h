@@ -121,7 +121,13 @@ typedef struct opf_solve_opts {
     int32_t precision;              /* OPF_PREC_* */
     int32_t recenter_every;         /* OPF_PREC_MIXED: iterations between FP64 re-centrings (0 = default) */
     int32_t engine;                 /* 0 = automatic, 1 = whole-grid kernels, 2 = one-CTA resident */
+    int32_t flags;                  /* OPF_SOLVE_* bits */
 } opf_solve_opts;
+
+/* opf_solve_opts.flags: drive the iteration chunks from the host (one plain
+ * CUDA graph per chunk and a status read after each) instead of one graph
+ * with a device-side WHILE node; same arithmetic, slower, profiler-visible. */
+#define OPF_SOLVE_HOST_LOOP 1
 
 typedef struct opf_sizes {
     int64_t n_global;               /* n: length of x */
@@ -130,6 +136,7 @@ typedef struct opf_sizes {
     int64_t n_rows;                 /* sum m_s */
     int64_t sum_nf;                 /* sum n_s * f_s of the stored factors (after precompute) */
     int64_t max_ns;
+    int64_t h2d_bytes;              /* bytes copied host -> device by opf_create */
 } opf_sizes;
 
 typedef struct opf_handle opf_handle;
@@ -191,8 +198,10 @@ int opf_set_locals(opf_handle *h, const double *xs, const double *lam, size_t L)
 
 int opf_get_sizes(opf_handle *h, opf_sizes *out);
 
-/* Per-phase device time of the last solve/step in milliseconds (CUDA events
- * on the handle's stream): [0] precompute, [1] iterations, [2] polish. */
+/* Statistics of the last precompute/solve (device times from CUDA events on
+ * the handle's stream): [0] precompute ms, [1] main iteration phase ms,
+ * [2] FP64 polish ms, [3] iterations in the main phase, [4] iterations in the
+ * polish, [5] re-centrings.  n = number of entries wanted (<= 6). */
 int opf_get_timing(opf_handle *h, double *ms, int n);
 
 void opf_destroy(opf_handle *h);

@@ -29,10 +29,13 @@ namespace opf {
 
 
 
-void launch_precompute(const PreArgs &a, cudaStream_t st);
+int launch_precompute(const PreArgs &a, cudaStream_t st);
+void launch_pack_factors(int S, const int4 *sub, const int4 *sub2, const long long *cap_off,
+                         const double *src, double *dst64, float *dst32, cudaStream_t st);
 template <typename T>
-void launch_iterate(const IterArgs<T> &a, const T *u_in, T *u_out, int vstride, double *partials,
-                    const DevStatus *st, bool check, cudaStream_t s);
+void launch_iterate(const IterArgs<T> &a, const T *u_in, T *u_out, double *partials,
+                    const DevStatus *st, bool check, int n_tiles, int block, int xcap, int vcap,
+                    int tcap, cudaStream_t s);
 void launch_check(const double *partials, int nblk, DevStatus *st, double rho, int add,
                   cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
 void launch_copy_if_running(long long n, const double *src, double *dst, const DevStatus *st,
@@ -61,9 +64,8 @@ template <typename T>
 void launch_recenter(int L, int G, int S, const int *gk, const double *xr_old, const double *xr_new,
                      T *ds, T *mu, double *lamr, const int2 *gseg, const int *uslot,
                      const double *c64, const double *lb, const double *ub, T *ct, T *lbt, T *ubt,
-                     const int *soff, const int *sn, const int *sf, const int *smode,
-                     const long long *sfoff, const double *F64, const double *bbar, double rho,
-                     T *bt, const DevStatus *st, cudaStream_t s);
+                     const int4 *sub, const int4 *sub2, const double *F64, const double *bbar,
+                     double rho, T *bt, const DevStatus *st, cudaStream_t s);
 void launch_enter_shift(int L, const int *gk, const double *xr, const double *ds64,
                         const double *mu64, float *ds32, float *mu32, double *lamr, cudaStream_t s);
 
@@ -85,6 +87,7 @@ static thread_local std::string g_last_error;
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
+    bool host_loop = false;
     double rho = 0;
     int k = 0, R = 0, kind = -1;
     void reset() {
@@ -96,45 +99,57 @@ struct GraphCache {
     }
 };
 
+// Grid tiling for one precision: tile t covers subsystems [s0[t], s0[t+1]).
+struct Tiling {
+    int n_tiles = 0, block = 128, xcap = 0, vcap = 0, tcap = 0;
+    int *d_s0 = nullptr;
+};
+
 struct opf_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     HostModel model;
-    int S = 0, L = 0, G = 0, vstride = 32, n_tasks = 0, iter_blocks = 0;
-    long long nA = 0, nB = 0, nP = 0, nF = 0, sum_nf = 0, n_rows = 0;
-    int max_ns = 0;
+    int S = 0, L = 0, G = 0;
+    long long nA = 0, nB = 0, nP = 0, nFcap = 0, nF = 0, sum_nf = 0, n_rows = 0, nitems = 0;
+    int max_ns = 0, sh_m = 0, sh_n = 0;
     std::vector<int> canon_slot_to_dev;     // canonical slot -> device slot
-    std::vector<int> h_sn, h_sf;
+    std::vector<int> h_sn, h_sm, h_soff, h_sf, h_mode;
     std::vector<void *> allocs;
     // per subsystem
     int *d_soff = nullptr, *d_sn = nullptr, *d_sm = nullptr, *d_sf = nullptr, *d_smode = nullptr;
     int *d_boff = nullptr, *d_pstatus = nullptr;
-    long long *d_aoff = nullptr, *d_poff = nullptr, *d_foff = nullptr;
-    int4 *d_tasks = nullptr;
+    long long *d_aoff = nullptr, *d_poff = nullptr, *d_fcap = nullptr;
+    int4 *d_sub = nullptr, *d_sub2 = nullptr;
+    int *d_items = nullptr;
     // per slot
-    int *d_gk = nullptr, *d_pk = nullptr, *d_uslot = nullptr;
-    int2 *d_seg = nullptr, *d_gseg = nullptr;
+    int *d_gk = nullptr, *d_pk = nullptr, *d_uslot = nullptr, *d_meta = nullptr, *d_segp = nullptr;
+    int2 *d_gseg = nullptr;
     double *d_A = nullptr, *d_b = nullptr, *d_W = nullptr, *d_Bw = nullptr, *d_P = nullptr;
-    double *d_F64 = nullptr, *d_bbar64 = nullptr;
+    double *d_Fcap = nullptr, *d_F64 = nullptr, *d_bbar64 = nullptr;
     float *d_F32 = nullptr;
     // per global
     double *d_c64 = nullptr, *d_lb64 = nullptr, *d_ub64 = nullptr, *d_x0 = nullptr;
     double *d_xr = nullptr, *d_xr2 = nullptr, *d_zeroG = nullptr, *d_x = nullptr, *d_objpart = nullptr;
     float *d_ct32 = nullptr, *d_lbt32 = nullptr, *d_ubt32 = nullptr;
+    double *d_recip64 = nullptr;
+    float *d_recip32 = nullptr;
     // state
     double *d_ds64 = nullptr, *d_mu64 = nullptr, *d_u64 = nullptr, *d_lamr = nullptr, *d_zeroL = nullptr;
     float *d_ds32 = nullptr, *d_mu32 = nullptr, *d_u32 = nullptr, *d_bt32 = nullptr;
     double *d_partials = nullptr;
     DevStatus *d_st = nullptr;
     DevStatus *h_st = nullptr;
+    Tiling t64, t32;
     // bookkeeping
     bool precomputed = false;
     bool have_prev_u = false;    // d_u64 + L holds the u that produced the last global update
-    double last_rho = 100.0;
+    double last_rho = 100.0, recip_rho = -1.0;
     long long total_iters = 0;
+    long long main_iters = 0, recenters = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    double timing[3] = {0, 0, 0};
+    double timing[6] = {0, 0, 0, 0, 0, 0};
+    long long h2d_bytes = 0;
     GraphCache g64, gmix;
     CtaLayout lay32{}, lay64{};
     bool cta32_ok = false, cta64_ok = false;
@@ -159,29 +174,33 @@ static int upload(opf_handle *h, T **p, const std::vector<T> &v) {
     int rc = dalloc(h, p, v.size());
     if (rc) return rc;
     if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    h->h2d_bytes += (long long)(v.size() * sizeof(T));
     return OPF_OK;
 }
 
 #define TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
 
-static void size_class(int n, int *W, int *R) {
-    if (n <= 8) { *W = 8; *R = 1; }
-    else if (n <= 16) { *W = 16; *R = 1; }
-    else if (n <= 32) { *W = 32; *R = 1; }
-    else { *W = 32; *R = (n + 31) / 32; }
-}
-
 static unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
+static int round4(int x) { return (x + 3) & ~3; }
 
 template <typename T>
 static bool make_cta_layout(opf_handle *h, CtaLayout *lay, size_t limit) {
     CtaLayout &c = *lay;
     c = CtaLayout{};
-    c.S = h->S; c.L = h->L; c.G = h->G; c.n_tasks = h->n_tasks; c.vstride = h->vstride;
+    c.S = h->S; c.L = h->L; c.G = h->G; c.nitems = (int)h->nitems;
     c.nF = h->nF;
     size_t off = 0;
     auto take = [&](unsigned *o, size_t bytes) { *o = (unsigned)off; off = align16((unsigned)(off + bytes)); };
+    long long vtot = 0;
+    for (int s = 0; s < h->S; ++s) vtot += round4(h->h_sn[s]);
     take(&c.off_F, (size_t)h->nF * sizeof(T));
+    take(&c.off_sub, (size_t)(h->S + 1) * sizeof(int4));
+    take(&c.off_sub2, (size_t)(h->S + 1) * sizeof(int4));
+    take(&c.off_items, (size_t)h->nitems * sizeof(int));
+    take(&c.off_meta, (size_t)h->L * sizeof(int));
+    take(&c.off_segp, (size_t)h->L * sizeof(int));
+    take(&c.off_gk, (size_t)h->L * sizeof(int));
+    take(&c.off_pk, (size_t)h->L * sizeof(int));
     take(&c.off_bt, (size_t)h->L * sizeof(T));
     take(&c.off_mu, (size_t)h->L * sizeof(T));
     take(&c.off_ds, (size_t)h->L * sizeof(T));
@@ -190,101 +209,112 @@ static bool make_cta_layout(opf_handle *h, CtaLayout *lay, size_t limit) {
     take(&c.off_ct, (size_t)h->G * sizeof(T));
     take(&c.off_lbt, (size_t)h->G * sizeof(T));
     take(&c.off_ubt, (size_t)h->G * sizeof(T));
-    take(&c.off_seg, (size_t)h->L * sizeof(int2));
-    take(&c.off_gk, (size_t)h->L * sizeof(int));
-    take(&c.off_pk, (size_t)h->L * sizeof(int));
-    take(&c.off_soff, (size_t)h->S * sizeof(int));
-    take(&c.off_sn, (size_t)h->S * sizeof(int));
-    take(&c.off_sf, (size_t)h->S * sizeof(int));
-    take(&c.off_smode, (size_t)h->S * sizeof(int));
-    take(&c.off_sfoff, (size_t)h->S * sizeof(long long));
-    take(&c.off_tasks, (size_t)h->n_tasks * sizeof(int4));
-    take(&c.off_sv, (size_t)32 * 2 * h->vstride * sizeof(T));
+    take(&c.off_recip, 256 * sizeof(T));
+    take(&c.off_xb, (size_t)h->L * sizeof(T));
+    take(&c.off_vb, (size_t)vtot * sizeof(T));
+    take(&c.off_tb, (size_t)h->nitems * sizeof(T));
     c.bytes = (unsigned)off;
     return off <= limit;
+}
+
+// Greedy tiling: consecutive subsystems until a tile holds >= target slots.
+static int make_tiling(opf_handle *h, Tiling *t, int target, int block) {
+    std::vector<int> s0;
+    t->xcap = t->vcap = t->tcap = 0;
+    int s = 0;
+    while (s < h->S) {
+        s0.push_back(s);
+        int slots = 0, v = 0, f = 0;
+        while (s < h->S && (slots == 0 || slots + h->h_sn[s] <= target)) {
+            slots += h->h_sn[s];
+            v += round4(h->h_sn[s]);
+            f += h->h_sf[s];
+            ++s;
+        }
+        t->xcap = std::max(t->xcap, slots);
+        t->vcap = std::max(t->vcap, v);
+        t->tcap = std::max(t->tcap, f);
+    }
+    s0.push_back(h->S);
+    t->n_tiles = (int)s0.size() - 1;
+    t->block = block;
+    t->vcap = round4(t->vcap);
+    t->xcap = round4(t->xcap);
+    CUDA_TRY(cudaMemcpyAsync(t->d_s0, s0.data(), s0.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    return OPF_OK;
 }
 
 static int build_layout(opf_handle *h) {
     HostModel &M = h->model;
     h->S = (int)M.subs.size();
     h->G = M.n;
-    // device order: larger classes first, then larger n
+    // device order: larger subsystems first (tiles then hold similar sizes)
     std::vector<int> order(h->S);
     std::iota(order.begin(), order.end(), 0);
-    auto key = [&](int s) {
-        int W, R;
-        size_class(M.subs[s].n, &W, &R);
-        return std::make_pair(-(W * R), -M.subs[s].n);
-    };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
-    // canonical slot offsets
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return M.subs[a].n > M.subs[b].n; });
     std::vector<int> csoff(h->S + 1, 0);
     for (int s = 0; s < h->S; ++s) csoff[s + 1] = csoff[s] + M.subs[s].n;
     h->L = csoff[h->S];
-    std::vector<int> soff(h->S), sn(h->S), sm(h->S), boff(h->S);
-    std::vector<long long> aoff(h->S), poff(h->S), foff(h->S);
+    if (h->L >= (1 << 24) || h->S >= (1 << 23)) {
+        g_last_error = "more than 2^24 local slots or 2^23 subsystems";
+        return OPF_E_CAPACITY;
+    }
+    std::vector<int> soff(h->S + 1), sn(h->S), sm(h->S), boff(h->S), meta(h->L);
+    std::vector<long long> aoff(h->S), poff(h->S), fcap(h->S);
     std::vector<double> A, b;
     h->canon_slot_to_dev.assign(h->L, 0);
     std::vector<int> gk(h->L);
-    long long ao = 0, po = 0, fo = 0;
-    int so = 0, bo = 0, Rmax = 1;
+    long long ao = 0, po = 0, fo = 0, fc = 0;
+    int so = 0, bo = 0;
     h->max_ns = 0;
     h->n_rows = 0;
+    h->sh_m = 0;
     for (int d = 0; d < h->S; ++d) {
         const HostSub &s = M.subs[order[d]];
         soff[d] = so; sn[d] = s.n; sm[d] = s.m; boff[d] = bo;
-        aoff[d] = ao; poff[d] = po; foff[d] = fo;
+        aoff[d] = ao; poff[d] = po; fcap[d] = fo;
         for (int r = 0; r < s.n; ++r) {
             h->canon_slot_to_dev[csoff[order[d]] + r] = so + r;
             gk[so + r] = s.vars[r];
+            meta[so + r] = (d << 8) | r;
         }
         A.insert(A.end(), s.A.begin(), s.A.end());
         b.insert(b.end(), s.b.begin(), s.b.end());
         so += s.n; bo += s.m;
         ao += (long long)s.m * s.n;
-        po += (long long)s.n * s.n;
-        fo += (long long)s.n * std::max(0, std::min(s.m, s.n / 2));
-        int W, R;
-        size_class(s.n, &W, &R);
-        Rmax = std::max(Rmax, R);
+        po += (long long)s.n * s.n + 33LL * (s.m + s.n) + 64;
+        const int fmax = std::max(0, std::min(s.m, s.n / 2));
+        fo += (long long)s.n * fmax;
+        fc += (long long)round4(s.n) * fmax;
         h->max_ns = std::max(h->max_ns, s.n);
+        h->sh_m = std::max(h->sh_m, s.m);
         h->n_rows += s.m;
     }
-    h->nA = ao; h->nB = bo; h->nP = po; h->nF = fo;
-    h->vstride = 32 * Rmax;
-    // warp tasks
-    std::vector<int4> tasks;
-    for (int d = 0; d < h->S;) {
-        int W, R;
-        size_class(sn[d], &W, &R);
-        int per = 32 / W, cnt = 0;
-        while (d + cnt < h->S && cnt < per) {
-            int W2, R2;
-            size_class(sn[d + cnt], &W2, &R2);
-            if (W2 != W || R2 != R) break;
-            ++cnt;
-        }
-        tasks.push_back(make_int4(d, cnt, W, R));
-        d += cnt;
-    }
-    h->n_tasks = (int)tasks.size();
-    h->iter_blocks = (h->n_tasks + 7) / 8;
+    soff[h->S] = so;
+    h->nA = ao; h->nB = bo; h->nP = po; h->nFcap = fo; h->nF = std::max<long long>(fc, 4);
+    h->sh_m = std::min(h->sh_m, 64);
+    h->sh_n = std::min(h->max_ns, 64);
     // u segments: copies of each global contiguous, canonical slot order inside
     std::vector<int> cnt(h->G, 0);
     for (int k = 0; k < h->L; ++k) cnt[gk[k]]++;
+    for (int i = 0; i < h->G; ++i)
+        if (cnt[i] > 255) {
+            g_last_error = "a global variable with more than 255 local copies";
+            return OPF_E_CAPACITY;
+        }
     std::vector<int> gstart(h->G + 1, 0);
     for (int i = 0; i < h->G; ++i) gstart[i + 1] = gstart[i] + cnt[i];
     std::vector<int> fill(gstart.begin(), gstart.end() - 1);
-    std::vector<int> pk(h->L), uslot(h->L);
+    std::vector<int> pk(h->L), uslot(h->L), segp(h->L);
     for (int cs = 0; cs < h->L; ++cs) {            // canonical order
         int k = h->canon_slot_to_dev[cs];
         int g = gk[k];
         pk[k] = fill[g]++;
         uslot[pk[k]] = k;
     }
-    std::vector<int2> seg(h->L), gseg(h->G);
+    std::vector<int2> gseg(h->G);
     for (int i = 0; i < h->G; ++i) gseg[i] = make_int2(gstart[i], cnt[i]);
-    for (int k = 0; k < h->L; ++k) seg[k] = gseg[gk[k]];
+    for (int k = 0; k < h->L; ++k) segp[k] = (gstart[gk[k]] << 8) | cnt[gk[k]];
     // start point of Sec. V-A
     std::vector<double> x0(h->G, 0.0);
     for (int i = 0; i < h->G; ++i) {
@@ -295,6 +325,8 @@ static int build_layout(opf_handle *h) {
         else if (std::isfinite(hi)) x0[i] = hi;
     }
     h->h_sn = sn;
+    h->h_sm = sm;
+    h->h_soff = soff;
     // ---- uploads
     TRY(upload(h, &h->d_soff, soff));
     TRY(upload(h, &h->d_sn, sn));
@@ -302,12 +334,12 @@ static int build_layout(opf_handle *h) {
     TRY(upload(h, &h->d_boff, boff));
     TRY(upload(h, &h->d_aoff, aoff));
     TRY(upload(h, &h->d_poff, poff));
-    TRY(upload(h, &h->d_foff, foff));
-    TRY(upload(h, &h->d_tasks, tasks));
+    TRY(upload(h, &h->d_fcap, fcap));
     TRY(upload(h, &h->d_gk, gk));
     TRY(upload(h, &h->d_pk, pk));
     TRY(upload(h, &h->d_uslot, uslot));
-    TRY(upload(h, &h->d_seg, seg));
+    TRY(upload(h, &h->d_meta, meta));
+    TRY(upload(h, &h->d_segp, segp));
     TRY(upload(h, &h->d_gseg, gseg));
     TRY(upload(h, &h->d_A, A));
     TRY(upload(h, &h->d_b, b));
@@ -316,12 +348,20 @@ static int build_layout(opf_handle *h) {
     TRY(upload(h, &h->d_ub64, M.ub));
     TRY(upload(h, &h->d_x0, x0));
     const size_t L = h->L, G = h->G;
+    long long items_cap = 0;
+    for (int d = 0; d < h->S; ++d) items_cap += std::max(0, std::min(sm[d], sn[d] / 2));
     TRY(dalloc(h, &h->d_sf, h->S));
     TRY(dalloc(h, &h->d_smode, h->S));
     TRY(dalloc(h, &h->d_pstatus, h->S));
+    TRY(dalloc(h, &h->d_sub, h->S + 1));
+    TRY(dalloc(h, &h->d_sub2, h->S + 1));
+    TRY(dalloc(h, &h->d_items, std::max<long long>(items_cap, 1)));
+    TRY(dalloc(h, &h->t64.d_s0, h->S + 1));
+    TRY(dalloc(h, &h->t32.d_s0, h->S + 1));
     TRY(dalloc(h, &h->d_W, h->nA));
     TRY(dalloc(h, &h->d_Bw, h->nB));
     TRY(dalloc(h, &h->d_P, h->nP));
+    TRY(dalloc(h, &h->d_Fcap, h->nFcap));
     TRY(dalloc(h, &h->d_F64, h->nF));
     TRY(dalloc(h, &h->d_F32, h->nF));
     TRY(dalloc(h, &h->d_bbar64, L));
@@ -333,6 +373,8 @@ static int build_layout(opf_handle *h) {
     TRY(dalloc(h, &h->d_ct32, G));
     TRY(dalloc(h, &h->d_lbt32, G));
     TRY(dalloc(h, &h->d_ubt32, G));
+    TRY(dalloc(h, &h->d_recip64, 256));
+    TRY(dalloc(h, &h->d_recip32, 256));
     TRY(dalloc(h, &h->d_ds64, L));
     TRY(dalloc(h, &h->d_mu64, L));
     TRY(dalloc(h, &h->d_u64, 2 * L));
@@ -342,7 +384,7 @@ static int build_layout(opf_handle *h) {
     TRY(dalloc(h, &h->d_mu32, L));
     TRY(dalloc(h, &h->d_u32, 2 * L));
     TRY(dalloc(h, &h->d_bt32, L));
-    TRY(dalloc(h, &h->d_partials, (size_t)6 * std::max(h->iter_blocks, 1)));
+    TRY(dalloc(h, &h->d_partials, (size_t)6 * (h->S + 1)));
     TRY(dalloc(h, &h->d_st, 1));
     CUDA_TRY(cudaMemsetAsync(h->d_zeroG, 0, G * sizeof(double), h->stream));
     CUDA_TRY(cudaMemsetAsync(h->d_zeroL, 0, L * sizeof(double), h->stream));
@@ -350,11 +392,6 @@ static int build_layout(opf_handle *h) {
     CUDA_TRY(cudaMallocHost(&h->h_st, sizeof(DevStatus)));
     memset(h->h_st, 0, sizeof(DevStatus));
     for (auto &e : h->ev) CUDA_TRY(cudaEventCreate(&e));
-    int optin = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    const size_t limit = optin > 4096 ? (size_t)optin - 4096 : 0;
-    h->cta32_ok = make_cta_layout<float>(h, &h->lay32, limit);
-    h->cta64_ok = make_cta_layout<double>(h, &h->lay64, limit);
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     return OPF_OK;
 }
@@ -412,32 +449,69 @@ extern "C" int opf_precompute(opf_handle *h) {
     CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->d_W, h->d_A, std::max<long long>(h->nA, 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->d_Bw, h->d_b, std::max<long long>(h->nB, 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    CUDA_TRY(cudaMemsetAsync(h->d_F64, 0, std::max<long long>(h->nF, 1) * sizeof(double), h->stream));
     PreArgs a;
-    a.S = h->S; a.sm = h->d_sm; a.sn = h->d_sn; a.soff = h->d_soff;
-    a.aoff = h->d_aoff; a.poff = h->d_poff; a.foff = h->d_foff; a.boff = h->d_boff;
-    a.W = h->d_W; a.Bw = h->d_Bw; a.P = h->d_P; a.F = h->d_F64;
+    a.S = h->S; a.sh_m = h->sh_m; a.sh_n = h->sh_n;
+    a.sm = h->d_sm; a.sn = h->d_sn; a.soff = h->d_soff;
+    a.aoff = h->d_aoff; a.poff = h->d_poff; a.foff = h->d_fcap; a.boff = h->d_boff;
+    a.W = h->d_W; a.Bw = h->d_Bw; a.P = h->d_P; a.F = h->d_Fcap;
     a.sf = h->d_sf; a.smode = h->d_smode; a.bbar = h->d_bbar64; a.status = h->d_pstatus;
-    launch_precompute(a, h->stream);
+    if (launch_precompute(a, h->stream)) { g_last_error = "cannot size the precompute kernel"; return OPF_E_CUDA; }
     CUDA_TRY(cudaGetLastError());
-    launch_cast<double, float>(std::max<long long>(h->nF, 1), h->d_F64, h->d_F32, h->stream);
-    CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
     std::vector<int> status(h->S);
     h->h_sf.resize(h->S);
     CUDA_TRY(cudaMemcpyAsync(status.data(), h->d_pstatus, h->S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->h_sf.data(), h->d_sf, h->S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
-    h->timing[0] = ms;
     for (int s = 0; s < h->S; ++s)
         if (status[s]) {
             g_last_error = "inconsistent local system A_s x_s = b_s";
             h->precomputed = false;
             return OPF_E_INFEASIBLE_LOCAL;
         }
+    // iteration layout: per subsystem (first slot, n, f, mode) and (factor
+    // offset, npad, padded-v prefix, f prefix); factor columns padded to npad
+    h->h_mode.resize(h->S);
+    CUDA_TRY(cudaMemcpyAsync(h->h_mode.data(), h->d_smode, h->S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    std::vector<int4> sub(h->S + 1), sub2(h->S + 1);
+    std::vector<int> items;
+    long long fo = 0, vpre = 0, tpre = 0;
     h->sum_nf = 0;
-    for (int s = 0; s < h->S; ++s) h->sum_nf += (long long)h->h_sn[s] * h->h_sf[s];
+    for (int s = 0; s < h->S; ++s) {
+        const int n = h->h_sn[s], f = h->h_sf[s], npad = round4(n);
+        sub[s] = make_int4(h->h_soff[s], n, f, h->h_mode[s]);
+        sub2[s] = make_int4((int)fo, npad, (int)vpre, (int)tpre);
+        for (int c = 0; c < f; ++c) items.push_back((s << 8) | c);
+        fo += (long long)f * npad;
+        vpre += npad;
+        tpre += f;
+        h->sum_nf += (long long)n * f;
+    }
+    sub[h->S] = make_int4(h->L, 0, 0, 0);
+    sub2[h->S] = make_int4((int)fo, 0, (int)vpre, (int)tpre);
+    h->nitems = (long long)items.size();
+    CUDA_TRY(cudaMemcpyAsync(h->d_sub, sub.data(), sub.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_sub2, sub2.data(), sub2.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
+    if (!items.empty())
+        CUDA_TRY(cudaMemcpyAsync(h->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    launch_pack_factors(h->S, h->d_sub, h->d_sub2, h->d_fcap, h->d_Fcap, h->d_F64, h->d_F32, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
+    CUDA_TRY(cudaEventSynchronize(h->ev[1]));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    h->timing[0] = ms;
+    h->nF = std::max<long long>(fo, 4);
+    TRY(make_tiling(h, &h->t64, 64, 64));
+    TRY(make_tiling(h, &h->t32, 256, 128));
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    const size_t limit = optin > 4096 ? (size_t)optin - 4096 : 0;
+    h->cta32_ok = make_cta_layout<float>(h, &h->lay32, limit);
+    h->cta64_ok = make_cta_layout<double>(h, &h->lay64, limit);
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->g64.reset();
+    h->gmix.reset();
     h->precomputed = true;
     return reset_state(h);
 }
@@ -453,50 +527,84 @@ extern "C" int opf_reset(opf_handle *h) {
 }
 
 template <typename T>
+static IterArgs<T> common_args(opf_handle *h) {
+    IterArgs<T> a;
+    a.sub = h->d_sub; a.sub2 = h->d_sub2; a.items = h->d_items;
+    a.meta = h->d_meta; a.segp = h->d_segp; a.gk = h->d_gk; a.pk = h->d_pk;
+    a.c64 = h->d_c64;
+    return a;
+}
+
+template <typename T>
 static IterArgs<T> iter_args(opf_handle *h, double rho);
 
 template <>
 IterArgs<double> iter_args<double>(opf_handle *h, double rho) {
-    IterArgs<double> a;
-    a.soff = h->d_soff; a.sn = h->d_sn; a.sf = h->d_sf; a.smode = h->d_smode; a.sfoff = h->d_foff;
-    a.F = h->d_F64; a.seg = h->d_seg; a.gk = h->d_gk; a.pk = h->d_pk;
-    a.bt = h->d_bbar64; a.mu = h->d_mu64; a.ds = h->d_ds64;
+    IterArgs<double> a = common_args<double>(h);
+    a.F = h->d_F64; a.bt = h->d_bbar64; a.mu = h->d_mu64; a.ds = h->d_ds64;
     a.ct = h->d_c64; a.lbt = h->d_lb64; a.ubt = h->d_ub64;
-    a.xr = h->d_zeroG; a.lamr = h->d_zeroL; a.c64 = h->d_c64;
-    a.tasks = h->d_tasks; a.n_tasks = h->n_tasks;
+    a.xr = h->d_zeroG; a.lamr = h->d_zeroL; a.recip = h->d_recip64;
+    a.tile_s0 = h->t64.d_s0;
     a.rho = rho; a.inv_rho = 1.0 / rho;
     return a;
 }
 
 template <>
 IterArgs<float> iter_args<float>(opf_handle *h, double rho) {
-    IterArgs<float> a;
-    a.soff = h->d_soff; a.sn = h->d_sn; a.sf = h->d_sf; a.smode = h->d_smode; a.sfoff = h->d_foff;
-    a.F = h->d_F32; a.seg = h->d_seg; a.gk = h->d_gk; a.pk = h->d_pk;
-    a.bt = h->d_bt32; a.mu = h->d_mu32; a.ds = h->d_ds32;
+    IterArgs<float> a = common_args<float>(h);
+    a.F = h->d_F32; a.bt = h->d_bt32; a.mu = h->d_mu32; a.ds = h->d_ds32;
     a.ct = h->d_ct32; a.lbt = h->d_lbt32; a.ubt = h->d_ubt32;
-    a.xr = h->d_xr; a.lamr = h->d_lamr; a.c64 = h->d_c64;
-    a.tasks = h->d_tasks; a.n_tasks = h->n_tasks;
+    a.xr = h->d_xr; a.lamr = h->d_lamr; a.recip = h->d_recip32;
+    a.tile_s0 = h->t32.d_s0;
     a.rho = (float)rho; a.inv_rho = (float)(1.0 / rho);
     return a;
 }
+
+// recip[N] = 1 / (rho N) for the global update, in both precisions
+static int set_recip(opf_handle *h, double rho) {
+    if (h->recip_rho == rho) return OPF_OK;
+    std::vector<double> r64(256, 0.0);
+    std::vector<float> r32(256, 0.0f);
+    for (int n = 1; n < 256; ++n) {
+        r64[n] = 1.0 / (rho * n);
+        r32[n] = (float)r64[n];
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->d_recip64, r64.data(), 256 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_recip32, r32.data(), 256 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->recip_rho = rho;
+    return OPF_OK;
+}
+
+template <typename T> static const Tiling &tiling(opf_handle *h);
+template <> const Tiling &tiling<double>(opf_handle *h) { return h->t64; }
+template <> const Tiling &tiling<float>(opf_handle *h) { return h->t32; }
 
 // Enqueue one chunk of k grid iterations (the last one tested) and the test.
 template <typename T>
 static void enqueue_grid_chunk(opf_handle *h, const IterArgs<T> &a, T *u, int k, double rho,
                                cudaGraphConditionalHandle cond, int use_cond) {
+    const Tiling &t = tiling<T>(h);
     for (int i = 0; i < k; ++i) {
         const T *uin = u + (size_t)(i & 1) * h->L;
         T *uout = u + (size_t)((i + 1) & 1) * h->L;
-        launch_iterate<T>(a, uin, uout, h->vstride, h->d_partials, h->d_st, i == k - 1, h->stream);
+        launch_iterate<T>(a, uin, uout, h->d_partials, h->d_st, i == k - 1, t.n_tiles, t.block, t.xcap,
+                          t.vcap, t.tcap, h->stream);
     }
-    launch_check(h->d_partials, h->iter_blocks, h->d_st, rho, k, cond, use_cond, h->stream);
+    launch_check(h->d_partials, t.n_tiles, h->d_st, rho, k, cond, use_cond, h->stream);
 }
 
-// Build a graph "while (!done) body" where body is enqueued by fn(cond).
+// Build a graph "while (!done) body" where body is enqueued by fn(cond, 1).
+// With host_loop the graph is the body alone (fn(0, 0)), relaunched by the
+// host until the device status says done (profilers see its kernel nodes).
 template <typename Fn>
-static int build_while_graph(opf_handle *h, GraphCache *gc, Fn fn) {
+static int build_while_graph(opf_handle *h, GraphCache *gc, Fn fn, bool host_loop) {
     gc->reset();
+    if (host_loop) {
+        gc->host_loop = true;
+        return OPF_OK;
+    }
+    gc->host_loop = false;
     CUDA_TRY(cudaGraphCreate(&gc->graph, 0));
     cudaGraphConditionalHandle cond;
     CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, gc->graph, 1, cudaGraphCondAssignDefault));
@@ -512,7 +620,7 @@ static int build_while_graph(opf_handle *h, GraphCache *gc, Fn fn) {
     CUDA_TRY(cudaGraphAddNode(&node, gc->graph, nullptr, nullptr, 0, cp));
     cudaGraph_t body = cp->conditional.phGraph_out[0];
     CUDA_TRY(cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    fn(cond);
+    fn(cond, 1);
     cudaGraph_t captured = nullptr;
     cudaError_t ec = cudaStreamEndCapture(h->stream, &captured);
     if (ec != cudaSuccess) {
@@ -542,27 +650,46 @@ static int read_status(opf_handle *h) {
     return OPF_OK;
 }
 
+// One launch of the WHILE graph, or (host loop) direct launches of the body
+// until the status says done.
+template <typename Fn>
+static int run_graph(opf_handle *h, GraphCache *gc, Fn fn) {
+    if (!gc->host_loop) {
+        CUDA_TRY(cudaGraphLaunch(gc->exec, h->stream));
+        return read_status(h);
+    }
+    for (;;) {
+        fn(cudaGraphConditionalHandle{}, 0);
+        CUDA_TRY(cudaGetLastError());
+        TRY(read_status(h));
+        if (h->h_st->done) return OPF_OK;
+    }
+}
+
 // FP64 iterations on the whole grid until the test or max_iter.
 static int run_grid64(opf_handle *h, const opf_solve_opts &o) {
     const double rho = o.rho;
+    TRY(set_recip(h, rho));
     launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
     CUDA_TRY(cudaGetLastError());
-    if (h->g64.kind != 0 || h->g64.rho != rho || h->g64.k != o.check_every) {
-        IterArgs<double> a = iter_args<double>(h, rho);
-        TRY(build_while_graph(h, &h->g64, [&](cudaGraphConditionalHandle c) {
-            enqueue_grid_chunk<double>(h, a, h->d_u64, o.check_every, rho, c, 1);
-        }));
+    const bool hl = (o.flags & OPF_SOLVE_HOST_LOOP) != 0;
+    IterArgs<double> a = iter_args<double>(h, rho);
+    auto body = [&](cudaGraphConditionalHandle c, int use) {
+        enqueue_grid_chunk<double>(h, a, h->d_u64, o.check_every, rho, c, use);
+    };
+    if (h->g64.kind != 0 || h->g64.rho != rho || h->g64.k != o.check_every || h->g64.host_loop != hl) {
+        TRY(build_while_graph(h, &h->g64, body, hl));
         h->g64.kind = 0; h->g64.rho = rho; h->g64.k = o.check_every;
     }
-    CUDA_TRY(cudaGraphLaunch(h->g64.exec, h->stream));
-    TRY(read_status(h));
+    TRY(run_graph(h, &h->g64, body));
     h->have_prev_u = h->h_st->iter > 0;
     return OPF_OK;
 }
 
-// FP64 iterations by the one-CTA engine (testing aid: same arithmetic).
+// FP64 iterations by the one-CTA engine (same arithmetic, instance in shared memory).
 static int run_cta64(opf_handle *h, const opf_solve_opts &o) {
     const double rho = o.rho;
+    TRY(set_recip(h, rho));
     if (prepare_cta_engine<double>(h->lay64.bytes)) { g_last_error = "cannot size CTA engine"; return OPF_E_CUDA; }
     launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
     IterArgs<double> a = iter_args<double>(h, rho);
@@ -577,6 +704,7 @@ static int run_cta64(opf_handle *h, const opf_solve_opts &o) {
 // FP32 iterations in the shifted frame, re-centred in FP64 every R iterations.
 static int run_mixed(opf_handle *h, const opf_solve_opts &o, bool use_cta, bool recenter) {
     const double rho = o.rho;
+    TRY(set_recip(h, rho));
     const int L = h->L, G = h->G, S = h->S;
     const int k = o.check_every;
     int R = o.recenter_every > 0 ? o.recenter_every : 1000;
@@ -589,20 +717,20 @@ static int run_mixed(opf_handle *h, const opf_solve_opts &o, bool use_cta, bool 
     launch_enter_shift(L, h->d_gk, h->d_xr, h->d_ds64, h->d_mu64, h->d_ds32, h->d_mu32, h->d_lamr, h->stream);
     launch_recenter<float>(L, G, S, h->d_gk, h->d_xr, h->d_xr, h->d_ds32, h->d_mu32, h->d_lamr,
                            h->d_gseg, h->d_uslot, h->d_c64, h->d_lb64, h->d_ub64, h->d_ct32, h->d_lbt32,
-                           h->d_ubt32, h->d_soff, h->d_sn, h->d_sf, h->d_smode, h->d_foff, h->d_F64,
-                           h->d_bbar64, rho, h->d_bt32, nullptr, h->stream);
+                           h->d_ubt32, h->d_sub, h->d_sub2, h->d_F64, h->d_bbar64, rho, h->d_bt32,
+                           nullptr, h->stream);
     launch_make_u<float>(L, h->d_pk, h->d_ds32, h->d_mu32, (float)rho, h->d_u32, nullptr, h->stream);
     CUDA_TRY(cudaGetLastError());
     if (use_cta && prepare_cta_engine<float>(h->lay32.bytes)) { g_last_error = "cannot size CTA engine"; return OPF_E_CUDA; }
     const int kind = (use_cta ? 2 : 1) + (recenter ? 0 : 2);
-    if (h->gmix.kind != kind || h->gmix.rho != rho || h->gmix.k != k || h->gmix.R != R) {
-        IterArgs<float> a = iter_args<float>(h, rho);
-        TRY(build_while_graph(h, &h->gmix, [&](cudaGraphConditionalHandle c) {
+    const bool hl = (o.flags & OPF_SOLVE_HOST_LOOP) != 0;
+    IterArgs<float> a = iter_args<float>(h, rho);
+    auto body = [&](cudaGraphConditionalHandle c, int use) {
             if (use_cta) {
-                launch_cta_engine<float>(a, h->lay32, h->d_u32, R, k, h->d_st, rho, c, 1, h->stream);
+                launch_cta_engine<float>(a, h->lay32, h->d_u32, R, k, h->d_st, rho, c, use, h->stream);
             } else {
                 const int chunks = recenter ? R / k : 1;
-                for (int i = 0; i < chunks; ++i) enqueue_grid_chunk<float>(h, a, h->d_u32, k, rho, c, 1);
+                for (int i = 0; i < chunks; ++i) enqueue_grid_chunk<float>(h, a, h->d_u32, k, rho, c, use);
             }
             if (!recenter) return;
             // re-centre on the next global update (u of the last iteration is in buffer 0)
@@ -610,14 +738,17 @@ static int run_mixed(opf_handle *h, const opf_solve_opts &o, bool use_cta, bool 
                                    h->d_c64, (float)rho, h->d_xr2, h->d_objpart, h->d_st, h->stream);
             launch_recenter<float>(L, G, S, h->d_gk, h->d_xr, h->d_xr2, h->d_ds32, h->d_mu32, h->d_lamr,
                                    h->d_gseg, h->d_uslot, h->d_c64, h->d_lb64, h->d_ub64, h->d_ct32,
-                                   h->d_lbt32, h->d_ubt32, h->d_soff, h->d_sn, h->d_sf, h->d_smode,
-                                   h->d_foff, h->d_F64, h->d_bbar64, rho, h->d_bt32, h->d_st, h->stream);
+                                   h->d_lbt32, h->d_ubt32, h->d_sub, h->d_sub2, h->d_F64, h->d_bbar64, rho,
+                                   h->d_bt32, h->d_st, h->stream);
             launch_copy_if_running(G, h->d_xr2, h->d_xr, h->d_st, h->stream);
             launch_make_u<float>(L, h->d_pk, h->d_ds32, h->d_mu32, (float)rho, h->d_u32, h->d_st, h->stream);
-        }));
+    };
+    if (h->gmix.kind != kind || h->gmix.rho != rho || h->gmix.k != k || h->gmix.R != R ||
+        h->gmix.host_loop != hl) {
+        TRY(build_while_graph(h, &h->gmix, body, hl));
         h->gmix.kind = kind; h->gmix.rho = rho; h->gmix.k = k; h->gmix.R = R;
     }
-    CUDA_TRY(cudaGraphLaunch(h->gmix.exec, h->stream));
+    TRY(run_graph(h, &h->gmix, body));
     // back to the unshifted FP64 state
     launch_unshift<float>(L, h->d_gk, h->d_xr, h->d_lamr, h->d_ds32, h->d_mu32, h->d_ds64, h->d_mu64, h->stream);
     CUDA_TRY(cudaGetLastError());
@@ -659,12 +790,21 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
         } else {
             TRY(run_grid64(h, o));
         }
+        h->main_iters = h->h_st->iter;
+        h->recenters = 0;
         CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
         CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
     } else {
         bool cta = o.engine == 2 || (o.engine == 0 && h->cta32_ok);
         if (cta && !h->cta32_ok) { g_last_error = "instance does not fit one CTA"; return OPF_E_CAPACITY; }
         TRY(run_mixed(h, o, cta, o.precision == OPF_PREC_MIXED));
+        h->main_iters = h->h_st->iter;
+        {
+            int R = o.recenter_every > 0 ? o.recenter_every : 1000;
+            R = std::max(o.check_every, (R / o.check_every) * o.check_every);
+            // one re-centring per completed body of R iterations before the stop
+            h->recenters = o.precision == OPF_PREC_MIXED ? (h->main_iters - 1) / R : 0;
+        }
         CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
         if (o.precision == OPF_PREC_FP32) {
             // global x of the last FP32 state, evaluated in FP64
@@ -691,6 +831,9 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
     cudaEventElapsedTime(&b, h->ev[2], h->ev[3]);
     h->timing[1] = a;
     h->timing[2] = b;
+    h->timing[3] = (double)h->main_iters;
+    h->timing[4] = (double)(h->h_st->iter - h->main_iters);
+    h->timing[5] = (double)h->recenters;
     h->total_iters = h->h_st->iter;
     if (h->h_st->numeric) { g_last_error = "NaN or Inf in the residuals"; return OPF_E_NUMERIC; }
     return h->h_st->converged ? OPF_OK : OPF_NOT_CONVERGED;
@@ -714,14 +857,17 @@ extern "C" int opf_step(opf_handle *h, double rho, int32_t n_iters) {
     opf_solve_opts o = default_opts();
     o.max_iter = 0x7fffffff;
     TRY(set_status(h, o, false));
+    TRY(set_recip(h, rho));
     launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
     IterArgs<double> a = iter_args<double>(h, rho);
+    const Tiling &t = h->t64;
     for (int i = 0; i < n_iters; ++i) {
         const double *uin = h->d_u64 + (size_t)(i & 1) * h->L;
         double *uout = h->d_u64 + (size_t)((i + 1) & 1) * h->L;
-        launch_iterate<double>(a, uin, uout, h->vstride, h->d_partials, h->d_st, i == n_iters - 1, h->stream);
+        launch_iterate<double>(a, uin, uout, h->d_partials, h->d_st, i == n_iters - 1, t.n_tiles, t.block,
+                               t.xcap, t.vcap, t.tcap, h->stream);
     }
-    launch_check(h->d_partials, h->iter_blocks, h->d_st, rho, n_iters, cudaGraphConditionalHandle{}, 0, h->stream);
+    launch_check(h->d_partials, t.n_tiles, h->d_st, rho, n_iters, cudaGraphConditionalHandle{}, 0, h->stream);
     CUDA_TRY(cudaGetLastError());
     TRY(read_status(h));
     // make the previous-u buffer be the one at offset L
@@ -805,12 +951,13 @@ extern "C" int opf_get_sizes(opf_handle *h, opf_sizes *out) {
     out->n_rows = h->n_rows;
     out->sum_nf = h->sum_nf;
     out->max_ns = h->max_ns;
+    out->h2d_bytes = h->h2d_bytes;
     return OPF_OK;
 }
 
 extern "C" int opf_get_timing(opf_handle *h, double *ms, int n) {
     if (!h || !ms) return OPF_E_INVALID;
-    for (int i = 0; i < n && i < 3; ++i) ms[i] = h->timing[i];
+    for (int i = 0; i < n && i < 6; ++i) ms[i] = h->timing[i];
     return OPF_OK;
 }
 

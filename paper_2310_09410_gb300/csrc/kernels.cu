@@ -49,276 +49,385 @@ __device__ __forceinline__ T ld(const T *p) {
 
 // ============================================================ precompute
 
-__global__ void __launch_bounds__(128) k_precompute(PreArgs a) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= a.S) return;
-    const int s = warp;
+// Coefficients c_k = <rows_k, v> for k < nr of the lane-distributed vector v
+// (entries v[t] at column lane + 32 t): per-lane partials go through a
+// shared/global transpose so the nr warp reductions run side by side.
+__device__ __forceinline__ void project_coeffs(const double *rows, int n, int nr, const double v[RMAX],
+                                               int T, int lane, double *red, double *coef) {
+    for (int k = 0; k < nr; ++k) {
+        double p = 0.0;
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t) {
+            const int c = lane + 32 * t;
+            if (t < T && c < n) p += rows[(long long)k * n + c] * v[t];
+        }
+        red[k * 32 + lane] = p;
+    }
+    __syncwarp();
+    for (int k = lane; k < nr; k += 32) {
+        double acc = 0.0;
+        for (int i = 0; i < 32; ++i) acc += red[k * 32 + i];
+        coef[k] = acc;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ double warp_norm(const double v[RMAX]) {
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < RMAX; ++t) s += v[t] * v[t];
+    return sqrt(warp_sum(s));
+}
+
+// One warp per subsystem.  Rows of A_s (turned into Q in place), the null-space
+// rows N and the reduction scratch live in shared memory when the subsystem
+// fits (m <= sh_m, n <= sh_n), otherwise in the per-subsystem global scratch.
+__global__ void __launch_bounds__(32) k_precompute(PreArgs a) {
+    extern __shared__ __align__(16) double shp[];
+    const int s = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (s >= a.S) return;
     const int m = a.sm[s], n = a.sn[s];
-    const int T = (n + 31) >> 5;   // entries per lane (n <= 256 -> T <= 8)
-    double *Aw = a.W + a.aoff[s];
-    double *bw = a.Bw + a.boff[s];
+    const int T = (n + 31) >> 5;
+    const bool use_sh = m <= a.sh_m && n <= a.sh_n;
+    const int mm = m > 0 ? m : 1;
+    double *Q, *N, *red, *coef, *beta;
+    if (use_sh) {
+        Q = shp;
+        N = Q + a.sh_m * a.sh_n;
+        red = N + a.sh_n * a.sh_n;
+        coef = red + 32 * (a.sh_m > a.sh_n ? a.sh_m : a.sh_n);
+        beta = coef + (a.sh_m > a.sh_n ? a.sh_m : a.sh_n);
+        for (int i = lane; i < m * n; i += 32) Q[i] = a.W[a.aoff[s] + i];
+        for (int i = lane; i < m; i += 32) beta[i] = a.Bw[a.boff[s] + i];
+    } else {
+        Q = a.W + a.aoff[s];
+        N = a.P + a.poff[s];
+        red = N + (long long)n * n;
+        coef = red + 32 * (m > n ? m : n);
+        beta = a.Bw + a.boff[s];
+    }
+    (void)mm;
+    __syncwarp();
     double bmax = 0.0;
-    for (int j = lane; j < m; j += 32) bmax = fmax(bmax, fabs(bw[j]));
+    for (int j = lane; j < m; j += 32) bmax = fmax(bmax, fabs(beta[j]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    // classical Gram-Schmidt, applied twice, on the rows; b follows the same operations
     int r = 0, bad = 0;
     for (int j = 0; j < m; ++j) {
         double v[RMAX];
 #pragma unroll
         for (int t = 0; t < RMAX; ++t) {
-            int c = lane + 32 * t;
-            v[t] = (t < T && c < n) ? Aw[(long long)j * n + c] : 0.0;
+            const int c = lane + 32 * t;
+            v[t] = (t < T && c < n) ? Q[(long long)j * n + c] : 0.0;
         }
-        double bj = bw[j];
-        double n0 = 0.0;
-#pragma unroll
-        for (int t = 0; t < RMAX; ++t) n0 += v[t] * v[t];
-        n0 = sqrt(warp_sum(n0));
-        for (int pass = 0; pass < 2; ++pass) {
+        double bj = beta[j];
+        const double n0 = warp_norm(v);
+        for (int pass = 0; pass < 2 && r > 0; ++pass) {
+            project_coeffs(Q, n, r, v, T, lane, red, coef);
             for (int k = 0; k < r; ++k) {
-                const double *q = Aw + (long long)k * n;
-                double d = 0.0;
+                const double ck = coef[k];
 #pragma unroll
                 for (int t = 0; t < RMAX; ++t) {
-                    int c = lane + 32 * t;
-                    if (t < T && c < n) d += q[c] * v[t];
+                    const int c = lane + 32 * t;
+                    if (t < T && c < n) v[t] -= ck * Q[(long long)k * n + c];
                 }
-                d = warp_sum(d);
-#pragma unroll
-                for (int t = 0; t < RMAX; ++t) {
-                    int c = lane + 32 * t;
-                    if (t < T && c < n) v[t] -= d * q[c];
-                }
-                bj -= d * bw[k];
+                bj -= ck * beta[k];
             }
+            __syncwarp();
         }
-        double nr = 0.0;
-#pragma unroll
-        for (int t = 0; t < RMAX; ++t) nr += v[t] * v[t];
-        nr = sqrt(warp_sum(nr));
-        __syncwarp();
+        const double nr = warp_norm(v);
         if (n0 > 0.0 && nr > 1e-10 * n0) {
-            double inv = 1.0 / nr;
+            const double inv = 1.0 / nr;
 #pragma unroll
             for (int t = 0; t < RMAX; ++t) {
-                int c = lane + 32 * t;
-                if (t < T && c < n) Aw[(long long)r * n + c] = v[t] * inv;
+                const int c = lane + 32 * t;
+                if (t < T && c < n) Q[(long long)r * n + c] = v[t] * inv;
             }
             __syncwarp();
-            if (lane == 0) bw[r] = bj * inv;
-            __syncwarp();
+            if (lane == 0) beta[r] = bj * inv;
             ++r;
         } else if (fabs(bj) > 1e-9 * (1.0 + bmax)) {
             bad = 1;
         }
+        __syncwarp();
     }
-    __syncwarp();
     // bbar = sum_k beta_k q_k
     const int so = a.soff[s];
     for (int c = lane; c < n; c += 32) {
         double acc = 0.0;
-        for (int k = 0; k < r; ++k) acc += bw[k] * Aw[(long long)k * n + c];
+        for (int k = 0; k < r; ++k) acc += beta[k] * Q[(long long)k * n + c];
         a.bbar[so + c] = acc;
     }
     double *F = a.F + a.foff[s];
     if (r <= n - r) {
-        // mode 0: F = Q^T, column k of F = row k of Q
         for (int k = 0; k < r; ++k)
-            for (int c = lane; c < n; c += 32) F[(long long)k * n + c] = Aw[(long long)k * n + c];
+            for (int c = lane; c < n; c += 32) F[(long long)k * n + c] = Q[(long long)k * n + c];
         if (lane == 0) { a.sf[s] = r; a.smode[s] = 0; }
     } else {
-        // mode 1: orthonormal basis of null(A_s) from pivoted Gram-Schmidt on
-        // the columns of P = I - Q^T Q (column-major n x n in scratch)
-        double *P = a.P + a.poff[s];
-        for (int col = 0; col < n; ++col) {
-            for (int c = lane; c < n; c += 32) {
-                double acc = (c == col) ? 1.0 : 0.0;
-                for (int k = 0; k < r; ++k) acc -= Aw[(long long)k * n + col] * Aw[(long long)k * n + c];
-                P[(long long)col * n + c] = acc;
-            }
-        }
-        __syncwarp();
+        // orthonormal basis of null(A_s): pivot on the column c with the largest
+        // remaining norm d_c = 1 - sum_k Q_kc^2 - sum_t N_tc^2, take
+        // e_c - Q^T Q e_c - N^T N e_c, orthogonalise once more, normalise
         const int nf = n - r;
-        for (int t = 0; t < nf; ++t) {
-            // pivot: column of largest remaining norm
-            double best = -1.0;
-            int bc = 0;
-            for (int col = 0; col < n; ++col) {
-                double nn = 0.0;
-                for (int c = lane; c < n; c += 32) { double x = P[(long long)col * n + c]; nn += x * x; }
-                nn = warp_sum(nn);
-                if (nn > best) { best = nn; bc = col; }
+        double d[RMAX];
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t) {
+            const int c = lane + 32 * t;
+            double acc = 1.0;
+            if (t < T && c < n) {
+                for (int k = 0; k < r; ++k) { const double q = Q[(long long)k * n + c]; acc -= q * q; }
+            } else {
+                acc = -1.0;
+            }
+            d[t] = acc;
+        }
+        for (int st = 0; st < nf; ++st) {
+            double best = -2.0;
+            int bc = 0x7fffffff;
+#pragma unroll
+            for (int t = 0; t < RMAX; ++t) {
+                const int c = lane + 32 * t;
+                if (t < T && c < n && d[t] > best) { best = d[t]; bc = c; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+                if (ob > best || (ob == best && oc < bc)) { best = ob; bc = oc; }
             }
             double v[RMAX];
 #pragma unroll
-            for (int q = 0; q < RMAX; ++q) {
-                int c = lane + 32 * q;
-                v[q] = (q < T && c < n) ? P[(long long)bc * n + c] : 0.0;
-            }
-            // re-orthogonalise against the null vectors found so far and Q
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int k = 0; k < t; ++k) {
-                    const double *q = F + (long long)k * n;
-                    double d = 0.0;
-#pragma unroll
-                    for (int qq = 0; qq < RMAX; ++qq) { int c = lane + 32 * qq; if (qq < T && c < n) d += q[c] * v[qq]; }
-                    d = warp_sum(d);
-#pragma unroll
-                    for (int qq = 0; qq < RMAX; ++qq) { int c = lane + 32 * qq; if (qq < T && c < n) v[qq] -= d * q[c]; }
+            for (int t = 0; t < RMAX; ++t) {
+                const int c = lane + 32 * t;
+                double acc = (c == bc) ? 1.0 : 0.0;
+                if (t < T && c < n) {
+                    for (int k = 0; k < r; ++k) acc -= Q[(long long)k * n + bc] * Q[(long long)k * n + c];
+                    for (int k = 0; k < st; ++k) acc -= N[(long long)k * n + bc] * N[(long long)k * n + c];
+                } else {
+                    acc = 0.0;
                 }
+                v[t] = acc;
+            }
+            // second pass against Q and the null rows found so far
+            if (r > 0) {
+                project_coeffs(Q, n, r, v, T, lane, red, coef);
                 for (int k = 0; k < r; ++k) {
-                    const double *q = Aw + (long long)k * n;
-                    double d = 0.0;
+                    const double ck = coef[k];
 #pragma unroll
-                    for (int qq = 0; qq < RMAX; ++qq) { int c = lane + 32 * qq; if (qq < T && c < n) d += q[c] * v[qq]; }
-                    d = warp_sum(d);
-#pragma unroll
-                    for (int qq = 0; qq < RMAX; ++qq) { int c = lane + 32 * qq; if (qq < T && c < n) v[qq] -= d * q[c]; }
+                    for (int t = 0; t < RMAX; ++t) {
+                        const int c = lane + 32 * t;
+                        if (t < T && c < n) v[t] -= ck * Q[(long long)k * n + c];
+                    }
                 }
+                __syncwarp();
             }
-            double nn = 0.0;
+            if (st > 0) {
+                project_coeffs(N, n, st, v, T, lane, red, coef);
+                for (int k = 0; k < st; ++k) {
+                    const double ck = coef[k];
 #pragma unroll
-            for (int qq = 0; qq < RMAX; ++qq) nn += v[qq] * v[qq];
-            nn = sqrt(warp_sum(nn));
-            double inv = nn > 0.0 ? 1.0 / nn : 0.0;
-#pragma unroll
-            for (int qq = 0; qq < RMAX; ++qq) {
-                int c = lane + 32 * qq;
-                if (qq < T && c < n) { v[qq] *= inv; F[(long long)t * n + c] = v[qq]; }
+                    for (int t = 0; t < RMAX; ++t) {
+                        const int c = lane + 32 * t;
+                        if (t < T && c < n) v[t] -= ck * N[(long long)k * n + c];
+                    }
+                }
+                __syncwarp();
             }
-            __syncwarp();
-            // remove the new direction from every column of P
-            for (int col = 0; col < n; ++col) {
-                double d = 0.0;
+            const double nn = warp_norm(v);
+            const double inv = nn > 0.0 ? 1.0 / nn : 0.0;
 #pragma unroll
-                for (int qq = 0; qq < RMAX; ++qq) { int c = lane + 32 * qq; if (qq < T && c < n) d += v[qq] * P[(long long)col * n + c]; }
-                d = warp_sum(d);
-#pragma unroll
-                for (int qq = 0; qq < RMAX; ++qq) { int c = lane + 32 * qq; if (qq < T && c < n) P[(long long)col * n + c] -= d * v[qq]; }
+            for (int t = 0; t < RMAX; ++t) {
+                const int c = lane + 32 * t;
+                if (t < T && c < n) {
+                    const double x = v[t] * inv;
+                    N[(long long)st * n + c] = x;
+                    d[t] -= x * x;
+                }
             }
             __syncwarp();
         }
+        for (int k = 0; k < nf; ++k)
+            for (int c = lane; c < n; c += 32) F[(long long)k * n + c] = N[(long long)k * n + c];
         if (lane == 0) { a.sf[s] = nf; a.smode[s] = 1; }
     }
     if (lane == 0) a.status[s] = bad;
 }
 
+// Factors written at capacity offsets (n x f, column stride n) are packed into
+// the iteration layout: column stride npad = n rounded up to 4 with zero
+// padding, consecutive subsystems, FP64 and FP32 copies.
+__global__ void k_pack_factors(int S, const int4 *sub, const int4 *sub2, const long long *cap_off,
+                               const double *src, double *dst64, float *dst32) {
+    const int s = blockIdx.x;
+    if (s >= S) return;
+    const int4 h = sub[s], q = sub2[s];
+    const int n = h.y, f = h.z, npad = q.y;
+    const double *a = src + cap_off[s];
+    for (int i = threadIdx.x; i < f * npad; i += blockDim.x) {
+        const int c = i / npad, r = i - c * npad;
+        const double v = r < n ? a[(long long)c * n + r] : 0.0;
+        dst64[q.x + i] = v;
+        dst32[q.x + i] = (float)v;
+    }
+}
+
 // ============================================================ iteration
-// One warp task: up to 32/W subsystems, W lanes each, R rows per lane.
-// sv: per-warp shared scratch of 2 * vstride T values.
-template <typename T, bool CHECK, bool SMEM>
-__device__ __forceinline__ void run_task(const IterArgs<T> &a, int task, int lane,
-                                         const T *__restrict__ u_in, T *__restrict__ u_out,
-                                         T *sv, int vstride, double acc[6]) {
-    const int4 tk = ld<SMEM>(a.tasks + task);
-    const int W = tk.z, R = tk.w;
-    const int grp = lane / W, gl = lane - grp * W;
-    const bool act = grp < tk.y;
-    const int s = tk.x + (act ? grp : 0);
-    const int n = act ? ld<SMEM>(a.sn + s) : 0;
-    const int f = act ? ld<SMEM>(a.sf + s) : 0;
-    const int mode = act ? ld<SMEM>(a.smode + s) : 0;
-    const int so = act ? ld<SMEM>(a.soff + s) : 0;
-    const long long fo = act ? ld<SMEM>(a.sfoff + s) : 0;
-    T *vb = sv + grp * W * R;
-    T *tb = sv + vstride + grp * W * R;
-    T v[RMAX], xg[RMAX];
-    // global update of each row's global (Eq. closed_1), then v = x_g + mu / rho
-#pragma unroll
-    for (int j = 0; j < RMAX; ++j) {
-        const int r = gl + W * j;
-        if (j < R && r < n) {
-            const int k = so + r;
-            const int2 sg = ld<SMEM>(a.seg + k);
-            T sigma = 0;
-            for (int q = 0; q < sg.y; ++q) sigma += u_in[sg.x + q];
-            const int g = ld<SMEM>(a.gk + k);
-            T xh = (sigma - ld<SMEM>(a.ct + g)) / (a.rho * (T)sg.y);
-            const T lo = ld<SMEM>(a.lbt + g), hi = ld<SMEM>(a.ubt + g);
-            if (xh < lo) xh = lo;
-            if (xh > hi) xh = hi;
-            xg[j] = xh;
-            v[j] = xh + a.mu[k] * a.inv_rho;
-            vb[r] = v[j];
-        }
+// A tile is a run of consecutive subsystems [s0, s1) (device order); one CTA
+// processes a tile in three phases separated by barriers:
+//   0. per slot k: global update x = clip((sum of u over the copies of its
+//      global - c~) / (rho N), lb~, ub~) (Eq. closed_1), v = x + mu / rho;
+//   1. per (subsystem, factor column c): t_c = <F_c, v> over the zero-padded
+//      column with 16-byte vector loads;
+//   2. per slot: y = (F t)_r, x_s = (v - y or y) + bbar~ (Eq. closed_2),
+//      mu += rho (x - x_s) (Eq. ADMM-3), u = rho x_s - mu, and on tested
+//      iterations the Sec. III-C sums in FP64.
+// Per-subsystem records: sub = (first slot, n, f, mode), sub2 = (factor
+// offset, npad, padded-v prefix, f prefix); entry S is a sentinel.
+
+template <typename T>
+__device__ __forceinline__ T dot_padded(const T *__restrict__ f, const T *__restrict__ v, int npad);
+
+template <>
+__device__ __forceinline__ float dot_padded<float>(const float *__restrict__ f, const float *__restrict__ v,
+                                                   int npad) {
+    float acc = 0.0f;
+    for (int r = 0; r < npad; r += 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(f + r);
+        const float4 b = *reinterpret_cast<const float4 *>(v + r);
+        acc = fmaf(a.x, b.x, acc);
+        acc = fmaf(a.y, b.y, acc);
+        acc = fmaf(a.z, b.z, acc);
+        acc = fmaf(a.w, b.w, acc);
     }
-    __syncwarp();
-    // t = F^T v  (column c per lane)
-#pragma unroll
-    for (int j = 0; j < RMAX; ++j) {
-        const int c = gl + W * j;
-        if (j < R && c < f) {
-            const T *Fc = a.F + fo + (long long)c * n;
-            T t = 0;
-            for (int r = 0; r < n; ++r) t += ld<SMEM>(Fc + r) * vb[r];
-            tb[c] = t;
-        }
+    return acc;
+}
+
+template <>
+__device__ __forceinline__ double dot_padded<double>(const double *__restrict__ f,
+                                                     const double *__restrict__ v, int npad) {
+    double acc = 0.0;
+    for (int r = 0; r < npad; r += 2) {
+        const double2 a = *reinterpret_cast<const double2 *>(f + r);
+        const double2 b = *reinterpret_cast<const double2 *>(v + r);
+        acc = fma(a.x, b.x, acc);
+        acc = fma(a.y, b.y, acc);
     }
-    __syncwarp();
-    // y = F t ;  x_s = M v + bbar ;  lambda += rho (x_g - x_s) ; u = rho x_s - lambda
-#pragma unroll
-    for (int j = 0; j < RMAX; ++j) {
-        const int r = gl + W * j;
-        if (j < R && r < n) {
-            const int k = so + r;
-            T y = 0;
-            const T *Fr = a.F + fo + r;
-            for (int c = 0; c < f; ++c) y += ld<SMEM>(Fr + (long long)c * n) * tb[c];
-            const T xm = (mode ? y : v[j] - y) + ld<SMEM>(a.bt + k);
-            const T res = xg[j] - xm;
-            const T mu_old = a.mu[k];
-            const T mu_new = mu_old + a.rho * res;
-            const T d_old = a.ds[k];
-            a.mu[k] = mu_new;
-            a.ds[k] = xm;
-            const int pos = ld<SMEM>(a.pk + k);
-            u_out[pos] = a.rho * xm - mu_new;
-            if constexpr (CHECK) {
-                const int g = ld<SMEM>(a.gk + k);
-                const double xr = a.xr[g];
-                const double xgd = xr + (double)xg[j];
-                const double xsd = xr + (double)xm;
-                const double dd = (double)xm - (double)d_old;
-                acc[0] += (double)res * (double)res;
-                acc[1] += dd * dd;
-                acc[2] += xgd * xgd;
-                acc[3] += xsd * xsd;
-                const double lamd = a.lamr[k] + (double)mu_new;
-                acc[4] += lamd * lamd;
-                const int2 sg = ld<SMEM>(a.seg + k);
-                if (pos == sg.x) acc[5] += a.c64[g] * xgd;
-            }
-        }
-    }
-    __syncwarp();
+    return acc;
 }
 
 template <typename T, bool CHECK>
-__global__ void __launch_bounds__(256) k_iterate(IterArgs<T> a, const T *__restrict__ u_in,
-                                                 T *__restrict__ u_out, int vstride,
-                                                 double *partials, const DevStatus *st) {
+__device__ __forceinline__ void tile_iteration(const IterArgs<T> &a, int s0, int s1,
+                                               const T *__restrict__ u_in, T *__restrict__ u_out,
+                                               T *xb, T *vb, T *tb, const T *recip, double acc[6]) {
+    const int4 h0 = a.sub[s0], h1 = a.sub[s1];
+    const int4 q0 = a.sub2[s0];
+    const int k0 = h0.x, k1 = h1.x;
+    const int v0 = q0.z, j0 = q0.w, j1 = a.sub2[s1].w;
+    // phase 0
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
+        const int mt = a.meta[k];
+        const int s = mt >> 8, r = mt & 255;
+        const int sp = a.segp[k];
+        const int us = sp >> 8, cnt = sp & 255;
+        T sigma = 0;
+        for (int q = 0; q < cnt; ++q) sigma += u_in[us + q];
+        const int g = a.gk[k];
+        T x = (sigma - a.ct[g]) * recip[cnt];
+        const T lo = a.lbt[g], hi = a.ubt[g];
+        if (x < lo) x = lo;
+        if (x > hi) x = hi;
+        xb[k - k0] = x;
+        const int4 q2 = a.sub2[s];
+        T *vs = vb + (q2.z - v0);
+        vs[r] = x + a.mu[k] * a.inv_rho;
+        if (r == 0)
+            for (int p = a.sub[s].y; p < q2.y; ++p) vs[p] = (T)0;
+    }
+    __syncthreads();
+    // phase 1
+    for (int j = j0 + (int)threadIdx.x; j < j1; j += blockDim.x) {
+        const int it = a.items[j];
+        const int s = it >> 8, c = it & 255;
+        const int4 q2 = a.sub2[s];
+        tb[q2.w - j0 + c] = dot_padded<T>(a.F + q2.x + (long long)c * q2.y, vb + (q2.z - v0), q2.y);
+    }
+    __syncthreads();
+    // phase 2
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
+        const int mt = a.meta[k];
+        const int s = mt >> 8, r = mt & 255;
+        const int4 h = a.sub[s];
+        const int4 q2 = a.sub2[s];
+        const T *Fr = a.F + q2.x + r;
+        const T *tt = tb + (q2.w - j0);
+        T y = 0;
+        for (int c = 0; c < h.z; ++c) y += Fr[(long long)c * q2.y] * tt[c];
+        const T v = vb[q2.z - v0 + r];
+        const T x = xb[k - k0];
+        const T xm = (h.w ? y : v - y) + a.bt[k];
+        const T res = x - xm;
+        const T mu_new = a.mu[k] + a.rho * res;
+        const T d_old = a.ds[k];
+        a.mu[k] = mu_new;
+        a.ds[k] = xm;
+        const int pos = a.pk[k];
+        u_out[pos] = a.rho * xm - mu_new;
+        if constexpr (CHECK) {
+            const int g = a.gk[k];
+            const double xr = a.xr[g];
+            const double xgd = xr + (double)x;
+            const double xsd = xr + (double)xm;
+            const double dd = (double)xm - (double)d_old;
+            acc[0] += (double)res * (double)res;
+            acc[1] += dd * dd;
+            acc[2] += xgd * xgd;
+            acc[3] += xsd * xsd;
+            const double lamd = a.lamr[k] + (double)mu_new;
+            acc[4] += lamd * lamd;
+            if (pos == (a.segp[k] >> 8)) acc[5] += a.c64[g] * xgd;
+        }
+    }
+}
+
+// Block sum of the six FP64 accumulators (fixed order); result in thread 0.
+__device__ __forceinline__ void block_sum6(double acc[6], double (*red)[6]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) red[w][q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) t[q] += red[i][q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[q] = t[q];
+    }
+}
+
+// Whole-grid engine: one CTA per tile, one launch per iteration.
+template <typename T, bool CHECK>
+__global__ void __launch_bounds__(256) k_tile_iter(IterArgs<T> a, const T *__restrict__ u_in,
+                                                   T *__restrict__ u_out, double *partials,
+                                                   const DevStatus *st, int xcap, int vcap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (st->done) return;
-    T *sv = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 2 * vstride;
-    const int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    T *vb = reinterpret_cast<T *>(smem_raw);
+    T *xb = vb + vcap;
+    T *tb = xb + xcap;
+    const int s0 = a.tile_s0[blockIdx.x], s1 = a.tile_s0[blockIdx.x + 1];
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    if (task < a.n_tasks) run_task<T, CHECK, false>(a, task, lane, u_in, u_out, sv, vstride, acc);
+    tile_iteration<T, CHECK>(a, s0, s1, u_in, u_out, xb, vb, tb, a.recip, acc);
     if constexpr (CHECK) {
         __shared__ double red[8][6];
+        block_sum6(acc, red);
+        if (threadIdx.x == 0)
 #pragma unroll
-        for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
-        const int w = threadIdx.x >> 5;
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < 6; ++q) red[w][q] = acc[q];
-        __syncthreads();
-        if (threadIdx.x < 6) {
-            double t = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][threadIdx.x];
-            partials[blockIdx.x * 6 + threadIdx.x] = t;
-        }
+            for (int q = 0; q < 6; ++q) partials[blockIdx.x * 6 + q] = acc[q];
     }
 }
 
@@ -379,8 +488,7 @@ __global__ void k_add_iters(DevStatus *st, long long n) {
 
 // ============================================================ CTA engine
 // Whole instance in shared memory; one CTA runs up to n_iters iterations,
-// testing every check_every.  Layout offsets in bytes inside dynamic smem.
-
+// testing every check_every.
 template <typename T>
 __device__ void copy_in(void *dst, const void *src, size_t bytes) {
     const int4 *s4 = reinterpret_cast<const int4 *>(src);
@@ -402,87 +510,74 @@ __global__ void __launch_bounds__(1024, 1) k_cta_engine(IterArgs<T> g, CtaLayout
         if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
         return;
     }
-    // stage the instance into shared memory (16-byte aligned regions)
-    copy_in<T>(sm + lay.off_F, g.F, lay.nF * sizeof(T));
-    copy_in<T>(sm + lay.off_bt, g.bt, (size_t)lay.L * sizeof(T));
-    copy_in<T>(sm + lay.off_mu, g.mu, (size_t)lay.L * sizeof(T));
-    copy_in<T>(sm + lay.off_ds, g.ds, (size_t)lay.L * sizeof(T));
-    copy_in<T>(sm + lay.off_u0, u_glob, (size_t)lay.L * sizeof(T));
-    copy_in<T>(sm + lay.off_ct, g.ct, (size_t)lay.G * sizeof(T));
-    copy_in<T>(sm + lay.off_lbt, g.lbt, (size_t)lay.G * sizeof(T));
-    copy_in<T>(sm + lay.off_ubt, g.ubt, (size_t)lay.G * sizeof(T));
-    copy_in<T>(sm + lay.off_seg, g.seg, (size_t)lay.L * sizeof(int2));
-    copy_in<T>(sm + lay.off_gk, g.gk, (size_t)lay.L * sizeof(int));
-    copy_in<T>(sm + lay.off_pk, g.pk, (size_t)lay.L * sizeof(int));
-    copy_in<T>(sm + lay.off_soff, g.soff, (size_t)lay.S * sizeof(int));
-    copy_in<T>(sm + lay.off_sn, g.sn, (size_t)lay.S * sizeof(int));
-    copy_in<T>(sm + lay.off_sf, g.sf, (size_t)lay.S * sizeof(int));
-    copy_in<T>(sm + lay.off_smode, g.smode, (size_t)lay.S * sizeof(int));
-    copy_in<T>(sm + lay.off_sfoff, g.sfoff, (size_t)lay.S * sizeof(long long));
-    copy_in<T>(sm + lay.off_tasks, g.tasks, (size_t)lay.n_tasks * sizeof(int4));
+    const int S = lay.S, L = lay.L, G = lay.G;
+    copy_in<T>(sm + lay.off_F, g.F, (size_t)lay.nF * sizeof(T));
+    copy_in<T>(sm + lay.off_sub, g.sub, (size_t)(S + 1) * sizeof(int4));
+    copy_in<T>(sm + lay.off_sub2, g.sub2, (size_t)(S + 1) * sizeof(int4));
+    copy_in<T>(sm + lay.off_items, g.items, (size_t)lay.nitems * sizeof(int));
+    copy_in<T>(sm + lay.off_meta, g.meta, (size_t)L * sizeof(int));
+    copy_in<T>(sm + lay.off_segp, g.segp, (size_t)L * sizeof(int));
+    copy_in<T>(sm + lay.off_gk, g.gk, (size_t)L * sizeof(int));
+    copy_in<T>(sm + lay.off_pk, g.pk, (size_t)L * sizeof(int));
+    copy_in<T>(sm + lay.off_bt, g.bt, (size_t)L * sizeof(T));
+    copy_in<T>(sm + lay.off_mu, g.mu, (size_t)L * sizeof(T));
+    copy_in<T>(sm + lay.off_ds, g.ds, (size_t)L * sizeof(T));
+    copy_in<T>(sm + lay.off_u0, u_glob, (size_t)L * sizeof(T));
+    copy_in<T>(sm + lay.off_ct, g.ct, (size_t)G * sizeof(T));
+    copy_in<T>(sm + lay.off_lbt, g.lbt, (size_t)G * sizeof(T));
+    copy_in<T>(sm + lay.off_ubt, g.ubt, (size_t)G * sizeof(T));
+    copy_in<T>(sm + lay.off_recip, g.recip, 256 * sizeof(T));
     __syncthreads();
     IterArgs<T> a = g;
     a.F = reinterpret_cast<const T *>(sm + lay.off_F);
+    a.sub = reinterpret_cast<const int4 *>(sm + lay.off_sub);
+    a.sub2 = reinterpret_cast<const int4 *>(sm + lay.off_sub2);
+    a.items = reinterpret_cast<const int *>(sm + lay.off_items);
+    a.meta = reinterpret_cast<const int *>(sm + lay.off_meta);
+    a.segp = reinterpret_cast<const int *>(sm + lay.off_segp);
+    a.gk = reinterpret_cast<const int *>(sm + lay.off_gk);
+    a.pk = reinterpret_cast<const int *>(sm + lay.off_pk);
     a.bt = reinterpret_cast<const T *>(sm + lay.off_bt);
     a.mu = reinterpret_cast<T *>(sm + lay.off_mu);
     a.ds = reinterpret_cast<T *>(sm + lay.off_ds);
     a.ct = reinterpret_cast<const T *>(sm + lay.off_ct);
     a.lbt = reinterpret_cast<const T *>(sm + lay.off_lbt);
     a.ubt = reinterpret_cast<const T *>(sm + lay.off_ubt);
-    a.seg = reinterpret_cast<const int2 *>(sm + lay.off_seg);
-    a.gk = reinterpret_cast<const int *>(sm + lay.off_gk);
-    a.pk = reinterpret_cast<const int *>(sm + lay.off_pk);
-    a.soff = reinterpret_cast<const int *>(sm + lay.off_soff);
-    a.sn = reinterpret_cast<const int *>(sm + lay.off_sn);
-    a.sf = reinterpret_cast<const int *>(sm + lay.off_sf);
-    a.smode = reinterpret_cast<const int *>(sm + lay.off_smode);
-    a.sfoff = reinterpret_cast<const long long *>(sm + lay.off_sfoff);
-    a.tasks = reinterpret_cast<const int4 *>(sm + lay.off_tasks);
+    const T *recip = reinterpret_cast<const T *>(sm + lay.off_recip);
     T *ub[2] = {reinterpret_cast<T *>(sm + lay.off_u0), reinterpret_cast<T *>(sm + lay.off_u1)};
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    T *sv = reinterpret_cast<T *>(sm + lay.off_sv) + warp * 2 * lay.vstride;
+    T *xb = reinterpret_cast<T *>(sm + lay.off_xb);
+    T *vb = reinterpret_cast<T *>(sm + lay.off_vb);
+    T *tb = reinterpret_cast<T *>(sm + lay.off_tb);
     __shared__ double red[32][6];
     __shared__ int stop;
     if (threadIdx.x == 0) stop = 0;
-    int par = 0, it = 0;
+    int par = 0;
     __syncthreads();
-    for (it = 0; it < n_iters; ++it) {
+    for (int it = 0; it < n_iters; ++it) {
         const bool chk = ((it + 1) % check_every) == 0 || it == n_iters - 1;
         double acc[6] = {0, 0, 0, 0, 0, 0};
-        if (chk) {
-            for (int t = warp; t < lay.n_tasks; t += nw)
-                run_task<T, true, true>(a, t, lane, ub[par], ub[par ^ 1], sv, lay.vstride, acc);
-        } else {
-            for (int t = warp; t < lay.n_tasks; t += nw)
-                run_task<T, false, true>(a, t, lane, ub[par], ub[par ^ 1], sv, lay.vstride, acc);
-        }
+        if (chk) tile_iteration<T, true>(a, 0, S, ub[par], ub[par ^ 1], xb, vb, tb, recip, acc);
+        else tile_iteration<T, false>(a, 0, S, ub[par], ub[par ^ 1], xb, vb, tb, recip, acc);
         par ^= 1;
+        __syncthreads();
         if (chk) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
-            if (lane == 0)
-#pragma unroll
-                for (int q = 0; q < 6; ++q) red[warp][q] = acc[q];
-            __syncthreads();
+            block_sum6(acc, red);
             if (threadIdx.x == 0) {
-                double s[6] = {0, 0, 0, 0, 0, 0};
-                for (int w = 0; w < nw; ++w)
-                    for (int q = 0; q < 6; ++q) s[q] += red[w][q];
                 const int since = ((it + 1) % check_every) == 0 ? check_every : ((it + 1) % check_every);
-                apply_test(st, s, rho_d, since);
+                apply_test(st, acc, rho_d, since);
                 stop = st->done;
             }
+            __syncthreads();
+            if (stop) break;
         }
-        __syncthreads();
-        if (stop) { ++it; break; }
     }
-    // write back the iterate; u of the last iteration goes to u_glob and the
-    // u that produced its global update to u_glob + L (parity kept by caller)
-    for (int i = threadIdx.x; i < lay.L; i += blockDim.x) {
+    // write back the iterate; u of the last iteration to u_glob, the u that
+    // produced its global update to u_glob + L
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
         g.mu[i] = a.mu[i];
         g.ds[i] = a.ds[i];
         u_glob[i] = ub[par][i];
-        u_glob[lay.L + i] = ub[par ^ 1][i];
+        u_glob[L + i] = ub[par ^ 1][i];
     }
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }
@@ -601,10 +696,8 @@ __global__ void k_recenter_globals(int G, const int2 *gseg, const int *uslot, co
 
 // per subsystem (one warp): bbar~ = M (x_ref[g] + lambda_ref / rho) + bbar - x_ref[g]
 template <typename T>
-__global__ void __launch_bounds__(128) k_recenter_bbar(int S, const int *soff, const int *sn,
-                                                       const int *sf, const int *smode,
-                                                       const long long *sfoff, const double *F,
-                                                       const int *gk, const double *xr,
+__global__ void __launch_bounds__(128) k_recenter_bbar(int S, const int4 *sub, const int4 *sub2,
+                                                       const double *F, const int *gk, const double *xr,
                                                        const double *lamr, const double *bbar,
                                                        double rho, T *bt, const DevStatus *st) {
     __shared__ double buf[4][2][OPF_MAX_NS];
@@ -612,20 +705,21 @@ __global__ void __launch_bounds__(128) k_recenter_bbar(int S, const int *soff, c
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * 4 + w;
     if (s >= S) return;
-    const int n = sn[s], f = sf[s], mode = smode[s], so = soff[s];
-    const double *Fs = F + sfoff[s];
+    const int4 h = sub[s], q = sub2[s];
+    const int so = h.x, n = h.y, f = h.z, mode = h.w, npad = q.y;
+    const double *Fs = F + q.x;
     double *v = buf[w][0], *t = buf[w][1];
     for (int r = lane; r < n; r += 32) v[r] = xr[gk[so + r]] + lamr[so + r] / rho;
     __syncwarp();
     for (int c = lane; c < f; c += 32) {
         double acc = 0.0;
-        for (int r = 0; r < n; ++r) acc += Fs[(long long)c * n + r] * v[r];
+        for (int r = 0; r < n; ++r) acc += Fs[(long long)c * npad + r] * v[r];
         t[c] = acc;
     }
     __syncwarp();
     for (int r = lane; r < n; r += 32) {
         double y = 0.0;
-        for (int c = 0; c < f; ++c) y += Fs[(long long)c * n + r] * t[c];
+        for (int c = 0; c < f; ++c) y += Fs[(long long)c * npad + r] * t[c];
         const double mv = mode ? y : v[r] - y;
         bt[so + r] = (T)(mv + bbar[so + r] - xr[gk[so + r]]);
     }
@@ -639,18 +733,28 @@ static inline int nblocks(long long n, int t) {
     return (int)b;
 }
 
-void launch_precompute(const PreArgs &a, cudaStream_t st) {
-    const int warps = 4;
-    k_precompute<<<(a.S + warps - 1) / warps, 32 * warps, 0, st>>>(a);
+int launch_precompute(const PreArgs &a, cudaStream_t st) {
+    const int big = a.sh_m > a.sh_n ? a.sh_m : a.sh_n;
+    const size_t shm = sizeof(double) * ((size_t)a.sh_m * a.sh_n + (size_t)a.sh_n * a.sh_n +
+                                         33 * (size_t)big + (size_t)a.sh_m + 2);
+    if (cudaFuncSetAttribute(k_precompute, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess)
+        return -1;
+    k_precompute<<<a.S, 32, shm, st>>>(a);
+    return 0;
+}
+
+void launch_pack_factors(int S, const int4 *sub, const int4 *sub2, const long long *cap_off,
+                         const double *src, double *dst64, float *dst32, cudaStream_t st) {
+    k_pack_factors<<<S, 128, 0, st>>>(S, sub, sub2, cap_off, src, dst64, dst32);
 }
 
 template <typename T>
-void launch_iterate(const IterArgs<T> &a, const T *u_in, T *u_out, int vstride, double *partials,
-                    const DevStatus *st, bool check, cudaStream_t s) {
-    const int blocks = (a.n_tasks + 7) / 8;
-    const size_t shm = 8 * 2 * (size_t)vstride * sizeof(T);
-    if (check) k_iterate<T, true><<<blocks, 256, shm, s>>>(a, u_in, u_out, vstride, partials, st);
-    else k_iterate<T, false><<<blocks, 256, shm, s>>>(a, u_in, u_out, vstride, partials, st);
+void launch_iterate(const IterArgs<T> &a, const T *u_in, T *u_out, double *partials,
+                    const DevStatus *st, bool check, int n_tiles, int block, int xcap, int vcap,
+                    int tcap, cudaStream_t s) {
+    const size_t shm = ((size_t)xcap + vcap + tcap) * sizeof(T);
+    if (check) k_tile_iter<T, true><<<n_tiles, block, shm, s>>>(a, u_in, u_out, partials, st, xcap, vcap);
+    else k_tile_iter<T, false><<<n_tiles, block, shm, s>>>(a, u_in, u_out, partials, st, xcap, vcap);
 }
 
 void launch_check(const double *partials, int nblk, DevStatus *st, double rho, int add,
@@ -720,19 +824,17 @@ template <typename T>
 void launch_recenter(int L, int G, int S, const int *gk, const double *xr_old, const double *xr_new,
                      T *ds, T *mu, double *lamr, const int2 *gseg, const int *uslot,
                      const double *c64, const double *lb, const double *ub, T *ct, T *lbt, T *ubt,
-                     const int *soff, const int *sn, const int *sf, const int *smode,
-                     const long long *sfoff, const double *F64, const double *bbar, double rho,
-                     T *bt, const DevStatus *st, cudaStream_t s) {
+                     const int4 *sub, const int4 *sub2, const double *F64, const double *bbar,
+                     double rho, T *bt, const DevStatus *st, cudaStream_t s) {
     k_recenter_slots<T><<<nblocks(L, 256), 256, 0, s>>>(L, gk, xr_old, xr_new, ds, mu, lamr, st);
     k_recenter_globals<T><<<nblocks(G, 256), 256, 0, s>>>(G, gseg, uslot, lamr, c64, lb, ub, xr_new,
                                                           ct, lbt, ubt, st);
-    k_recenter_bbar<T><<<(S + 3) / 4, 128, 0, s>>>(S, soff, sn, sf, smode, sfoff, F64, gk, xr_new,
-                                                   lamr, bbar, rho, bt, st);
+    k_recenter_bbar<T><<<(S + 3) / 4, 128, 0, s>>>(S, sub, sub2, F64, gk, xr_new, lamr, bbar, rho, bt, st);
 }
 
 #define OPF_INST(T)                                                                                   \
-    template void launch_iterate<T>(const IterArgs<T> &, const T *, T *, int, double *,               \
-                                    const DevStatus *, bool, cudaStream_t);                           \
+    template void launch_iterate<T>(const IterArgs<T> &, const T *, T *, double *, const DevStatus *, \
+                                    bool, int, int, int, int, int, cudaStream_t);                     \
     template int prepare_cta_engine<T>(unsigned);                                                     \
     template void launch_cta_engine<T>(const IterArgs<T> &, const CtaLayout &, T *, int, int,         \
                                        DevStatus *, double, cudaGraphConditionalHandle, int,          \
@@ -747,10 +849,9 @@ void launch_recenter(int L, int G, int S, const int *gk, const double *xr_old, c
                                     const T *, double *, double *, cudaStream_t);                     \
     template void launch_recenter<T>(int, int, int, const int *, const double *, const double *, T *, \
                                      T *, double *, const int2 *, const int *, const double *,        \
-                                     const double *, const double *, T *, T *, T *, const int *,      \
-                                     const int *, const int *, const int *, const long long *,        \
-                                     const double *, const double *, double, T *, const DevStatus *,  \
-                                     cudaStream_t);
+                                     const double *, const double *, T *, T *, T *, const int4 *,     \
+                                     const int4 *, const double *, const double *, double, T *,       \
+                                     const DevStatus *, cudaStream_t);
 OPF_INST(double)
 OPF_INST(float)
 template void launch_cast<double, float>(long long, const double *, float *, cudaStream_t);

@@ -36,31 +36,20 @@ int build_generic_model(int n, const double *c, const double *lb, const double *
                         const double *A, const double *b, const int *idx,
                         HostModel *out, std::string *err);
 
-// ------------------------------------------------------------ device layout
-// A warp task covers 32 / W subsystems of one size class (W lanes each, R
-// rows per lane, n <= W * R).
-struct Task {
-    int first;   // first subsystem (device order)
-    int count;   // subsystems in this task
-    int W;       // lanes per subsystem: 8, 16 or 32
-    int R;       // rows per lane (1..8, W == 32 when R > 1)
-};
+constexpr int RMAX = 8;   // entries per lane in the precompute (n <= 256)
 
-constexpr int RMAX = 8;
-
-// Arguments of one iteration, in precision T.  All pointers may address
-// global or shared memory (generic addressing).
+// Arguments of one iteration, in precision T.  Pointers may address global or
+// shared memory (generic addressing).
 template <typename T>
 struct IterArgs {
-    // per subsystem (device order)
-    const int *soff;      // first slot
-    const int *sn;        // n_s
-    const int *sf;        // f_s: columns of the stored factor
-    const int *smode;     // 0: M = I - F F^T, 1: M = F F^T
-    const long long *sfoff;   // factor offset (elements)
-    const T *F;           // factors, column-major n x f per subsystem
+    // per subsystem (device order), S + 1 entries (entry S is a sentinel)
+    const int4 *sub;      // (first slot, n, f, mode)  mode 0: M = I - F F^T, 1: M = F F^T
+    const int4 *sub2;     // (factor offset, npad, padded-v prefix, f prefix)
+    const T *F;           // factors: f columns of npad entries (zero-padded) each
+    const int *items;     // per factor column: (subsystem << 8) | column
     // per slot (device order)
-    const int2 *seg;      // (start, count) of the slot's global in u
+    const int *meta;      // (subsystem << 8) | row
+    const int *segp;      // (start of the global's copies in u << 8) | number of copies
     const int *gk;        // global index
     const int *pk;        // position of the slot in u
     const T *bt;          // bbar shifted by the reference point
@@ -73,9 +62,8 @@ struct IterArgs {
     const double *xr;     // x_ref per global
     const double *lamr;   // lambda_ref per slot
     const double *c64;    // original costs
-    // tasks
-    const int4 *tasks;    // (first, count, W, R)
-    int n_tasks;
+    const T *recip;       // recip[N] = 1 / (rho N), N < 256
+    const int *tile_s0;   // first subsystem of each grid tile (n_tiles + 1 entries)
     T rho, inv_rho;
 };
 
@@ -90,9 +78,11 @@ struct DevStatus {
 };
 
 // Per subsystem s (device order): A_s (m x n row-major) at W + aoff[s] and b_s
-// at Bw + boff[s] are work copies, overwritten.  P + poff[s] is n x n scratch.
+// at Bw + boff[s] are work copies, overwritten.  P + poff[s] is the scratch of
+// subsystems too large for shared memory (n*n + 33*(m+n) + 64 doubles).
 struct PreArgs {
     int S;
+    int sh_m, sh_n;     // largest m, n handled in shared memory
     const int *sm, *sn, *soff;
     const long long *aoff, *poff, *foff;
     const int *boff;
@@ -105,10 +95,11 @@ struct PreArgs {
 
 // Byte offsets of the one-CTA engine's shared-memory image.
 struct CtaLayout {
-    int S, L, G, n_tasks, vstride;
+    int S, L, G, nitems;
     long long nF;                 // factor elements
-    unsigned off_F, off_bt, off_mu, off_ds, off_u0, off_u1, off_ct, off_lbt, off_ubt;
-    unsigned off_seg, off_gk, off_pk, off_soff, off_sn, off_sf, off_smode, off_sfoff, off_tasks, off_sv;
+    unsigned off_F, off_sub, off_sub2, off_items, off_meta, off_segp, off_gk, off_pk;
+    unsigned off_bt, off_mu, off_ds, off_u0, off_u1, off_ct, off_lbt, off_ubt, off_recip;
+    unsigned off_xb, off_vb, off_tb;
     unsigned bytes;
 };
 

@@ -27,6 +27,7 @@ OPF_E_CAPACITY = -8
 
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ENGINE_AUTO, ENGINE_GRID, ENGINE_CTA = 0, 1, 2
+SOLVE_HOST_LOOP = 1
 
 _P = C.c_void_p
 
@@ -52,12 +53,13 @@ class Options(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("rho", C.c_double), ("eps_rel", C.c_double), ("eps_abs_pres", C.c_double),
                 ("max_iter", C.c_int32), ("check_every", C.c_int32), ("precision", C.c_int32),
-                ("recenter_every", C.c_int32), ("engine", C.c_int32)]
+                ("recenter_every", C.c_int32), ("engine", C.c_int32), ("flags", C.c_int32)]
 
 
 class Sizes(C.Structure):
     _fields_ = [("n_global", C.c_int64), ("n_sub", C.c_int64), ("n_slots", C.c_int64),
-                ("n_rows", C.c_int64), ("sum_nf", C.c_int64), ("max_ns", C.c_int64)]
+                ("n_rows", C.c_int64), ("sum_nf", C.c_int64), ("max_ns", C.c_int64),
+                ("h2d_bytes", C.c_int64)]
 
 
 _lib = None
@@ -208,9 +210,9 @@ class Solver:
         _check(load().opf_precompute(self._h), "opf_precompute")
 
     def solve(self, rho=100.0, eps_rel=1e-8, eps_abs_pres=1e-4, max_iter=1_000_000, check_every=50,
-              precision=PREC_FP64, recenter_every=0, engine=ENGINE_AUTO):
+              precision=PREC_FP64, recenter_every=0, engine=ENGINE_AUTO, flags=0):
         o = SolveOpts(rho, eps_rel, eps_abs_pres, int(max_iter), int(check_every), int(precision),
-                      int(recenter_every), int(engine))
+                      int(recenter_every), int(engine), int(flags))
         rc = load().opf_solve_ex(self._h, C.byref(o))
         _check(rc, "opf_solve_ex", ok=(OPF_OK, OPF_NOT_CONVERGED))
         return rc == OPF_OK
@@ -258,9 +260,10 @@ class Solver:
         _check(load().opf_set_locals(self._h, _ptr(xs), _ptr(lam), len(xs)), "opf_set_locals")
 
     def timing(self):
-        t = np.zeros(3)
-        _check(load().opf_get_timing(self._h, _ptr(t), 3), "opf_get_timing")
-        return {"precompute_ms": t[0], "iterate_ms": t[1], "polish_ms": t[2]}
+        t = np.zeros(6)
+        _check(load().opf_get_timing(self._h, _ptr(t), 6), "opf_get_timing")
+        return {"precompute_ms": t[0], "iterate_ms": t[1], "polish_ms": t[2],
+                "main_iters": int(t[3]), "polish_iters": int(t[4]), "recenters": int(t[5])}
 
     def close(self):
         if self._h:
