@@ -204,6 +204,40 @@ int opf_get_sizes(opf_handle *h, opf_sizes *out);
  * polish, [5] re-centrings.  n = number of entries wanted (<= 6). */
 int opf_get_timing(opf_handle *h, double *ms, int n);
 
+/* Allocation-free global update, for callers that cannot allocate device
+ * memory: work enqueued while a CUDA stream is being captured (cudaMalloc
+ * cannot be captured), control loops that forbid allocation once running, and
+ * hosts whose device memory comes only from their own allocator.  The paper
+ * has no counterpart: this is the global update of Eq. closed_1 and the
+ * objective c^T x (what opf_get_solution returns) over caller device arrays,
+ * without a handle.
+ *   n          number of globals, 1 <= n <= OPF_STATIC_MAX_GLOBALS
+ *   seg_off    device, n + 1 int32 offsets: the local copies of global i are
+ *              u[seg_off[i] .. seg_off[i+1]) (at least one each)
+ *   u          device, seg_off[n] doubles: rho x_k - lambda_k of every copy,
+ *              grouped by global (summed in that order)
+ *   c, lb, ub  device, n doubles each (bounds may be +-INFINITY)
+ *   rho        > 0
+ *   x          device, n doubles out: clip((sum u - c_i) / (rho N_i), lb_i, ub_i)
+ *   objective  device, 1 double out: c^T x
+ *   stream     cudaStream_t (NULL = legacy default stream); the call only
+ *              enqueues work, synchronise the stream before reading outputs.
+ * Scratch is a fixed device array of OPF_STATIC_MAX_BLOCKS doubles, one per
+ * block of 256 globals, held by every device that loads the library until
+ * the process exits.  The first call on a device (with that device current)
+ * looks up the array's address, which needs no allocation; make that first
+ * call before any stream capture.  Every call on a device shares the array:
+ * calls that may overlap on the GPU (different streams without ordering)
+ * race and must be serialised by the caller.  Each call writes every entry
+ * it reads, so stale contents from an earlier call are never used.
+ * Returns OPF_OK, OPF_E_INVALID (null pointer, n < 1, rho <= 0),
+ * OPF_E_CAPACITY (n above the limit; message in opf_last_error), OPF_E_CUDA. */
+#define OPF_STATIC_MAX_BLOCKS 8192
+#define OPF_STATIC_MAX_GLOBALS (256 * OPF_STATIC_MAX_BLOCKS)
+int opf_global_update_static(int32_t n, const int32_t *seg_off, const double *u, const double *c,
+                             const double *lb, const double *ub, double rho, double *x,
+                             double *objective, void *stream);
+
 void opf_destroy(opf_handle *h);
 const char *opf_strerror(int code);
 /* Message of the last OPF_E_INVALID / OPF_E_CUDA on this thread. */

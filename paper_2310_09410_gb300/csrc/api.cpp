@@ -75,6 +75,8 @@ using namespace opf;
 
 static thread_local std::string g_last_error;
 
+void opf::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 #define CUDA_TRY(call)                                                                   \
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \

@@ -95,9 +95,10 @@ def load(path: str = LIB_PATH):
     lib.opf_strerror.restype = C.c_char_p
     lib.opf_last_error.argtypes = []
     lib.opf_last_error.restype = C.c_char_p
+    lib.opf_global_update_static.argtypes = [C.c_int32, _P, _P, _P, _P, _P, C.c_double, _P, _P, _P]
     for name in ("opf_create", "opf_create_generic", "opf_precompute", "opf_solve", "opf_solve_ex",
                  "opf_step", "opf_reset", "opf_get_solution", "opf_get_residuals", "opf_get_locals",
-                 "opf_set_locals", "opf_get_sizes", "opf_get_timing"):
+                 "opf_set_locals", "opf_get_sizes", "opf_get_timing", "opf_global_update_static"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -120,6 +121,12 @@ def _check(code, where, ok=(OPF_OK,)):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def global_update_static(n, seg_off_ptr, u_ptr, c_ptr, lb_ptr, ub_ptr, rho, x_ptr, obj_ptr, stream=None):
+    """Allocation-free global update on caller device pointers (see include/opf.h)."""
+    _check(load().opf_global_update_static(int(n), seg_off_ptr, u_ptr, c_ptr, lb_ptr, ub_ptr, float(rho),
+                                           x_ptr, obj_ptr, stream), "opf_global_update_static")
 
 
 class Solver:
