@@ -120,8 +120,10 @@ typedef struct opf_solve_opts {
     int32_t check_every;            /* iterations between tests; even, >= 2 */
     int32_t precision;              /* OPF_PREC_* */
     int32_t recenter_every;         /* OPF_PREC_MIXED: iterations between FP64 re-centrings (0 = default) */
-    int32_t engine;                 /* 0 = automatic, 1 = whole-grid kernels, 2 = one-CTA resident */
+    int32_t engine;                 /* 0 = automatic, 1 = whole-grid kernels, 2 = cluster resident,
+                                       3 = warp per subsystem (FP32, at most 192 subsystems) */
     int32_t flags;                  /* OPF_SOLVE_* bits */
+    int32_t cluster;                /* engine 2: CTAs per cluster (1, 2, 4, 8, 16; 0 = automatic) */
 } opf_solve_opts;
 
 /* opf_solve_opts.flags: drive the iteration chunks from the host (one plain

@@ -15,6 +15,7 @@
 //   the loop condition on the device, so a solve is one graph launch and one
 //   final status read.
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -41,11 +42,17 @@ void launch_check(const double *partials, int nblk, DevStatus *st, double rho, i
 void launch_copy_if_running(long long n, const double *src, double *dst, const DevStatus *st,
                             cudaStream_t s);
 void launch_add_iters(DevStatus *st, long long n, cudaStream_t s);
-template <typename T> int prepare_cta_engine(unsigned bytes);
+template <typename T> int prepare_cluster_engine(unsigned bytes, int P);
 template <typename T>
-void launch_cta_engine(const IterArgs<T> &g, const CtaLayout &lay, T *u_glob, int n_iters,
-                       int check_every, DevStatus *st, double rho, cudaGraphConditionalHandle cond,
-                       int use_cond, cudaStream_t s);
+int launch_cluster_engine(const IterArgs<T> &g, const ClusterLayout &lay, const int *pr, T *u_glob,
+                          int n_iters, int check_every, DevStatus *st, double rho,
+                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
+template <typename T> int cluster_occupancy(const ClusterLayout &lay);
+int prepare_warp_engine(unsigned bytes);
+int launch_warp_engine(const IterArgs<float> &g, const WarpLayout &lay, const int *pr, float *u_glob, int n_iters,
+                       int check_every, DevStatus *st, double rho, cudaGraphConditionalHandle cond, int use_cond,
+                       cudaStream_t s);
+int warp_engine_occupancy(const WarpLayout &lay);
 template <typename T>
 void launch_make_u(int L, const int *pk, const T *ds, const T *mu, T rho, T *u, const DevStatus *st,
                    cudaStream_t s);
@@ -91,7 +98,7 @@ struct GraphCache {
     cudaGraph_t graph = nullptr;
     bool host_loop = false;
     double rho = 0;
-    int k = 0, R = 0, kind = -1;
+    int k = 0, R = 0, kind = -1, P = 0;
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -99,6 +106,27 @@ struct GraphCache {
         graph = nullptr;
         kind = -1;
     }
+};
+
+// Cluster plan for one precision: P CTAs, part ranges and part-relative records.
+struct ClusterPlan {
+    int P = 0;
+    bool ok = false;
+    ClusterLayout lay{};
+    int *d_pr = nullptr;
+    int4 *d_srec = nullptr;
+    int *d_items = nullptr, *d_meta = nullptr, *d_udst = nullptr, *d_gsegp = nullptr, *d_cdst = nullptr;
+};
+
+// Warp-engine plan (FP32): subsystem s -> CTA s % P, warp s / P.
+struct WarpPlan {
+    int P = 0;
+    bool built = false, ok = false;
+    WarpLayout lay{};
+    int *d_pr = nullptr, *d_klb = nullptr, *d_fbig = nullptr;
+    int *d_wrseg = nullptr, *d_wdsp = nullptr, *d_wdd = nullptr;
+    int3 *d_wrep = nullptr;
+    float *d_F2 = nullptr;
 };
 
 // Grid tiling for one precision: tile t covers subsystems [s0[t], s0[t+1]).
@@ -153,8 +181,9 @@ struct opf_handle {
     double timing[6] = {0, 0, 0, 0, 0, 0};
     long long h2d_bytes = 0;
     GraphCache g64, gmix;
-    CtaLayout lay32{}, lay64{};
-    bool cta32_ok = false, cta64_ok = false;
+    ClusterPlan c32, c64;
+    WarpPlan w32;
+    std::vector<int> h_tpre, h_vpre, h_foff, h_npad, h_pk, h_gk, h_gstart, h_uslot;
 };
 
 template <typename T>
@@ -184,40 +213,6 @@ static int upload(opf_handle *h, T **p, const std::vector<T> &v) {
 
 static unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
 static int round4(int x) { return (x + 3) & ~3; }
-
-template <typename T>
-static bool make_cta_layout(opf_handle *h, CtaLayout *lay, size_t limit) {
-    CtaLayout &c = *lay;
-    c = CtaLayout{};
-    c.S = h->S; c.L = h->L; c.G = h->G; c.nitems = (int)h->nitems;
-    c.nF = h->nF;
-    size_t off = 0;
-    auto take = [&](unsigned *o, size_t bytes) { *o = (unsigned)off; off = align16((unsigned)(off + bytes)); };
-    long long vtot = 0;
-    for (int s = 0; s < h->S; ++s) vtot += round4(h->h_sn[s]);
-    take(&c.off_F, (size_t)h->nF * sizeof(T));
-    take(&c.off_sub, (size_t)(h->S + 1) * sizeof(int4));
-    take(&c.off_sub2, (size_t)(h->S + 1) * sizeof(int4));
-    take(&c.off_items, (size_t)h->nitems * sizeof(int));
-    take(&c.off_meta, (size_t)h->L * sizeof(int));
-    take(&c.off_segp, (size_t)h->L * sizeof(int));
-    take(&c.off_gk, (size_t)h->L * sizeof(int));
-    take(&c.off_pk, (size_t)h->L * sizeof(int));
-    take(&c.off_bt, (size_t)h->L * sizeof(T));
-    take(&c.off_mu, (size_t)h->L * sizeof(T));
-    take(&c.off_ds, (size_t)h->L * sizeof(T));
-    take(&c.off_u0, (size_t)h->L * sizeof(T));
-    take(&c.off_u1, (size_t)h->L * sizeof(T));
-    take(&c.off_ct, (size_t)h->G * sizeof(T));
-    take(&c.off_lbt, (size_t)h->G * sizeof(T));
-    take(&c.off_ubt, (size_t)h->G * sizeof(T));
-    take(&c.off_recip, 256 * sizeof(T));
-    take(&c.off_xb, (size_t)h->L * sizeof(T));
-    take(&c.off_vb, (size_t)vtot * sizeof(T));
-    take(&c.off_tb, (size_t)h->nitems * sizeof(T));
-    c.bytes = (unsigned)off;
-    return off <= limit;
-}
 
 // Greedy tiling: consecutive subsystems until a tile holds >= target slots.
 static int make_tiling(opf_handle *h, Tiling *t, int target, int block) {
@@ -317,6 +312,10 @@ static int build_layout(opf_handle *h) {
     std::vector<int2> gseg(h->G);
     for (int i = 0; i < h->G; ++i) gseg[i] = make_int2(gstart[i], cnt[i]);
     for (int k = 0; k < h->L; ++k) segp[k] = (gstart[gk[k]] << 8) | cnt[gk[k]];
+    h->h_pk = pk;
+    h->h_gk = gk;
+    h->h_gstart = gstart;
+    h->h_uslot = uslot;
     // start point of Sec. V-A
     std::vector<double> x0(h->G, 0.0);
     for (int i = 0; i < h->G; ++i) {
@@ -360,6 +359,23 @@ static int build_layout(opf_handle *h) {
     TRY(dalloc(h, &h->d_items, std::max<long long>(items_cap, 1)));
     TRY(dalloc(h, &h->t64.d_s0, h->S + 1));
     TRY(dalloc(h, &h->t32.d_s0, h->S + 1));
+    TRY(dalloc(h, &h->w32.d_pr, 8 * 17));
+    TRY(dalloc(h, &h->w32.d_wrseg, h->L));
+    TRY(dalloc(h, &h->w32.d_wdsp, h->L));
+    TRY(dalloc(h, &h->w32.d_wdd, (size_t)h->L * 16));
+    TRY(dalloc(h, &h->w32.d_wrep, h->L));
+    TRY(dalloc(h, &h->w32.d_klb, h->S + 1));
+    TRY(dalloc(h, &h->w32.d_fbig, h->S + 1));
+    TRY(dalloc(h, &h->w32.d_F2, h->nF));
+    for (ClusterPlan *cp : {&h->c32, &h->c64}) {
+        TRY(dalloc(h, &cp->d_pr, 8 * 17));
+        TRY(dalloc(h, &cp->d_srec, h->S + 1));
+        TRY(dalloc(h, &cp->d_items, std::max<long long>(items_cap, 1)));
+        TRY(dalloc(h, &cp->d_meta, h->L));
+        TRY(dalloc(h, &cp->d_udst, h->L));
+        TRY(dalloc(h, &cp->d_gsegp, h->G));
+        TRY(dalloc(h, &cp->d_cdst, h->L));
+    }
     TRY(dalloc(h, &h->d_W, h->nA));
     TRY(dalloc(h, &h->d_Bw, h->nB));
     TRY(dalloc(h, &h->d_P, h->nP));
@@ -476,6 +492,8 @@ extern "C" int opf_precompute(opf_handle *h) {
     CUDA_TRY(cudaMemcpyAsync(h->h_mode.data(), h->d_smode, h->S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     std::vector<int4> sub(h->S + 1), sub2(h->S + 1);
+    h->h_tpre.assign(h->S + 1, 0); h->h_vpre.assign(h->S + 1, 0); h->h_foff.assign(h->S + 1, 0);
+    h->h_npad.assign(h->S, 0);
     std::vector<int> items;
     long long fo = 0, vpre = 0, tpre = 0;
     h->sum_nf = 0;
@@ -483,6 +501,7 @@ extern "C" int opf_precompute(opf_handle *h) {
         const int n = h->h_sn[s], f = h->h_sf[s], npad = round4(n);
         sub[s] = make_int4(h->h_soff[s], n, f, h->h_mode[s]);
         sub2[s] = make_int4((int)fo, npad, (int)vpre, (int)tpre);
+        h->h_foff[s] = (int)fo; h->h_vpre[s] = (int)vpre; h->h_tpre[s] = (int)tpre; h->h_npad[s] = npad;
         for (int c = 0; c < f; ++c) items.push_back((s << 8) | c);
         fo += (long long)f * npad;
         vpre += npad;
@@ -490,6 +509,7 @@ extern "C" int opf_precompute(opf_handle *h) {
         h->sum_nf += (long long)n * f;
     }
     sub[h->S] = make_int4(h->L, 0, 0, 0);
+    h->h_foff[h->S] = (int)fo; h->h_vpre[h->S] = (int)vpre; h->h_tpre[h->S] = (int)tpre;
     sub2[h->S] = make_int4((int)fo, 0, (int)vpre, (int)tpre);
     h->nitems = (long long)items.size();
     CUDA_TRY(cudaMemcpyAsync(h->d_sub, sub.data(), sub.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
@@ -506,11 +526,9 @@ extern "C" int opf_precompute(opf_handle *h) {
     h->nF = std::max<long long>(fo, 4);
     TRY(make_tiling(h, &h->t64, 64, 64));
     TRY(make_tiling(h, &h->t32, 256, 128));
-    int optin = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    const size_t limit = optin > 4096 ? (size_t)optin - 4096 : 0;
-    h->cta32_ok = make_cta_layout<float>(h, &h->lay32, limit);
-    h->cta64_ok = make_cta_layout<double>(h, &h->lay64, limit);
+    h->c32.P = h->c64.P = 0;
+    h->c32.ok = h->c64.ok = false;
+    h->w32.built = h->w32.ok = false;
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->g64.reset();
     h->gmix.reset();
@@ -531,6 +549,7 @@ extern "C" int opf_reset(opf_handle *h) {
 template <typename T>
 static IterArgs<T> common_args(opf_handle *h) {
     IterArgs<T> a;
+    memset(&a, 0, sizeof(a));
     a.sub = h->d_sub; a.sub2 = h->d_sub2; a.items = h->d_items;
     a.meta = h->d_meta; a.segp = h->d_segp; a.gk = h->d_gk; a.pk = h->d_pk;
     a.c64 = h->d_c64;
@@ -559,6 +578,310 @@ IterArgs<float> iter_args<float>(opf_handle *h, double rho) {
     a.xr = h->d_xr; a.lamr = h->d_lamr; a.recip = h->d_recip32;
     a.tile_s0 = h->t32.d_s0;
     a.rho = (float)rho; a.inv_rho = (float)(1.0 / rho);
+    return a;
+}
+
+static unsigned align16u(size_t x) { return (unsigned)((x + 15) & ~(size_t)15); }
+
+// Partition the instance over P CTAs of one cluster (contiguous subsystem
+// ranges balanced by work, contiguous global ranges balanced by copies), build
+// the part-relative records and the shared-memory layout.
+template <typename T>
+static int build_cluster_plan(opf_handle *h, ClusterPlan *cp, int P) {
+    cp->ok = false;
+    cp->P = P;
+    const int S = h->S, G = h->G, L = h->L;
+    std::vector<double> cost(S);
+    double total = 0;
+    for (int s = 0; s < S; ++s) {
+        cost[s] = 6.0 * h->h_sn[s] + (double)h->h_sf[s] * h->h_npad[s] + (double)h->h_sn[s] * h->h_sf[s];
+        total += cost[s];
+    }
+    std::vector<int> sp(P + 1, S);
+    sp[0] = 0;
+    {
+        double acc = 0;
+        int p = 1;
+        for (int s = 0; s < S && p < P; ++s) {
+            acc += cost[s];
+            while (p < P && acc >= total * p / P) sp[p++] = s + 1;
+        }
+        for (int p2 = 1; p2 <= P; ++p2) sp[p2] = std::max(sp[p2], sp[p2 - 1]);
+        sp[P] = S;
+    }
+    std::vector<int> gp(P + 1, G);
+    gp[0] = 0;
+    {
+        double tot = 0;
+        for (int i = 0; i < G; ++i) tot += 1.0 + (h->h_gstart[i + 1] - h->h_gstart[i]);
+        double acc = 0;
+        int p = 1;
+        for (int i = 0; i < G && p < P; ++i) {
+            acc += 1.0 + (h->h_gstart[i + 1] - h->h_gstart[i]);
+            while (p < P && acc >= tot * p / P) gp[p++] = i + 1;
+        }
+        for (int p2 = 1; p2 <= P; ++p2) gp[p2] = std::max(gp[p2], gp[p2 - 1]);
+        gp[P] = G;
+    }
+    std::vector<int> part_of_sub(S), owner_of_g(G);
+    for (int p = 0; p < P; ++p) {
+        for (int s = sp[p]; s < sp[p + 1]; ++s) part_of_sub[s] = p;
+        for (int i = gp[p]; i < gp[p + 1]; ++i) owner_of_g[i] = p;
+    }
+    std::vector<int> pr(8 * (P + 1));
+    auto PR = [&](int field, int p) -> int & { return pr[field * (P + 1) + p]; };
+    for (int p = 0; p <= P; ++p) {
+        const int s = sp[p];
+        PR(0, p) = h->h_soff[s];
+        PR(1, p) = s;
+        PR(2, p) = h->h_tpre[s];
+        PR(3, p) = h->h_foff[s];
+        PR(4, p) = h->h_vpre[s];
+        PR(5, p) = h->h_tpre[s];
+        PR(6, p) = gp[p];
+        PR(7, p) = h->h_gstart[gp[p]];
+    }
+    std::vector<int4> srec(S + 1, make_int4(0, 0, 0, 0));
+    std::vector<int> items, meta(L), udst(L), gsegp(G), cdst(L);
+    for (int s = 0; s < S; ++s) {
+        const int p = part_of_sub[s];
+        srec[s] = make_int4(h->h_foff[s] - PR(3, p), h->h_vpre[s] - PR(4, p), h->h_tpre[s] - PR(5, p),
+                            (h->h_sf[s] << 10) | (h->h_npad[s] << 1) | (h->h_mode[s] & 1));
+        for (int c = 0; c < h->h_sf[s]; ++c) items.push_back(((s - sp[p]) << 8) | c);
+        for (int r = 0; r < h->h_sn[s]; ++r) {
+            const int k = h->h_soff[s] + r;
+            meta[k] = ((s - sp[p]) << 8) | r;
+            const int gi = h->h_gk[k];
+            const int o = owner_of_g[gi];
+            udst[k] = (o << 24) | (h->h_pk[k] - PR(7, o));
+            cdst[h->h_pk[k]] = (p << 24) | (h->h_vpre[s] + r - PR(4, p));
+        }
+    }
+    for (int i = 0; i < G; ++i) {
+        const int o = owner_of_g[i];
+        gsegp[i] = ((h->h_gstart[i] - PR(7, o)) << 8) | (h->h_gstart[i + 1] - h->h_gstart[i]);
+    }
+    // layout: maxima over the parts
+    long long mf = 0, ms = 0, mj = 0, mk = 0, mv = 0, mg = 0, mu = 0;
+    for (int p = 0; p < P; ++p) {
+        mf = std::max<long long>(mf, PR(3, p + 1) - PR(3, p));
+        ms = std::max<long long>(ms, PR(1, p + 1) - PR(1, p));
+        mj = std::max<long long>(mj, PR(2, p + 1) - PR(2, p));
+        mk = std::max<long long>(mk, PR(0, p + 1) - PR(0, p));
+        mv = std::max<long long>(mv, PR(4, p + 1) - PR(4, p));
+        mg = std::max<long long>(mg, PR(6, p + 1) - PR(6, p));
+        mu = std::max<long long>(mu, PR(7, p + 1) - PR(7, p));
+    }
+    ClusterLayout &c = cp->lay;
+    c = ClusterLayout{};
+    c.P = P;
+    c.L = L;
+    size_t off = 0;
+    auto take = [&](unsigned *o, size_t bytes) { *o = (unsigned)off; off = align16u(off + bytes); };
+    take(&c.off_F, (size_t)mf * sizeof(T));
+    take(&c.off_srec, (size_t)ms * sizeof(int4));
+    take(&c.off_items, (size_t)mj * sizeof(int));
+    take(&c.off_meta, (size_t)mk * sizeof(int));
+    take(&c.off_udst, (size_t)mk * sizeof(int));
+    take(&c.off_bt, (size_t)mk * sizeof(T));
+    take(&c.off_ds, (size_t)mk * sizeof(T));
+    take(&c.off_mu, (size_t)mk * sizeof(T));
+    take(&c.off_vbx, (size_t)mv * sizeof(T));
+    take(&c.off_vbw, (size_t)mv * sizeof(T));
+    take(&c.off_tb, (size_t)mj * sizeof(T));
+    take(&c.off_gsegp, (size_t)mg * sizeof(int));
+    take(&c.off_ct, (size_t)mg * sizeof(T));
+    take(&c.off_lbt, (size_t)mg * sizeof(T));
+    take(&c.off_ubt, (size_t)mg * sizeof(T));
+    take(&c.off_uloc, (size_t)mu * sizeof(T));
+    take(&c.off_cdst, (size_t)mu * sizeof(int));
+    take(&c.off_recip, 256 * sizeof(T));
+    take(&c.off_red, 16 * 6 * sizeof(double) + 16);
+    take(&c.off_xrg, (size_t)mg * sizeof(double));
+    take(&c.off_cg, (size_t)mg * sizeof(double));
+    take(&c.off_xrs, (size_t)mk * sizeof(double));
+    take(&c.off_lrs, (size_t)mk * sizeof(double));
+    c.bytes = (unsigned)off;
+    long long work = std::max(mk, std::max(mg, mj));
+    int threads = (int)std::min<long long>(1024, std::max<long long>(64, (work + 31) / 32 * 32));
+    c.threads = threads;
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if ((long long)c.bytes + 4096 > optin) return OPF_OK;              // does not fit: plan not ok
+    if (prepare_cluster_engine<T>(c.bytes, P)) { cudaGetLastError(); return OPF_OK; }
+    if (cluster_occupancy<T>(c) < 1) { cudaGetLastError(); return OPF_OK; }
+    CUDA_TRY(cudaMemcpyAsync(cp->d_pr, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(cp->d_srec, srec.data(), srec.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
+    if (!items.empty())
+        CUDA_TRY(cudaMemcpyAsync(cp->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(cp->d_meta, meta.data(), L * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(cp->d_udst, udst.data(), L * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(cp->d_gsegp, gsegp.data(), G * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(cp->d_cdst, cdst.data(), L * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    cp->ok = true;
+    return OPF_OK;
+}
+
+// Cluster size: the requested one, else the smallest power of two giving at
+// most `target` slots per CTA that fits; the plan is rebuilt when P changes.
+template <typename T>
+static int get_cluster_plan(opf_handle *h, ClusterPlan *cp, int requested, int target) {
+    int want = requested;
+    if (want <= 0) {
+        want = 1;
+        while (want < 16 && (long long)h->L > (long long)want * target) want *= 2;
+    }
+    want = std::min(16, std::max(1, want));
+    if (cp->P == want && cp->ok) return OPF_OK;
+    for (int P = want; P <= 16; P *= 2) {
+        TRY(build_cluster_plan<T>(h, cp, P));
+        if (cp->ok || requested > 0) break;
+    }
+    return OPF_OK;
+}
+
+constexpr int kWarpEngineWarps = 12;
+
+static int build_warp_plan(opf_handle *h) {
+    WarpPlan &wp = h->w32;
+    wp.built = true;
+    wp.ok = false;
+    const int S = h->S, G = h->G, L = h->L;
+    const int P = (S + kWarpEngineWarps - 1) / kWarpEngineWarps;
+    if (P < 1 || P > 16 || h->max_ns > 64) return OPF_OK;
+    for (int s = 0; s < S; ++s)
+        if (h->h_sf[s] > 32) return OPF_OK;
+    wp.P = P;
+    // local slots (subsystem s lives in CTA s % P, warp s / P)
+    std::vector<int> nk(P, 0), klb(S + 1, 0), fb(P, 0), fbig(S + 1, 0);
+    for (int s = 0; s < S; ++s) {
+        const int p = s % P;
+        klb[s] = nk[p];
+        nk[p] += h->h_sn[s];
+        if (h->h_sn[s] > 32) fb[p] += h->h_sf[s] * h->h_npad[s];
+    }
+    std::vector<int> kb(P + 1, 0), fb0(P + 1, 0);
+    for (int p = 0; p < P; ++p) { kb[p + 1] = kb[p] + nk[p]; fb0[p + 1] = fb0[p] + fb[p]; }
+    {
+        std::vector<int> fill(fb0.begin(), fb0.end() - 1);
+        for (int s = 0; s < S; ++s)
+            if (h->h_sn[s] > 32) {
+                const int p = s % P;
+                fbig[s] = fill[p];
+                const size_t cnt = (size_t)h->h_sf[s] * h->h_npad[s];
+                if (cnt)
+                    CUDA_TRY(cudaMemcpyAsync(wp.d_F2 + fill[p], h->d_F32 + h->h_foff[s], cnt * sizeof(float),
+                                             cudaMemcpyDeviceToDevice, h->stream));
+                fill[p] += (int)cnt;
+            }
+    }
+    // per CTA: a replica segment for every global with a copy there
+    std::vector<std::vector<int>> rbase(P);          // rbase[p][g] (or -1), built sparse via map
+    std::vector<std::vector<int3>> rep(P);
+    std::vector<int> nru(P, 0);
+    std::vector<std::map<int, int>> seg_of(P);
+    for (int s = 0; s < S; ++s) {
+        const int p = s % P;
+        for (int r = 0; r < h->h_sn[s]; ++r) {
+            const int gi = h->h_gk[h->h_soff[s] + r];
+            if (seg_of[p].count(gi)) continue;
+            const int cnt = h->h_gstart[gi + 1] - h->h_gstart[gi];
+            seg_of[p][gi] = nru[p];
+            rep[p].push_back(make_int3(nru[p], h->h_gstart[gi], cnt));
+            nru[p] += cnt;
+        }
+    }
+    // which CTAs hold copies of each global
+    std::vector<std::vector<int>> holders(G);
+    for (int p = 0; p < P; ++p)
+        for (auto &kv : seg_of[p]) holders[kv.first].push_back(p);
+    // per local slot: replica segment and destination list
+    std::vector<int> wrseg(L), wdsp(L), wdd;
+    std::vector<int> db(P + 1, 0);
+    std::vector<std::vector<int>> dd(P);
+    for (int s = 0; s < S; ++s) {
+        const int p = s % P;
+        for (int r = 0; r < h->h_sn[s]; ++r) {
+            const int k = h->h_soff[s] + r;
+            const int gi = h->h_gk[k];
+            const int q = h->h_pk[k] - h->h_gstart[gi];
+            const int cnt = h->h_gstart[gi + 1] - h->h_gstart[gi];
+            const int kl = kb[p] + klb[s] + r;
+            wrseg[kl] = (seg_of[p][gi] << 8) | cnt;
+            const int nd = (int)holders[gi].size();
+            wdsp[kl] = ((int)dd[p].size() << 8) | nd;
+            for (int p2 : holders[gi]) dd[p].push_back((p2 << 24) | (seg_of[p2][gi] + q));
+        }
+    }
+    for (int p = 0; p < P; ++p) db[p + 1] = db[p] + (int)dd[p].size();
+    for (int p = 0; p < P; ++p) wdd.insert(wdd.end(), dd[p].begin(), dd[p].end());
+    std::vector<int3> wrep;
+    std::vector<int> rb(P + 1, 0), ru(P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+        rb[p + 1] = rb[p] + (int)rep[p].size();
+        ru[p + 1] = ru[p] + nru[p];
+        wrep.insert(wrep.end(), rep[p].begin(), rep[p].end());
+    }
+    std::vector<int> pr(8 * (P + 1), 0);
+    auto PR = [&](int field, int p) -> int & { return pr[field * (P + 1) + p]; };
+    for (int p = 0; p <= P; ++p) {
+        PR(0, p) = kb[p];
+        PR(2, p) = db[p];
+        PR(3, p) = fb0[p];
+        PR(4, p) = rb[p];
+        PR(7, p) = ru[p];
+    }
+    int mru = 0, mdd = 0, mf = 0;
+    for (int p = 0; p < P; ++p) {
+        mru = std::max(mru, nru[p]);
+        mdd = std::max(mdd, (int)dd[p].size());
+        mf = std::max(mf, fb[p]);
+    }
+    WarpLayout &c = wp.lay;
+    c = WarpLayout{};
+    c.P = P; c.L = L; c.S = S;
+    c.useg_len = (mru + 3) & ~3;
+    c.fbig_len = (mf + 3) & ~3;
+    size_t off = 0;
+    auto take = [&](unsigned *o, size_t bytes) { *o = (unsigned)off; off = align16u(off + bytes); };
+    take(&c.off_useg, (size_t)2 * c.useg_len * sizeof(float));
+    take(&c.off_dd, (size_t)mdd * sizeof(int));
+    take(&c.off_fbig, (size_t)2 * c.fbig_len * sizeof(float));   // column-major factors, then row-major copies
+    take(&c.off_vbig, (size_t)kWarpEngineWarps * 64 * sizeof(float));
+    take(&c.off_red, 16 * 6 * sizeof(double) + 16);
+    c.bytes = (unsigned)off;
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if ((long long)c.bytes + 4096 > optin) return OPF_OK;
+    if (prepare_warp_engine(c.bytes)) { cudaGetLastError(); return OPF_OK; }
+    if (warp_engine_occupancy(c) < 1) { cudaGetLastError(); return OPF_OK; }
+    if ((size_t)wdd.size() > (size_t)h->L * 16 || wrep.size() > (size_t)h->L) return OPF_OK;
+    CUDA_TRY(cudaMemcpyAsync(wp.d_pr, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(wp.d_klb, klb.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(wp.d_fbig, fbig.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(wp.d_wrseg, wrseg.data(), L * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(wp.d_wdsp, wdsp.data(), L * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    if (!wdd.empty())
+        CUDA_TRY(cudaMemcpyAsync(wp.d_wdd, wdd.data(), wdd.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    if (!wrep.empty())
+        CUDA_TRY(cudaMemcpyAsync(wp.d_wrep, wrep.data(), wrep.size() * sizeof(int3), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    wp.ok = true;
+    return OPF_OK;
+}
+
+static IterArgs<float> with_warp_plan(opf_handle *h, IterArgs<float> a, const WarpPlan &wp) {
+    a.klb = wp.d_klb; a.fbig = wp.d_fbig; a.F2 = wp.d_F2;
+    a.wrseg = wp.d_wrseg; a.wdsp = wp.d_wdsp; a.wdd = wp.d_wdd; a.wrep = wp.d_wrep;
+    a.u_prev_out = h->d_u32 + h->L;
+    return a;
+}
+
+template <typename T>
+static IterArgs<T> with_plan(IterArgs<T> a, const ClusterPlan &cp) {
+    a.srec = cp.d_srec; a.citems = cp.d_items; a.cmeta = cp.d_meta;
+    a.udst = cp.d_udst; a.gsegp = cp.d_gsegp; a.cdst = cp.d_cdst;
     return a;
 }
 
@@ -688,15 +1011,18 @@ static int run_grid64(opf_handle *h, const opf_solve_opts &o) {
     return OPF_OK;
 }
 
-// FP64 iterations by the one-CTA engine (same arithmetic, instance in shared memory).
-static int run_cta64(opf_handle *h, const opf_solve_opts &o) {
+// FP64 iterations by the cluster engine (same arithmetic, instance in the
+// shared memory of one thread-block cluster), one launch up to max_iter.
+static int run_cluster64(opf_handle *h, const opf_solve_opts &o) {
     const double rho = o.rho;
     TRY(set_recip(h, rho));
-    if (prepare_cta_engine<double>(h->lay64.bytes)) { g_last_error = "cannot size CTA engine"; return OPF_E_CUDA; }
     launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
-    IterArgs<double> a = iter_args<double>(h, rho);
-    cudaGraphConditionalHandle none{};
-    launch_cta_engine<double>(a, h->lay64, h->d_u64, o.max_iter, o.check_every, h->d_st, rho, none, 0, h->stream);
+    IterArgs<double> a = with_plan(iter_args<double>(h, rho), h->c64);
+    if (launch_cluster_engine<double>(a, h->c64.lay, h->c64.d_pr, h->d_u64, o.max_iter, o.check_every, h->d_st,
+                                      rho, cudaGraphConditionalHandle{}, 0, h->stream)) {
+        g_last_error = "cluster engine launch failed";
+        return OPF_E_CUDA;
+    }
     CUDA_TRY(cudaGetLastError());
     TRY(read_status(h));
     h->have_prev_u = h->h_st->iter > 0;
@@ -704,7 +1030,9 @@ static int run_cta64(opf_handle *h, const opf_solve_opts &o) {
 }
 
 // FP32 iterations in the shifted frame, re-centred in FP64 every R iterations.
-static int run_mixed(opf_handle *h, const opf_solve_opts &o, bool use_cta, bool recenter) {
+// eng: 1 whole-grid kernels, 2 cluster engine, 3 warp engine
+static int run_mixed(opf_handle *h, const opf_solve_opts &o, int eng, bool recenter) {
+    const bool use_cta = eng != 1;
     const double rho = o.rho;
     TRY(set_recip(h, rho));
     const int L = h->L, G = h->G, S = h->S;
@@ -723,13 +1051,17 @@ static int run_mixed(opf_handle *h, const opf_solve_opts &o, bool use_cta, bool 
                            nullptr, h->stream);
     launch_make_u<float>(L, h->d_pk, h->d_ds32, h->d_mu32, (float)rho, h->d_u32, nullptr, h->stream);
     CUDA_TRY(cudaGetLastError());
-    if (use_cta && prepare_cta_engine<float>(h->lay32.bytes)) { g_last_error = "cannot size CTA engine"; return OPF_E_CUDA; }
-    const int kind = (use_cta ? 2 : 1) + (recenter ? 0 : 2);
+
+    const int kind = eng + (recenter ? 0 : 8);
     const bool hl = (o.flags & OPF_SOLVE_HOST_LOOP) != 0;
-    IterArgs<float> a = iter_args<float>(h, rho);
+    IterArgs<float> a = eng == 3 ? with_warp_plan(h, iter_args<float>(h, rho), h->w32)
+                                 : with_plan(iter_args<float>(h, rho), h->c32);
     auto body = [&](cudaGraphConditionalHandle c, int use) {
-            if (use_cta) {
-                launch_cta_engine<float>(a, h->lay32, h->d_u32, R, k, h->d_st, rho, c, use, h->stream);
+            if (eng == 3) {
+                launch_warp_engine(a, h->w32.lay, h->w32.d_pr, h->d_u32, R, k, h->d_st, rho, c, use, h->stream);
+            } else if (eng == 2) {
+                launch_cluster_engine<float>(a, h->c32.lay, h->c32.d_pr, h->d_u32, R, k, h->d_st, rho, c, use,
+                                             h->stream);
             } else {
                 const int chunks = recenter ? R / k : 1;
                 for (int i = 0; i < chunks; ++i) enqueue_grid_chunk<float>(h, a, h->d_u32, k, rho, c, use);
@@ -746,9 +1078,10 @@ static int run_mixed(opf_handle *h, const opf_solve_opts &o, bool use_cta, bool 
             launch_make_u<float>(L, h->d_pk, h->d_ds32, h->d_mu32, (float)rho, h->d_u32, h->d_st, h->stream);
     };
     if (h->gmix.kind != kind || h->gmix.rho != rho || h->gmix.k != k || h->gmix.R != R ||
-        h->gmix.host_loop != hl) {
+        h->gmix.host_loop != hl || h->gmix.P != (eng == 3 ? 100 + h->w32.P : eng == 2 ? h->c32.P : 0)) {
         TRY(build_while_graph(h, &h->gmix, body, hl));
         h->gmix.kind = kind; h->gmix.rho = rho; h->gmix.k = k; h->gmix.R = R;
+        h->gmix.P = eng == 3 ? 100 + h->w32.P : eng == 2 ? h->c32.P : 0;
     }
     TRY(run_graph(h, &h->gmix, body));
     // back to the unshifted FP64 state
@@ -776,7 +1109,8 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
     if (!h->precomputed) return OPF_E_STATE;
     opf_solve_opts o = opts ? *opts : default_opts();
     if (!(o.rho > 0) || o.max_iter < 1 || o.check_every < 2 || (o.check_every & 1) ||
-        o.precision < 0 || o.precision > 2 || o.engine < 0 || o.engine > 2 || std::isnan(o.eps_rel) ||
+        o.precision < 0 || o.precision > 2 || o.engine < 0 || o.engine > 3 || o.cluster < 0 ||
+        o.cluster > 16 || (o.cluster & (o.cluster - 1)) || std::isnan(o.eps_rel) ||
         std::isnan(o.eps_abs_pres)) {
         g_last_error = "solve options: need rho > 0, max_iter >= 1, even check_every >= 2";
         return OPF_E_INVALID;
@@ -786,20 +1120,34 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
     TRY(set_status(h, o, false));
     CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
     if (o.precision == OPF_PREC_FP64) {
+        bool cl = false;
         if (o.engine == 2) {
-            if (!h->cta64_ok) { g_last_error = "instance does not fit one CTA in FP64"; return OPF_E_CAPACITY; }
-            TRY(run_cta64(h, o));
-        } else {
-            TRY(run_grid64(h, o));
+            TRY(get_cluster_plan<double>(h, &h->c64, o.cluster, 96));
+            cl = h->c64.ok;
         }
+        if (o.engine == 3) { g_last_error = "the warp engine runs FP32 iterations only"; return OPF_E_INVALID; }
+        if (o.engine == 2 && !cl) { g_last_error = "instance does not fit one cluster in FP64"; return OPF_E_CAPACITY; }
+        if (cl) TRY(run_cluster64(h, o));
+        else TRY(run_grid64(h, o));
         h->main_iters = h->h_st->iter;
         h->recenters = 0;
         CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
         CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
     } else {
-        bool cta = o.engine == 2 || (o.engine == 0 && h->cta32_ok);
-        if (cta && !h->cta32_ok) { g_last_error = "instance does not fit one CTA"; return OPF_E_CAPACITY; }
-        TRY(run_mixed(h, o, cta, o.precision == OPF_PREC_MIXED));
+        int eng = 1;
+        if (o.engine == 0 || o.engine == 3) {
+            if (!h->w32.built) TRY(build_warp_plan(h));
+            if (h->w32.ok) eng = 3;
+        }
+        if (eng == 1 && (o.engine == 0 || o.engine == 2)) {
+            TRY(get_cluster_plan<float>(h, &h->c32, o.cluster, 192));
+            if (h->c32.ok) eng = 2;
+        }
+        if ((o.engine == 2 || o.engine == 3) && eng != o.engine) {
+            g_last_error = "instance does not fit the requested resident engine";
+            return OPF_E_CAPACITY;
+        }
+        TRY(run_mixed(h, o, eng, o.precision == OPF_PREC_MIXED));
         h->main_iters = h->h_st->iter;
         {
             int R = o.recenter_every > 0 ? o.recenter_every : 1000;

@@ -23,11 +23,13 @@
 // bounds - x_ref and bbar~ = M (x_ref[g] + lambda_ref/rho) + bbar - x_ref[g].
 // This is the same algorithm after a change of variables; with a zero
 // reference it is plain ADMM.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "opf_internal.h"
 
@@ -486,100 +488,604 @@ __global__ void k_add_iters(DevStatus *st, long long n) {
     if (threadIdx.x == 0 && blockIdx.x == 0) st->iter += n;
 }
 
-// ============================================================ CTA engine
-// Whole instance in shared memory; one CTA runs up to n_iters iterations,
-// testing every check_every.
+// ============================================================ cluster engine
+// One instance resident in the shared memory of a thread-block cluster of P
+// CTAs (P = 1 .. 16); up to n_iters iterations per launch, tested every
+// check_every.  CTA `rank` owns a contiguous range of subsystems (its local
+// slots and factor columns) and a contiguous range of globals (their copies'
+// entries of u, in u order).  Per iteration:
+//   A. owner, per global i: sigma = sum of u over its copies, x_i = clip(...)
+//      (Eq. closed_1); x is stored at each copy's padded-v position in the
+//      CTA that holds the copy (distributed shared memory store);
+//   -- cluster barrier --
+//   B. per factor column: t_c = <F_c, x + w> with w = mu / rho;
+//   -- CTA barrier --
+//   C. per slot: y = (F t)_r, x_s = (v - y or y) + bbar~ (Eq. closed_2),
+//      mu += rho (x - x_s) (Eq. ADMM-3), w = mu / rho, and u = rho x_s - mu
+//      stored in the owner CTA of the slot's global;
+//   -- cluster barrier --
+// Remote traffic is stores only; the barriers (release / acquire) order them.
+namespace cg = cooperative_groups;
+
 template <typename T>
 __device__ void copy_in(void *dst, const void *src, size_t bytes) {
-    const int4 *s4 = reinterpret_cast<const int4 *>(src);
-    int4 *d4 = reinterpret_cast<int4 *>(dst);
-    const size_t n4 = bytes / 16;
-    for (size_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = s4[i];
+    if (bytes == 0) return;
     const unsigned char *sb = reinterpret_cast<const unsigned char *>(src);
     unsigned char *db = reinterpret_cast<unsigned char *>(dst);
-    for (size_t i = n4 * 16 + threadIdx.x; i < bytes; i += blockDim.x) db[i] = sb[i];
+    if (((reinterpret_cast<size_t>(src) | reinterpret_cast<size_t>(dst)) & 15) == 0) {
+        const int4 *s4 = reinterpret_cast<const int4 *>(src);
+        int4 *d4 = reinterpret_cast<int4 *>(dst);
+        const size_t n4 = bytes / 16;
+        for (size_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = s4[i];
+        for (size_t i = n4 * 16 + threadIdx.x; i < bytes; i += blockDim.x) db[i] = sb[i];
+    } else {
+        for (size_t i = threadIdx.x; i < bytes; i += blockDim.x) db[i] = sb[i];
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024, 1) k_cta_engine(IterArgs<T> g, CtaLayout lay, T *u_glob,
-                                                        int n_iters, int check_every, DevStatus *st,
-                                                        double rho_d, cudaGraphConditionalHandle cond,
-                                                        int use_cond) {
+__device__ __forceinline__ T dot_padded2(const T *__restrict__ f, const T *__restrict__ x,
+                                         const T *__restrict__ w, int npad);
+
+template <>
+__device__ __forceinline__ float dot_padded2<float>(const float *__restrict__ f, const float *__restrict__ x,
+                                                    const float *__restrict__ w, int npad) {
+    float a0 = 0.0f, a1 = 0.0f;
+    for (int r = 0; r < npad; r += 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(f + r);
+        const float4 b = *reinterpret_cast<const float4 *>(x + r);
+        const float4 c = *reinterpret_cast<const float4 *>(w + r);
+        a0 = fmaf(a.x, b.x + c.x, a0);
+        a1 = fmaf(a.y, b.y + c.y, a1);
+        a0 = fmaf(a.z, b.z + c.z, a0);
+        a1 = fmaf(a.w, b.w + c.w, a1);
+    }
+    return a0 + a1;
+}
+
+template <>
+__device__ __forceinline__ double dot_padded2<double>(const double *__restrict__ f, const double *__restrict__ x,
+                                                      const double *__restrict__ w, int npad) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int r = 0; r < npad; r += 2) {
+        const double2 a = *reinterpret_cast<const double2 *>(f + r);
+        const double2 b = *reinterpret_cast<const double2 *>(x + r);
+        const double2 c = *reinterpret_cast<const double2 *>(w + r);
+        a0 = fma(a.x, b.x + c.x, a0);
+        a1 = fma(a.y, b.y + c.y, a1);
+    }
+    return a0 + a1;
+}
+
+// Part ranges: pr[field * (P + 1) + rank], fields in this order.
+enum { PR_K = 0, PR_S, PR_J, PR_F, PR_V, PR_T, PR_G, PR_U, PR_NFIELDS };
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_cluster_engine(IterArgs<T> g, ClusterLayout lay, const int *pr,
+                                                         T *u_glob, int n_iters, int check_every,
+                                                         DevStatus *st, double rho_d,
+                                                         cudaGraphConditionalHandle cond, int use_cond) {
     extern __shared__ __align__(16) unsigned char sm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int P = lay.P;
+    const int rank = (int)cl.block_rank();
+    const int P1 = P + 1;
     if (st->done) {
-        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+        if (use_cond && rank == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
         return;
     }
-    const int S = lay.S, L = lay.L, G = lay.G;
-    copy_in<T>(sm + lay.off_F, g.F, (size_t)lay.nF * sizeof(T));
-    copy_in<T>(sm + lay.off_sub, g.sub, (size_t)(S + 1) * sizeof(int4));
-    copy_in<T>(sm + lay.off_sub2, g.sub2, (size_t)(S + 1) * sizeof(int4));
-    copy_in<T>(sm + lay.off_items, g.items, (size_t)lay.nitems * sizeof(int));
-    copy_in<T>(sm + lay.off_meta, g.meta, (size_t)L * sizeof(int));
-    copy_in<T>(sm + lay.off_segp, g.segp, (size_t)L * sizeof(int));
-    copy_in<T>(sm + lay.off_gk, g.gk, (size_t)L * sizeof(int));
-    copy_in<T>(sm + lay.off_pk, g.pk, (size_t)L * sizeof(int));
-    copy_in<T>(sm + lay.off_bt, g.bt, (size_t)L * sizeof(T));
-    copy_in<T>(sm + lay.off_mu, g.mu, (size_t)L * sizeof(T));
-    copy_in<T>(sm + lay.off_ds, g.ds, (size_t)L * sizeof(T));
-    copy_in<T>(sm + lay.off_u0, u_glob, (size_t)L * sizeof(T));
-    copy_in<T>(sm + lay.off_ct, g.ct, (size_t)G * sizeof(T));
-    copy_in<T>(sm + lay.off_lbt, g.lbt, (size_t)G * sizeof(T));
-    copy_in<T>(sm + lay.off_ubt, g.ubt, (size_t)G * sizeof(T));
-    copy_in<T>(sm + lay.off_recip, g.recip, 256 * sizeof(T));
-    __syncthreads();
-    IterArgs<T> a = g;
-    a.F = reinterpret_cast<const T *>(sm + lay.off_F);
-    a.sub = reinterpret_cast<const int4 *>(sm + lay.off_sub);
-    a.sub2 = reinterpret_cast<const int4 *>(sm + lay.off_sub2);
-    a.items = reinterpret_cast<const int *>(sm + lay.off_items);
-    a.meta = reinterpret_cast<const int *>(sm + lay.off_meta);
-    a.segp = reinterpret_cast<const int *>(sm + lay.off_segp);
-    a.gk = reinterpret_cast<const int *>(sm + lay.off_gk);
-    a.pk = reinterpret_cast<const int *>(sm + lay.off_pk);
-    a.bt = reinterpret_cast<const T *>(sm + lay.off_bt);
-    a.mu = reinterpret_cast<T *>(sm + lay.off_mu);
-    a.ds = reinterpret_cast<T *>(sm + lay.off_ds);
-    a.ct = reinterpret_cast<const T *>(sm + lay.off_ct);
-    a.lbt = reinterpret_cast<const T *>(sm + lay.off_lbt);
-    a.ubt = reinterpret_cast<const T *>(sm + lay.off_ubt);
-    const T *recip = reinterpret_cast<const T *>(sm + lay.off_recip);
-    T *ub[2] = {reinterpret_cast<T *>(sm + lay.off_u0), reinterpret_cast<T *>(sm + lay.off_u1)};
-    T *xb = reinterpret_cast<T *>(sm + lay.off_xb);
-    T *vb = reinterpret_cast<T *>(sm + lay.off_vb);
+    const int k0 = pr[PR_K * P1 + rank], nk = pr[PR_K * P1 + rank + 1] - k0;
+    const int s0 = pr[PR_S * P1 + rank], ns = pr[PR_S * P1 + rank + 1] - s0;
+    const int j0 = pr[PR_J * P1 + rank], nj = pr[PR_J * P1 + rank + 1] - j0;
+    const int f0 = pr[PR_F * P1 + rank], nf = pr[PR_F * P1 + rank + 1] - f0;
+    const int v0 = pr[PR_V * P1 + rank], nv = pr[PR_V * P1 + rank + 1] - v0;
+    const int g0 = pr[PR_G * P1 + rank], ng = pr[PR_G * P1 + rank + 1] - g0;
+    const int u0 = pr[PR_U * P1 + rank], nu = pr[PR_U * P1 + rank + 1] - u0;
+    const int L = lay.L;
+    T *F = reinterpret_cast<T *>(sm + lay.off_F);
+    int4 *srec = reinterpret_cast<int4 *>(sm + lay.off_srec);
+    int *items = reinterpret_cast<int *>(sm + lay.off_items);
+    int *meta = reinterpret_cast<int *>(sm + lay.off_meta);
+    int *udst = reinterpret_cast<int *>(sm + lay.off_udst);
+    T *bt = reinterpret_cast<T *>(sm + lay.off_bt);
+    T *ds = reinterpret_cast<T *>(sm + lay.off_ds);
+    T *mu = reinterpret_cast<T *>(sm + lay.off_mu);
+    T *vbx = reinterpret_cast<T *>(sm + lay.off_vbx);
+    T *vbw = reinterpret_cast<T *>(sm + lay.off_vbw);
     T *tb = reinterpret_cast<T *>(sm + lay.off_tb);
-    __shared__ double red[32][6];
-    __shared__ int stop;
-    if (threadIdx.x == 0) stop = 0;
-    int par = 0;
+    int *gsegp = reinterpret_cast<int *>(sm + lay.off_gsegp);
+    T *ct = reinterpret_cast<T *>(sm + lay.off_ct);
+    T *lbt = reinterpret_cast<T *>(sm + lay.off_lbt);
+    T *ubt = reinterpret_cast<T *>(sm + lay.off_ubt);
+    T *uloc = reinterpret_cast<T *>(sm + lay.off_uloc);
+    int *cdst = reinterpret_cast<int *>(sm + lay.off_cdst);
+    T *recip = reinterpret_cast<T *>(sm + lay.off_recip);
+    double *red = reinterpret_cast<double *>(sm + lay.off_red);    // [16][6], used in rank 0
+    // FP64 data of the stopping test, staged once per launch (the reference
+    // point only changes between launches)
+    double *xrg = reinterpret_cast<double *>(sm + lay.off_xrg);    // x_ref of owned globals
+    double *cg64 = reinterpret_cast<double *>(sm + lay.off_cg);    // costs of owned globals
+    double *xrs = reinterpret_cast<double *>(sm + lay.off_xrs);    // x_ref of each local slot's global
+    double *lrs = reinterpret_cast<double *>(sm + lay.off_lrs);    // lambda_ref of each local slot
+    int *stop = reinterpret_cast<int *>(sm + lay.off_red + 16 * 6 * sizeof(double));
+    copy_in<T>(F, g.F + f0, (size_t)nf * sizeof(T));
+    copy_in<T>(srec, g.srec + s0, (size_t)ns * sizeof(int4));
+    copy_in<T>(items, g.citems + j0, (size_t)nj * sizeof(int));
+    copy_in<T>(meta, g.cmeta + k0, (size_t)nk * sizeof(int));
+    copy_in<T>(udst, g.udst + k0, (size_t)nk * sizeof(int));
+    copy_in<T>(bt, g.bt + k0, (size_t)nk * sizeof(T));
+    copy_in<T>(ds, g.ds + k0, (size_t)nk * sizeof(T));
+    copy_in<T>(mu, g.mu + k0, (size_t)nk * sizeof(T));
+    copy_in<T>(gsegp, g.gsegp + g0, (size_t)ng * sizeof(int));
+    copy_in<T>(ct, g.ct + g0, (size_t)ng * sizeof(T));
+    copy_in<T>(lbt, g.lbt + g0, (size_t)ng * sizeof(T));
+    copy_in<T>(ubt, g.ubt + g0, (size_t)ng * sizeof(T));
+    copy_in<T>(uloc, u_glob + u0, (size_t)nu * sizeof(T));
+    copy_in<T>(cdst, g.cdst + u0, (size_t)nu * sizeof(int));
+    copy_in<T>(recip, g.recip, 256 * sizeof(T));
+    copy_in<T>(xrg, g.xr + g0, (size_t)ng * sizeof(double));
+    copy_in<T>(cg64, g.c64 + g0, (size_t)ng * sizeof(double));
+    copy_in<T>(lrs, g.lamr + k0, (size_t)nk * sizeof(double));
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) xrs[k] = g.xr[g.gk[k0 + k]];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) { vbx[i] = (T)0; vbw[i] = (T)0; }
+    if (threadIdx.x == 0) *stop = 0;
     __syncthreads();
+    const T rho = g.rho, inv_rho = g.inv_rho;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        const int mt = meta[k];
+        vbw[srec[mt >> 8].y + (mt & 255)] = mu[k] * inv_rho;
+    }
+    cl.sync();   // every CTA staged before the first remote store
+    T *u_prev = u_glob + L;
+    int it = 0;
+    for (it = 0; it < n_iters; ++it) {
+        const bool chk = ((it + 1) % check_every) == 0 || it == n_iters - 1;
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        // A: owner global update, x to every copy
+        for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+            const int sp = gsegp[i];
+            const int p0 = sp >> 8, cnt = sp & 255;
+            T sigma = 0;
+            for (int q = 0; q < cnt; ++q) sigma += uloc[p0 + q];
+            T x = (sigma - ct[i]) * recip[cnt];
+            const T lo = lbt[i], hi = ubt[i];
+            if (x < lo) x = lo;
+            if (x > hi) x = hi;
+            for (int q = 0; q < cnt; ++q) {
+                const int d = cdst[p0 + q];
+                const int r = d >> 24, pos = d & 0xffffff;
+                T *dst = (r == rank) ? vbx : cl.map_shared_rank(vbx, r);
+                dst[pos] = x;
+            }
+            if (chk) {
+                for (int q = 0; q < cnt; ++q) u_prev[u0 + p0 + q] = uloc[p0 + q];
+                const double xd = xrg[i] + (double)x;
+                acc[2] += (double)cnt * xd * xd;
+                acc[5] += cg64[i] * xd;
+            }
+        }
+        cl.sync();
+        // B: t = F^T (x + w) per factor column
+        for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+            const int itm = items[j];
+            const int4 r = srec[itm >> 8];
+            const int c = itm & 255, npad = (r.w >> 1) & 0x1ff;
+            tb[r.z + c] = dot_padded2<T>(F + r.x + c * npad, vbx + r.y, vbw + r.y, npad);
+        }
+        __syncthreads();
+        // C: projection, dual update, u to the owner
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+            const int mt = meta[k];
+            const int4 r = srec[mt >> 8];
+            const int row = mt & 255;
+            const int f = r.w >> 10, npad = (r.w >> 1) & 0x1ff, mode = r.w & 1;
+            const T *Fr = F + r.x + row;
+            const T *tt = tb + r.z;
+            T y0 = 0, y1 = 0;
+            int c = 0;
+            for (; c + 1 < f; c += 2) {
+                y0 += Fr[c * npad] * tt[c];
+                y1 += Fr[(c + 1) * npad] * tt[c + 1];
+            }
+            if (c < f) y0 += Fr[c * npad] * tt[c];
+            const int pos = r.y + row;
+            const T x = vbx[pos];
+            const T v = x + vbw[pos];
+            const T xm = (mode ? (y0 + y1) : v - (y0 + y1)) + bt[k];
+            const T res = x - xm;
+            const T mu_new = mu[k] + rho * res;
+            const T d_old = ds[k];
+            ds[k] = xm;
+            mu[k] = mu_new;
+            vbw[pos] = mu_new * inv_rho;
+            const int d = udst[k];
+            const int ro = d >> 24, up = d & 0xffffff;
+            T *ud = (ro == rank) ? uloc : cl.map_shared_rank(uloc, ro);
+            ud[up] = rho * xm - mu_new;
+            if (chk) {
+                const double xsd = xrs[k] + (double)xm;
+                const double dd = (double)xm - (double)d_old;
+                acc[0] += (double)res * (double)res;
+                acc[1] += dd * dd;
+                acc[3] += xsd * xsd;
+                const double lamd = lrs[k] + (double)mu_new;
+                acc[4] += lamd * lamd;
+            }
+        }
+        cl.sync();
+        if (chk) {
+            __shared__ double bred[32][6];
+            block_sum6(acc, bred);
+            if (threadIdx.x == 0) {
+                double *dst = cl.map_shared_rank(red, 0);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) dst[rank * 6 + q] = acc[q];
+            }
+            cl.sync();
+            if (rank == 0 && threadIdx.x == 0) {
+                double s6[6] = {0, 0, 0, 0, 0, 0};
+                for (int r = 0; r < P; ++r)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) s6[q] += red[r * 6 + q];
+                const int since = ((it + 1) % check_every) == 0 ? check_every : ((it + 1) % check_every);
+                apply_test(st, s6, rho_d, since);
+                *stop = st->done;
+            }
+            cl.sync();
+            const int halt = *cl.map_shared_rank(stop, 0);
+            if (halt) break;
+        }
+    }
+    // write back: slots' mu and x_s, the owner's u (the previous u was saved on the last tested iteration)
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        g.mu[k0 + k] = mu[k];
+        g.ds[k0 + k] = ds[k];
+    }
+    for (int p = threadIdx.x; p < nu; p += blockDim.x) u_glob[u0 + p] = uloc[p];
+    cl.sync();   // no CTA exits while others may still read its shared memory
+    if (use_cond && rank == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, *stop ? 0u : 1u);
+}
+
+// ============================================================ warp engine
+// FP32 persistent engine for instances of at most 16 x 12 subsystems: a
+// cluster of P CTAs, one warp per subsystem for the whole solve (subsystem
+// s = warp * P + rank, so every CTA gets a mix of sizes); lane l owns local
+// rows l and l + 32.  A subsystem with n <= 32 keeps its factor F in
+// registers (lane c: column c for t = F^T v; lane r: row r for y = F t), so
+// both mat-vecs are chains of warp shuffles and FMAs; a larger one (n <= 64)
+// reads F from shared memory.  For one iteration:
+//   x = clip((sum of u over the global's copies - c~) / (rho N), lb~, ub~)   (Eq. closed_1)
+//   v = x + mu / rho;  t = F^T v;  y = F t
+//   x_s = (v - y or y) + bbar~  (Eq. closed_2),  mu += rho (x - x_s) (Eq. ADMM-3)
+//   u = rho x_s - mu stored into every replica of the global's u (each CTA
+//   keeps one for each global it has copies of; other CTAs through
+//   distributed shared memory, double-buffered by iteration parity)
+// followed by one barrier (cluster-wide, or __syncthreads when P = 1).
+constexpr int WE_WARPS = 12;
+constexpr int WE_NREG = 32;   // factor rows held in registers (n <= 32)
+constexpr int WE_FREG = 16;   // factor columns held in registers
+constexpr int WE_DREG = 4;    // u destinations held in registers
+
+__device__ __forceinline__ void we_barrier(cg::cluster_group &cl, int P) {
+    if (P == 1) __syncthreads();
+    else cl.sync();
+}
+
+__global__ void __launch_bounds__(32 * WE_WARPS, 1)
+k_warp_engine(IterArgs<float> g, WarpLayout lay, const int *pr, float *u_glob, int n_iters, int check_every,
+              DevStatus *st, double rho_d, cudaGraphConditionalHandle cond, int use_cond) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int P = lay.P, P1 = P + 1;
+    const int rank = (int)cl.block_rank();
+    if (st->done) {
+        if (use_cond && rank == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+        return;
+    }
+    const int kb = pr[PR_K * P1 + rank];                                              // local slots
+    const int fb0 = pr[PR_F * P1 + rank], nfb = pr[PR_F * P1 + rank + 1] - fb0;       // big factors
+    const int db0 = pr[PR_J * P1 + rank], ndb = pr[PR_J * P1 + rank + 1] - db0;       // u destinations
+    const int rb0 = pr[PR_V * P1 + rank], nrb = pr[PR_V * P1 + rank + 1] - rb0;       // replica segments
+    float *ubuf[2] = {reinterpret_cast<float *>(sm + lay.off_useg),
+                      reinterpret_cast<float *>(sm + lay.off_useg) + lay.useg_len};   // read t % 2, write the other
+    int *dd = reinterpret_cast<int *>(sm + lay.off_dd);
+    float *Fbig = reinterpret_cast<float *>(sm + lay.off_fbig);
+    float *vbig = reinterpret_cast<float *>(sm + lay.off_vbig);    // 64 floats per warp
+    double *red = reinterpret_cast<double *>(sm + lay.off_red);
+    int *stop = reinterpret_cast<int *>(sm + lay.off_red + 16 * 6 * sizeof(double));
+    copy_in<float>(dd, g.wdd + db0, (size_t)ndb * sizeof(int));
+    copy_in<float>(Fbig, g.F2 + fb0, (size_t)nfb * sizeof(float));
+    for (int i = threadIdx.x; i < nrb; i += blockDim.x) {
+        const int3 r = g.wrep[rb0 + i];
+        for (int q = 0; q < r.z; ++q) ubuf[0][r.x + q] = u_glob[r.y + q];
+    }
+    if (threadIdx.x == 0) *stop = 0;
+    const float rho = g.rho, inv_rho = g.inv_rho;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // ---- per-warp subsystem and per-lane row state (registers)
+    const int s = warp * P + rank;
+    const bool have = s < lay.S;
+    int n = 0, f = 0, mode = 0, soff = 0, big = 0, npad = 0;
+    const float *Fs = nullptr;
+    float *Frm = nullptr;
+    float Fc[WE_NREG], Fr[WE_FREG];
+#pragma unroll
+    for (int r = 0; r < WE_NREG; ++r) Fc[r] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < WE_FREG; ++c) Fr[c] = 0.0f;
+    float bt[2] = {0, 0}, ds[2] = {0, 0}, mu[2] = {0, 0}, ct[2] = {0, 0}, lo[2] = {0, 0}, hi[2] = {0, 0};
+    float rcp[2] = {0, 0};
+    int rseg[2] = {0, 0}, dsp[2] = {0, 0}, qk[2] = {0, 0}, pk[2] = {0, 0};
+    int ndr = 0;
+    float *dptr[WE_DREG];
+#pragma unroll
+    for (int e = 0; e < WE_DREG; ++e) dptr[e] = nullptr;
+    if (have) {
+        const int4 h = g.sub[s], q = g.sub2[s];
+        soff = h.x; n = h.y; f = h.z; mode = h.w;
+        npad = q.y;
+        big = n > 32;
+        if (!big) {
+            const float *Fg = g.F + q.x;
+#pragma unroll
+            for (int r = 0; r < WE_NREG; ++r)
+                if (lane < f && r < n) Fc[r] = Fg[lane * npad + r];
+#pragma unroll
+            for (int c = 0; c < WE_FREG; ++c)
+                if (c < f && lane < n) Fr[c] = Fg[c * npad + lane];
+        } else {
+            Fs = Fbig + (g.fbig[s] - fb0);                      // column-major, column stride npad
+            Frm = Fbig + lay.fbig_len + (g.fbig[s] - fb0);      // row-major copy, row stride f
+            for (int i = lane; i < f * n; i += 32) {
+                const int r = i / f, c = i - r * f;
+                Frm[i] = Fs[c * npad + r];
+            }
+        }
+        const int kl0 = g.klb[s];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int row = lane + 32 * j;
+            if (row < n) {
+                const int kg = soff + row;
+                const int gi = g.gk[kg];
+                bt[j] = g.bt[kg];
+                ds[j] = g.ds[kg];
+                mu[j] = g.mu[kg];
+                ct[j] = g.ct[gi];
+                lo[j] = g.lbt[gi];
+                hi[j] = g.ubt[gi];
+                const int sp = g.segp[kg];
+                rcp[j] = g.recip[sp & 255];
+                pk[j] = g.pk[kg];
+                qk[j] = pk[j] - (sp >> 8);
+                rseg[j] = g.wrseg[kb + kl0 + row];
+                dsp[j] = g.wdsp[kb + kl0 + row];
+            }
+        }
+        // first row: up to WE_DREG destinations resolved to pointers (buffer 0;
+        // the parity offset is added per iteration)
+        if (lane < n) {
+            const int d0 = dsp[0] >> 8, nd = dsp[0] & 255;
+            ndr = nd < WE_DREG ? nd : WE_DREG;
+#pragma unroll
+            for (int e = 0; e < WE_DREG; ++e)
+                if (e < ndr) {
+                    const int d = g.wdd[db0 + d0 + e];
+                    const int ro = d >> 24, up = d & 0xffffff;
+                    dptr[e] = (ro == rank ? ubuf[0] : cl.map_shared_rank(ubuf[0], ro)) + up;
+                }
+        }
+    }
+    __syncthreads();
+    if (P > 1) cl.sync();
+    int par = 0;
     for (int it = 0; it < n_iters; ++it) {
         const bool chk = ((it + 1) % check_every) == 0 || it == n_iters - 1;
         double acc[6] = {0, 0, 0, 0, 0, 0};
-        if (chk) tile_iteration<T, true>(a, 0, S, ub[par], ub[par ^ 1], xb, vb, tb, recip, acc);
-        else tile_iteration<T, false>(a, 0, S, ub[par], ub[par ^ 1], xb, vb, tb, recip, acc);
-        par ^= 1;
-        __syncthreads();
-        if (chk) {
-            block_sum6(acc, red);
-            if (threadIdx.x == 0) {
-                const int since = ((it + 1) % check_every) == 0 ? check_every : ((it + 1) % check_every);
-                apply_test(st, acc, rho_d, since);
-                stop = st->done;
+        const float *useg = ubuf[par];
+        const int nxt = (par ^ 1) * lay.useg_len;      // offset of the buffer written this iteration
+        if (have) {
+            float x[2] = {0.0f, 0.0f}, v[2] = {0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int row = lane + 32 * j;
+                if (row < n) {
+                    const int base = rseg[j] >> 8, cnt = rseg[j] & 255;
+                    float sg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                    for (int qq = 0; qq < 8; ++qq)
+                        if (qq < cnt) sg[qq & 3] += useg[base + qq];
+                    for (int qq = 8; qq < cnt; ++qq) sg[qq & 3] += useg[base + qq];
+                    float xv = ((sg[0] + sg[1]) + (sg[2] + sg[3]) - ct[j]) * rcp[j];
+                    if (xv < lo[j]) xv = lo[j];
+                    if (xv > hi[j]) xv = hi[j];
+                    x[j] = xv;
+                    v[j] = xv + mu[j] * inv_rho;
+                    if (chk) {   // FP64 data of the test read from global memory
+                        g.u_prev_out[pk[j]] = useg[base + qk[j]];
+                        const int gi = g.gk[soff + row];
+                        const double xd = g.xr[gi] + (double)xv;
+                        acc[2] += xd * xd;
+                        if (qk[j] == 0) acc[5] += g.c64[gi] * xd;
+                    }
+                }
             }
-            __syncthreads();
-            if (stop) break;
+            float t = 0.0f, y[2] = {0.0f, 0.0f};
+            if (!big) {
+                // t_c (lane c) = sum_r F[r][c] v_r, then y_r (lane r) = sum_c F[r][c] t_c;
+                // warp-uniform bounds: n shuffles for t and f for y
+                float t1 = 0.0f;
+#pragma unroll
+                for (int r = 0; r < WE_NREG; r += 2) {
+                    if (r >= n) break;
+                    t = fmaf(Fc[r], __shfl_sync(0xffffffffu, v[0], r), t);
+                    t1 = fmaf(Fc[r + 1], __shfl_sync(0xffffffffu, v[0], r + 1), t1);
+                }
+                t += t1;
+                float y1 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < WE_FREG; c += 2) {
+                    if (c >= f) break;
+                    y[0] = fmaf(Fr[c], __shfl_sync(0xffffffffu, t, c), y[0]);
+                    y1 = fmaf(Fr[c + 1], __shfl_sync(0xffffffffu, t, c + 1), y1);
+                }
+                y[0] += y1;
+            } else {
+                float *vb = vbig + warp * 64;
+                vb[lane] = v[0];
+                vb[lane + 32] = v[1];
+                __syncwarp();
+                if (lane < f) {
+                    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+                    int r = 0;
+                    for (; r + 3 < n; r += 4) {
+                        a0 = fmaf(Frm[(r + 0) * f + lane], vb[r + 0], a0);
+                        a1 = fmaf(Frm[(r + 1) * f + lane], vb[r + 1], a1);
+                        a2 = fmaf(Frm[(r + 2) * f + lane], vb[r + 2], a2);
+                        a3 = fmaf(Frm[(r + 3) * f + lane], vb[r + 3], a3);
+                    }
+                    for (; r < n; ++r) a0 = fmaf(Frm[r * f + lane], vb[r], a0);
+                    t = (a0 + a1) + (a2 + a3);
+                }
+                __syncwarp();
+                const int r2 = lane + 32 < npad ? lane + 32 : lane;   // stays inside the column
+                float b0 = 0.0f, b1 = 0.0f, e0 = 0.0f, e1 = 0.0f;
+                int c = 0;
+                for (; c + 1 < f; c += 2) {
+                    const float ta = __shfl_sync(0xffffffffu, t, c);
+                    const float tb2 = __shfl_sync(0xffffffffu, t, c + 1);
+                    b0 = fmaf(Fs[c * npad + lane], ta, b0);
+                    b1 = fmaf(Fs[(c + 1) * npad + lane], tb2, b1);
+                    e0 = fmaf(Fs[c * npad + r2], ta, e0);
+                    e1 = fmaf(Fs[(c + 1) * npad + r2], tb2, e1);
+                }
+                if (c < f) {
+                    const float ta = __shfl_sync(0xffffffffu, t, c);
+                    b0 = fmaf(Fs[c * npad + lane], ta, b0);
+                    e0 = fmaf(Fs[c * npad + r2], ta, e0);
+                }
+                y[0] = b0 + b1;
+                y[1] = e0 + e1;   // used only when lane + 32 < n
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int row = lane + 32 * j;
+                if (row < n) {
+                    const float xm = (mode ? y[j] : v[j] - y[j]) + bt[j];
+                    const float res = x[j] - xm;
+                    const float mu_new = mu[j] + rho * res;
+                    const float d_old = ds[j];
+                    ds[j] = xm;
+                    mu[j] = mu_new;
+                    const float un = rho * xm - mu_new;
+                    const int d0 = dsp[j] >> 8, nd = dsp[j] & 255;
+                    int e0 = 0;
+                    if (j == 0) {
+#pragma unroll
+                        for (int e = 0; e < WE_DREG; ++e)
+                            if (e < ndr) dptr[e][nxt] = un;
+                        e0 = ndr;
+                    }
+                    for (int e = e0; e < nd; ++e) {
+                        const int d = dd[d0 + e];
+                        const int ro = d >> 24, up = d & 0xffffff;
+                        float *ud = (ro == rank) ? ubuf[par ^ 1] : cl.map_shared_rank(ubuf[par ^ 1], ro);
+                        ud[up] = un;
+                    }
+                    if (chk) {
+                        const int kg = soff + row;
+                        const double xsd = g.xr[g.gk[kg]] + (double)xm;
+                        const double dd2 = (double)xm - (double)d_old;
+                        acc[0] += (double)res * (double)res;
+                        acc[1] += dd2 * dd2;
+                        acc[3] += xsd * xsd;
+                        const double lamd = g.lamr[kg] + (double)mu_new;
+                        acc[4] += lamd * lamd;
+                    }
+                }
+            }
+        }
+        par ^= 1;
+        we_barrier(cl, P);
+        if (chk) {
+            __shared__ double bred[32][6];
+            block_sum6(acc, bred);
+            if (threadIdx.x == 0) {
+                double *dst = P > 1 ? cl.map_shared_rank(red, 0) : red;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) dst[rank * 6 + q] = acc[q];
+            }
+            we_barrier(cl, P);
+            if (rank == 0 && threadIdx.x == 0) {
+                double s6[6] = {0, 0, 0, 0, 0, 0};
+                for (int r = 0; r < P; ++r)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) s6[q] += red[r * 6 + q];
+                const int since = ((it + 1) % check_every) == 0 ? check_every : ((it + 1) % check_every);
+                apply_test(st, s6, rho_d, since);
+                *stop = st->done;
+            }
+            we_barrier(cl, P);
+            if (*(P > 1 ? cl.map_shared_rank(stop, 0) : stop)) break;
         }
     }
-    // write back the iterate; u of the last iteration to u_glob, the u that
-    // produced its global update to u_glob + L
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        g.mu[i] = a.mu[i];
-        g.ds[i] = a.ds[i];
-        u_glob[i] = ub[par][i];
-        u_glob[L + i] = ub[par ^ 1][i];
+    // write back the slots' mu, x_s and current u (each copy by its slot)
+    if (have) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int row = lane + 32 * j;
+            if (row < n) {
+                g.mu[soff + row] = mu[j];
+                g.ds[soff + row] = ds[j];
+                u_glob[pk[j]] = ubuf[par][(rseg[j] >> 8) + qk[j]];
+            }
+        }
     }
-    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, stop ? 0u : 1u);
+    if (P > 1) cl.sync();
+    if (use_cond && rank == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, *stop ? 0u : 1u);
+}
+
+int prepare_warp_engine(unsigned bytes) {
+    if (cudaFuncSetAttribute(k_warp_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return -1;
+    if (cudaFuncSetAttribute(k_warp_engine, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return -1;
+    return 0;
+}
+
+static void fill_cluster_cfg(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr, int P, int threads,
+                             unsigned bytes, cudaStream_t s) {
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->gridDim = dim3(P, 1, 1);
+    cfg->blockDim = dim3(threads, 1, 1);
+    cfg->dynamicSmemBytes = bytes;
+    cfg->stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg->attrs = attr;
+    cfg->numAttrs = 1;
+}
+
+int launch_warp_engine(const IterArgs<float> &g, const WarpLayout &lay, const int *pr, float *u_glob, int n_iters,
+                       int check_every, DevStatus *st, double rho, cudaGraphConditionalHandle cond, int use_cond,
+                       cudaStream_t s) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    fill_cluster_cfg(&cfg, attr, lay.P, 32 * WE_WARPS, lay.bytes, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_warp_engine, g, lay, pr, u_glob, n_iters, check_every, st, rho,
+                                       cond, use_cond);
+    return e == cudaSuccess ? 0 : -1;
+}
+
+int warp_engine_occupancy(const WarpLayout &lay) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    fill_cluster_cfg(&cfg, attr, lay.P, 32 * WE_WARPS, lay.bytes, 0);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_warp_engine, &cfg) != cudaSuccess) return 0;
+    return n;
 }
 
 // ============================================================ small kernels
@@ -775,18 +1281,55 @@ void launch_enter_shift(int L, const int *gk, const double *xr, const double *ds
 }
 
 template <typename T>
-int prepare_cta_engine(unsigned bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_cta_engine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
-    return e == cudaSuccess ? 0 : -1;
+int prepare_cluster_engine(unsigned bytes, int P) {
+    if (cudaFuncSetAttribute(k_cluster_engine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return -1;
+    if (P > 8 && cudaFuncSetAttribute(k_cluster_engine<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return -1;
+    return 0;
 }
 
 template <typename T>
-void launch_cta_engine(const IterArgs<T> &g, const CtaLayout &lay, T *u_glob, int n_iters,
-                       int check_every, DevStatus *st, double rho, cudaGraphConditionalHandle cond,
-                       int use_cond, cudaStream_t s) {
-    k_cta_engine<T><<<1, 1024, lay.bytes, s>>>(g, lay, u_glob, n_iters, check_every, st, rho, cond,
-                                               use_cond);
+int launch_cluster_engine(const IterArgs<T> &g, const ClusterLayout &lay, const int *pr, T *u_glob,
+                          int n_iters, int check_every, DevStatus *st, double rho,
+                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(lay.P, 1, 1);
+    cfg.blockDim = dim3(lay.threads, 1, 1);
+    cfg.dynamicSmemBytes = lay.bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = lay.P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_cluster_engine<T>, g, lay, pr, u_glob, n_iters, check_every, st,
+                                       rho, cond, use_cond);
+    return e == cudaSuccess ? 0 : -1;
+}
+
+// Largest cluster of P CTAs with `bytes` of shared memory each that can be
+// resident (0 if none).
+template <typename T>
+int cluster_occupancy(const ClusterLayout &lay) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(lay.P, 1, 1);
+    cfg.blockDim = dim3(lay.threads, 1, 1);
+    cfg.dynamicSmemBytes = lay.bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = lay.P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_cluster_engine<T>, &cfg) != cudaSuccess) return 0;
+    return n;
 }
 
 template <typename T>
@@ -835,10 +1378,11 @@ void launch_recenter(int L, int G, int S, const int *gk, const double *xr_old, c
 #define OPF_INST(T)                                                                                   \
     template void launch_iterate<T>(const IterArgs<T> &, const T *, T *, double *, const DevStatus *, \
                                     bool, int, int, int, int, int, cudaStream_t);                     \
-    template int prepare_cta_engine<T>(unsigned);                                                     \
-    template void launch_cta_engine<T>(const IterArgs<T> &, const CtaLayout &, T *, int, int,         \
-                                       DevStatus *, double, cudaGraphConditionalHandle, int,          \
-                                       cudaStream_t);                                                 \
+    template int prepare_cluster_engine<T>(unsigned, int);                                            \
+    template int launch_cluster_engine<T>(const IterArgs<T> &, const ClusterLayout &, const int *, T *,\
+                                          int, int, DevStatus *, double, cudaGraphConditionalHandle,  \
+                                          int, cudaStream_t);                                         \
+    template int cluster_occupancy<T>(const ClusterLayout &);                                         \
     template void launch_make_u<T>(int, const int *, const T *, const T *, T, T *, const DevStatus *, \
                                    cudaStream_t);                                                     \
     template int launch_global_x<T>(int, const int2 *, const T *, const T *, const T *, const T *,    \

@@ -67,6 +67,25 @@ struct IterArgs {
     const double *c64;    // original costs
     const T *recip;       // recip[N] = 1 / (rho N), N < 256
     const int *tile_s0;   // first subsystem of each grid tile (n_tiles + 1 entries)
+    // cluster engine records (offsets relative to the CTA's part); the grid
+    // engine never reads these, the cluster engine never reads items / meta
+    const int *citems;    // per factor column: (subsystem in part << 8) | column
+    const int *cmeta;     // per slot: (subsystem in part << 8) | row
+    const int4 *srec;     // per subsystem: (factor offset, padded-v offset, t offset, f<<10 | npad<<1 | mode)
+    const int *gsegp;     // per global: (start of its copies in the owner's u part << 8) | copies
+    const int *udst;      // per slot: (owner rank << 24) | position in the owner's u part
+    const int *cdst;      // per u entry: (rank holding the copy << 24) | padded-v offset there
+    // warp engine: factors of subsystems with n > 32 packed per CTA and each
+    // one's offset; each subsystem's first local slot; per local slot the
+    // replica segment ((start << 8) | copies) and destination list
+    // ((offset << 8) | count) of its u; destinations ((rank << 24) | position);
+    // replica list (local start, start in u, copies) per CTA
+    const T *F2;
+    const int *fbig;
+    const int *klb;
+    const int *wrseg, *wdsp, *wdd;
+    const int3 *wrep;
+    T *u_prev_out;        // u of the previous iteration, written on tested iterations
     T rho, inv_rho;
 };
 
@@ -96,13 +115,20 @@ struct PreArgs {
     int *status;        // out: 0 ok, 1 inconsistent local system
 };
 
-// Byte offsets of the one-CTA engine's shared-memory image.
-struct CtaLayout {
-    int S, L, G, nitems;
-    long long nF;                 // factor elements
-    unsigned off_F, off_sub, off_sub2, off_items, off_meta, off_segp, off_gk, off_pk;
-    unsigned off_bt, off_mu, off_ds, off_u0, off_u1, off_ct, off_lbt, off_ubt, off_recip;
-    unsigned off_xb, off_vb, off_tb;
+// Shared-memory image of one CTA of the cluster engine (sizes are the maxima
+// over the P parts), byte offsets.
+struct ClusterLayout {
+    int P, L, threads;
+    unsigned off_F, off_srec, off_items, off_meta, off_udst, off_bt, off_ds, off_mu, off_vbx, off_vbw;
+    unsigned off_tb, off_gsegp, off_ct, off_lbt, off_ubt, off_uloc, off_cdst, off_recip, off_red;
+    unsigned off_xrg, off_cg, off_xrs, off_lrs;
+    unsigned bytes;
+};
+
+// Shared-memory image of one CTA of the warp engine, byte offsets.
+struct WarpLayout {
+    int P, L, S, useg_len, fbig_len;
+    unsigned off_useg, off_dd, off_fbig, off_vbig, off_red;
     unsigned bytes;
 };
 

@@ -26,7 +26,8 @@ OPF_E_CUDA = -7
 OPF_E_CAPACITY = -8
 
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
-ENGINE_AUTO, ENGINE_GRID, ENGINE_CTA = 0, 1, 2
+ENGINE_AUTO, ENGINE_GRID, ENGINE_CTA, ENGINE_WARP = 0, 1, 2, 3
+ENGINE_CLUSTER = ENGINE_CTA
 SOLVE_HOST_LOOP = 1
 
 _P = C.c_void_p
@@ -53,7 +54,8 @@ class Options(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("rho", C.c_double), ("eps_rel", C.c_double), ("eps_abs_pres", C.c_double),
                 ("max_iter", C.c_int32), ("check_every", C.c_int32), ("precision", C.c_int32),
-                ("recenter_every", C.c_int32), ("engine", C.c_int32), ("flags", C.c_int32)]
+                ("recenter_every", C.c_int32), ("engine", C.c_int32), ("flags", C.c_int32),
+                ("cluster", C.c_int32)]
 
 
 class Sizes(C.Structure):
@@ -217,9 +219,9 @@ class Solver:
         _check(load().opf_precompute(self._h), "opf_precompute")
 
     def solve(self, rho=100.0, eps_rel=1e-8, eps_abs_pres=1e-4, max_iter=1_000_000, check_every=50,
-              precision=PREC_FP64, recenter_every=0, engine=ENGINE_AUTO, flags=0):
+              precision=PREC_FP64, recenter_every=0, engine=ENGINE_AUTO, flags=0, cluster=0):
         o = SolveOpts(rho, eps_rel, eps_abs_pres, int(max_iter), int(check_every), int(precision),
-                      int(recenter_every), int(engine), int(flags))
+                      int(recenter_every), int(engine), int(flags), int(cluster))
         rc = load().opf_solve_ex(self._h, C.byref(o))
         _check(rc, "opf_solve_ex", ok=(OPF_OK, OPF_NOT_CONVERGED))
         return rc == OPF_OK

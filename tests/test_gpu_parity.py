@@ -53,20 +53,39 @@ def test_fp64_iterates_match_oracle(name, seed):
     assert abs(obj - ref.objective) <= TOL_ITER * max(1.0, abs(ref.objective))
 
 
-@pytest.mark.parametrize("name,seed", [("13", 1001), ("34", 5034)])
-def test_cta_engine_fp64_matches_oracle(name, seed):
+@pytest.mark.parametrize("name,seed,cluster", [("13", 1001, 1), ("13", 1001, 16), ("34", 5034, 4),
+                                               ("123", 2001, 8), ("123", 2001, 16)])
+def test_cluster_engine_fp64_matches_oracle(name, seed, cluster):
     f = synth.preset_feeder(name, seed)
     M = lindist.build(f)
     ref = oracle_iterates(M, 100)
     with opf.Solver.from_feeder(f) as s:
         s.precompute()
-        s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64, engine=opf.ENGINE_CTA)
+        s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64, engine=opf.ENGINE_CTA,
+                cluster=cluster)
         xs, lam = s.locals()
         x, _ = s.solution()
         assert s.residuals()["iters"] == 100
     assert rel_err(xs, ref.xs) <= TOL_ITER
     assert rel_err(lam, ref.lam) <= TOL_ITER
     assert rel_err(x, ref.x) <= TOL_ITER
+
+
+@pytest.mark.parametrize("engine", [opf.ENGINE_GRID, opf.ENGINE_CLUSTER, opf.ENGINE_WARP])
+@pytest.mark.parametrize("name,seed", [("13", 1002), ("123", 2001)])
+def test_fp32_engines_track_oracle(name, seed, engine):
+    """FP32 iterations without re-centring stay within single-precision
+    distance of the FP64 oracle over 100 iterations, on every engine."""
+    f = synth.preset_feeder(name, seed)
+    M = lindist.build(f)
+    ref = oracle_iterates(M, 100)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP32, engine=engine)
+        xs, lam = s.locals()
+        assert s.residuals()["iters"] == 100
+    assert rel_err(xs, ref.xs) <= 1e-4
+    assert rel_err(lam, ref.lam) <= 1e-4
 
 
 def generic_model(seed, **kw):
@@ -104,15 +123,16 @@ def test_zip_delta_loads_match_oracle():
     assert rel_err(lam, ref.lam) <= TOL_ITER
 
 
-@pytest.mark.parametrize("precision", [opf.PREC_FP64, opf.PREC_MIXED])
+@pytest.mark.parametrize("precision,engine", [(opf.PREC_FP64, opf.ENGINE_AUTO), (opf.PREC_MIXED, opf.ENGINE_AUTO),
+                                              (opf.PREC_FP64, opf.ENGINE_GRID), (opf.PREC_MIXED, opf.ENGINE_GRID)])
 @pytest.mark.parametrize("name,seed", [("13", 1003), ("123", 2002)])
-def test_converged_objective(name, seed, precision):
+def test_converged_objective(name, seed, precision, engine):
     f = synth.preset_feeder(name, seed)
     M = lindist.build(f)
     obj_star, _ = oracle_admm.lp_optimum(M)
     with opf.Solver.from_feeder(f) as s:
         s.precompute()
-        ok = s.solve(precision=precision)
+        ok = s.solve(precision=precision, engine=engine)
         _, obj = s.solution()
         r = s.residuals()
     assert ok
