@@ -4,8 +4,9 @@ One step = one complete solve through the library, inputs resident on the
 device: the Algorithm 1 precomputation (Sec. III-B) followed by ADMM
 iterations to the stopping test (Sec. III-C with eps_rel = 1e-8 and
 pres <= 1e-4, which puts the objective within 1e-6 of the LP optimum) and the
-read-back of the objective.  The default path iterates in FP32 inside one
-shared-memory-resident CTA, re-centred in FP64, followed by an FP64 polish;
+read-back of the objective.  The default path iterates in FP32 with one warp
+per subsystem inside one thread-block cluster, re-centred in FP64, followed
+by an FP64 polish;
 ``--precision fp64`` times plain FP64 iterations.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
@@ -187,6 +188,23 @@ def run_reference(args, rank, world):
     return 0
 
 
+# DRAM bytes of one k_warp_engine launch (1000 iterations) from the ncu
+# capture in profiles/k_warp_engine_123bus.md; null for other kernels.
+WARP_ENGINE_TRAFFIC_PER_LAUNCH = 352256 + 1536
+ITERS_PER_LAUNCH = 1000
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """Largest value over the ranks (the timing reduction of the replicas)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def count_launches(stats, precision, k=50, R=1000):
     """Kernels of ours per step: precompute (3) + solve + objective read (1)."""
     n = 3 + 1
@@ -205,6 +223,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the iteration kernels directly instead of one graph with a device WHILE "
+                         "node (same kernels and arithmetic; profilers cannot see kernels in such graphs)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -228,17 +249,20 @@ def main():
     prec = opf.PREC_MIXED if args.precision == "mixed" else opf.PREC_FP64
     stream = torch.cuda.Stream(device=local)
     solver = opf.Solver.from_feeder(f, device=local, stream=stream.cuda_stream)
-    sizes = solver.sizes()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    flags = opf.SOLVE_HOST_LOOP if args.host_loop else 0
 
     def step():
         solver.precompute()
-        ok = solver.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=prec)
+        ok = solver.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=prec, flags=flags)
         _, obj = solver.solution()
         return ok, obj
 
     for _ in range(args.warmup):
         step()
+    solver.precompute()
+    sizes = solver.sizes()            # factor sizes are known after the precomputation
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -269,11 +293,7 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), world, f"cuda:{local}")
     value = world * args.steps / (total_ms / 1e3)
 
     # end to end through the C ABI from host arrays (create, precompute, solve, read x)
@@ -283,17 +303,13 @@ def main():
         t0 = time.perf_counter()
         s2 = opf.Solver.from_feeder(f, device=local, stream=stream.cuda_stream)
         s2.precompute()
-        s2.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=prec)
+        s2.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=prec, flags=flags)
         x, obj = s2.solution()
         e2e_times.append(time.perf_counter() - t0)
         h2d = s2.sizes()["h2d_bytes"]
         d2h = x.nbytes + 8
         s2.close()
-    e2e_total = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_times), world, f"cuda:{local}")
     e2e_value = world * len(e2e_times) / e2e_total
 
     # roofline of the dominant kernel: the iteration phase (one-CTA engine or grid iterations)
@@ -302,10 +318,15 @@ def main():
     n_it = it_main if args.precision == "mixed" else sum(iters)
     achieved = bpi * n_it / (sum(iter_ms) / 1e3) / 1e9
     peak, peak_kind = measured_peak()
+    mixed = args.precision == "mixed"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
-            "kernel": "k_cta_engine<float> (FP32 iterations, instance resident in shared memory)"
-            if args.precision == "mixed" else "k_iterate<double> (FP64 grid iterations)",
+            "frac": achieved / peak,
+            "traffic": WARP_ENGINE_TRAFFIC_PER_LAUNCH if mixed else None,
+            "traffic_unit": "bytes per launch of %d iterations" % ITERS_PER_LAUNCH if mixed else None,
+            "algorithmic_bytes_per_launch": bpi * ITERS_PER_LAUNCH if mixed else None,
+            "kernel": "k_warp_engine (FP32 iterations; one warp per subsystem, factors in registers, "
+                      "instance resident in one thread-block cluster)"
+            if args.precision == "mixed" else "k_tile_iter<double> (FP64 iterations, one CTA per tile)",
             "bytes_per_iter": bpi, "iters_timed": n_it, "peak_source": peak_kind + " hbm_gbs"}
 
     if rank == 0:
