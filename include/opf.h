@@ -240,6 +240,82 @@ int opf_global_update_static(int32_t n, const int32_t *seg_off, const double *u,
                              const double *lb, const double *ub, double rho, double *x,
                              double *objective, void *stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many instances of one model solved together.  Every instance shares the
+ * handle's A_s, c and bounds (the local systems of Sec. III-B, hence M_s =
+ * -Abar_s) and has its own right-hand side b, so its own bbar = A_s^+ b.
+ * Load scenarios of one feeder are such instances when every load has
+ * constant power (alpha = beta = 0 in VDLM-1..5): the loads enter only the
+ * rhs of the p^d, q^d rows.  Each instance runs Algorithm 1 with its own
+ * Sec. III-C test and stops on its own; the iterations of all instances are
+ * advanced together by one persistent kernel per re-centring interval (a CUDA
+ * graph loops until every instance stopped).
+ * The batch keeps a pointer to the handle: destroy the batch first.  Not
+ * thread-safe; the handle's stream orders all work. */
+typedef struct opf_batch opf_batch;
+
+/* n_inst >= 1 instances, each starting as a copy of the handle's own rhs and
+ * at the start point of Sec. V-A.  Needs a precomputed handle (OPF_E_STATE);
+ * computes A_s^+ once per handle (FP64).  OPF_E_OOM if device memory is short. */
+int opf_batch_create(opf_handle *h, int32_t n_inst, opf_batch **out);
+
+/* rhs of instances [first, first + count): host array of count * n_rows
+ * doubles, instance-major, rows in canonical order (subsystems in creation
+ * order, each subsystem's rows in its own order; n_rows from opf_get_sizes).
+ * The instances restart from the start point.  OPF_E_INFEASIBLE_LOCAL if some
+ * A_s x_s = b_s has no solution for an instance (message names it). */
+int opf_batch_set_rhs(opf_batch *b, int32_t first, int32_t count, const double *rhs);
+
+/* Same from load values (feeder handles): load_p, load_q are host arrays of
+ * count * n_load * 3 doubles, [instance][load][phase] like opf_feeder.load_a /
+ * load_b (entries of absent phases are ignored).  OPF_E_INVALID for generic
+ * handles or when a load has a ZIP exponent (then A_s depends on the loads). */
+int opf_batch_set_loads(opf_batch *b, int32_t first, int32_t count, const double *load_p,
+                        const double *load_q);
+
+/* Runs every instance to its own stopping test (options as opf_solve_ex;
+ * engine and cluster ignored).  OPF_PREC_MIXED: FP32 iterations re-centred
+ * every recenter_every iterations on an FP64 reference, then FP64 iterations
+ * until the test holds in FP64.  Returns OPF_OK when every instance
+ * converged, OPF_NOT_CONVERGED when some hit max_iter (per-instance results in
+ * opf_batch_get_status), OPF_E_NUMERIC on NaN/Inf. */
+int opf_batch_solve(opf_batch *b, const opf_solve_opts *opts);
+
+/* n_iters FP64 iterations of every instance without the test (for checking
+ * against a reference implementation iteration by iteration). */
+int opf_batch_step(opf_batch *b, double rho, int32_t n_iters);
+
+/* Engine shape for one precision (OPF_PREC_FP32 or OPF_PREC_FP64): k_inst
+ * instances per CTA (power of two <= 32) and warps per CTA (<= 16); 0 = pick
+ * (FP32: the fastest of the candidate shapes timed on the batch; FP64: the
+ * largest k_inst <= 4 that fits).  out (get): ok, k_inst, warps, chunks per
+ * lane, tasks, chunks per CTA, shared bytes, CTAs. */
+int opf_batch_set_shape(opf_batch *b, int32_t precision, int32_t k_inst, int32_t warps);
+int opf_batch_get_shape(opf_batch *b, int32_t precision, int32_t *out, int32_t n_out);
+
+/* Global x (count * n_global doubles, canonical order) and objective c^T x of
+ * instances [first, first + count) after the last solve or step; either
+ * output may be NULL. */
+int opf_batch_get_solution(opf_batch *b, int32_t first, int32_t count, double *x, double *objective);
+
+/* Per instance: res[4 i ..] = pres, dres, eps_prim, eps_dual of its last test,
+ * iterations, converged flag (any output may be NULL). */
+int opf_batch_get_status(opf_batch *b, int32_t first, int32_t count, double *res, int32_t *iters,
+                         int32_t *converged);
+
+/* x_s and lambda of one instance, canonical slot order (n_slots each). */
+int opf_batch_get_locals(opf_batch *b, int32_t inst, double *xs, double *lam);
+
+/* Last solve: [0] FP32 phase ms, [1] FP64 phase ms, [2] autotune ms (0 when
+ * the shape was known), [3] mean iterations, [4] converged instances. */
+int opf_batch_get_timing(opf_batch *b, double *out, int32_t n_out);
+
+/* (k_inst, warps, ms) triples timed by the last FP32 autotune; returns how
+ * many values exist (out may be NULL). */
+int opf_batch_get_tune_log(opf_batch *b, double *out, int32_t n_out);
+
+void opf_batch_destroy(opf_batch *b);
+
 void opf_destroy(opf_handle *h);
 const char *opf_strerror(int code);
 /* Message of the last OPF_E_INVALID / OPF_E_CUDA on this thread. */

@@ -93,98 +93,8 @@ void opf::set_last_error(const std::string &msg) { g_last_error = msg; }
         }                                                                                \
     } while (0)
 
-struct GraphCache {
-    cudaGraphExec_t exec = nullptr;
-    cudaGraph_t graph = nullptr;
-    bool host_loop = false;
-    double rho = 0;
-    int k = 0, R = 0, kind = -1, P = 0;
-    void reset() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        exec = nullptr;
-        graph = nullptr;
-        kind = -1;
-    }
-};
+#include "handle.h"
 
-// Cluster plan for one precision: P CTAs, part ranges and part-relative records.
-struct ClusterPlan {
-    int P = 0;
-    bool ok = false;
-    ClusterLayout lay{};
-    int *d_pr = nullptr;
-    int4 *d_srec = nullptr;
-    int *d_items = nullptr, *d_meta = nullptr, *d_udst = nullptr, *d_gsegp = nullptr, *d_cdst = nullptr;
-};
-
-// Warp-engine plan (FP32): subsystem s -> CTA s % P, warp s / P.
-struct WarpPlan {
-    int P = 0;
-    bool built = false, ok = false;
-    WarpLayout lay{};
-    int *d_pr = nullptr, *d_klb = nullptr, *d_fbig = nullptr;
-    int *d_wrseg = nullptr, *d_wdsp = nullptr, *d_wdd = nullptr;
-    int3 *d_wrep = nullptr;
-    float *d_F2 = nullptr;
-};
-
-// Grid tiling for one precision: tile t covers subsystems [s0[t], s0[t+1]).
-struct Tiling {
-    int n_tiles = 0, block = 128, xcap = 0, vcap = 0, tcap = 0;
-    int *d_s0 = nullptr;
-};
-
-struct opf_handle {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    HostModel model;
-    int S = 0, L = 0, G = 0;
-    long long nA = 0, nB = 0, nP = 0, nFcap = 0, nF = 0, sum_nf = 0, n_rows = 0, nitems = 0;
-    int max_ns = 0, sh_m = 0, sh_n = 0;
-    std::vector<int> canon_slot_to_dev;     // canonical slot -> device slot
-    std::vector<int> h_sn, h_sm, h_soff, h_sf, h_mode;
-    std::vector<void *> allocs;
-    // per subsystem
-    int *d_soff = nullptr, *d_sn = nullptr, *d_sm = nullptr, *d_sf = nullptr, *d_smode = nullptr;
-    int *d_boff = nullptr, *d_pstatus = nullptr;
-    long long *d_aoff = nullptr, *d_poff = nullptr, *d_fcap = nullptr;
-    int4 *d_sub = nullptr, *d_sub2 = nullptr;
-    int *d_items = nullptr;
-    // per slot
-    int *d_gk = nullptr, *d_pk = nullptr, *d_uslot = nullptr, *d_meta = nullptr, *d_segp = nullptr;
-    int2 *d_gseg = nullptr;
-    double *d_A = nullptr, *d_b = nullptr, *d_W = nullptr, *d_Bw = nullptr, *d_P = nullptr;
-    double *d_Fcap = nullptr, *d_F64 = nullptr, *d_bbar64 = nullptr;
-    float *d_F32 = nullptr;
-    // per global
-    double *d_c64 = nullptr, *d_lb64 = nullptr, *d_ub64 = nullptr, *d_x0 = nullptr;
-    double *d_xr = nullptr, *d_xr2 = nullptr, *d_zeroG = nullptr, *d_x = nullptr, *d_objpart = nullptr;
-    float *d_ct32 = nullptr, *d_lbt32 = nullptr, *d_ubt32 = nullptr;
-    double *d_recip64 = nullptr;
-    float *d_recip32 = nullptr;
-    // state
-    double *d_ds64 = nullptr, *d_mu64 = nullptr, *d_u64 = nullptr, *d_lamr = nullptr, *d_zeroL = nullptr;
-    float *d_ds32 = nullptr, *d_mu32 = nullptr, *d_u32 = nullptr, *d_bt32 = nullptr;
-    double *d_partials = nullptr;
-    DevStatus *d_st = nullptr;
-    DevStatus *h_st = nullptr;
-    Tiling t64, t32;
-    // bookkeeping
-    bool precomputed = false;
-    bool have_prev_u = false;    // d_u64 + L holds the u that produced the last global update
-    double last_rho = 100.0, recip_rho = -1.0;
-    long long total_iters = 0;
-    long long main_iters = 0, recenters = 0;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    double timing[6] = {0, 0, 0, 0, 0, 0};
-    long long h2d_bytes = 0;
-    GraphCache g64, gmix;
-    ClusterPlan c32, c64;
-    WarpPlan w32;
-    std::vector<int> h_tpre, h_vpre, h_foff, h_npad, h_pk, h_gk, h_gstart, h_uslot;
-};
 
 template <typename T>
 static int dalloc(opf_handle *h, T **p, size_t n) {
@@ -288,6 +198,14 @@ static int build_layout(opf_handle *h) {
         h->n_rows += s.m;
     }
     soff[h->S] = so;
+    h->h_boff = boff;
+    {
+        std::vector<int> crow0(h->S + 1, 0);
+        for (int cs = 0; cs < h->S; ++cs) crow0[cs + 1] = crow0[cs] + M.subs[cs].m;
+        h->canon_row_to_dev.assign(crow0[h->S], 0);
+        for (int d = 0; d < h->S; ++d)
+            for (int i = 0; i < sm[d]; ++i) h->canon_row_to_dev[crow0[order[d]] + i] = boff[d] + i;
+    }
     h->nA = ao; h->nB = bo; h->nP = po; h->nFcap = fo; h->nF = std::max<long long>(fc, 4);
     h->sh_m = std::min(h->sh_m, 64);
     h->sh_n = std::min(h->max_ns, 64);
@@ -461,20 +379,59 @@ static int reset_state(opf_handle *h) {
     return OPF_OK;
 }
 
-extern "C" int opf_precompute(opf_handle *h) {
-    if (!h) return OPF_E_INVALID;
-    CUDA_TRY(cudaSetDevice(h->device));
-    CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
+// The precompute kernel on fresh work copies of A and b; with_pinv adds the
+// A_s^+ outputs.
+static int launch_precompute_kernel(opf_handle *h, bool with_pinv) {
     CUDA_TRY(cudaMemcpyAsync(h->d_W, h->d_A, std::max<long long>(h->nA, 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->d_Bw, h->d_b, std::max<long long>(h->nB, 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     PreArgs a;
+    memset(&a, 0, sizeof(a));
     a.S = h->S; a.sh_m = h->sh_m; a.sh_n = h->sh_n;
     a.sm = h->d_sm; a.sn = h->d_sn; a.soff = h->d_soff;
     a.aoff = h->d_aoff; a.poff = h->d_poff; a.foff = h->d_fcap; a.boff = h->d_boff;
     a.W = h->d_W; a.Bw = h->d_Bw; a.P = h->d_P; a.F = h->d_Fcap;
     a.sf = h->d_sf; a.smode = h->d_smode; a.bbar = h->d_bbar64; a.status = h->d_pstatus;
+    if (with_pinv) {
+        a.Tw = h->d_Tw; a.toff = h->d_toff; a.pinv = h->d_pinv; a.pioff = h->d_pioff; a.nrej = h->d_nrej;
+    }
     if (launch_precompute(a, h->stream)) { g_last_error = "cannot size the precompute kernel"; return OPF_E_CUDA; }
     CUDA_TRY(cudaGetLastError());
+    return OPF_OK;
+}
+
+int opf::ensure_pinv(opf_handle *h) {
+    if (h->have_pinv) return OPF_OK;
+    if (!h->precomputed) return OPF_E_STATE;
+    CUDA_TRY(cudaSetDevice(h->device));
+    if (!h->d_pinv) {
+        h->h_pioff.assign(h->S + 1, 0);
+        h->h_toff.assign(h->S + 1, 0);
+        for (int d = 0; d < h->S; ++d) {
+            h->h_pioff[d + 1] = h->h_pioff[d] + (long long)h->h_sn[d] * h->h_sm[d];
+            h->h_toff[d + 1] = h->h_toff[d] + 2LL * h->h_sm[d] * h->h_sm[d];
+        }
+        TRY(dalloc(h, &h->d_pinv, (size_t)std::max<long long>(h->h_pioff[h->S], 1)));
+        TRY(dalloc(h, &h->d_Tw, (size_t)std::max<long long>(h->h_toff[h->S], 1)));
+        TRY(upload(h, &h->d_pioff, h->h_pioff));
+        TRY(upload(h, &h->d_toff, h->h_toff));
+        TRY(dalloc(h, &h->d_nrej, (size_t)h->S));
+    }
+    TRY(launch_precompute_kernel(h, true));
+    h->h_nrej.resize(h->S);
+    CUDA_TRY(cudaMemcpyAsync(h->h_nrej.data(), h->d_nrej, h->S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->have_pinv = true;
+    return OPF_OK;
+}
+
+const char *opf::last_error_cstr() { return g_last_error.c_str(); }
+
+extern "C" int opf_precompute(opf_handle *h) {
+    if (!h) return OPF_E_INVALID;
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
+    h->have_pinv = false;
+    TRY(launch_precompute_kernel(h, false));
     std::vector<int> status(h->S);
     h->h_sf.resize(h->S);
     CUDA_TRY(cudaMemcpyAsync(status.data(), h->d_pstatus, h->S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));

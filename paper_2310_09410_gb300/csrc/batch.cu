@@ -1,0 +1,673 @@
+// Batched ADMM (Algorithm 1) over many instances of one model: every instance
+// shares A_s, c and the bounds (so M_s = -Abar_s and its factor F) and has its
+// own right-hand side b, hence its own bbar = A_s^+ b.
+//
+//  k_batch_engine  n_iters iterations of Algorithm 1 for the K instances of
+//                  one CTA, all resident: factors, u = rho x_s - lambda and x
+//                  in shared memory; lambda, bbar~ and the test data streamed
+//                  from L2 as 16-byte vectors.  Per iteration:
+//                    G. per (global, instance): Eq. closed_1 as a fixed-order
+//                       sum over the global's copies of u;
+//                    -- CTA barrier --
+//                    L. per warp task: J member subsystems x K instances;
+//                       v = x_g + lambda / rho, x_s = M v + bbar~ as one pass
+//                       over the factor rows (w_r = <F_r, v>, y += w_r F_r),
+//                       lambda <- rho (v - x_s) (Eq. ADMM-3 with
+//                       x_g = v - lambda / rho), u = rho x_s - lambda;
+//                    -- CTA barrier --
+//                  and every check_every iterations the Sec. III-C sums per
+//                  instance in FP64 and the test; finished instances freeze.
+//  k_bref_*        FP64 re-centring: x_ref = next global update of the FP64
+//                  state, lambda_ref = lambda, shifted data written in the
+//                  engine layout (the engine iterates on x_s - x_ref[g] and
+//                  lambda - lambda_ref, the change of variables of the
+//                  single-instance engines).
+//  k_bunshift_*    back to the unshifted FP64 state.
+//  k_bbar          bbar = A_s^+ b per instance and subsystem (Sec. III-B).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "opf_internal.h"
+#include "test_rule.cuh"
+
+namespace opf {
+
+namespace {
+
+template <typename T>
+struct Q4 {
+    T v[4];
+};
+
+__device__ __forceinline__ Q4<float> ld4(const float *p) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    return {{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ Q4<double> ld4(const double *p) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float *p, const Q4<float> &q) {
+    *reinterpret_cast<float4 *>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const Q4<double> &q) {
+    *reinterpret_cast<double2 *>(p) = make_double2(q.v[0], q.v[1]);
+    *reinterpret_cast<double2 *>(p + 2) = make_double2(q.v[2], q.v[3]);
+}
+
+template <typename T>
+__device__ __forceinline__ T clampT(T x, T lo, T hi) {
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+
+}  // namespace
+
+// ============================================================ engine
+// NQ: chunks of 4 slots a lane can hold (registers v, y and the current
+// factor row: 3 * 4 * NQ values).
+template <typename T, int NQ>
+__global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_iters, int check_every) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *Fs = reinterpret_cast<T *>(smraw);
+    T *us = reinterpret_cast<T *>(smraw + a.off_u);
+    T *xs = reinterpret_cast<T *>(smraw + a.off_x);
+    double *red = reinterpret_cast<double *>(smraw + a.off_red);
+    int *flags = reinterpret_cast<int *>(smraw + a.off_flag);    // [0,K) running, [K,2K) just finished
+    const int K = a.K, ks = a.kshift, J = a.J;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int nthr = blockDim.x;
+    const int c = blockIdx.x;
+    if (tid < K) {
+        const int in = a.inst[c * K + tid];
+        flags[tid] = (in >= 0 && !a.st[in].done) ? 1 : 0;
+        flags[K + tid] = 0;
+    }
+    __syncthreads();
+    {
+        int any = 0;
+        for (int q = 0; q < K; ++q) any |= flags[q];
+        if (!any) return;
+    }
+    // factors into shared memory (nF is a multiple of 4)
+    for (int i = tid * 4; i < a.nF; i += nthr * 4) st4(Fs + i, ld4(a.Fpk + i));
+    const size_t sb = (size_t)c * a.NCH * K * 4;     // this CTA's slot arrays
+    const size_t gb = (size_t)c * a.G * K;           // global arrays
+    const size_t bb = (size_t)c * a.NB * K;          // bounded-global arrays
+    const int nsl = a.NCH * K * 4;
+    for (int i = tid * 4; i < nsl; i += nthr * 4) {
+        const Q4<T> d = ld4(a.ds + sb + i), m = ld4(a.mu + sb + i);
+        Q4<T> u;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) u.v[e] = a.rho * d.v[e] - m.v[e];
+        st4(us + i, u);
+    }
+    __syncthreads();
+    const int sc = tid & (K - 1);
+    const int jpos = lane >> ks;
+    const T rho = a.rho, inv_rho = a.inv_rho;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    int last_check = 0;
+    const int GK = a.G * K;
+    for (int it = 0; it < n_iters; ++it) {
+        const bool check = check_every > 0 && ((it + 1) % check_every == 0);
+        const bool wds = check || it == n_iters - 1 || (check_every > 0 && ((it + 2) % check_every == 0));
+        const bool act = flags[sc] != 0;
+        // ---- G: global update (Eq. closed_1)
+        for (int item = tid; item < GK; item += nthr) {
+            const int i = item >> ks;
+            const int4 gt = __ldg(a.gtab + i);
+            T s = T(0);
+            for (int q = 0; q < gt.y; ++q) s += us[__ldg(a.useg + gt.x + q) + sc * 4];
+            T xv = (s - a.ct[gb + item]) * __ldg(a.recip + i);
+            if (gt.z >= 0) xv = clampT(xv, a.lbt[bb + ((size_t)gt.z << ks) + sc], a.ubt[bb + ((size_t)gt.z << ks) + sc]);
+            xs[item] = xv;
+            if (check) {
+                const double xa = (double)xv + (double)a.xrf[gb + item];
+                acc[2] += (double)gt.y * xa * xa;
+                acc[5] += (double)__ldg(a.cost + i) * xa;
+            }
+        }
+        __syncthreads();
+        // ---- L: local update (Eq. closed_2) and dual update (Eq. ADMM-3)
+        for (int ti = __ldg(a.wtask + w); ti < __ldg(a.wtask + w + 1); ++ti) {
+            const BatchTask tk = a.tasks[__ldg(a.tlist + ti)];
+            const int mode1 = (tk.modes >> (jpos >> tk.lp)) & 1;
+            T v[4 * NQ], y[4 * NQ], fr[4 * NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) { v[4 * q + e] = T(0); y[4 * q + e] = T(0); }
+                if (q < tk.nq) {
+                    const int ch = tk.ch0 + q * J + jpos;
+                    const int4 g4 = __ldg(a.chg + ch);
+                    const Q4<T> m4 = ld4(a.mu + sb + ((size_t)ch * K + sc) * 4);
+                    const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (gg[e] >= 0) v[4 * q + e] = xs[(gg[e] << ks) + sc] + m4.v[e] * inv_rho;
+                }
+            }
+            for (int r = 0; r < tk.f; ++r) {
+                const T *Fr = Fs + tk.foff + ((size_t)r * tk.nq * J + jpos) * 4;
+                T part = T(0);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    if (q < tk.nq) {
+                        const Q4<T> f4 = ld4(Fr + q * J * 4);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            fr[4 * q + e] = f4.v[e];
+                            part += f4.v[e] * v[4 * q + e];
+                        }
+                    }
+                }
+                for (int o = K; o < (tk.p << ks); o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    if (q < tk.nq)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) y[4 * q + e] += fr[4 * q + e] * part;
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                if (q < tk.nq) {
+                    const int ch = tk.ch0 + q * J + jpos;
+                    const size_t idx = sb + ((size_t)ch * K + sc) * 4;
+                    const Q4<T> b4 = ld4(a.bt + idx);
+                    Q4<T> x4, m4, u4;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const T vv = v[4 * q + e], yy = y[4 * q + e];
+                        const T xsv = (mode1 ? yy : vv - yy) + b4.v[e];
+                        const T mun = rho * (vv - xsv);
+                        x4.v[e] = xsv;
+                        m4.v[e] = mun;
+                        u4.v[e] = rho * xsv - mun;
+                    }
+                    st4(us + ((size_t)ch * K + sc) * 4, u4);
+                    if (check) {
+                        const int4 g4 = __ldg(a.chg + ch);
+                        const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
+                        const Q4<T> o4 = ld4(a.ds + idx);
+                        const Q4<T> l4 = ld4(a.lref + idx);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (gg[e] < 0) continue;
+                            const double xg = (double)xs[(gg[e] << ks) + sc];
+                            const double xsd = (double)x4.v[e];
+                            const double d0 = xg - xsd, d1 = xsd - (double)o4.v[e];
+                            const double xa = xsd + (double)a.xrf[gb + ((size_t)gg[e] << ks) + sc];
+                            const double la = (double)m4.v[e] + (double)l4.v[e];
+                            acc[0] += d0 * d0;
+                            acc[1] += d1 * d1;
+                            acc[3] += xa * xa;
+                            acc[4] += la * la;
+                        }
+                    }
+                    if (act) {
+                        st4(a.mu + idx, m4);
+                        if (wds) st4(a.ds + idx, x4);
+                    }
+                }
+            }
+        }
+        if (check) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                for (int o = K; o < 32; o <<= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+                if (lane < K) red[((size_t)w * K + lane) * 6 + q] = acc[q];
+                acc[q] = 0.0;
+            }
+            __syncthreads();
+            if (tid < K) {
+                flags[K + tid] = 0;
+                if (flags[tid]) {
+                    const int in = a.inst[c * K + tid];
+                    double s6[6] = {0, 0, 0, 0, 0, 0};
+                    for (int ww = 0; ww < a.n_warps; ++ww)
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) s6[q] += red[((size_t)ww * K + tid) * 6 + q];
+                    apply_test(&a.st[in], s6, a.rho_d, check_every);
+                    if (a.st[in].done) {
+                        flags[tid] = 0;
+                        flags[K + tid] = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            // x~ of instances that just finished (each thread its own items of G)
+            for (int item = tid; item < GK; item += nthr)
+                if (flags[K + (item & (K - 1))]) a.xo[gb + item] = xs[item];
+            last_check = it + 1;
+            int any = 0;
+            for (int q = 0; q < K; ++q) any |= flags[q];
+            if (!any) return;
+        } else {
+            __syncthreads();
+        }
+    }
+    if (tid < K && flags[tid]) a.st[a.inst[c * K + tid]].iter += n_iters - last_check;
+    for (int item = tid; item < GK; item += nthr)
+        if (flags[item & (K - 1)]) a.xo[gb + item] = xs[item];
+}
+
+// ============================================================ per-instance data
+// Engine column of an instance: ipos[inst] = c * K + sc (-1: not placed).
+
+// Start point of Sec. V-A for instances [i0, i0 + cnt): x_s = x0[g], lambda = 0.
+__global__ void k_binit(int i0, int cnt, int L, const int *gk, const double *x0, double *xs, double *lam,
+                        DevStatus *st, long long max_iter, double eps_rel, double eps_abs) {
+    const long long n = (long long)cnt * L;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int in = i0 + (int)(t / L), k = (int)(t % L);
+        xs[(size_t)in * L + k] = x0[gk[k]];
+        lam[(size_t)in * L + k] = 0.0;
+        if (k == 0) {
+            DevStatus z;
+            memset(&z, 0, sizeof(z));
+            z.max_iter = max_iter;
+            z.eps_rel = eps_rel;
+            z.eps_abs_pres = eps_abs;
+            st[in] = z;
+        }
+    }
+}
+
+__global__ void k_bfill(int cnt, int nrows, const double *b0, double *rhs) {
+    const long long n = (long long)cnt * nrows;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        rhs[t] = b0[t % nrows];
+}
+
+// rhs in device row order from canonical rows, or from load values.
+__global__ void k_brhs_perm(int i0, int cnt, int nrows, const int *c2d, const double *src, double *rhs) {
+    const long long n = (long long)cnt * nrows;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t / nrows), r = (int)(t % nrows);
+        rhs[(size_t)(i0 + j) * nrows + c2d[r]] = src[t];
+    }
+}
+
+__global__ void k_brhs_loads(int i0, int cnt, int nrows, int nload, const int *rsrc, const double *rcoef,
+                             const double *b0, const double *lp, const double *lq, double *rhs) {
+    const long long n = (long long)cnt * nrows;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t / nrows), r = (int)(t % nrows);
+        const int s = rsrc[r];
+        double v = b0[r];
+        if (s >= 0) {
+            const double *src = (s & 1) ? lq : lp;
+            v = rcoef[r] * src[(size_t)j * nload * 3 + (s >> 1)];
+        }
+        rhs[(size_t)(i0 + j) * nrows + r] = v;
+    }
+}
+
+// bbar = A_s^+ b per (instance, slot): slot k of device subsystem d = meta >> 8
+// at position meta & 255.
+__global__ void k_bbar(int i0, int cnt, int L, const int *meta, const int *sm, const int *boff,
+                       const long long *pioff, const double *pinv, int nrows, const double *rhs,
+                       double *bbar) {
+    const long long n = (long long)cnt * L;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int in = i0 + (int)(t / L), k = (int)(t % L);
+        const int d = meta[k] >> 8, cpos = meta[k] & 255, m = sm[d];
+        const double *P = pinv + pioff[d] + (long long)cpos * m;
+        const double *b = rhs + (size_t)in * nrows + boff[d];
+        double acc = 0.0;
+        for (int i = 0; i < m; ++i) acc += P[i] * b[i];
+        bbar[(size_t)in * L + k] = acc;
+    }
+}
+
+// Consistency of A_s x = b_s per instance: every rejected-row combination
+// must annihilate b_s (relative to the largest |b| of the subsystem).
+__global__ void k_bconsistent(int i0, int cnt, int S, const int *sm, const int *boff, const long long *toff,
+                              const int *nrej, const double *Tw, int nrows, const double *rhs, int *bad) {
+    const long long n = (long long)cnt * S;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int in = i0 + (int)(t / S), d = (int)(t % S);
+        const int m = sm[d], nr = nrej[d];
+        if (nr == 0) continue;
+        const double *b = rhs + (size_t)in * nrows + boff[d];
+        double bmax = 0.0;
+        for (int i = 0; i < m; ++i) bmax = fmax(bmax, fabs(b[i]));
+        const double *Tr = Tw + toff[d] + (long long)m * m;
+        for (int q = 0; q < nr; ++q) {
+            double acc = 0.0;
+            for (int i = 0; i < m; ++i) acc += Tr[(long long)q * m + i] * b[i];
+            if (!(fabs(acc) <= 1e-9 * (1.0 + bmax))) bad[in] = 1;
+        }
+    }
+}
+
+// ============================================================ re-centring
+// Per (instance, global), instances still running: x_ref = clip((sum over the
+// copies of rho x_s - lambda) - c) / (rho N)) in FP64 (the next global
+// update), c~ = c + sum lambda_ref, bounds - x_ref, all in the engine layout.
+template <typename T>
+__global__ void k_bref_globals(int n_inst, int G, int L, int K, int kshift, int NB, const int *ipos,
+                               const int2 *gseg, const int *uslot, const int *bidx, const double *c64,
+                               const double *lb, const double *ub, double rho, const double *xsv,
+                               const double *lam, DevStatus *st, double *xref, T *ct, T *xrf, T *lbt,
+                               T *ubt) {
+    const long long n = (long long)n_inst * G;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int in = (int)(t / G), i = (int)(t % G);
+        if (st[in].done || ipos[in] < 0) continue;
+        const int2 sg = gseg[i];
+        const double *xi = xsv + (size_t)in * L, *li = lam + (size_t)in * L;
+        double s = 0.0, ls = 0.0;
+        for (int q = 0; q < sg.y; ++q) {
+            const int k = uslot[sg.x + q];
+            s += rho * xi[k] - li[k];
+            ls += li[k];
+        }
+        double x = (s - c64[i]) / (rho * sg.y);
+        x = fmin(fmax(x, lb[i]), ub[i]);
+        xref[(size_t)in * G + i] = x;
+        const int pos = ipos[in], cc = pos >> kshift, sc = pos & (K - 1);
+        const size_t e = ((size_t)cc * G + i) * K + sc;
+        ct[e] = (T)(c64[i] + ls);
+        xrf[e] = (T)x;
+        const int b = bidx[i];
+        if (b >= 0) {
+            const size_t eb = ((size_t)cc * NB + b) * K + sc;
+            lbt[eb] = (T)(lb[i] - x);
+            ubt[eb] = (T)(ub[i] - x);
+        }
+        if (i == 0) st[in].pad = 1;     // shifted: unshift after the engine
+    }
+}
+
+// Per (subsystem, instance), one warp: bbar~ = M (x_ref[g] + lambda_ref / rho)
+// + bbar - x_ref[g], d = x_s - x_ref[g], mu = 0, lambda_ref, in the engine layout.
+template <typename T>
+__global__ void __launch_bounds__(128) k_bref_slots(int S, int n_inst, int G, int L, int K, int kshift, int NCH,
+                                                    const int *ipos, const int4 *sub, const int4 *sub2,
+                                                    const double *F64, const int *gk, const int *sch,
+                                                    double rho, const double *xref, const double *xsv,
+                                                    const double *lam, const double *bbar,
+                                                    const DevStatus *st, T *bt, T *ds, T *mu, T *lref) {
+    __shared__ double buf[4][2][OPF_MAX_NS];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long task = (long long)blockIdx.x * 4 + wl;
+    if (task >= (long long)S * n_inst) return;
+    const int in = (int)(task / S), d = (int)(task % S);
+    if (st[in].done || ipos[in] < 0) return;
+    const int4 h = sub[d], q2 = sub2[d];
+    const int so = h.x, n = h.y, f = h.z, mode = h.w, npad = q2.y;
+    const double *Fs = F64 + q2.x;
+    const double *xr = xref + (size_t)in * G;
+    const double *xi = xsv + (size_t)in * L, *li = lam + (size_t)in * L, *bi = bbar + (size_t)in * L;
+    double *v = buf[wl][0], *tt = buf[wl][1];
+    for (int r = lane; r < n; r += 32) v[r] = xr[gk[so + r]] + li[so + r] / rho;
+    __syncwarp();
+    for (int cc = lane; cc < f; cc += 32) {
+        double acc = 0.0;
+        for (int r = 0; r < n; ++r) acc += Fs[(long long)cc * npad + r] * v[r];
+        tt[cc] = acc;
+    }
+    __syncwarp();
+    const int pos = ipos[in], cta = pos >> kshift, sc = pos & (K - 1);
+    for (int r = lane; r < n; r += 32) {
+        double yv = 0.0;
+        for (int cc = 0; cc < f; ++cc) yv += Fs[(long long)cc * npad + r] * tt[cc];
+        const double mv = mode ? yv : v[r] - yv;
+        const int k = so + r;
+        const double xg = xr[gk[k]];
+        const int p = sch[k];
+        const size_t e = (((size_t)cta * NCH + (p >> 2)) * K + sc) * 4 + (p & 3);
+        bt[e] = (T)(mv + bi[k] - xg);
+        ds[e] = (T)(xi[k] - xg);
+        mu[e] = T(0);
+        lref[e] = (T)li[k];
+    }
+}
+
+// Back to the unshifted FP64 state for instances that ran (status pad = 1).
+template <typename T>
+__global__ void k_bunshift_slots(int n_inst, int G, int L, int K, int kshift, int NCH, const int *ipos,
+                                 const int *gk, const int *sch, const double *xref, const T *ds, const T *mu,
+                                 const DevStatus *st, double *xsv, double *lam) {
+    const long long n = (long long)n_inst * L;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int in = (int)(t / L), k = (int)(t % L);
+        if (!st[in].pad || ipos[in] < 0) continue;
+        const int pos = ipos[in], cta = pos >> kshift, sc = pos & (K - 1);
+        const int p = sch[k];
+        const size_t e = (((size_t)cta * NCH + (p >> 2)) * K + sc) * 4 + (p & 3);
+        xsv[(size_t)in * L + k] = xref[(size_t)in * G + gk[k]] + (double)ds[e];
+        lam[(size_t)in * L + k] += (double)mu[e];
+    }
+}
+
+template <typename T>
+__global__ void k_bunshift_globals(int n_inst, int G, int K, int kshift, const int *ipos, const double *xref,
+                                   const T *xo, const DevStatus *st, double *x) {
+    const long long n = (long long)n_inst * G;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int in = (int)(t / G), i = (int)(t % G);
+        if (!st[in].pad || ipos[in] < 0) continue;
+        const int pos = ipos[in], cta = pos >> kshift, sc = pos & (K - 1);
+        x[(size_t)in * G + i] = xref[(size_t)in * G + i] + (double)xo[((size_t)cta * G + i) * K + sc];
+    }
+}
+
+// Clears the shifted marks; flag = 1 while some instance still runs (and the
+// graph condition, when a conditional node drives the loop).
+__global__ void k_bany(int n_inst, DevStatus *st, int *flag, cudaGraphConditionalHandle cond, int use_cond) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        st[i].pad = 0;
+        mine |= st[i].done ? 0 : 1;
+    }
+    if (mine) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *flag = any;
+        if (use_cond) cudaGraphSetConditional(cond, any ? 1u : 0u);
+    }
+}
+
+// Objective c^T x per instance (one warp each, fixed order).
+__global__ void k_bobjective(int n_inst, int G, const double *c64, const double *x, double *obj) {
+    const int wg = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (wg >= n_inst) return;
+    double s = 0.0;
+    for (int i = lane; i < G; i += 32) s += c64[i] * x[(size_t)wg * G + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) obj[wg] = s;
+}
+
+// Prepares the polish: instances that stopped without a numeric failure run again.
+__global__ void k_brestart(int n_inst, DevStatus *st, long long add_max) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst; i += gridDim.x * blockDim.x) {
+        if (st[i].numeric) continue;
+        st[i].done = 0;
+        st[i].converged = 0;
+        if (st[i].max_iter < st[i].iter + add_max) st[i].max_iter = st[i].iter + add_max;
+    }
+}
+
+// Factors packed per task: element (r, q, jpos, e) of task t from the FP64
+// factor of member mb = jpos >> lp (tmem[t * J + mb], -1: none), slot
+// c = ((jpos & (p-1)) * nq + q) * 4 + e.
+template <typename T>
+__global__ void k_bpack(int n_tasks, int J, const BatchTask *tasks, const int *tmem, const int4 *sub,
+                        const int4 *sub2, const double *F64, T *dst) {
+    const int t = blockIdx.x;
+    if (t >= n_tasks) return;
+    const BatchTask tk = tasks[t];
+    const int n = tk.f * tk.nq * J * 4;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        const int e = x & 3, jpos = (x >> 2) % J, q = (x / (4 * J)) % tk.nq, r = x / (4 * J * tk.nq);
+        const int mb = jpos >> tk.lp, part = jpos & (tk.p - 1);
+        const int d = tmem[t * J + mb];
+        double v = 0.0;
+        if (d >= 0) {
+            const int4 h = sub[d], q2 = sub2[d];
+            const int cpos = (part * tk.nq + q) * 4 + e;
+            if (r < h.z && cpos < h.y) v = F64[q2.x + (long long)r * q2.y + cpos];
+        }
+        dst[tk.foff + x] = (T)v;
+    }
+}
+
+// ============================================================ launchers
+static inline int bl(long long n, int t) {
+    long long b = (n + t - 1) / t;
+    if (b < 1) b = 1;
+    if (b > 8192) b = 8192;
+    return (int)b;
+}
+
+template <typename T, int NQ>
+static int set_engine_smem(unsigned bytes) {
+    return cudaFuncSetAttribute(k_batch_engine<T, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+                   cudaSuccess ? 0 : -1;
+}
+
+template <typename T>
+int batch_engine_prepare(int nq, unsigned bytes) {
+    switch (nq) {
+        case 1: return set_engine_smem<T, 1>(bytes);
+        case 2: return set_engine_smem<T, 2>(bytes);
+        case 4: return set_engine_smem<T, 4>(bytes);
+        default: return -1;
+    }
+}
+
+template <typename T>
+int batch_engine_launch(const BatchArgs<T> &a, int nq, int ctas, int threads, unsigned bytes, int n_iters,
+                        int check_every, cudaStream_t s) {
+    switch (nq) {
+        case 1: k_batch_engine<T, 1><<<ctas, threads, bytes, s>>>(a, n_iters, check_every); break;
+        case 2: k_batch_engine<T, 2><<<ctas, threads, bytes, s>>>(a, n_iters, check_every); break;
+        case 4: k_batch_engine<T, 4><<<ctas, threads, bytes, s>>>(a, n_iters, check_every); break;
+        default: return -1;
+    }
+    return 0;
+}
+
+template <typename T>
+int batch_engine_max_ctas_per_sm(int nq, int threads, unsigned bytes) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (nq) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_engine<T, 1>, threads, bytes); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_engine<T, 2>, threads, bytes); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_engine<T, 4>, threads, bytes); break;
+        default: break;
+    }
+    return e == cudaSuccess ? n : -1;
+}
+
+template int batch_engine_prepare<float>(int, unsigned);
+template int batch_engine_prepare<double>(int, unsigned);
+template int batch_engine_launch<float>(const BatchArgs<float> &, int, int, int, unsigned, int, int, cudaStream_t);
+template int batch_engine_launch<double>(const BatchArgs<double> &, int, int, int, unsigned, int, int, cudaStream_t);
+template int batch_engine_max_ctas_per_sm<float>(int, int, unsigned);
+template int batch_engine_max_ctas_per_sm<double>(int, int, unsigned);
+
+void launch_binit(int i0, int cnt, int L, const int *gk, const double *x0, double *xs, double *lam,
+                  DevStatus *st, long long max_iter, double eps_rel, double eps_abs, cudaStream_t s) {
+    k_binit<<<bl((long long)cnt * L, 256), 256, 0, s>>>(i0, cnt, L, gk, x0, xs, lam, st, max_iter, eps_rel, eps_abs);
+}
+
+void launch_bfill(int cnt, int nrows, const double *b0, double *rhs, cudaStream_t s) {
+    k_bfill<<<bl((long long)cnt * nrows, 256), 256, 0, s>>>(cnt, nrows, b0, rhs);
+}
+
+void launch_brhs_perm(int i0, int cnt, int nrows, const int *c2d, const double *src, double *rhs, cudaStream_t s) {
+    k_brhs_perm<<<bl((long long)cnt * nrows, 256), 256, 0, s>>>(i0, cnt, nrows, c2d, src, rhs);
+}
+
+void launch_brhs_loads(int i0, int cnt, int nrows, int nload, const int *rsrc, const double *rcoef,
+                       const double *b0, const double *lp, const double *lq, double *rhs, cudaStream_t s) {
+    k_brhs_loads<<<bl((long long)cnt * nrows, 256), 256, 0, s>>>(i0, cnt, nrows, nload, rsrc, rcoef, b0, lp, lq, rhs);
+}
+
+void launch_bbar(int i0, int cnt, int L, const int *meta, const int *sm, const int *boff, const long long *pioff,
+                 const double *pinv, int nrows, const double *rhs, double *bbar, cudaStream_t s) {
+    k_bbar<<<bl((long long)cnt * L, 256), 256, 0, s>>>(i0, cnt, L, meta, sm, boff, pioff, pinv, nrows, rhs, bbar);
+}
+
+void launch_bconsistent(int i0, int cnt, int S, const int *sm, const int *boff, const long long *toff,
+                        const int *nrej, const double *Tw, int nrows, const double *rhs, int *bad, cudaStream_t s) {
+    k_bconsistent<<<bl((long long)cnt * S, 128), 128, 0, s>>>(i0, cnt, S, sm, boff, toff, nrej, Tw, nrows, rhs, bad);
+}
+
+template <typename T>
+void launch_bref(int n_inst, int S, int G, int L, int K, int kshift, int NCH, int NB, const int *ipos,
+                 const int2 *gseg, const int *uslot, const int *bidx, const double *c64, const double *lb,
+                 const double *ub, double rho, const double *xsv, const double *lam, DevStatus *st,
+                 double *xref, T *ct, T *xrf, T *lbt, T *ubt, const int4 *sub, const int4 *sub2,
+                 const double *F64, const int *gk, const int *sch, const double *bbar, T *bt, T *ds, T *mu,
+                 T *lref, cudaStream_t s) {
+    k_bref_globals<T><<<bl((long long)n_inst * G, 256), 256, 0, s>>>(n_inst, G, L, K, kshift, NB, ipos, gseg, uslot,
+                                                                    bidx, c64, lb, ub, rho, xsv, lam, st, xref,
+                                                                    ct, xrf, lbt, ubt);
+    const long long warps = (long long)S * n_inst;
+    k_bref_slots<T><<<(int)((warps + 3) / 4), 128, 0, s>>>(S, n_inst, G, L, K, kshift, NCH, ipos, sub, sub2, F64,
+                                                           gk, sch, rho, xref, xsv, lam, bbar, st, bt, ds, mu, lref);
+}
+
+template <typename T>
+void launch_bunshift(int n_inst, int G, int L, int K, int kshift, int NCH, const int *ipos, const int *gk,
+                     const int *sch, const double *xref, const T *ds, const T *mu, const T *xo,
+                     const DevStatus *st, double *xsv, double *lam, double *x, cudaStream_t s) {
+    k_bunshift_slots<T><<<bl((long long)n_inst * L, 256), 256, 0, s>>>(n_inst, G, L, K, kshift, NCH, ipos, gk, sch,
+                                                                      xref, ds, mu, st, xsv, lam);
+    k_bunshift_globals<T><<<bl((long long)n_inst * G, 256), 256, 0, s>>>(n_inst, G, K, kshift, ipos, xref, xo, st, x);
+}
+
+template void launch_bref<float>(int, int, int, int, int, int, int, int, const int *, const int2 *, const int *,
+                                 const int *, const double *, const double *, const double *, double,
+                                 const double *, const double *, DevStatus *, double *, float *, float *,
+                                 float *, float *, const int4 *, const int4 *, const double *, const int *,
+                                 const int *, const double *, float *, float *, float *, float *, cudaStream_t);
+template void launch_bref<double>(int, int, int, int, int, int, int, int, const int *, const int2 *, const int *,
+                                  const int *, const double *, const double *, const double *, double,
+                                  const double *, const double *, DevStatus *, double *, double *, double *,
+                                  double *, double *, const int4 *, const int4 *, const double *, const int *,
+                                  const int *, const double *, double *, double *, double *, double *,
+                                  cudaStream_t);
+template void launch_bunshift<float>(int, int, int, int, int, int, const int *, const int *, const int *,
+                                     const double *, const float *, const float *, const float *,
+                                     const DevStatus *, double *, double *, double *, cudaStream_t);
+template void launch_bunshift<double>(int, int, int, int, int, int, const int *, const int *, const int *,
+                                      const double *, const double *, const double *, const double *,
+                                      const DevStatus *, double *, double *, double *, cudaStream_t);
+
+void launch_bany(int n_inst, DevStatus *st, int *flag, cudaGraphConditionalHandle cond, int use_cond,
+                 cudaStream_t s) {
+    k_bany<<<1, 1024, 0, s>>>(n_inst, st, flag, cond, use_cond);
+}
+
+void launch_bobjective(int n_inst, int G, const double *c64, const double *x, double *obj, cudaStream_t s) {
+    k_bobjective<<<bl((long long)n_inst * 32, 256), 256, 0, s>>>(n_inst, G, c64, x, obj);
+}
+
+void launch_brestart(int n_inst, DevStatus *st, long long add_max, cudaStream_t s) {
+    k_brestart<<<bl(n_inst, 256), 256, 0, s>>>(n_inst, st, add_max);
+}
+
+template <typename T>
+void launch_bpack(int n_tasks, int J, const BatchTask *tasks, const int *tmem, const int4 *sub, const int4 *sub2,
+                  const double *F64, T *dst, cudaStream_t s) {
+    if (n_tasks > 0) k_bpack<T><<<n_tasks, 256, 0, s>>>(n_tasks, J, tasks, tmem, sub, sub2, F64, dst);
+}
+template void launch_bpack<float>(int, int, const BatchTask *, const int *, const int4 *, const int4 *,
+                                  const double *, float *, cudaStream_t);
+template void launch_bpack<double>(int, int, const BatchTask *, const int *, const int4 *, const int4 *,
+                                   const double *, double *, cudaStream_t);
+
+}  // namespace opf

@@ -32,6 +32,7 @@
 #include <cstring>
 
 #include "opf_internal.h"
+#include "test_rule.cuh"
 
 namespace opf {
 
@@ -115,6 +116,16 @@ __global__ void __launch_bounds__(32) k_precompute(PreArgs a) {
     for (int j = lane; j < m; j += 32) bmax = fmax(bmax, fabs(beta[j]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    // T (optional): the identity under the same row operations, so that beta = T b
+    const bool want_t = a.pinv != nullptr;
+    double *Ta = nullptr, *Tr = nullptr;
+    if (want_t) {
+        Ta = a.Tw + a.toff[s];
+        Tr = Ta + (long long)m * m;
+        for (int i = lane; i < m * m; i += 32) Ta[i] = (i / m == i % m) ? 1.0 : 0.0;
+        __syncwarp();
+    }
+    int nrj = 0;
     // classical Gram-Schmidt, applied twice, on the rows; b follows the same operations
     int r = 0, bad = 0;
     for (int j = 0; j < m; ++j) {
@@ -136,6 +147,8 @@ __global__ void __launch_bounds__(32) k_precompute(PreArgs a) {
                     if (t < T && c < n) v[t] -= ck * Q[(long long)k * n + c];
                 }
                 bj -= ck * beta[k];
+                if (want_t)
+                    for (int i = lane; i < m; i += 32) Ta[(long long)j * m + i] -= ck * Ta[(long long)k * m + i];
             }
             __syncwarp();
         }
@@ -149,10 +162,28 @@ __global__ void __launch_bounds__(32) k_precompute(PreArgs a) {
             }
             __syncwarp();
             if (lane == 0) beta[r] = bj * inv;
+            if (want_t)
+                for (int i = lane; i < m; i += 32) Ta[(long long)r * m + i] = Ta[(long long)j * m + i] * inv;
             ++r;
-        } else if (fabs(bj) > 1e-9 * (1.0 + bmax)) {
-            bad = 1;
+        } else {
+            if (want_t) {
+                for (int i = lane; i < m; i += 32) Tr[(long long)nrj * m + i] = Ta[(long long)j * m + i];
+                ++nrj;
+            }
+            if (fabs(bj) > 1e-9 * (1.0 + bmax)) bad = 1;
         }
+        __syncwarp();
+    }
+    // A_s^+ = Q^T T_acc (n x m)
+    if (want_t) {
+        double *Pi = a.pinv + a.pioff[s];
+        for (int c = lane; c < n; c += 32)
+            for (int i = 0; i < m; ++i) {
+                double acc = 0.0;
+                for (int k = 0; k < r; ++k) acc += Q[(long long)k * n + c] * Ta[(long long)k * m + i];
+                Pi[(long long)c * m + i] = acc;
+            }
+        if (lane == 0) a.nrej[s] = nrj;
         __syncwarp();
     }
     // bbar = sum_k beta_k q_k
@@ -431,26 +462,6 @@ __global__ void __launch_bounds__(256) k_tile_iter(IterArgs<T> a, const T *__res
 #pragma unroll
             for (int q = 0; q < 6; ++q) partials[blockIdx.x * 6 + q] = acc[q];
     }
-}
-
-// Stopping test of Sec. III-C (plus the absolute gate on pres).
-__device__ void apply_test(DevStatus *st, const double s[6], double rho, long long add_iters) {
-    const double pres = sqrt(s[0]);
-    const double dres = rho * sqrt(s[1]);
-    const double eprim = fmax(sqrt(s[2]), sqrt(s[3]));
-    const double edual = sqrt(s[4]);
-    st->iter += add_iters;
-    st->pres = pres;
-    st->dres = dres;
-    st->eprim = eprim;
-    st->edual = edual;
-    st->obj = s[5];
-    bool finite = true;
-    for (int q = 0; q < 6; ++q) finite = finite && isfinite(s[q]);
-    st->numeric = finite ? 0 : 1;
-    st->converged = (finite && pres <= st->eps_rel * eprim && dres <= st->eps_rel * edual &&
-                     pres <= st->eps_abs_pres) ? 1 : 0;
-    if (st->converged || st->numeric || st->iter >= st->max_iter) st->done = 1;
 }
 
 // Fixed-order reduction of the per-block partials (deterministic).

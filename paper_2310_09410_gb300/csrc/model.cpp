@@ -38,6 +38,8 @@ inline bool has(unsigned m, int p) { return (m >> p) & 1u; }
 struct Row {
     std::vector<std::pair<int, double>> a;
     double rhs = 0.0;
+    int src = -1;          // rhs = coef * (load value src), see HostSub::rsrc
+    double coef = 0.0;
     void add(int v, double x) { a.emplace_back(v, x); }
 };
 
@@ -139,6 +141,7 @@ int build_feeder_model(const opf_feeder *f, HostModel *out, std::string *err) {
             for (int q = 0; q < 4; ++q) push(-inf, inf, 0.0, 0);
     }
     M.n = nv;
+    M.n_load = nd;
     for (int v = 0; v < nv; ++v)
         if (!(M.lb[v] <= M.ub[v]) || std::isnan(M.c[v])) return fail(err, "empty or NaN bound / cost");
 
@@ -188,8 +191,11 @@ int build_feeder_model(const opf_feeder *f, HostModel *out, std::string *err) {
                 // p^d linear in w_hat around w_hat = 1 with slope a*alpha/2
                 Row r1; r1.add(vload(l, p, PD), 1.0); r1.add(vbus(i, p), -0.5 * a * al * wscale);
                 r1.rhs = a * (1.0 - 0.5 * al);
+                r1.src = 2 * (3 * l + p); r1.coef = 1.0 - 0.5 * al;
                 Row r2; r2.add(vload(l, p, QD), 1.0); r2.add(vbus(i, p), -0.5 * b * be * wscale);
                 r2.rhs = b * (1.0 - 0.5 * be);
+                r2.src = 2 * (3 * l + p) + 1; r2.coef = 1.0 - 0.5 * be;
+                if (al != 0.0 || be != 0.0) M.A_depends_on_loads = true;
                 rows.push_back(r1); rows.push_back(r2);
             }
             if (!delta) {
@@ -259,11 +265,15 @@ int build_feeder_model(const opf_feeder *f, HostModel *out, std::string *err) {
         s.m = (int)rows.size();
         s.A.assign((size_t)s.m * s.n, 0.0);
         s.b.resize(s.m);
+        s.rsrc.resize(s.m);
+        s.rcoef.resize(s.m);
         std::map<int, int> col;
         for (int k = 0; k < s.n; ++k) col[s.vars[k]] = k;
         for (int r = 0; r < s.m; ++r) {
             for (auto &t : rows[r].a) s.A[(size_t)r * s.n + col.at(t.first)] += t.second;
             s.b[r] = rows[r].rhs;
+            s.rsrc[r] = rows[r].src;
+            s.rcoef[r] = rows[r].coef;
         }
         M.subs.push_back(std::move(s));
     };

@@ -22,10 +22,16 @@ struct HostSub {
     int m = 0, n = 0;
     std::vector<int> vars;
     std::vector<double> A, b;
+    // per row: which load value the right-hand side is proportional to
+    // (-1: a constant; else 2 * (3 * load + phase) + 0 for a, 1 for b) and the factor
+    std::vector<int> rsrc;
+    std::vector<double> rcoef;
 };
 
 struct HostModel {
     int n = 0;
+    int n_load = 0;               // feeder loads (0 for generic models)
+    bool A_depends_on_loads = false;   // a ZIP exponent makes A_s a function of the load values
     std::vector<double> c, lb, ub;
     std::vector<uint8_t> volt;
     std::vector<HostSub> subs;   // canonical subsystem order
@@ -112,6 +118,14 @@ struct PreArgs {
     double *F;          // out: factor, column-major n x f
     int *sf, *smode;    // out
     double *bbar;       // out: per slot
+    // optional (pinv != nullptr): the same row operations applied to the
+    // identity give T with beta = T b; pinv = Q^T T_acc = A_s^+ (n x m,
+    // row-major at pioff[s]) and the rejected rows' combinations T_rej
+    // (rows 0 .. nrej[s]-1 of the m x m block at Tw + toff[s] + m*m), whose
+    // products with b_s vanish exactly when A_s x = b_s is consistent
+    double *Tw, *pinv;
+    const long long *toff, *pioff;
+    int *nrej;
     int *status;        // out: 0 ok, 1 inconsistent local system
 };
 
@@ -130,6 +144,49 @@ struct WarpLayout {
     int P, L, S, useg_len, fbig_len;
     unsigned off_useg, off_dd, off_fbig, off_vbig, off_red;
     unsigned bytes;
+};
+
+// ------------------------------------------------------------ batched engine
+// One warp task of the batched engine.  Lanes are (member position jpos,
+// instance column sc), lane = jpos * K + sc, J * K = 32.  A member subsystem
+// spans p = 2^lp consecutive positions; position jpos holds chunks
+// (part * nq + q), q < nq, of its member's slots, part = jpos % p, 4 slots
+// per chunk.  Chunk (q, jpos) of the task is chunk ch0 + q * J + jpos of the
+// CTA's chunk array.
+struct BatchTask {
+    int ch0;     // first chunk
+    int nq;      // chunks per position
+    int f;       // factor rows (maximum over the members; absent rows are zero)
+    int foff;    // factor element (r, q, jpos, e) at foff + ((r * nq + q) * J + jpos) * 4 + e
+    int p, lp;   // positions per member and log2(p)
+    int modes;   // bit mb: member mb uses M = F^T F (1) or M = I - F^T F (0)
+    int pad;
+};
+
+// Arguments of one batched-engine launch.  Instance column sc of CTA c holds
+// instance inst[c * K + sc] (-1: empty).  Engine arrays (type T):
+//   per slot      [c][NCH][K][4]   mu, ds, bt (bbar~), lref (lambda_ref)
+//   per global    [c][G][K]        ct (c~), xrf (x_ref), xo (x~ at the end)
+//   per bounded   [c][NB][K]       lbt, ubt (bounds - x_ref)
+template <typename T>
+struct BatchArgs {
+    int K, kshift, J, NCH, G, NB, n_warps, nF;
+    unsigned off_u, off_x, off_red, off_flag;   // shared-memory byte offsets
+    const BatchTask *tasks;
+    const int *wtask;          // [n_warps + 1] ranges into tlist
+    const int *tlist;
+    const int4 *chg;           // [NCH] global of each chunk's 4 slots (-1: padding)
+    const int4 *gtab;          // [G] (first copy in useg, copies, bounded index or -1, 0)
+    const int *useg;           // copies of each global: u offset ch * K * 4 + e
+    const T *Fpk;              // [nF] factors, task-interleaved
+    const T *recip;            // [G] 1 / (rho N_i)
+    const T *cost;             // [G] c_i
+    T *mu, *ds, *xo;
+    const T *bt, *lref, *ct, *xrf, *lbt, *ubt;
+    const int *inst;
+    DevStatus *st;             // per instance
+    T rho, inv_rho;
+    double rho_d;
 };
 
 }  // namespace opf

@@ -98,9 +98,27 @@ def load(path: str = LIB_PATH):
     lib.opf_last_error.argtypes = []
     lib.opf_last_error.restype = C.c_char_p
     lib.opf_global_update_static.argtypes = [C.c_int32, _P, _P, _P, _P, _P, C.c_double, _P, _P, _P]
+    lib.opf_batch_create.argtypes = [H, C.c_int32, C.POINTER(H)]
+    lib.opf_batch_set_rhs.argtypes = [H, C.c_int32, C.c_int32, _P]
+    lib.opf_batch_set_loads.argtypes = [H, C.c_int32, C.c_int32, _P, _P]
+    lib.opf_batch_solve.argtypes = [H, C.POINTER(SolveOpts)]
+    lib.opf_batch_step.argtypes = [H, C.c_double, C.c_int32]
+    lib.opf_batch_set_shape.argtypes = [H, C.c_int32, C.c_int32, C.c_int32]
+    lib.opf_batch_get_shape.argtypes = [H, C.c_int32, _P, C.c_int32]
+    lib.opf_batch_get_solution.argtypes = [H, C.c_int32, C.c_int32, _P, _P]
+    lib.opf_batch_get_status.argtypes = [H, C.c_int32, C.c_int32, _P, _P, _P]
+    lib.opf_batch_get_locals.argtypes = [H, C.c_int32, _P, _P]
+    lib.opf_batch_get_timing.argtypes = [H, _P, C.c_int32]
+    lib.opf_batch_get_tune_log.argtypes = [H, _P, C.c_int32]
+    lib.opf_batch_destroy.argtypes = [H]
+    lib.opf_batch_destroy.restype = None
     for name in ("opf_create", "opf_create_generic", "opf_precompute", "opf_solve", "opf_solve_ex",
                  "opf_step", "opf_reset", "opf_get_solution", "opf_get_residuals", "opf_get_locals",
-                 "opf_set_locals", "opf_get_sizes", "opf_get_timing", "opf_global_update_static"):
+                 "opf_set_locals", "opf_get_sizes", "opf_get_timing", "opf_global_update_static",
+                 "opf_batch_create", "opf_batch_set_rhs", "opf_batch_set_loads", "opf_batch_solve",
+                 "opf_batch_step", "opf_batch_set_shape", "opf_batch_get_shape", "opf_batch_get_solution",
+                 "opf_batch_get_status", "opf_batch_get_locals", "opf_batch_get_timing",
+                 "opf_batch_get_tune_log"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -278,6 +296,106 @@ class Solver:
         if self._h:
             load().opf_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Many instances of one model (wraps an ``opf_batch``): every instance
+    shares the solver's A_s, c and bounds and has its own right-hand side."""
+
+    def __init__(self, solver: "Solver", n_inst: int):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.opf_batch_create(solver._h, int(n_inst), C.byref(h)), "opf_batch_create")
+        self._b = h
+        self._solver = solver           # the batch refers to the handle: keep it alive
+        self.n = int(n_inst)
+        sz = solver.sizes()
+        self.n_global, self.n_slots, self.n_rows = sz["n_global"], sz["n_slots"], sz["n_rows"]
+
+    def set_rhs(self, first, rhs):
+        rhs = np.ascontiguousarray(rhs, np.float64).reshape(-1, self.n_rows)
+        _check(load().opf_batch_set_rhs(self._b, int(first), rhs.shape[0], _ptr(rhs)), "opf_batch_set_rhs")
+
+    def set_loads(self, first, load_p, load_q):
+        """load_p, load_q: [count, n_load, 3] (like feeder load_a / load_b)."""
+        lp = np.ascontiguousarray(load_p, np.float64)
+        lq = np.ascontiguousarray(load_q, np.float64)
+        if lp.shape != lq.shape or lp.ndim != 3 or lp.shape[2] != 3:
+            raise ValueError("load arrays must both be [count, n_load, 3]")
+        _check(load().opf_batch_set_loads(self._b, int(first), lp.shape[0], _ptr(lp), _ptr(lq)),
+               "opf_batch_set_loads")
+
+    def set_shape(self, precision, k_inst=0, warps=0):
+        _check(load().opf_batch_set_shape(self._b, int(precision), int(k_inst), int(warps)), "opf_batch_set_shape")
+
+    def shape(self, precision=PREC_FP32):
+        out = np.zeros(8, np.int32)
+        _check(load().opf_batch_get_shape(self._b, int(precision), _ptr(out), 8), "opf_batch_get_shape")
+        keys = ("ok", "k_inst", "warps", "chunks_per_lane", "tasks", "chunks", "smem_bytes", "ctas")
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def solve(self, rho=100.0, eps_rel=1e-8, eps_abs_pres=1e-4, max_iter=1_000_000, check_every=50,
+              precision=PREC_MIXED, recenter_every=0, flags=0):
+        o = SolveOpts(rho, eps_rel, eps_abs_pres, int(max_iter), int(check_every), int(precision),
+                      int(recenter_every), 0, int(flags), 0)
+        rc = load().opf_batch_solve(self._b, C.byref(o))
+        _check(rc, "opf_batch_solve", ok=(OPF_OK, OPF_NOT_CONVERGED))
+        return rc == OPF_OK
+
+    def step(self, n_iters, rho=100.0):
+        _check(load().opf_batch_step(self._b, float(rho), int(n_iters)), "opf_batch_step")
+
+    def solution(self, first=0, count=None):
+        count = self.n - first if count is None else count
+        x = np.zeros((count, self.n_global))
+        obj = np.zeros(count)
+        _check(load().opf_batch_get_solution(self._b, int(first), int(count), _ptr(x), _ptr(obj)),
+               "opf_batch_get_solution")
+        return x, obj
+
+    def status(self, first=0, count=None):
+        count = self.n - first if count is None else count
+        res = np.zeros((count, 4))
+        it = np.zeros(count, np.int32)
+        conv = np.zeros(count, np.int32)
+        _check(load().opf_batch_get_status(self._b, int(first), int(count), _ptr(res), _ptr(it), _ptr(conv)),
+               "opf_batch_get_status")
+        return {"pres": res[:, 0], "dres": res[:, 1], "eps_prim": res[:, 2], "eps_dual": res[:, 3],
+                "iters": it, "converged": conv.astype(bool)}
+
+    def locals(self, inst):
+        xs, lam = np.zeros(self.n_slots), np.zeros(self.n_slots)
+        _check(load().opf_batch_get_locals(self._b, int(inst), _ptr(xs), _ptr(lam)), "opf_batch_get_locals")
+        return xs, lam
+
+    def timing(self):
+        t = np.zeros(8)
+        _check(load().opf_batch_get_timing(self._b, _ptr(t), 8), "opf_batch_get_timing")
+        return {"fp32_ms": t[0], "fp64_ms": t[1], "tune_ms": t[2], "mean_iters": t[3], "converged": int(t[4])}
+
+    def tune_log(self):
+        lib = load()
+        n = lib.opf_batch_get_tune_log(self._b, None, 0)
+        out = np.zeros(max(n, 1))
+        lib.opf_batch_get_tune_log(self._b, _ptr(out), n)
+        return [(int(out[i]), int(out[i + 1]), float(out[i + 2])) for i in range(0, n, 3)]
+
+    def close(self):
+        if self._b:
+            load().opf_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

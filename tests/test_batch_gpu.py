@@ -1,0 +1,183 @@
+"""GPU parity of batched solves (many load scenarios of one feeder) through the C ABI.
+
+* FP64 iterates of every instance after 100 iterations within 1e-10 relative of
+  the oracle run on that instance's own model (scenario loads in the rhs);
+* FP32 iterations stay within single-precision distance of the oracle;
+* mixed-precision solves reach each instance's LP optimum within 1e-6 relative
+  with pres <= 1e-4, on small batches and on the full 1024-scenario batch
+  (sampled instances checked against the oracle one by one).
+"""
+import numpy as np
+import pytest
+
+from oracle import admm as oracle_admm, lindist
+from paper_2310_09410_gb300 import opf, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_ITER = 1e-10
+TOL_OBJ = 1e-6
+TOL_PRES = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
+
+
+def scenarios(f, seeds):
+    return [synth.load_scenario(f, s) for s in seeds]
+
+
+def load_arrays(fs):
+    return (np.stack([g["load_a"] for g in fs]), np.stack([g["load_b"] for g in fs]))
+
+
+def oracle_iterates(M, iters, rho=100.0):
+    return oracle_admm.admm(oracle_admm.Prepared(M), rho=rho, max_iter=iters, check_every=0)
+
+
+@pytest.mark.parametrize("name,seed,n_scen,k64", [("123", 2001, 6, 4), ("13", 1001, 5, 2), ("34", 5034, 3, 1)])
+def test_fp64_batch_iterates_match_oracle(name, seed, n_scen, k64):
+    f = synth.preset_feeder(name, seed)
+    fs = scenarios(f, [4000 + j for j in range(n_scen)])
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        with opf.Batch(s, n_scen + 1) as b:            # the last instance keeps the feeder's own loads
+            b.set_shape(opf.PREC_FP64, k64)
+            lp, lq = load_arrays(fs)
+            b.set_loads(0, lp, lq)
+            b.step(100)
+            for j, g in enumerate(fs + [f]):
+                ref = oracle_iterates(lindist.build(g), 100)
+                xs, lam = b.locals(j)
+                assert rel_err(xs, ref.xs) <= TOL_ITER, j
+                assert rel_err(lam, ref.lam) <= TOL_ITER, j
+            x, obj = b.solution()
+            ref = oracle_iterates(lindist.build(fs[0]), 100)
+            assert rel_err(x[0], ref.x) <= TOL_ITER
+            assert abs(obj[0] - ref.objective) <= TOL_ITER * max(1.0, abs(ref.objective))
+
+
+def test_fp64_batch_generic_rank_deficient_rhs():
+    g = synth.random_generic(4, max_n=40, n_global=120)
+    M = lindist.from_generic(g)
+    rng = np.random.default_rng(9)
+    with opf.Solver.from_generic(g["c"], g["lb"], g["ub"], g["subs"]) as s:
+        s.precompute()
+        with opf.Batch(s, 3) as b:
+            rhs, models = [], []
+            for j in range(3):
+                subs = []
+                for sub in g["subs"]:
+                    A = np.asarray(sub["A"], float)
+                    bnew = A @ rng.normal(size=A.shape[1])        # consistent by construction
+                    subs.append(dict(sub, b=bnew))
+                rhs.append(np.concatenate([sb["b"] for sb in subs]))
+                models.append(lindist.from_generic(dict(g, subs=subs)))
+            b.set_rhs(0, np.stack(rhs))
+            b.step(100, rho=3.0)
+            for j in range(3):
+                ref = oracle_iterates(models[j], 100, rho=3.0)
+                xs, lam = b.locals(j)
+                assert rel_err(xs, ref.xs) <= TOL_ITER
+                assert rel_err(lam, ref.lam) <= TOL_ITER
+            # an inconsistent rhs is rejected and named
+            bad = rhs[0].copy()
+            bad += 1.0
+            deficient = any(np.linalg.matrix_rank(np.asarray(sb["A"], float)) < np.asarray(sb["A"]).shape[0]
+                            for sb in g["subs"])
+            if deficient:
+                with pytest.raises(opf.OPFError) as e:
+                    b.set_rhs(1, bad[None, :])
+                assert e.value.code == opf.OPF_E_INFEASIBLE_LOCAL
+    assert M.n == len(g["c"])
+
+
+@pytest.mark.parametrize("k32", [8, 4])
+def test_fp32_batch_tracks_oracle(k32):
+    f = synth.preset_feeder("123", 2001)
+    fs = scenarios(f, [4100, 4101, 4102])
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        with opf.Batch(s, 3) as b:
+            b.set_shape(opf.PREC_FP32, k32)
+            b.set_loads(0, *load_arrays(fs))
+            b.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP32)
+            st = b.status()
+            assert np.all(st["iters"] == 100)
+            for j, g in enumerate(fs):
+                ref = oracle_iterates(lindist.build(g), 100)
+                xs, lam = b.locals(j)
+                assert rel_err(xs, ref.xs) <= 1e-4
+                assert rel_err(lam, ref.lam) <= 1e-4
+
+
+@pytest.mark.parametrize("name,seed,n_scen", [("13", 1003, 6), ("123", 2002, 5)])
+def test_batch_converged_objective(name, seed, n_scen):
+    f = synth.preset_feeder(name, seed)
+    fs = scenarios(f, [4200 + j for j in range(n_scen)])
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        with opf.Batch(s, n_scen) as b:
+            b.set_loads(0, *load_arrays(fs))
+            ok = b.solve(precision=opf.PREC_MIXED)
+            st = b.status()
+            _, obj = b.solution()
+            assert b.shape(opf.PREC_FP32)["ok"] == 1
+            assert len(b.tune_log()) >= 2
+    assert ok
+    assert np.all(st["converged"])
+    assert np.all(st["pres"] <= TOL_PRES)
+    for j, g in enumerate(fs):
+        obj_star, _ = oracle_admm.lp_optimum(lindist.build(g))
+        assert abs(obj[j] - obj_star) <= TOL_OBJ * abs(obj_star), (j, obj[j], obj_star)
+
+
+def test_full_batch_sampled_against_oracle():
+    """The 1024-scenario batch of the 123-bus feeder as the benchmark runs it;
+    sampled instances are checked against the oracle's LP optimum."""
+    f = synth.preset_feeder("123", 2001)
+    n = 1024
+    fs = scenarios(f, [4000 + j for j in range(n)])
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        with opf.Batch(s, n) as b:
+            b.set_loads(0, *load_arrays(fs))
+            ok = b.solve(precision=opf.PREC_MIXED)
+            st = b.status()
+            _, obj = b.solution()
+    assert ok
+    assert np.all(st["converged"]) and np.all(st["pres"] <= TOL_PRES)
+    for j in (0, 1, 517, 1023):
+        obj_star, _ = oracle_admm.lp_optimum(lindist.build(fs[j]))
+        assert abs(obj[j] - obj_star) <= TOL_OBJ * abs(obj_star), (j, obj[j], obj_star)
+
+
+def test_batch_errors():
+    f = synth.preset_feeder("13", 1001)
+    with opf.Solver.from_feeder(f) as s:
+        with pytest.raises(opf.OPFError) as e:
+            opf.Batch(s, 2)                                   # not precomputed
+        assert e.value.code == opf.OPF_E_STATE
+        s.precompute()
+        with opf.Batch(s, 2) as b:
+            with pytest.raises(opf.OPFError):
+                b.solution()                                  # no iteration yet
+            with pytest.raises(opf.OPFError) as e:
+                b.set_loads(1, np.zeros((2, len(f["load_bus"]), 3)), np.zeros((2, len(f["load_bus"]), 3)))
+            assert e.value.code == opf.OPF_E_INVALID         # range past the end
+            with pytest.raises(opf.OPFError):
+                b.set_shape(opf.PREC_FP32, 3)
+    fz = synth.with_zip_delta(synth.preset_feeder("34", 5034), seed=3)
+    with opf.Solver.from_feeder(fz) as s:
+        s.precompute()
+        with opf.Batch(s, 1) as b:
+            with pytest.raises(opf.OPFError) as e:
+                b.set_loads(0, fz["load_a"][None], fz["load_b"][None])
+            assert e.value.code == opf.OPF_E_INVALID
