@@ -66,17 +66,194 @@ __device__ __forceinline__ T clampT(T x, T lo, T hi) {
 }  // namespace
 
 // ============================================================ engine
-// NQ: chunks of 4 slots a lane can hold (registers v, y and the current
-// factor row: 3 * 4 * NQ values).
-template <typename T, int NQ>
+// K-wide register rows: K consecutive values moved with the widest aligned
+// vector loads/stores (the offsets used are multiples of K elements).
+template <typename T, int K>
+struct RowK {
+    T v[K];
+};
+
+template <typename T, int K, bool L2ONLY>
+__device__ __forceinline__ void load_row(RowK<T, K> &r, const T *p) {
+    if constexpr (K * sizeof(T) >= 16) {
+#pragma unroll
+        for (int i = 0; i < K; i += 16 / sizeof(T)) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 t = L2ONLY ? __ldcg(reinterpret_cast<const float4 *>(p + i))
+                                        : *reinterpret_cast<const float4 *>(p + i);
+                r.v[i] = t.x; r.v[i + 1] = t.y; r.v[i + 2] = t.z; r.v[i + 3] = t.w;
+            } else {
+                const double2 t = L2ONLY ? __ldcg(reinterpret_cast<const double2 *>(p + i))
+                                         : *reinterpret_cast<const double2 *>(p + i);
+                r.v[i] = t.x; r.v[i + 1] = t.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) r.v[i] = L2ONLY ? __ldcg(p + i) : p[i];
+    }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void store_row(T *p, const RowK<T, K> &r) {
+    if constexpr (K * sizeof(T) >= 16) {
+#pragma unroll
+        for (int i = 0; i < K; i += 16 / sizeof(T)) {
+            if constexpr (sizeof(T) == 4)
+                *reinterpret_cast<float4 *>(p + i) = make_float4(r.v[i], r.v[i + 1], r.v[i + 2], r.v[i + 3]);
+            else
+                *reinterpret_cast<double2 *>(p + i) = make_double2(r.v[i], r.v[i + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) p[i] = r.v[i];
+    }
+}
+
+__device__ __forceinline__ Q4<float> ld4cg(const float *p) {
+    const float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+    return {{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ Q4<double> ld4cg(const double *p) {
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2 *>(p + 2));
+    return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4cg(float *p, const Q4<float> &q) {
+    __stcg(reinterpret_cast<float4 *>(p), make_float4(q.v[0], q.v[1], q.v[2], q.v[3]));
+}
+__device__ __forceinline__ void st4cg(double *p, const Q4<double> &q) {
+    __stcg(reinterpret_cast<double2 *>(p), make_double2(q.v[0], q.v[1]));
+    __stcg(reinterpret_cast<double2 *>(p + 2), make_double2(q.v[2], q.v[3]));
+}
+
+// One warp task with exactly NQT chunks per position.  chg holds g * K per
+// slot (-1: padding); bt holds +bbar~ for members with M = F^T F and -bbar~
+// for M = I - F^T F, so that y = bt + F^T w gives x_s = y or v - y.
+template <typename T, int K, int NQT>
+__device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *us, const T *xs, T *mu_c,
+                                           const T *bt_c, T *ds_c, const T *lr_c, const T *xr_c,
+                                           const int4 *chg, int jpos, int sc, T rho, T inv_rho, bool check,
+                                           bool act, bool wds, double acc[6]) {
+    constexpr int J = 32 / K;
+    const int mode1 = (tk.modes >> (jpos >> tk.lp)) & 1;
+    T v[4 * NQT], y[4 * NQT];
+    const int ch0 = tk.ch0 + jpos;
+#pragma unroll
+    for (int q = 0; q < NQT; ++q) {
+        const int ch = ch0 + q * J;
+        const int off = (ch * K + sc) * 4;
+        const int4 g4 = __ldg(chg + ch);
+        const Q4<T> m4 = ld4cg(mu_c + off);
+        const Q4<T> b4 = ld4cg(bt_c + off);
+        const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            y[4 * q + e] = b4.v[e];
+            v[4 * q + e] = gg[e] >= 0 ? xs[gg[e] + sc] + m4.v[e] * inv_rho : T(0);
+        }
+    }
+    // x_s = M v + bbar~ over the factor rows, two rows per step
+    const int rstride = NQT * J * 4;
+    const T *F0 = Fs + tk.foff + jpos * 4;
+    const int red_top = tk.p * K;
+    for (int r = 0; r < tk.f; r += 2, F0 += 2 * rstride) {
+        const bool two = r + 1 < tk.f;
+        const T *F1 = F0 + rstride;
+        T p0[4] = {T(0), T(0), T(0), T(0)}, p1[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int q = 0; q < NQT; ++q) {
+            const Q4<T> f0 = ld4(F0 + q * J * 4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) p0[e] += f0.v[e] * v[4 * q + e];
+        }
+        if (two) {
+#pragma unroll
+            for (int q = 0; q < NQT; ++q) {
+                const Q4<T> f1 = ld4(F1 + q * J * 4);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) p1[e] += f1.v[e] * v[4 * q + e];
+            }
+        }
+        T s0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
+        T s1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
+        for (int o = K; o < red_top; o <<= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+#pragma unroll
+        for (int q = 0; q < NQT; ++q) {
+            const Q4<T> f0 = ld4(F0 + q * J * 4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) y[4 * q + e] += f0.v[e] * s0;
+        }
+        if (two) {
+#pragma unroll
+            for (int q = 0; q < NQT; ++q) {
+                const Q4<T> f1 = ld4(F1 + q * J * 4);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) y[4 * q + e] += f1.v[e] * s1;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQT; ++q) {
+        const int ch = ch0 + q * J;
+        const int off = (ch * K + sc) * 4;
+        Q4<T> x4, m4, u4;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const T vv = v[4 * q + e];
+            const T xsv = mode1 ? y[4 * q + e] : vv - y[4 * q + e];
+            const T mun = rho * (vv - xsv);
+            x4.v[e] = xsv;
+            m4.v[e] = mun;
+            u4.v[e] = rho * xsv - mun;
+        }
+        st4(us + off, u4);
+        if (check) {
+            const int4 g4 = __ldg(chg + ch);
+            const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
+            const Q4<T> o4 = ld4cg(ds_c + off);
+            const Q4<T> l4 = ld4cg(lr_c + off);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (gg[e] < 0) continue;
+                const double xg = (double)xs[gg[e] + sc];
+                const double xsd = (double)x4.v[e];
+                const double d0 = xg - xsd, d1 = xsd - (double)o4.v[e];
+                const double xa = xsd + (double)__ldcg(xr_c + gg[e]);
+                const double la = (double)m4.v[e] + (double)l4.v[e];
+                acc[0] += d0 * d0;
+                acc[1] += d1 * d1;
+                acc[3] += xa * xa;
+                acc[4] += la * la;
+            }
+        }
+        if (act) {
+            st4cg(mu_c + off, m4);
+            if (wds) st4cg(ds_c + off, x4);
+        }
+    }
+}
+
+// Globals per thread whose segment records stay in registers.
+constexpr int kGR = 8;
+
+// K: instance columns per CTA (compile time), J = 32 / K member positions.
+// NQ: chunks of 4 slots a lane can hold (registers v and y: 2 * 4 * NQ).
+// FG: factors read from global memory (L1/L2) instead of shared memory.
+template <typename T, int K, int NQ, bool FG>
 __global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_iters, int check_every) {
+    constexpr int J = 32 / K;
+    constexpr int KS = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : K == 16 ? 4 : 5;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *Fs = reinterpret_cast<T *>(smraw);
+    T *Fsm = reinterpret_cast<T *>(smraw);
+    const T *Fs = FG ? a.Fpk : Fsm;
     T *us = reinterpret_cast<T *>(smraw + a.off_u);
     T *xs = reinterpret_cast<T *>(smraw + a.off_x);
     double *red = reinterpret_cast<double *>(smraw + a.off_red);
     int *flags = reinterpret_cast<int *>(smraw + a.off_flag);    // [0,K) running, [K,2K) just finished
-    const int K = a.K, ks = a.kshift, J = a.J;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int nthr = blockDim.x;
     const int c = blockIdx.x;
@@ -92,21 +269,39 @@ __global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_i
         if (!any) return;
     }
     // factors into shared memory (nF is a multiple of 4)
-    for (int i = tid * 4; i < a.nF; i += nthr * 4) st4(Fs + i, ld4(a.Fpk + i));
+    if (!FG)
+        for (int i = tid * 4; i < a.nF; i += nthr * 4) st4(Fsm + i, ld4(a.Fpk + i));
     const size_t sb = (size_t)c * a.NCH * K * 4;     // this CTA's slot arrays
     const size_t gb = (size_t)c * a.G * K;           // global arrays
     const size_t bb = (size_t)c * a.NB * K;          // bounded-global arrays
     const int nsl = a.NCH * K * 4;
+    T *mu_c = a.mu + sb, *ds_c = a.ds + sb;
+    const T *bt_c = a.bt + sb, *lr_c = a.lref + sb;
     for (int i = tid * 4; i < nsl; i += nthr * 4) {
-        const Q4<T> d = ld4(a.ds + sb + i), m = ld4(a.mu + sb + i);
+        const Q4<T> d = ld4cg(a.ds + sb + i), m = ld4cg(a.mu + sb + i);
         Q4<T> u;
 #pragma unroll
         for (int e = 0; e < 4; ++e) u.v[e] = a.rho * d.v[e] - m.v[e];
         st4(us + i, u);
     }
+    // segment records of this thread's globals i = tid + r * nthr
+    unsigned gseg[kGR];
+    int gbnd[kGR];
+#pragma unroll
+    for (int r = 0; r < kGR; ++r) {
+        const int i = tid + r * nthr;
+        gseg[r] = 0u;
+        gbnd[r] = -1;
+        if (i < a.G) {
+            const int4 gt = __ldg(a.gtab + i);
+            gseg[r] = (unsigned)gt.x | ((unsigned)gt.y << 24);
+            gbnd[r] = gt.z;
+        }
+    }
     __syncthreads();
     const int sc = tid & (K - 1);
-    const int jpos = lane >> ks;
+    const int jpos = lane >> KS;
+    const T *xr_c = a.xrf + gb + sc;
     const T rho = a.rho, inv_rho = a.inv_rho;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     int last_check = 0;
@@ -115,103 +310,58 @@ __global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_i
         const bool check = check_every > 0 && ((it + 1) % check_every == 0);
         const bool wds = check || it == n_iters - 1 || (check_every > 0 && ((it + 2) % check_every == 0));
         const bool act = flags[sc] != 0;
-        // ---- G: global update (Eq. closed_1)
-        for (int item = tid; item < GK; item += nthr) {
-            const int i = item >> ks;
-            const int4 gt = __ldg(a.gtab + i);
-            T s = T(0);
-            for (int q = 0; q < gt.y; ++q) s += us[__ldg(a.useg + gt.x + q) + sc * 4];
-            T xv = (s - a.ct[gb + item]) * __ldg(a.recip + i);
-            if (gt.z >= 0) xv = clampT(xv, a.lbt[bb + ((size_t)gt.z << ks) + sc], a.ubt[bb + ((size_t)gt.z << ks) + sc]);
-            xs[item] = xv;
-            if (check) {
-                const double xa = (double)xv + (double)a.xrf[gb + item];
-                acc[2] += (double)gt.y * xa * xa;
-                acc[5] += (double)__ldg(a.cost + i) * xa;
+        // ---- G: global update (Eq. closed_1), one thread per global, all K columns
+#pragma unroll
+        for (int r = 0; r < kGR; ++r) {
+            const int i = tid + r * nthr;
+            if (i < a.G) {
+                const unsigned st0 = gseg[r] & 0xffffffu, cnt = gseg[r] >> 24;
+                RowK<T, K> sum, cr;
+#pragma unroll
+                for (int q = 0; q < K; ++q) sum.v[q] = T(0);
+                load_row<T, K, true>(cr, a.ct + gb + (size_t)i * K);
+                const T rcp = __ldg(a.recip + i);
+                for (unsigned q = 0; q < cnt; ++q) {
+                    const int uo = __ldg(a.useg + st0 + q);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) sum.v[k] += us[uo + k * 4];
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) sum.v[k] = (sum.v[k] - cr.v[k]) * rcp;
+                if (gbnd[r] >= 0) {
+                    RowK<T, K> lo, hi;
+                    load_row<T, K, true>(lo, a.lbt + bb + (size_t)gbnd[r] * K);
+                    load_row<T, K, true>(hi, a.ubt + bb + (size_t)gbnd[r] * K);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) sum.v[k] = clampT(sum.v[k], lo.v[k], hi.v[k]);
+                }
+                store_row<T, K>(xs + (size_t)i * K, sum);
             }
         }
         __syncthreads();
+        if (check) {
+            // objective and ||B x||^2 per column (thread column sc = tid % K)
+            for (int item = tid; item < GK; item += nthr) {
+                const int i = item >> KS;
+                const double xa = (double)xs[item] + (double)__ldcg(a.xrf + gb + item);
+                acc[2] += (double)__ldg(&a.gtab[i].y) * xa * xa;
+                acc[5] += (double)__ldg(a.cost + i) * xa;
+            }
+        }
         // ---- L: local update (Eq. closed_2) and dual update (Eq. ADMM-3)
         for (int ti = __ldg(a.wtask + w); ti < __ldg(a.wtask + w + 1); ++ti) {
             const BatchTask tk = a.tasks[__ldg(a.tlist + ti)];
-            const int mode1 = (tk.modes >> (jpos >> tk.lp)) & 1;
-            T v[4 * NQ], y[4 * NQ], fr[4 * NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) { v[4 * q + e] = T(0); y[4 * q + e] = T(0); }
-                if (q < tk.nq) {
-                    const int ch = tk.ch0 + q * J + jpos;
-                    const int4 g4 = __ldg(a.chg + ch);
-                    const Q4<T> m4 = ld4(a.mu + sb + ((size_t)ch * K + sc) * 4);
-                    const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (gg[e] >= 0) v[4 * q + e] = xs[(gg[e] << ks) + sc] + m4.v[e] * inv_rho;
-                }
-            }
-            for (int r = 0; r < tk.f; ++r) {
-                const T *Fr = Fs + tk.foff + ((size_t)r * tk.nq * J + jpos) * 4;
-                T part = T(0);
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    if (q < tk.nq) {
-                        const Q4<T> f4 = ld4(Fr + q * J * 4);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            fr[4 * q + e] = f4.v[e];
-                            part += f4.v[e] * v[4 * q + e];
-                        }
-                    }
-                }
-                for (int o = K; o < (tk.p << ks); o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-#pragma unroll
-                for (int q = 0; q < NQ; ++q)
-                    if (q < tk.nq)
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) y[4 * q + e] += fr[4 * q + e] * part;
-            }
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                if (q < tk.nq) {
-                    const int ch = tk.ch0 + q * J + jpos;
-                    const size_t idx = sb + ((size_t)ch * K + sc) * 4;
-                    const Q4<T> b4 = ld4(a.bt + idx);
-                    Q4<T> x4, m4, u4;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const T vv = v[4 * q + e], yy = y[4 * q + e];
-                        const T xsv = (mode1 ? yy : vv - yy) + b4.v[e];
-                        const T mun = rho * (vv - xsv);
-                        x4.v[e] = xsv;
-                        m4.v[e] = mun;
-                        u4.v[e] = rho * xsv - mun;
-                    }
-                    st4(us + ((size_t)ch * K + sc) * 4, u4);
-                    if (check) {
-                        const int4 g4 = __ldg(a.chg + ch);
-                        const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
-                        const Q4<T> o4 = ld4(a.ds + idx);
-                        const Q4<T> l4 = ld4(a.lref + idx);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            if (gg[e] < 0) continue;
-                            const double xg = (double)xs[(gg[e] << ks) + sc];
-                            const double xsd = (double)x4.v[e];
-                            const double d0 = xg - xsd, d1 = xsd - (double)o4.v[e];
-                            const double xa = xsd + (double)a.xrf[gb + ((size_t)gg[e] << ks) + sc];
-                            const double la = (double)m4.v[e] + (double)l4.v[e];
-                            acc[0] += d0 * d0;
-                            acc[1] += d1 * d1;
-                            acc[3] += xa * xa;
-                            acc[4] += la * la;
-                        }
-                    }
-                    if (act) {
-                        st4(a.mu + idx, m4);
-                        if (wds) st4(a.ds + idx, x4);
-                    }
-                }
+            switch (tk.nq) {
+                case 1: batch_task<T, K, 1>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
+                                            inv_rho, check, act, wds, acc); break;
+                case 2: batch_task<T, K, 2>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
+                                            inv_rho, check, act, wds, acc); break;
+                case 3: if constexpr (NQ >= 3) batch_task<T, K, 3>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c,
+                                                                   a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                   wds, acc); break;
+                default: if constexpr (NQ >= 4) batch_task<T, K, 4>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c,
+                                                                    a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                    wds, acc); break;
             }
         }
         if (check) {
@@ -238,9 +388,14 @@ __global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_i
                 }
             }
             __syncthreads();
-            // x~ of instances that just finished (each thread its own items of G)
-            for (int item = tid; item < GK; item += nthr)
-                if (flags[K + (item & (K - 1))]) a.xo[gb + item] = xs[item];
+            // x~ of instances that just finished (each thread the globals it wrote)
+#pragma unroll
+            for (int r = 0; r < kGR; ++r) {
+                const int i = tid + r * nthr;
+                if (i < a.G)
+                    for (int k = 0; k < K; ++k)
+                        if (flags[K + k]) a.xo[gb + (size_t)i * K + k] = xs[(size_t)i * K + k];
+            }
             last_check = it + 1;
             int any = 0;
             for (int q = 0; q < K; ++q) any |= flags[q];
@@ -250,8 +405,13 @@ __global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_i
         }
     }
     if (tid < K && flags[tid]) a.st[a.inst[c * K + tid]].iter += n_iters - last_check;
-    for (int item = tid; item < GK; item += nthr)
-        if (flags[item & (K - 1)]) a.xo[gb + item] = xs[item];
+#pragma unroll
+    for (int r = 0; r < kGR; ++r) {
+        const int i = tid + r * nthr;
+        if (i < a.G)
+            for (int k = 0; k < K; ++k)
+                if (flags[k]) a.xo[gb + (size_t)i * K + k] = xs[(size_t)i * K + k];
+    }
 }
 
 // ============================================================ per-instance data
@@ -421,7 +581,8 @@ __global__ void __launch_bounds__(128) k_bref_slots(int S, int n_inst, int G, in
         const double xg = xr[gk[k]];
         const int p = sch[k];
         const size_t e = (((size_t)cta * NCH + (p >> 2)) * K + sc) * 4 + (p & 3);
-        bt[e] = (T)(mv + bi[k] - xg);
+        const double btv = mv + bi[k] - xg;
+        bt[e] = (T)(mode ? btv : -btv);      // the engine starts y at this value
         ds[e] = (T)(xi[k] - xg);
         mu[e] = T(0);
         lref[e] = (T)li[k];
@@ -529,53 +690,57 @@ static inline int bl(long long n, int t) {
     return (int)b;
 }
 
-template <typename T, int NQ>
-static int set_engine_smem(unsigned bytes) {
-    return cudaFuncSetAttribute(k_batch_engine<T, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-                   cudaSuccess ? 0 : -1;
-}
-
+// Instantiated shapes: FP32 with factors in shared memory (K = 2, 4, 8; NQ = 4);
+// FP64 (NQ = 2, K = 1, 2, 4) with factors in shared or global memory.
 template <typename T>
-int batch_engine_prepare(int nq, unsigned bytes) {
-    switch (nq) {
-        case 1: return set_engine_smem<T, 1>(bytes);
-        case 2: return set_engine_smem<T, 2>(bytes);
-        case 4: return set_engine_smem<T, 4>(bytes);
-        default: return -1;
+static const void *engine_fn(int K, int nq, bool fg) {
+    if constexpr (sizeof(T) == 4) {
+        if (fg || nq != 4) return nullptr;
+        if (K == 2) return (const void *)k_batch_engine<float, 2, 4, false>;
+        if (K == 4) return (const void *)k_batch_engine<float, 4, 4, false>;
+        if (K == 8) return (const void *)k_batch_engine<float, 8, 4, false>;
+    } else {
+        if (nq != 2) return nullptr;
+        if (K == 1) return fg ? (const void *)k_batch_engine<double, 1, 2, true> : (const void *)k_batch_engine<double, 1, 2, false>;
+        if (K == 2) return fg ? (const void *)k_batch_engine<double, 2, 2, true> : (const void *)k_batch_engine<double, 2, 2, false>;
+        if (K == 4) return fg ? (const void *)k_batch_engine<double, 4, 2, true> : (const void *)k_batch_engine<double, 4, 2, false>;
     }
+    return nullptr;
 }
 
 template <typename T>
-int batch_engine_launch(const BatchArgs<T> &a, int nq, int ctas, int threads, unsigned bytes, int n_iters,
+int batch_engine_prepare(int K, int nq, bool fg, unsigned bytes) {
+    const void *fn = engine_fn<T>(K, nq, fg);
+    if (!fn) return -1;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess ? 0 : -1;
+}
+
+template <typename T>
+int batch_engine_launch(const BatchArgs<T> &a, int nq, bool fg, int ctas, int threads, unsigned bytes, int n_iters,
                         int check_every, cudaStream_t s) {
-    switch (nq) {
-        case 1: k_batch_engine<T, 1><<<ctas, threads, bytes, s>>>(a, n_iters, check_every); break;
-        case 2: k_batch_engine<T, 2><<<ctas, threads, bytes, s>>>(a, n_iters, check_every); break;
-        case 4: k_batch_engine<T, 4><<<ctas, threads, bytes, s>>>(a, n_iters, check_every); break;
-        default: return -1;
-    }
-    return 0;
+    const void *fn = engine_fn<T>(a.K, nq, fg);
+    if (!fn) return -1;
+    BatchArgs<T> aa = a;
+    void *args[] = {(void *)&aa, (void *)&n_iters, (void *)&check_every};
+    return cudaLaunchKernel(fn, dim3(ctas), dim3(threads), args, bytes, s) == cudaSuccess ? 0 : -1;
 }
 
 template <typename T>
-int batch_engine_max_ctas_per_sm(int nq, int threads, unsigned bytes) {
+int batch_engine_max_ctas_per_sm(int K, int nq, bool fg, int threads, unsigned bytes) {
+    const void *fn = engine_fn<T>(K, nq, fg);
+    if (!fn) return -1;
     int n = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (nq) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_engine<T, 1>, threads, bytes); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_engine<T, 2>, threads, bytes); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_engine<T, 4>, threads, bytes); break;
-        default: break;
-    }
-    return e == cudaSuccess ? n : -1;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, bytes) == cudaSuccess ? n : -1;
 }
 
-template int batch_engine_prepare<float>(int, unsigned);
-template int batch_engine_prepare<double>(int, unsigned);
-template int batch_engine_launch<float>(const BatchArgs<float> &, int, int, int, unsigned, int, int, cudaStream_t);
-template int batch_engine_launch<double>(const BatchArgs<double> &, int, int, int, unsigned, int, int, cudaStream_t);
-template int batch_engine_max_ctas_per_sm<float>(int, int, unsigned);
-template int batch_engine_max_ctas_per_sm<double>(int, int, unsigned);
+template int batch_engine_prepare<float>(int, int, bool, unsigned);
+template int batch_engine_prepare<double>(int, int, bool, unsigned);
+template int batch_engine_launch<float>(const BatchArgs<float> &, int, bool, int, int, unsigned, int, int,
+                                        cudaStream_t);
+template int batch_engine_launch<double>(const BatchArgs<double> &, int, bool, int, int, unsigned, int, int,
+                                         cudaStream_t);
+template int batch_engine_max_ctas_per_sm<float>(int, int, bool, int, unsigned);
+template int batch_engine_max_ctas_per_sm<double>(int, int, bool, int, unsigned);
 
 void launch_binit(int i0, int cnt, int L, const int *gk, const double *x0, double *xs, double *lam,
                   DevStatus *st, long long max_iter, double eps_rel, double eps_abs, cudaStream_t s) {

@@ -24,11 +24,11 @@
 #include "handle.h"
 
 namespace opf {
-template <typename T> int batch_engine_prepare(int nq, unsigned bytes);
+template <typename T> int batch_engine_prepare(int K, int nq, bool fg, unsigned bytes);
 template <typename T>
-int batch_engine_launch(const BatchArgs<T> &a, int nq, int ctas, int threads, unsigned bytes, int n_iters,
+int batch_engine_launch(const BatchArgs<T> &a, int nq, bool fg, int ctas, int threads, unsigned bytes, int n_iters,
                         int check_every, cudaStream_t s);
-template <typename T> int batch_engine_max_ctas_per_sm(int nq, int threads, unsigned bytes);
+template <typename T> int batch_engine_max_ctas_per_sm(int K, int nq, bool fg, int threads, unsigned bytes);
 void launch_binit(int i0, int cnt, int L, const int *gk, const double *x0, double *xs, double *lam,
                   DevStatus *st, long long max_iter, double eps_rel, double eps_abs, cudaStream_t s);
 void launch_bfill(int cnt, int nrows, const double *b0, double *rhs, cudaStream_t s);
@@ -73,7 +73,7 @@ static constexpr unsigned kMaxSmem = 227u * 1024u;
 
 // One engine plan: shape, tables and the engine-layout arrays.
 struct BPlan {
-    bool ok = false, dbl = false;
+    bool ok = false, dbl = false, fg = false;   // fg: factors read from global memory
     int K = 0, ks = 0, J = 0, W = 0, nq = 0, threads = 0;
     int NCH = 0, NB = 0, nF = 0, n_tasks = 0, C = 0;
     unsigned off_u = 0, off_x = 0, off_red = 0, off_flag = 0, bytes = 0;
@@ -149,11 +149,12 @@ int ilog2(int x) {
 
 // Builds the tables of a plan with K instance columns, W warps and NQ chunks
 // per lane; returns OPF_E_CAPACITY when the shape cannot hold the model.
-int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq) {
+int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) {
     opf_handle *h = b->h;
     cudaStream_t st = h->stream;
     p->release();
     p->dbl = dbl;
+    p->fg = fg;
     p->K = K; p->ks = ilog2(K); p->J = 32 / K; p->W = W; p->nq = nq; p->threads = 32 * W;
     const int J = p->J, NPL = 4 * nq, S = h->S, L = h->L, G = h->G;
     const size_t sz = dbl ? sizeof(double) : sizeof(float);
@@ -214,7 +215,7 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq) {
                     const int c = (part * tk.nq + q) * 4 + e;
                     g[e] = -1;
                     if (c < n) {
-                        g[e] = h->h_gk[so + c];
+                        g[e] = h->h_gk[so + c] * K;      // shared-memory row of the global
                         sch[so + c] = (ch + q * J + jpos) * 4 + e;
                     }
                 }
@@ -262,16 +263,17 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq) {
     }
     wtask[W] = (int)tlist.size();
     // shared memory
-    p->off_u = a16((size_t)p->nF * sz);
+    p->off_u = fg ? 0u : a16((size_t)p->nF * sz);
     p->off_x = p->off_u + a16((size_t)p->NCH * K * 4 * sz);
     p->off_red = p->off_x + a16((size_t)G * K * sz);
     p->off_flag = p->off_red + a16((size_t)W * K * 6 * sizeof(double));
     p->bytes = p->off_flag + a16((size_t)2 * K * sizeof(int));
     if (p->bytes > kMaxSmem) { set_last_error("batch plan: shared memory"); return OPF_E_CAPACITY; }
-    const int rc = dbl ? batch_engine_prepare<double>(nq, p->bytes) : batch_engine_prepare<float>(nq, p->bytes);
+    if (G > 8 * p->threads) { set_last_error("batch plan: more than 8 globals per thread"); return OPF_E_CAPACITY; }
+    const int rc = dbl ? batch_engine_prepare<double>(K, nq, fg, p->bytes) : batch_engine_prepare<float>(K, nq, fg, p->bytes);
     if (rc) { set_last_error("batch plan: engine attributes"); return OPF_E_CUDA; }
-    const int occ = dbl ? batch_engine_max_ctas_per_sm<double>(nq, p->threads, p->bytes)
-                        : batch_engine_max_ctas_per_sm<float>(nq, p->threads, p->bytes);
+    const int occ = dbl ? batch_engine_max_ctas_per_sm<double>(K, nq, fg, p->threads, p->bytes)
+                        : batch_engine_max_ctas_per_sm<float>(K, nq, fg, p->threads, p->bytes);
     if (occ < 1) { set_last_error("batch plan: the engine does not fit an SM"); return OPF_E_CAPACITY; }
     // columns
     p->C = (b->n + K - 1) / K;
@@ -369,7 +371,7 @@ void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_eve
                    (T *)p.xrf, (T *)p.lbt, (T *)p.ubt, h->d_sub, h->d_sub2, h->d_F64, h->d_gk, p.d_sch,
                    b->d_bbar, (T *)p.bt, (T *)p.ds, (T *)p.mu, (T *)p.lref, s);
     BatchArgs<T> a = engine_args<T>(b, p, rho);
-    batch_engine_launch<T>(a, p.nq, p.C, p.threads, p.bytes, n_iters, check_every, s);
+    batch_engine_launch<T>(a, p.nq, p.fg, p.C, p.threads, p.bytes, n_iters, check_every, s);
     launch_bunshift<T>(b->n, b->G, b->L, p.K, p.ks, p.NCH, p.d_ipos, h->d_gk, p.d_sch, b->d_xref,
                        (const T *)p.ds, (const T *)p.mu, (const T *)p.xo, b->d_st, b->d_xs, b->d_lam, b->d_x, s);
     launch_bany(b->n, b->d_st, b->d_flag, cond, use_cond, s);
@@ -444,12 +446,15 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
     if (p.ok) return OPF_OK;
     opf_handle *h = b->h;
     if (dbl) {
+        // factors in shared memory when they fit, else read through L1/L2 (the
+        // FP64 iteration is bound by the FP64 FMA rate either way)
         const int fk = b->force_k64, fw = b->force_w64 > 0 ? b->force_w64 : 16;
         const int ks[] = {4, 2, 1};
-        for (int K : ks) {
-            if (fk && K != fk) continue;
-            if (build_plan(b, &p, true, K, fw, 2) == OPF_OK) return OPF_OK;
-        }
+        for (int fg = 0; fg < 2; ++fg)
+            for (int K : ks) {
+                if (fk && K != fk) continue;
+                if (build_plan(b, &p, true, K, fw, 2, fg != 0) == OPF_OK) return OPF_OK;
+            }
         p.release();
         set_last_error("batch: no FP64 engine shape fits");
         return OPF_E_CAPACITY;
@@ -457,13 +462,13 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
     std::vector<std::pair<int, int>> cand;
     if (b->force_k32) cand.push_back({b->force_k32, b->force_w32 > 0 ? b->force_w32 : 16});
     else {
-        const int Ks[] = {8, 4, 16, 2};
+        const int Ks[] = {8, 4, 2};
         const int Ws[] = {16, 12, 8};
         for (int K : Ks) for (int W : Ws) cand.push_back({K, W});
     }
     b->tune_log.clear();
     if (cand.size() == 1) {
-        BTRY(build_plan(b, &p, false, cand[0].first, cand[0].second, 4));
+        BTRY(build_plan(b, &p, false, cand[0].first, cand[0].second, 4, false));
         return OPF_OK;
     }
     // timing runs on a copy of the status; the FP64 state is not touched by
@@ -473,7 +478,7 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
     int bk = 0, bw = 0;
     const int iters = 2 * std::max(k, 2);
     for (auto &c : cand) {
-        if (build_plan(b, &p, false, c.first, c.second, 4) != OPF_OK) continue;
+        if (build_plan(b, &p, false, c.first, c.second, 4, false) != OPF_OK) continue;
         BTRY(plan_set_rho(b, &p, rho));
         launch_bref<float>(b->n, h->S, b->G, b->L, p.K, p.ks, p.NCH, p.NB, p.d_ipos, h->d_gseg, h->d_uslot,
                            b->d_bidx, h->d_c64, h->d_lb64, h->d_ub64, rho, b->d_xs, b->d_lam, b->d_st, b->d_xref,
@@ -481,9 +486,9 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
                            h->d_F64, h->d_gk, p.d_sch, b->d_bbar, (float *)p.bt, (float *)p.ds, (float *)p.mu,
                            (float *)p.lref, h->stream);
         BatchArgs<float> a = engine_args<float>(b, p, rho);
-        batch_engine_launch<float>(a, p.nq, p.C, p.threads, p.bytes, 4, 0, h->stream);   // warm-up
+        batch_engine_launch<float>(a, p.nq, false, p.C, p.threads, p.bytes, 4, 0, h->stream);   // warm-up
         BCUDA(cudaEventRecord(b->ev[0], h->stream));
-        batch_engine_launch<float>(a, p.nq, p.C, p.threads, p.bytes, iters, 0, h->stream);
+        batch_engine_launch<float>(a, p.nq, false, p.C, p.threads, p.bytes, iters, 0, h->stream);
         BCUDA(cudaEventRecord(b->ev[1], h->stream));
         BCUDA(cudaEventSynchronize(b->ev[1]));
         BCUDA(cudaGetLastError());
@@ -498,7 +503,7 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
     // the status copies carry the pad (shifted) marks of the timing runs: clear them
     BCUDA(cudaMemcpyAsync(b->d_st, b->d_st_save, b->n * sizeof(DevStatus), cudaMemcpyDeviceToDevice, h->stream));
     if (!bk) { p.release(); set_last_error("batch: no FP32 engine shape fits"); return OPF_E_CAPACITY; }
-    BTRY(build_plan(b, &p, false, bk, bw, 4));
+    BTRY(build_plan(b, &p, false, bk, bw, 4, false));
     return OPF_OK;
 }
 

@@ -165,7 +165,7 @@ struct BatchTask {
 
 // Arguments of one batched-engine launch.  Instance column sc of CTA c holds
 // instance inst[c * K + sc] (-1: empty).  Engine arrays (type T):
-//   per slot      [c][NCH][K][4]   mu, ds, bt (bbar~), lref (lambda_ref)
+//   per slot      [c][NCH][K][4]   mu, ds, bt (+bbar~ if M = F^T F, else -bbar~), lref (lambda_ref)
 //   per global    [c][G][K]        ct (c~), xrf (x_ref), xo (x~ at the end)
 //   per bounded   [c][NB][K]       lbt, ubt (bounds - x_ref)
 template <typename T>
@@ -175,7 +175,7 @@ struct BatchArgs {
     const BatchTask *tasks;
     const int *wtask;          // [n_warps + 1] ranges into tlist
     const int *tlist;
-    const int4 *chg;           // [NCH] global of each chunk's 4 slots (-1: padding)
+    const int4 *chg;           // [NCH] g * K of each chunk's 4 slots (-1: padding)
     const int4 *gtab;          // [G] (first copy in useg, copies, bounded index or -1, 0)
     const int *useg;           // copies of each global: u offset ch * K * 4 + e
     const T *Fpk;              // [nF] factors, task-interleaved
