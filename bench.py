@@ -1,13 +1,18 @@
-"""Benchmark: OPF solves/s of the 123-bus synthetic feeder (single instance).
+"""Benchmark: OPF solves/s on one GB300.
 
-One step = one complete solve through the library, inputs resident on the
-device: the Algorithm 1 precomputation (Sec. III-B) followed by ADMM
-iterations to the stopping test (Sec. III-C with eps_rel = 1e-8 and
-pres <= 1e-4, which puts the objective within 1e-6 of the LP optimum) and the
-read-back of the objective.  The default path iterates in FP32 with one warp
-per subsystem inside one thread-block cluster, re-centred in FP64, followed
-by an FP64 polish;
-``--precision fp64`` times plain FP64 iterations.
+Default workload (``--workload batch``): 1024 load scenarios of the 123-bus
+synthetic feeder (seed 2001; scenario j scales every load by U[0.6, 1.2] x
+N(1, 0.05) from seed 4000 + j), all solved together by the batched engine.
+One step = one pass of the whole path over the batch, inputs resident on the
+device: the feeder's FP64 factorization (Sec. III-B), the per-scenario
+bbar = A_s^+ b, ADMM iterations of every instance to its own stopping test
+(Sec. III-C with eps_rel = 1e-8 and pres <= 1e-4; FP32 iterations re-centred
+in FP64, then an FP64 polish) and the read-back of the 1024 objectives.  The
+same line reports the plain single-instance FP64 GPU path on the feeder
+(``plain_fp64``) that the metric compares against.
+
+``--workload single`` times one instance of the 123-bus feeder per step
+(``--precision fp64`` for plain FP64 iterations).
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
 on the library's stream, with a write of a 512 MiB buffer (larger than the
@@ -16,14 +21,15 @@ over ranks.  Under torchrun every rank solves its own replica (no collective
 on the data path: scaling "weak").
 
 Extra fields: ``e2e`` (the same metric through the C ABI from host arrays,
-host->device upload and device->host read of x inside the timed region),
-``roofline`` of the dominant kernel, ``clocks`` sampled by nvidia-smi during
-the timed region, ``cpu_baseline`` (the FP64 CPU oracle on this host), and
+host->device upload of the loads and device->host read of x and the
+objectives inside the timed region), ``roofline`` of the dominant kernel,
+``clocks`` sampled by nvidia-smi during the timed region, ``cpu_baseline``
+(the FP64 CPU oracle on this host, one thread, on a bounded sample) and
 ``gpu_launches``.
 
 ``--impl reference`` times the CPU oracle (plain FP64 C loop of Algorithm 1,
-one core) on the same workload and prints the same line with
-``"impl": "reference"``.
+one thread) on the same workload, one scenario per step, and prints the same
+line with ``"impl": "reference"``.
 """
 from __future__ import annotations
 
@@ -41,20 +47,42 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = "123"
-SEED = 2001
+FEEDER, SEED = "123", 2001
+N_SCEN, SCEN_SEED0 = 1024, 4000
 RHO, EPS_REL, EPS_ABS = 100.0, 1e-8, 1e-4
 METRIC = "OPF solves/s to 1e-4 residual (batched/served vs plain FP64); p50/p99 latency"
 UNIT = "solves/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
+# SM count and FP32 lanes of the part, and its maximum SM clock, for the FP32
+# SIMT peak of the batched engine (an ALU-bound kernel).
+N_SM, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 
-def workload_config(precision):
+# DRAM bytes per launch of the dominant kernels from the ncu captures in
+# profiles/ (None until a capture of the current kernel exists).
+BATCH_ENGINE_TRAFFIC_PER_LAUNCH = None
+WARP_ENGINE_TRAFFIC_PER_LAUNCH = 352256 + 1536
+ITERS_PER_LAUNCH = 1000
+
+
+def batch_config(n):
+    return {
+        "workload": f"{n} load scenarios of the 123-bus synthetic radial 3-phase feeder (seed 2001; "
+                    "85 loads scaled by U[0.6,1.2] x N(1,0.05) per scenario, seeds 4000+j), 10 DERs, "
+                    "rho=100, each instance stopped at eps_rel=1e-8 and pres<=1e-4",
+        "buses": 123, "instances": n, "precision": "FP32 iterations re-centred in FP64 + FP64 polish",
+        "step": "factorization of the feeder (FP64) + per-scenario bbar = A_s^+ b + ADMM to the test "
+                "for every instance + objectives read back",
+        "l2": "512 MiB buffer written between timed steps",
+        "parallelism": "replicas",
+    }
+
+
+def single_config(precision):
     return {
         "workload": "123-bus synthetic radial 3-phase feeder (seed 2001), single instance, "
                     "85 loads, 10 DERs, rho=100, stop at eps_rel=1e-8 and pres<=1e-4",
-        "buses": 123,
-        "precision": precision,
+        "buses": 123, "precision": precision,
         "step": "precompute + ADMM iterations to the stopping test + objective read-back",
         "l2": "512 MiB buffer written between timed steps (working set ~1 MB < L2)",
         "parallelism": "replicas",
@@ -63,7 +91,13 @@ def workload_config(precision):
 
 def feeder():
     from paper_2310_09410_gb300 import synth
-    return synth.preset_feeder(WORKLOAD, SEED)
+    return synth.preset_feeder(FEEDER, SEED)
+
+
+def scenario_loads(f, n):
+    from paper_2310_09410_gb300 import synth
+    fs = [synth.load_scenario(f, SCEN_SEED0 + j) for j in range(n)]
+    return fs, np.stack([g["load_a"] for g in fs]), np.stack([g["load_b"] for g in fs])
 
 
 class ClockSampler:
@@ -122,11 +156,17 @@ class ClockSampler:
 
 
 def algorithmic_bytes_per_iter(sizes, w):
-    """Minimum bytes one iteration must move: each factor entry once, per slot
-    lambda and x_s read+write, bbar read, u written and read (7 words), three
-    index words (global, u position, segment start+count: 16 bytes), per global
-    cost and both bounds (3 words)."""
+    """Minimum bytes one single-instance iteration must move: each factor entry
+    once, per slot lambda and x_s read+write, bbar read, u written and read (7
+    words), three index words (16 bytes), per global cost and both bounds."""
     return w * (sizes["sum_nf"] + 7 * sizes["n_slots"] + 3 * sizes["n_global"]) + 16 * sizes["n_slots"]
+
+
+def algorithmic_flops_per_iter(sizes):
+    """Flops of one iteration of one instance: the two products with the
+    factor (2 flops per entry each), 8 per slot (v, x_s, lambda, u and the
+    copy's share of the segment sum) and 2 per global (shift and scale)."""
+    return 4 * sizes["sum_nf"] + 8 * sizes["n_slots"] + 2 * sizes["n_global"]
 
 
 def measured_peak():
@@ -138,60 +178,59 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(f, budget_s=15.0):
-    """FP64 CPU oracle, one thread, on a bounded sample of the same workload."""
+def oracle_solve(g):
     from oracle import admm as oracle_admm, lindist
+    M = lindist.build(g)
+    P = oracle_admm.Prepared(M)
+    return oracle_admm.admm(P, rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, max_iter=2_000_000, check_every=50)
+
+
+def cpu_baseline(instances, budget_s=15.0, what="scenarios of the batch"):
+    """FP64 CPU oracle, one thread, on a bounded sample of the same workload."""
     t0 = time.perf_counter()
-    n = 0
-    iters = 0
+    n = iters = 0
     while True:
-        M = lindist.build(f)
-        P = oracle_admm.Prepared(M)
-        r = oracle_admm.admm(P, rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, max_iter=2_000_000,
-                             check_every=50)
+        r = oracle_solve(instances[n % len(instances)])
         n += 1
         iters += r.iters
         el = time.perf_counter() - t0
         if el >= budget_s or n >= 50:
             break
     return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full solves of the same 123-bus instance (LP build, precompute, "
-                      f"{iters // n} iterations each) in {el:.1f} s, plain FP64 C loop, one thread"}
+            "sample": f"{n} full solves ({what}: LP build, precompute, {iters // n} iterations each on "
+                      f"average) in {el:.1f} s, plain FP64 C loop, one thread"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
     f = feeder()
-    from oracle import admm as oracle_admm, lindist
-
-    def one():
-        M = lindist.build(f)
-        P = oracle_admm.Prepared(M)
-        return oracle_admm.admm(P, rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS,
-                                max_iter=2_000_000, check_every=50)
-    for _ in range(args.warmup):
-        one()
+    if args.workload == "batch":
+        fs, _, _ = scenario_loads(f, max(args.steps + args.warmup, 1))
+        config = batch_config(N_SCEN)
+        what = "one scenario of the batch per step"
+    else:
+        fs = [f]
+        config = single_config("fp64 (CPU oracle)")
+        what = "the instance"
+    for j in range(args.warmup):
+        oracle_solve(fs[j % len(fs)])
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r = one()
+    iters = 0
+    for j in range(args.steps):
+        iters += oracle_solve(fs[(args.warmup + j) % len(fs)]).iters
     el = time.perf_counter() - t0
     value = args.steps / el
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config("fp64 (CPU oracle)"), "impl": "reference",
+            "config": config, "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full solves ({r.iters} iterations each), one thread"},
+                             "sample": f"{args.steps} full solves ({what}, {iters // max(args.steps, 1)} "
+                                       f"iterations on average), one thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
-
-
-# DRAM bytes of one k_warp_engine launch (1000 iterations) from the ncu
-# capture in profiles/k_warp_engine_123bus.md; null for other kernels.
-WARP_ENGINE_TRAFFIC_PER_LAUNCH = 352256 + 1536
-ITERS_PER_LAUNCH = 1000
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
@@ -205,8 +244,8 @@ def max_over_ranks(value: float, world: int, device) -> float:
     return float(t.item())
 
 
-def count_launches(stats, precision, k=50, R=1000):
-    """Kernels of ours per step: precompute (3) + solve + objective read (1)."""
+def count_launches_single(stats, precision, k=50, R=1000):
+    """Kernels of ours per single-instance step: precompute (3) + solve + objective read (1)."""
     n = 3 + 1
     if precision == "fp64":
         return n + 1 + (stats["main_iters"] // k) * (k + 1)
@@ -215,32 +254,171 @@ def count_launches(stats, precision, k=50, R=1000):
     return n + 8 + bodies * 7 + 1 + 1 + (pol // k) * (k + 1)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--host-loop", action="store_true",
-                    help="launch the iteration kernels directly instead of one graph with a device WHILE "
-                         "node (same kernels and arithmetic; profilers cannot see kernels in such graphs)")
-    args = ap.parse_args()
+def count_launches_batch(t):
+    """Kernels of ours per batched step: factorization (3) and A_s^+ (1), rhs
+    and bbar (4), six per loop pass (re-centring 2, engine, unshift 2, loop
+    test), the polish restart and objective (2), objective read (1)."""
+    return 3 + 1 + 4 + 6 * (t["fp32_passes"] + t["fp64_passes"]) + 2 + 1
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
 
+def plain_fp64_reference(opf, f, device, stream, n=2):
+    """Solves/s of the plain single-instance FP64 GPU path on the feeder."""
+    import torch
+    s = opf.Solver.from_feeder(f, device=device, stream=stream.cuda_stream)
+    times = []
+    for j in range(n + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.precompute()
+        ok = s.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=opf.PREC_FP64)
+        s.solution()
+        e1.record(stream)
+        e1.synchronize()
+        if j:                        # the first solve builds the graph
+            times.append(e0.elapsed_time(e1))
+        if not ok:
+            raise SystemExit("the plain FP64 solve did not converge")
+    iters = s.residuals()["iters"]
+    s.close()
+    return {"value": 1e3 * len(times) / sum(times), "unit": UNIT, "iterations": int(iters),
+            "path": "single instance, FP64 iterations on the grid engine (opf_solve_ex, engine auto)"}
+
+
+def run_batch(args, rank, world, local):
     import torch
     import torch.distributed as dist
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA device")
-    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2310_09410_gb300 import opf
+
+    n = args.instances
+    f = feeder()
+    fs, lp, lq = scenario_loads(f, n)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=local)
+    dlp = torch.from_numpy(lp).to(dev)
+    dlq = torch.from_numpy(lq).to(dev)
+    torch.cuda.synchronize()
+    solver = opf.Solver.from_feeder(f, device=local, stream=stream.cuda_stream)
+    solver.precompute()
+    batch = opf.Batch(solver, n)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flags = opf.SOLVE_HOST_LOOP if args.host_loop else 0
+
+    def step():
+        solver.precompute()
+        batch.set_loads_device(0, n, dlp.data_ptr(), dlq.data_ptr())
+        ok = batch.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=opf.PREC_MIXED, flags=flags)
+        _, obj = batch.solution()
+        return ok, obj
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
     if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times, launches, iters, objs = [], 0, [], None
+    fp32_ms = fp64_ms = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ok, objs = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        t = batch.timing()
+        fp32_ms += t["fp32_ms"]
+        fp64_ms += t["fp64_ms"]
+        launches += count_launches_batch(t)
+        iters.append(t["mean_iters"])
+        if not ok:
+            raise SystemExit("an instance of a timed batch did not converge")
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(float(sum(times)), world, f"cuda:{local}")
+    value = world * n * args.steps / (total_ms / 1e3)
+    st = batch.status()
+
+    # end to end from host arrays: loads uploaded, x and objectives read back
+    e2e_times = []
+    for _ in range(max(2, args.steps // 2)):
+        t0 = time.perf_counter()
+        solver.precompute()
+        batch.set_loads(0, lp, lq)
+        batch.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=opf.PREC_MIXED, flags=flags)
+        x, _ = batch.solution()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_total = max_over_ranks(sum(e2e_times), world, f"cuda:{local}")
+    e2e_value = world * n * len(e2e_times) / e2e_total
+    h2d = lp.nbytes + lq.nbytes
+    d2h = x.nbytes + 8 * n
+
+    # dominant kernel: the FP32 engine, timed alone on direct launches
+    solver.precompute()
+    batch.set_loads_device(0, n, dlp.data_ptr(), dlq.data_ptr())
+    batch.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=opf.PREC_MIXED,
+                flags=opf.SOLVE_HOST_LOOP)
+    th = batch.timing()
+    sizes = solver.sizes()
+    fpi = algorithmic_flops_per_iter(sizes)
+    st_h = batch.status()
+    inst_iters = float(np.sum(st_h["iters"]))
+    passes = max(th["fp32_passes"], 1)
+    achieved = fpi * inst_iters / (th["engine_ms"] / 1e3) / 1e12 if th["engine_ms"] > 0 else None
+    peak = N_SM * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    shape = batch.shape(opf.PREC_FP32)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": BATCH_ENGINE_TRAFFIC_PER_LAUNCH,
+            "traffic_unit": "DRAM bytes per engine launch (ncu)",
+            "kernel": "k_batch_engine<float> (FP32; %d instances per CTA, %d warps, %d CTAs; factors, u and x "
+                      "in shared memory, lambda and bbar~ streamed from L2)"
+                      % (shape["k_inst"], shape["warps"], shape["ctas"]),
+            "flops_per_instance_iteration": fpi,
+            "instance_iterations_timed": inst_iters,
+            "launches_timed": passes,
+            "engine_ms": th["engine_ms"],
+            "peak_source": "FP32 FMA lanes x 2 flops x max SM clock (152 x 128 x 2 x 2070 MHz)",
+            "note": "instance iterations include the FP64 polish (%d pass(es), under 1%% of them)"
+                    % th["fp64_passes"]}
+
+    plain = plain_fp64_reference(opf, f, local, stream)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": batch_config(n),
+                "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
+                               "note": "every instance of a batch returns with the batch"},
+                "phases_ms": {"fp32": fp32_ms / args.steps, "fp64_polish": fp64_ms / args.steps},
+                "iterations": {"mean": float(np.mean(iters)), "max": int(np.max(st["iters"])),
+                               "min": int(np.min(st["iters"]))},
+                "converged": int(np.sum(st["converged"])), "max_pres": float(np.max(st["pres"])),
+                "objective_mean": float(np.mean(objs)),
+                "plain_fp64": dict(plain, speedup=value / plain["value"]),
+                "shape": shape, "tune_log": batch.tune_log(),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "roofline": roof, "clocks": clocks, "gpu_launches": int(launches)}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(fs)
+        print(json.dumps(line), flush=True)
+    batch.close()
+    solver.close()
+    return 0
+
+
+def run_single(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
     import __graft_entry__
     __graft_entry__.build()
     from paper_2310_09410_gb300 import opf
@@ -250,7 +428,6 @@ def main():
     stream = torch.cuda.Stream(device=local)
     solver = opf.Solver.from_feeder(f, device=local, stream=stream.cuda_stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
-
     flags = opf.SOLVE_HOST_LOOP if args.host_loop else 0
 
     def step():
@@ -262,7 +439,7 @@ def main():
     for _ in range(args.warmup):
         step()
     solver.precompute()
-    sizes = solver.sizes()            # factor sizes are known after the precomputation
+    sizes = solver.sizes()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -286,7 +463,7 @@ def main():
         iter_ms.append(st["iterate_ms"])
         it_main += st["main_iters"]
         it_pol += st["polish_iters"]
-        launches += count_launches(st, args.precision)
+        launches += count_launches_single(st, args.precision)
         if not ok:
             raise SystemExit("a timed solve did not converge")
     torch.cuda.synchronize()
@@ -296,7 +473,6 @@ def main():
     total_ms = max_over_ranks(float(sum(times)), world, f"cuda:{local}")
     value = world * args.steps / (total_ms / 1e3)
 
-    # end to end through the C ABI from host arrays (create, precompute, solve, read x)
     e2e_times = []
     h2d = d2h = 0
     for _ in range(max(3, args.steps // 4)):
@@ -312,7 +488,6 @@ def main():
     e2e_total = max_over_ranks(sum(e2e_times), world, f"cuda:{local}")
     e2e_value = world * len(e2e_times) / e2e_total
 
-    # roofline of the dominant kernel: the iteration phase (one-CTA engine or grid iterations)
     w = 4 if args.precision == "mixed" else 8
     bpi = algorithmic_bytes_per_iter(sizes, w)
     n_it = it_main if args.precision == "mixed" else sum(iters)
@@ -326,15 +501,15 @@ def main():
             "algorithmic_bytes_per_launch": bpi * ITERS_PER_LAUNCH if mixed else None,
             "kernel": "k_warp_engine (FP32 iterations; one warp per subsystem, factors in registers, "
                       "instance resident in one thread-block cluster)"
-            if args.precision == "mixed" else "k_tile_iter<double> (FP64 iterations, one CTA per tile)",
+            if mixed else "k_tile_iter<double> (FP64 iterations, one CTA per tile)",
             "bytes_per_iter": bpi, "iters_timed": n_it, "peak_source": peak_kind + " hbm_gbs"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64" if args.precision == "mixed" else "f64",
-                "data": "synthetic", "config": workload_config(args.precision),
+                "dtype": "f32+f64" if mixed else "f64",
+                "data": "synthetic", "config": single_config(args.precision),
                 "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
                 "iterations": {"mean": float(np.mean(iters)), "main": it_main // args.steps,
                                "polish": it_pol // args.steps},
@@ -343,12 +518,48 @@ def main():
                         "d2h_bytes_per_step": int(d2h)},
                 "roofline": roof, "clocks": clocks, "gpu_launches": int(launches)}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(f)
+            line["cpu_baseline"] = cpu_baseline([f], what="the same instance")
         print(json.dumps(line), flush=True)
     solver.close()
-    if world > 1:
-        dist.destroy_process_group()
     return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "single"])
+    ap.add_argument("--instances", type=int, default=N_SCEN)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="single-instance workload only")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the iteration kernels directly instead of one graph with a device WHILE "
+                         "node (same kernels and arithmetic; profilers cannot see kernels in such graphs)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        if args.workload == "batch":
+            return run_batch(args, rank, world, local)
+        return run_single(args, rank, world, local)
+    finally:
+        if world > 1:
+            dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -273,6 +273,12 @@ int opf_batch_set_rhs(opf_batch *b, int32_t first, int32_t count, const double *
 int opf_batch_set_loads(opf_batch *b, int32_t first, int32_t count, const double *load_p,
                         const double *load_q);
 
+/* As opf_batch_set_loads with load_p, load_q in device memory of the
+ * handle's device (no host transfer); the caller keeps them alive until the
+ * handle's stream has passed this call. */
+int opf_batch_set_loads_device(opf_batch *b, int32_t first, int32_t count, const double *load_p,
+                               const double *load_q);
+
 /* Runs every instance to its own stopping test (options as opf_solve_ex;
  * engine and cluster ignored).  OPF_PREC_MIXED: FP32 iterations re-centred
  * every recenter_every iterations on an FP64 reference, then FP64 iterations
@@ -307,7 +313,9 @@ int opf_batch_get_status(opf_batch *b, int32_t first, int32_t count, double *res
 int opf_batch_get_locals(opf_batch *b, int32_t inst, double *xs, double *lam);
 
 /* Last solve: [0] FP32 phase ms, [1] FP64 phase ms, [2] autotune ms (0 when
- * the shape was known), [3] mean iterations, [4] converged instances. */
+ * the shape was known), [3] mean iterations, [4] converged instances,
+ * [5] FP32 loop passes (engine launches), [6] FP64 loop passes, [7] FP32
+ * engine-kernel ms alone (timed only with OPF_SOLVE_HOST_LOOP, else 0). */
 int opf_batch_get_timing(opf_batch *b, double *out, int32_t n_out);
 
 /* (k_inst, warps, ms) triples timed by the last FP32 autotune; returns how

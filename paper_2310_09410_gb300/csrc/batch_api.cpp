@@ -113,6 +113,10 @@ struct opf_batch {
     bool have_x = false;
     double timing[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t eng_ev[2] = {nullptr, nullptr};
+    double engine_ms[2] = {0, 0};        // host-loop runs: engine launches alone (FP32, FP64)
+    long long bodies[2] = {0, 0};        // loop passes of the last solve (FP32, FP64)
+    long long iter_base[2] = {0, 0};     // iteration count at the start of each phase
     std::vector<double> tune_log;   // (K, W, ms) triples of the last autotune
 };
 
@@ -363,7 +367,8 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
 // "still running" flag (and graph condition).
 template <typename T>
 void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_every,
-                  cudaGraphConditionalHandle cond, int use_cond) {
+                  cudaGraphConditionalHandle cond, int use_cond, cudaEvent_t e0 = nullptr,
+                  cudaEvent_t e1 = nullptr) {
     opf_handle *h = b->h;
     cudaStream_t s = h->stream;
     launch_bref<T>(b->n, h->S, b->G, b->L, p.K, p.ks, p.NCH, p.NB, p.d_ipos, h->d_gseg, h->d_uslot, b->d_bidx,
@@ -371,16 +376,25 @@ void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_eve
                    (T *)p.xrf, (T *)p.lbt, (T *)p.ubt, h->d_sub, h->d_sub2, h->d_F64, h->d_gk, p.d_sch,
                    b->d_bbar, (T *)p.bt, (T *)p.ds, (T *)p.mu, (T *)p.lref, s);
     BatchArgs<T> a = engine_args<T>(b, p, rho);
+    if (e0) cudaEventRecord(e0, s);
     batch_engine_launch<T>(a, p.nq, p.fg, p.C, p.threads, p.bytes, n_iters, check_every, s);
+    if (e1) cudaEventRecord(e1, s);
     launch_bunshift<T>(b->n, b->G, b->L, p.K, p.ks, p.NCH, p.d_ipos, h->d_gk, p.d_sch, b->d_xref,
                        (const T *)p.ds, (const T *)p.mu, (const T *)p.xo, b->d_st, b->d_xs, b->d_lam, b->d_x, s);
     launch_bany(b->n, b->d_st, b->d_flag, cond, use_cond, s);
 }
 
 void enqueue_body_any(opf_batch *b, BPlan &p, double rho, int n_iters, int k, cudaGraphConditionalHandle c,
-                      int use) {
-    if (p.dbl) enqueue_body<double>(b, p, rho, n_iters, k, c, use);
-    else enqueue_body<float>(b, p, rho, n_iters, k, c, use);
+                      int use, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
+    if (p.dbl) enqueue_body<double>(b, p, rho, n_iters, k, c, use, e0, e1);
+    else enqueue_body<float>(b, p, rho, n_iters, k, c, use, e0, e1);
+}
+
+int read_status(opf_batch *b) {
+    b->h_st.resize(b->n);
+    BCUDA(cudaMemcpyAsync(b->h_st.data(), b->d_st, b->n * sizeof(DevStatus), cudaMemcpyDeviceToHost, b->h->stream));
+    BCUDA(cudaStreamSynchronize(b->h->stream));
+    return OPF_OK;
 }
 
 // Runs "while (an instance runs) body" (a WHILE graph, or host relaunches).
@@ -388,12 +402,17 @@ int run_loop(opf_batch *b, BPlan &p, double rho, int R, int k, bool host_loop) {
     opf_handle *h = b->h;
     BTRY(plan_set_rho(b, &p, rho));
     if (host_loop) {
+        // direct launches; the engine launches are timed alone with events
         for (;;) {
-            enqueue_body_any(b, p, rho, R, k, cudaGraphConditionalHandle{}, 0);
+            enqueue_body_any(b, p, rho, R, k, cudaGraphConditionalHandle{}, 0, b->eng_ev[0], b->eng_ev[1]);
             BCUDA(cudaGetLastError());
             int flag = 0;
             BCUDA(cudaMemcpyAsync(&flag, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
             BCUDA(cudaStreamSynchronize(h->stream));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, b->eng_ev[0], b->eng_ev[1]);
+            b->engine_ms[p.dbl ? 1 : 0] += ms;
+            b->bodies[p.dbl ? 1 : 0] += 1;
             if (!flag) return OPF_OK;
         }
     }
@@ -429,13 +448,12 @@ int run_loop(opf_batch *b, BPlan &p, double rho, int R, int k, bool host_loop) {
     // only when some instance runs (the first body pass recomputes it)
     BCUDA(cudaGraphLaunch(gc.exec, h->stream));
     BCUDA(cudaStreamSynchronize(h->stream));
-    return OPF_OK;
-}
-
-int read_status(opf_batch *b) {
-    b->h_st.resize(b->n);
-    BCUDA(cudaMemcpyAsync(b->h_st.data(), b->d_st, b->n * sizeof(DevStatus), cudaMemcpyDeviceToHost, b->h->stream));
-    BCUDA(cudaStreamSynchronize(b->h->stream));
+    // passes of the loop: every pass runs R iterations of the instances still
+    // running, so the longest-running instance decides their number
+    BTRY(read_status(b));
+    long long most = 0;
+    for (const DevStatus &st : b->h_st) most = std::max(most, st.iter - b->iter_base[p.dbl ? 1 : 0]);
+    b->bodies[p.dbl ? 1 : 0] += std::max(1LL, (most + R - 1) / R);
     return OPF_OK;
 }
 
@@ -598,6 +616,8 @@ int opf_batch_create(opf_handle *h, int32_t n_inst, opf_batch **out) {
         return fail(rc);
     for (int i = 0; i < 4; ++i)
         if (cudaEventCreate(&b->ev[i]) != cudaSuccess) { set_last_error("cudaEventCreate"); return fail(OPF_E_CUDA); }
+    for (int i = 0; i < 2; ++i)
+        if (cudaEventCreate(&b->eng_ev[i]) != cudaSuccess) { set_last_error("cudaEventCreate"); return fail(OPF_E_CUDA); }
     // every instance starts as a copy of the handle's own right-hand side
     launch_bfill(n_inst, b->nrows, b->d_b0, b->d_rhs, h->stream);
     if ((rc = after_rhs(b, 0, n_inst))) return fail(rc);
@@ -619,7 +639,8 @@ int opf_batch_set_rhs(opf_batch *b, int32_t first, int32_t count, const double *
     return after_rhs(b, first, count);
 }
 
-int opf_batch_set_loads(opf_batch *b, int32_t first, int32_t count, const double *load_p, const double *load_q) {
+static int set_loads_impl(opf_batch *b, int32_t first, int32_t count, const double *load_p, const double *load_q,
+                          bool on_device) {
     BTRY(check_range(b, first, count));
     if (count == 0) return OPF_OK;
     opf_handle *h = b->h;
@@ -631,13 +652,26 @@ int opf_batch_set_loads(opf_batch *b, int32_t first, int32_t count, const double
     }
     BCUDA(cudaSetDevice(h->device));
     const size_t n = (size_t)count * nl * 3;
-    BTRY(stage(b, 2 * n));
-    BCUDA(cudaMemcpyAsync(b->d_stage, load_p, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    BCUDA(cudaMemcpyAsync(b->d_stage + n, load_q, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    launch_brhs_loads(first, count, b->nrows, nl, b->d_rsrc, b->d_rcoef, b->d_b0, b->d_stage, b->d_stage + n,
-                      b->d_rhs, h->stream);
+    const double *lp = load_p, *lq = load_q;
+    if (!on_device) {
+        BTRY(stage(b, 2 * n));
+        BCUDA(cudaMemcpyAsync(b->d_stage, load_p, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        BCUDA(cudaMemcpyAsync(b->d_stage + n, load_q, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        lp = b->d_stage;
+        lq = b->d_stage + n;
+    }
+    launch_brhs_loads(first, count, b->nrows, nl, b->d_rsrc, b->d_rcoef, b->d_b0, lp, lq, b->d_rhs, h->stream);
     BCUDA(cudaGetLastError());
     return after_rhs(b, first, count);
+}
+
+int opf_batch_set_loads(opf_batch *b, int32_t first, int32_t count, const double *load_p, const double *load_q) {
+    return set_loads_impl(b, first, count, load_p, load_q, false);
+}
+
+int opf_batch_set_loads_device(opf_batch *b, int32_t first, int32_t count, const double *load_p,
+                               const double *load_q) {
+    return set_loads_impl(b, first, count, load_p, load_q, true);
 }
 
 int opf_batch_set_shape(opf_batch *b, int32_t precision, int32_t k_inst, int32_t warps) {
@@ -690,6 +724,9 @@ int opf_batch_solve(opf_batch *b, const opf_solve_opts *opts) {
     BCUDA(cudaMemcpyAsync(b->d_st, b->h_st.data(), b->n * sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
     BCUDA(cudaEventRecord(b->ev[0], h->stream));
     double tune_ms = 0;
+    b->bodies[0] = b->bodies[1] = 0;
+    b->engine_ms[0] = b->engine_ms[1] = 0;
+    b->iter_base[0] = 0;
     if (o.precision != OPF_PREC_FP64) {
         cudaEvent_t t0 = b->ev[2], t1 = b->ev[3];
         const bool tuned_before = b->p32.ok;
@@ -704,6 +741,10 @@ int opf_batch_solve(opf_batch *b, const opf_solve_opts *opts) {
     BCUDA(cudaEventRecord(b->ev[1], h->stream));
     if (o.precision != OPF_PREC_FP32) {
         BTRY(ensure_plan(b, true, o.rho, k));
+        BTRY(read_status(b));
+        long long least = 0;
+        for (size_t i = 0; i < b->h_st.size(); ++i) least = i ? std::min(least, b->h_st[i].iter) : b->h_st[i].iter;
+        b->iter_base[1] = least;
         if (o.precision == OPF_PREC_MIXED) launch_brestart(b->n, b->d_st, 2LL * k, h->stream);
         BTRY(run_loop(b, b->p64, o.rho, R, k, hl));
     }
@@ -728,6 +769,9 @@ int opf_batch_solve(opf_batch *b, const opf_solve_opts *opts) {
     }
     b->timing[3] = it_sum / b->n;
     b->timing[4] = n_conv;
+    b->timing[5] = (double)b->bodies[0];
+    b->timing[6] = (double)b->bodies[1];
+    b->timing[7] = b->engine_ms[0];
     if (n_num) { set_last_error("batch: NaN or Inf in some instance's residuals"); return OPF_E_NUMERIC; }
     return n_conv == b->n ? OPF_OK : OPF_NOT_CONVERGED;
 }
@@ -815,6 +859,7 @@ void opf_batch_destroy(opf_batch *b) {
     for (void *p : b->allocs) cudaFree(p);
     if (b->d_stage) cudaFree(b->d_stage);
     for (auto &e : b->ev) if (e) cudaEventDestroy(e);
+    for (auto &e : b->eng_ev) if (e) cudaEventDestroy(e);
     delete b;
 }
 

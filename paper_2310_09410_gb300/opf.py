@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
     lib.opf_batch_create.argtypes = [H, C.c_int32, C.POINTER(H)]
     lib.opf_batch_set_rhs.argtypes = [H, C.c_int32, C.c_int32, _P]
     lib.opf_batch_set_loads.argtypes = [H, C.c_int32, C.c_int32, _P, _P]
+    lib.opf_batch_set_loads_device.argtypes = [H, C.c_int32, C.c_int32, _P, _P]
     lib.opf_batch_solve.argtypes = [H, C.POINTER(SolveOpts)]
     lib.opf_batch_step.argtypes = [H, C.c_double, C.c_int32]
     lib.opf_batch_set_shape.argtypes = [H, C.c_int32, C.c_int32, C.c_int32]
@@ -115,7 +116,8 @@ def load(path: str = LIB_PATH):
     for name in ("opf_create", "opf_create_generic", "opf_precompute", "opf_solve", "opf_solve_ex",
                  "opf_step", "opf_reset", "opf_get_solution", "opf_get_residuals", "opf_get_locals",
                  "opf_set_locals", "opf_get_sizes", "opf_get_timing", "opf_global_update_static",
-                 "opf_batch_create", "opf_batch_set_rhs", "opf_batch_set_loads", "opf_batch_solve",
+                 "opf_batch_create", "opf_batch_set_rhs", "opf_batch_set_loads", "opf_batch_set_loads_device",
+                 "opf_batch_solve",
                  "opf_batch_step", "opf_batch_set_shape", "opf_batch_get_shape", "opf_batch_get_solution",
                  "opf_batch_get_status", "opf_batch_get_locals", "opf_batch_get_timing",
                  "opf_batch_get_tune_log"):
@@ -337,6 +339,11 @@ class Batch:
         _check(load().opf_batch_set_loads(self._b, int(first), lp.shape[0], _ptr(lp), _ptr(lq)),
                "opf_batch_set_loads")
 
+    def set_loads_device(self, first, count, load_p_ptr, load_q_ptr):
+        """Device pointers to [count, n_load, 3] doubles each (e.g. torch tensors' data_ptr())."""
+        _check(load().opf_batch_set_loads_device(self._b, int(first), int(count), load_p_ptr, load_q_ptr),
+               "opf_batch_set_loads_device")
+
     def set_shape(self, precision, k_inst=0, warps=0):
         _check(load().opf_batch_set_shape(self._b, int(precision), int(k_inst), int(warps)), "opf_batch_set_shape")
 
@@ -383,7 +390,8 @@ class Batch:
     def timing(self):
         t = np.zeros(8)
         _check(load().opf_batch_get_timing(self._b, _ptr(t), 8), "opf_batch_get_timing")
-        return {"fp32_ms": t[0], "fp64_ms": t[1], "tune_ms": t[2], "mean_iters": t[3], "converged": int(t[4])}
+        return {"fp32_ms": t[0], "fp64_ms": t[1], "tune_ms": t[2], "mean_iters": t[3], "converged": int(t[4]),
+                "fp32_passes": int(t[5]), "fp64_passes": int(t[6]), "engine_ms": t[7]}
 
     def tune_log(self):
         lib = load()

@@ -78,3 +78,15 @@ def test_generic_validation_on_host(lib):
     with pytest.raises(opf.OPFError) as e:
         opf.Solver.from_generic(np.zeros(6), -np.ones(6), np.ones(6), uncovered)
     assert e.value.code == opf.OPF_E_INVALID
+
+
+def test_batch_entry_points_reject_bad_handles_on_host(lib):
+    out = ctypes.c_void_p()
+    lib.opf_batch_create.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]
+    assert lib.opf_batch_create(None, 4, ctypes.byref(out)) == opf.OPF_E_INVALID
+    assert lib.opf_batch_solve(None, None) == opf.OPF_E_INVALID
+    assert lib.opf_batch_step(None, 100.0, 10) == opf.OPF_E_INVALID
+    assert lib.opf_batch_set_shape(None, opf.PREC_FP32, 8, 16) == opf.OPF_E_INVALID
+    assert lib.opf_batch_get_status(None, 0, 1, None, None, None) == opf.OPF_E_INVALID
+    assert lib.opf_batch_set_loads(None, 0, 1, None, None) == opf.OPF_E_INVALID
+    lib.opf_batch_destroy(None)                      # a no-op
