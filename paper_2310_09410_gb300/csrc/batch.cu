@@ -134,10 +134,11 @@ template <typename T, int K, int NQT>
 __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *us, const T *xs, T *mu_c,
                                            const T *bt_c, T *ds_c, const T *lr_c, const T *xr_c,
                                            const int4 *chg, int jpos, int sc, T rho, T inv_rho, bool check,
-                                           bool act, bool wds, double acc[6]) {
+                                           bool act, bool wds, double *redw) {
     constexpr int J = 32 / K;
     const int mode1 = (tk.modes >> (jpos >> tk.lp)) & 1;
     T v[4 * NQT], y[4 * NQT];
+    double c0 = 0.0, c1 = 0.0, c3 = 0.0, c4 = 0.0;
     const int ch0 = tk.ch0 + jpos;
 #pragma unroll
     for (int q = 0; q < NQT; ++q) {
@@ -216,35 +217,51 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
             const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
             const Q4<T> o4 = ld4cg(ds_c + off);
             const Q4<T> l4 = ld4cg(lr_c + off);
+            T t0 = T(0), t1 = T(0), t3 = T(0), t4 = T(0);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (gg[e] < 0) continue;
-                const double xg = (double)xs[gg[e] + sc];
-                const double xsd = (double)x4.v[e];
-                const double d0 = xg - xsd, d1 = xsd - (double)o4.v[e];
-                const double xa = xsd + (double)__ldcg(xr_c + gg[e]);
-                const double la = (double)m4.v[e] + (double)l4.v[e];
-                acc[0] += d0 * d0;
-                acc[1] += d1 * d1;
-                acc[3] += xa * xa;
-                acc[4] += la * la;
+                const T d0 = xs[gg[e] + sc] - x4.v[e], d1 = x4.v[e] - o4.v[e];
+                const T xa = x4.v[e] + __ldcg(xr_c + gg[e]);
+                const T la = m4.v[e] + l4.v[e];
+                t0 += d0 * d0;
+                t1 += d1 * d1;
+                t3 += xa * xa;
+                t4 += la * la;
             }
+            c0 += (double)t0;
+            c1 += (double)t1;
+            c3 += (double)t3;
+            c4 += (double)t4;
         }
         if (act) {
             st4cg(mu_c + off, m4);
             if (wds) st4cg(ds_c + off, x4);
         }
     }
+    if (check) {
+        // per instance column: sum over the J member positions, in lane order
+        for (int o = K; o < 32; o <<= 1) {
+            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            c3 += __shfl_xor_sync(0xffffffffu, c3, o);
+            c4 += __shfl_xor_sync(0xffffffffu, c4, o);
+        }
+        if (jpos == 0) {
+            redw[sc * 6 + 0] += c0;
+            redw[sc * 6 + 1] += c1;
+            redw[sc * 6 + 3] += c3;
+            redw[sc * 6 + 4] += c4;
+        }
+    }
 }
-
-// Globals per thread whose segment records stay in registers.
-constexpr int kGR = 8;
 
 // K: instance columns per CTA (compile time), J = 32 / K member positions.
 // NQ: chunks of 4 slots a lane can hold (registers v and y: 2 * 4 * NQ).
 // FG: factors read from global memory (L1/L2) instead of shared memory.
 template <typename T, int K, int NQ, bool FG>
-__global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_iters, int check_every) {
+__global__ void __launch_bounds__(512, 1)
+    k_batch_engine(BatchArgs<T> a, int n_iters, int check_every) {
     constexpr int J = 32 / K;
     constexpr int KS = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : K == 16 ? 4 : 5;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -254,6 +271,7 @@ __global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_i
     T *xs = reinterpret_cast<T *>(smraw + a.off_x);
     double *red = reinterpret_cast<double *>(smraw + a.off_red);
     int *flags = reinterpret_cast<int *>(smraw + a.off_flag);    // [0,K) running, [K,2K) just finished
+    int *tnext = flags + 2 * K;                                    // next task of the dynamic schedule
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int nthr = blockDim.x;
     const int c = blockIdx.x;
@@ -284,100 +302,127 @@ __global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_i
         for (int e = 0; e < 4; ++e) u.v[e] = a.rho * d.v[e] - m.v[e];
         st4(us + i, u);
     }
-    // segment records of this thread's globals i = tid + r * nthr
-    unsigned gseg[kGR];
-    int gbnd[kGR];
-#pragma unroll
-    for (int r = 0; r < kGR; ++r) {
-        const int i = tid + r * nthr;
-        gseg[r] = 0u;
-        gbnd[r] = -1;
-        if (i < a.G) {
-            const int4 gt = __ldg(a.gtab + i);
-            gseg[r] = (unsigned)gt.x | ((unsigned)gt.y << 24);
-            gbnd[r] = gt.z;
-        }
-    }
     __syncthreads();
+    constexpr int KQ = K < 4 ? K : 4;          // columns per global-update item
+    constexpr int NQD = K / KQ;                  // items per global
+    constexpr int QS = NQD == 1 ? 0 : NQD == 2 ? 1 : NQD == 4 ? 2 : 3;
+    const int GQ = a.G * NQD;
     const int sc = tid & (K - 1);
     const int jpos = lane >> KS;
     const T *xr_c = a.xrf + gb + sc;
     const T rho = a.rho, inv_rho = a.inv_rho;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double *redw = red + (size_t)w * K * 6;      // this warp's test sums per column
+    const int n_warps = nthr >> 5;
     int last_check = 0;
     const int GK = a.G * K;
     for (int it = 0; it < n_iters; ++it) {
         const bool check = check_every > 0 && ((it + 1) % check_every == 0);
         const bool wds = check || it == n_iters - 1 || (check_every > 0 && ((it + 2) % check_every == 0));
         const bool act = flags[sc] != 0;
-        // ---- G: global update (Eq. closed_1), one thread per global, all K columns
+        if (check && lane < K)
 #pragma unroll
-        for (int r = 0; r < kGR; ++r) {
-            const int i = tid + r * nthr;
-            if (i < a.G) {
-                const unsigned st0 = gseg[r] & 0xffffffu, cnt = gseg[r] >> 24;
-                RowK<T, K> sum, cr;
+            for (int q = 0; q < 6; ++q) redw[lane * 6 + q] = 0.0;
+        if (tid == 0) *tnext = 0;
+        // ---- G: global update (Eq. closed_1); a thread item is one global and
+        // KQ of its columns, four items per thread with their loads in flight
+        for (int b0 = tid; b0 < GQ; b0 += 4 * nthr) {
+            int4 gt[4];
+            RowK<T, KQ> cr[4];
 #pragma unroll
-                for (int q = 0; q < K; ++q) sum.v[q] = T(0);
-                load_row<T, K, true>(cr, a.ct + gb + (size_t)i * K);
+            for (int j = 0; j < 4; ++j) {
+                const int item = b0 + j * nthr;
+                gt[j] = make_int4(0, 0, -1, 0);
+                if (item < GQ) {
+                    const int i = item >> QS;
+                    gt[j] = __ldg(a.gtab + i);
+                    load_row<T, KQ, true>(cr[j], a.ct + gb + (size_t)i * K + (item & (NQD - 1)) * KQ);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int item = b0 + j * nthr;
+                if (item >= GQ) continue;
+                const int i = item >> QS, h = item & (NQD - 1);
+                RowK<T, KQ> sum;
+#pragma unroll
+                for (int k = 0; k < KQ; ++k) sum.v[k] = T(0);
                 const T rcp = __ldg(a.recip + i);
-                for (unsigned q = 0; q < cnt; ++q) {
-                    const int uo = __ldg(a.useg + st0 + q);
+                for (int q = 0; q < gt[j].y; ++q) {
+                    const int uo = __ldg(a.useg + gt[j].x + q) + h * KQ * 4;
 #pragma unroll
-                    for (int k = 0; k < K; ++k) sum.v[k] += us[uo + k * 4];
+                    for (int k = 0; k < KQ; ++k) sum.v[k] += us[uo + k * 4];
                 }
 #pragma unroll
-                for (int k = 0; k < K; ++k) sum.v[k] = (sum.v[k] - cr.v[k]) * rcp;
-                if (gbnd[r] >= 0) {
-                    RowK<T, K> lo, hi;
-                    load_row<T, K, true>(lo, a.lbt + bb + (size_t)gbnd[r] * K);
-                    load_row<T, K, true>(hi, a.ubt + bb + (size_t)gbnd[r] * K);
+                for (int k = 0; k < KQ; ++k) sum.v[k] = (sum.v[k] - cr[j].v[k]) * rcp;
+                if (gt[j].z >= 0) {
+                    RowK<T, KQ> lo, hi;
+                    load_row<T, KQ, true>(lo, a.lbt + bb + (size_t)gt[j].z * K + h * KQ);
+                    load_row<T, KQ, true>(hi, a.ubt + bb + (size_t)gt[j].z * K + h * KQ);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) sum.v[k] = clampT(sum.v[k], lo.v[k], hi.v[k]);
+                    for (int k = 0; k < KQ; ++k) sum.v[k] = clampT(sum.v[k], lo.v[k], hi.v[k]);
                 }
-                store_row<T, K>(xs + (size_t)i * K, sum);
+                store_row<T, KQ>(xs + (size_t)i * K + h * KQ, sum);
             }
         }
         __syncthreads();
         if (check) {
             // objective and ||B x||^2 per column (thread column sc = tid % K)
+            double c2 = 0.0, c5 = 0.0;
             for (int item = tid; item < GK; item += nthr) {
                 const int i = item >> KS;
                 const double xa = (double)xs[item] + (double)__ldcg(a.xrf + gb + item);
-                acc[2] += (double)__ldg(&a.gtab[i].y) * xa * xa;
-                acc[5] += (double)__ldg(a.cost + i) * xa;
+                c2 += (double)__ldg(&a.gtab[i].y) * xa * xa;
+                c5 += (double)__ldg(a.cost + i) * xa;
+            }
+            for (int o = K; o < 32; o <<= 1) {
+                c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+                c5 += __shfl_xor_sync(0xffffffffu, c5, o);
+            }
+            if (lane < K) {
+                redw[lane * 6 + 2] += c2;
+                redw[lane * 6 + 5] += c5;
             }
         }
         // ---- L: local update (Eq. closed_2) and dual update (Eq. ADMM-3)
-        for (int ti = __ldg(a.wtask + w); ti < __ldg(a.wtask + w + 1); ++ti) {
-            const BatchTask tk = a.tasks[__ldg(a.tlist + ti)];
-            switch (tk.nq) {
-                case 1: batch_task<T, K, 1>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
-                                            inv_rho, check, act, wds, acc); break;
-                case 2: batch_task<T, K, 2>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
-                                            inv_rho, check, act, wds, acc); break;
-                case 3: if constexpr (NQ >= 3) batch_task<T, K, 3>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                   a.chg, jpos, sc, rho, inv_rho, check, act,
-                                                                   wds, acc); break;
-                default: if constexpr (NQ >= 4) batch_task<T, K, 4>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                    a.chg, jpos, sc, rho, inv_rho, check, act,
-                                                                    wds, acc); break;
+        // tasks in decreasing cost; warps take the next one as they finish
+        // (test iterations: task t on warp t % n_warps, a fixed summation order)
+        {
+            int t = w;
+            if (!check) {
+                if (lane == 0) t = atomicAdd(tnext, 1);
+                t = __shfl_sync(0xffffffffu, t, 0);
+            }
+            while (t < a.n_tasks) {
+                int tn = t + n_warps;
+                if (!check) {
+                    if (lane == 0) tn = atomicAdd(tnext, 1);
+                    tn = __shfl_sync(0xffffffffu, tn, 0);
+                }
+                const BatchTask tk = a.tasks[t];
+                switch (tk.nq) {
+                    case 1: batch_task<T, K, 1>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
+                                                inv_rho, check, act, wds, redw); break;
+                    case 2: if constexpr (NQ >= 2) batch_task<T, K, 2>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c,
+                                                                       xr_c, a.chg, jpos, sc, rho, inv_rho, check,
+                                                                       act, wds, redw); break;
+                    case 3: if constexpr (NQ >= 3) batch_task<T, K, 3>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c,
+                                                                       xr_c, a.chg, jpos, sc, rho, inv_rho, check,
+                                                                       act, wds, redw); break;
+                    default: if constexpr (NQ >= 4) batch_task<T, K, 4>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c,
+                                                                        xr_c, a.chg, jpos, sc, rho, inv_rho, check,
+                                                                        act, wds, redw); break;
+                }
+                t = tn;
             }
         }
         if (check) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                for (int o = K; o < 32; o <<= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-                if (lane < K) red[((size_t)w * K + lane) * 6 + q] = acc[q];
-                acc[q] = 0.0;
-            }
             __syncthreads();
             if (tid < K) {
                 flags[K + tid] = 0;
                 if (flags[tid]) {
                     const int in = a.inst[c * K + tid];
                     double s6[6] = {0, 0, 0, 0, 0, 0};
-                    for (int ww = 0; ww < a.n_warps; ++ww)
+                    for (int ww = 0; ww < n_warps; ++ww)
 #pragma unroll
                         for (int q = 0; q < 6; ++q) s6[q] += red[((size_t)ww * K + tid) * 6 + q];
                     apply_test(&a.st[in], s6, a.rho_d, check_every);
@@ -388,13 +433,11 @@ __global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_i
                 }
             }
             __syncthreads();
-            // x~ of instances that just finished (each thread the globals it wrote)
-#pragma unroll
-            for (int r = 0; r < kGR; ++r) {
-                const int i = tid + r * nthr;
-                if (i < a.G)
-                    for (int k = 0; k < K; ++k)
-                        if (flags[K + k]) a.xo[gb + (size_t)i * K + k] = xs[(size_t)i * K + k];
+            // x~ of instances that just finished (each thread the entries it wrote)
+            for (int item = tid; item < GQ; item += nthr) {
+                const int i = item >> QS, h = item & (NQD - 1);
+                for (int k = 0; k < KQ; ++k)
+                    if (flags[K + h * KQ + k]) a.xo[gb + (size_t)i * K + h * KQ + k] = xs[(size_t)i * K + h * KQ + k];
             }
             last_check = it + 1;
             int any = 0;
@@ -405,12 +448,10 @@ __global__ void __launch_bounds__(512, 1) k_batch_engine(BatchArgs<T> a, int n_i
         }
     }
     if (tid < K && flags[tid]) a.st[a.inst[c * K + tid]].iter += n_iters - last_check;
-#pragma unroll
-    for (int r = 0; r < kGR; ++r) {
-        const int i = tid + r * nthr;
-        if (i < a.G)
-            for (int k = 0; k < K; ++k)
-                if (flags[k]) a.xo[gb + (size_t)i * K + k] = xs[(size_t)i * K + k];
+    for (int item = tid; item < GQ; item += nthr) {
+        const int i = item >> QS, h = item & (NQD - 1);
+        for (int k = 0; k < KQ; ++k)
+            if (flags[h * KQ + k]) a.xo[gb + (size_t)i * K + h * KQ + k] = xs[(size_t)i * K + h * KQ + k];
     }
 }
 

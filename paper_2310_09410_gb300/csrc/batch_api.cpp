@@ -80,7 +80,7 @@ struct BPlan {
     double rho = -1.0;
     std::vector<void *> allocs;
     BatchTask *d_tasks = nullptr;
-    int *d_wtask = nullptr, *d_tlist = nullptr, *d_tmem = nullptr, *d_sch = nullptr, *d_useg = nullptr;
+    int *d_tmem = nullptr, *d_sch = nullptr, *d_useg = nullptr;
     int *d_inst = nullptr, *d_ipos = nullptr;
     int4 *d_chg = nullptr, *d_gtab = nullptr;
     void *d_F = nullptr, *d_recip = nullptr, *d_cost = nullptr;
@@ -199,6 +199,23 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
             tasks.push_back(t);
         }
     }
+    // decreasing cost (the engine hands tasks out in this order)
+    {
+        std::vector<double> cost(tasks.size());
+        for (size_t t = 0; t < tasks.size(); ++t)
+            cost[t] = tasks[t].nq * (tasks[t].f * (6.0 * 4 + 4 + 2 * tasks[t].lp) + 40.0) + 30.0;
+        std::vector<int> ord(tasks.size());
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        std::vector<BatchTask> t2;
+        std::vector<int> m2;
+        for (int t : ord) {
+            t2.push_back(tasks[t]);
+            m2.insert(m2.end(), tmem.begin() + (size_t)t * J, tmem.begin() + (size_t)(t + 1) * J);
+        }
+        tasks.swap(t2);
+        tmem.swap(m2);
+    }
     // chunk / factor offsets and slot tables
     int ch = 0, fo = 0;
     std::vector<int4> chg;
@@ -246,32 +263,12 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
             useg[s0 + q] = (pos >> 2) * K * 4 + (pos & 3);
         }
     }
-    // list scheduling of the tasks over the warps (longest first)
-    std::vector<double> cost(tasks.size());
-    for (size_t t = 0; t < tasks.size(); ++t)
-        cost[t] = tasks[t].nq * (tasks[t].f * (6.0 * 4 + 4 + 2 * tasks[t].lp) + 40.0) + 30.0;
-    std::vector<int> ord(tasks.size());
-    std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    std::vector<std::vector<int>> wl(W);
-    std::vector<double> load(W, 0.0);
-    for (int t : ord) {
-        const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        wl[w].push_back(t);
-        load[w] += cost[t];
-    }
-    std::vector<int> wtask(W + 1, 0), tlist;
-    for (int w = 0; w < W; ++w) {
-        wtask[w] = (int)tlist.size();
-        tlist.insert(tlist.end(), wl[w].begin(), wl[w].end());
-    }
-    wtask[W] = (int)tlist.size();
     // shared memory
     p->off_u = fg ? 0u : a16((size_t)p->nF * sz);
     p->off_x = p->off_u + a16((size_t)p->NCH * K * 4 * sz);
     p->off_red = p->off_x + a16((size_t)G * K * sz);
     p->off_flag = p->off_red + a16((size_t)W * K * 6 * sizeof(double));
-    p->bytes = p->off_flag + a16((size_t)2 * K * sizeof(int));
+    p->bytes = p->off_flag + a16((size_t)(2 * K + 1) * sizeof(int));
     if (p->bytes > kMaxSmem) { set_last_error("batch plan: shared memory"); return OPF_E_CAPACITY; }
     if (G > 8 * p->threads) { set_last_error("batch plan: more than 8 globals per thread"); return OPF_E_CAPACITY; }
     const int rc = dbl ? batch_engine_prepare<double>(K, nq, fg, p->bytes) : batch_engine_prepare<float>(K, nq, fg, p->bytes);
@@ -286,8 +283,6 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     // device tables
     std::vector<void *> &A = p->allocs;
     BTRY(bupload(A, &p->d_tasks, tasks, st));
-    BTRY(bupload(A, &p->d_wtask, wtask, st));
-    BTRY(bupload(A, &p->d_tlist, tlist, st));
     BTRY(bupload(A, &p->d_tmem, tmem, st));
     BTRY(bupload(A, &p->d_sch, sch, st));
     BTRY(bupload(A, &p->d_useg, useg, st));
@@ -350,9 +345,10 @@ template <typename T>
 BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
     BatchArgs<T> a;
     memset(&a, 0, sizeof(a));
-    a.K = p.K; a.kshift = p.ks; a.J = p.J; a.NCH = p.NCH; a.G = b->G; a.NB = p.NB; a.n_warps = p.W; a.nF = p.nF;
+    a.K = p.K; a.kshift = p.ks; a.J = p.J; a.NCH = p.NCH; a.G = b->G; a.NB = p.NB; a.n_tasks = p.n_tasks;
+    a.nF = p.nF;
     a.off_u = p.off_u; a.off_x = p.off_x; a.off_red = p.off_red; a.off_flag = p.off_flag;
-    a.tasks = p.d_tasks; a.wtask = p.d_wtask; a.tlist = p.d_tlist; a.chg = p.d_chg; a.gtab = p.d_gtab;
+    a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab;
     a.useg = p.d_useg;
     a.Fpk = (const T *)p.d_F; a.recip = (const T *)p.d_recip; a.cost = (const T *)p.d_cost;
     a.mu = (T *)p.mu; a.ds = (T *)p.ds; a.xo = (T *)p.xo;
@@ -675,8 +671,9 @@ int opf_batch_set_loads_device(opf_batch *b, int32_t first, int32_t count, const
 }
 
 int opf_batch_set_shape(opf_batch *b, int32_t precision, int32_t k_inst, int32_t warps) {
+    const int wmax = 16;
     if (!b || (precision != OPF_PREC_FP32 && precision != OPF_PREC_FP64) || k_inst < 0 || k_inst > 32 ||
-        (k_inst & (k_inst - 1)) || warps < 0 || warps > 16) {
+        (k_inst & (k_inst - 1)) || warps < 0 || warps > wmax) {
         set_last_error("batch shape: precision FP32 or FP64, K a power of two <= 32 (0: auto), warps <= 16");
         return OPF_E_INVALID;
     }
