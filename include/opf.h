@@ -200,6 +200,13 @@ int opf_set_locals(opf_handle *h, const double *xs, const double *lam, size_t L)
 
 int opf_get_sizes(opf_handle *h, opf_sizes *out);
 
+/* New load values for a feeder handle (host arrays [n_load*3] like
+ * opf_feeder.load_a / load_b): only the right-hand sides of the load rows
+ * change; call opf_precompute again before iterating (OPF_E_STATE until
+ * then).  OPF_E_INVALID for generic handles or when a load has a ZIP
+ * exponent (A_s would change too). */
+int opf_set_loads(opf_handle *h, const double *load_p, const double *load_q);
+
 /* Statistics of the last precompute/solve (device times from CUDA events on
  * the handle's stream): [0] precompute ms, [1] main iteration phase ms,
  * [2] FP64 polish ms, [3] iterations in the main phase, [4] iterations in the
@@ -323,6 +330,62 @@ int opf_batch_get_timing(opf_batch *b, double *out, int32_t n_out);
 int opf_batch_get_tune_log(opf_batch *b, double *out, int32_t n_out);
 
 void opf_batch_destroy(opf_batch *b);
+
+/* ------------------------------------------------------------------ server
+ * OPF solves of several feeders and load scenarios that arrive over time,
+ * served with continuous batching: each model (feeder topology) keeps the
+ * ADMM state of its running requests resident on the device, admits queued
+ * requests into free slots as earlier ones finish, and advances all of them
+ * together; models run on separate streams.  Every request runs Algorithm 1
+ * in FP32 (re-centred every chunk_iters iterations) until its Sec. III-C
+ * test holds, then in FP64 until the test holds there (or max_iter).  A
+ * request's result does not depend on the other requests in flight.  Not
+ * thread-safe: one host thread drives a server. */
+typedef struct opf_server opf_server;
+
+typedef struct opf_server_opts {
+    double rho, eps_rel, eps_abs_pres;  /* the stopping test, as opf_solve_opts */
+    int32_t max_iter;               /* per request */
+    int32_t check_every;            /* iterations between tests; even, >= 2 */
+    int32_t chunk_iters;            /* iterations per pass (a multiple of check_every) */
+    int32_t keep_solutions;         /* 1: keep x of finished requests for opf_server_take_solution */
+    int64_t mem_budget;             /* device bytes for request slots over all models (0: no limit) */
+} opf_server_opts;
+
+int opf_server_create(const opf_server_opts *o, opf_server **out);
+
+/* Adds a model served from n_handles precomputed feeder handles of the same
+ * topology (the server keeps the pointers; destroy the server first).  When
+ * the batched engine holds the model, handles[0] carries a batch of up to
+ * `capacity` request slots (fewer if the memory budget is short); otherwise
+ * each handle serves one request at a time on a worker thread (single-
+ * instance engines).  model_id receives the model's index.  OPF_E_STATE if
+ * handles[0] is not precomputed, OPF_E_CAPACITY if the budget admits no slot. */
+int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_handles, int32_t capacity,
+                         int32_t *model_id);
+
+/* Queues a request of model `model` with its loads (host arrays [n_load*3],
+ * copied) and a caller tag that identifies it in opf_server_poll. */
+int opf_server_submit(opf_server *s, int32_t model, const double *load_p, const double *load_q, int64_t tag);
+
+/* One pass: admit, advance every running request by chunk_iters
+ * iterations, retire finished ones.  Blocks until the pass is done. */
+int opf_server_step(opf_server *s);
+
+/* Up to max_n finished requests (in finishing order): tag, converged flag,
+ * objective c^T x, iterations and latency in seconds from submit to finish
+ * (any array may be NULL).  Returns how many were written (>= 0). */
+int opf_server_poll(opf_server *s, int64_t *tags, int32_t *converged, double *objective, int32_t *iters,
+                    double *latency_s, int32_t max_n);
+
+/* x (n_global doubles) of a finished request when keep_solutions is set. */
+int opf_server_take_solution(opf_server *s, int64_t tag, double *x, int32_t n);
+
+/* [0] submitted, [1] polled, [2] queued, [3] running, [4] slots, [5] passes,
+ * [6] device bytes held for slots. */
+int opf_server_stats(opf_server *s, int64_t *out, int32_t n);
+
+void opf_server_destroy(opf_server *s);
 
 void opf_destroy(opf_handle *h);
 const char *opf_strerror(int code);

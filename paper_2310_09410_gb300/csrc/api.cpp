@@ -1262,6 +1262,33 @@ extern "C" int opf_get_sizes(opf_handle *h, opf_sizes *out) {
     return OPF_OK;
 }
 
+extern "C" int opf_set_loads(opf_handle *h, const double *load_p, const double *load_q) {
+    if (!h || !load_p || !load_q) return OPF_E_INVALID;
+    HostModel &M = h->model;
+    if (M.n_load == 0) { g_last_error = "loads: the handle was not built from a feeder"; return OPF_E_INVALID; }
+    if (M.A_depends_on_loads) {
+        g_last_error = "loads: a ZIP load exponent makes A_s depend on the load values";
+        return OPF_E_INVALID;
+    }
+    // right-hand sides of the rows fed by a load value (the others are unchanged)
+    std::vector<double> b((size_t)h->nB);
+    size_t cr = 0;
+    for (HostSub &sub : M.subs)
+        for (int i = 0; i < sub.m; ++i, ++cr) {
+            if (i < (int)sub.rsrc.size() && sub.rsrc[i] >= 0) {
+                const int src = sub.rsrc[i];
+                sub.b[i] = sub.rcoef[i] * ((src & 1) ? load_q : load_p)[src >> 1];
+            }
+            b[h->canon_row_to_dev[cr]] = sub.b[i];
+        }
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaMemcpyAsync(h->d_b, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->precomputed = false;
+    h->have_pinv = false;
+    return OPF_OK;
+}
+
 extern "C" int opf_get_timing(opf_handle *h, double *ms, int n) {
     if (!h || !ms) return OPF_E_INVALID;
     for (int i = 0; i < n && i < 6; ++i) ms[i] = h->timing[i];

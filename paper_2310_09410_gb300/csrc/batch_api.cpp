@@ -21,7 +21,7 @@
 #include <string>
 #include <vector>
 
-#include "handle.h"
+#include "batch_internal.h"
 
 namespace opf {
 template <typename T> int batch_engine_prepare(int K, int nq, bool fg, unsigned bytes);
@@ -71,56 +71,8 @@ void launch_bpack(int n_tasks, int J, const BatchTask *tasks, const int *tmem, c
 
 static constexpr unsigned kMaxSmem = 227u * 1024u;
 
-// One engine plan: shape, tables and the engine-layout arrays.
-struct BPlan {
-    bool ok = false, dbl = false, fg = false;   // fg: factors read from global memory
-    int K = 0, ks = 0, J = 0, W = 0, nq = 0, threads = 0;
-    int NCH = 0, NB = 0, nF = 0, n_tasks = 0, C = 0;
-    unsigned off_u = 0, off_x = 0, off_red = 0, off_flag = 0, bytes = 0;
-    double rho = -1.0;
-    std::vector<void *> allocs;
-    BatchTask *d_tasks = nullptr;
-    int *d_tmem = nullptr, *d_sch = nullptr, *d_useg = nullptr;
-    int *d_inst = nullptr, *d_ipos = nullptr;
-    int4 *d_chg = nullptr, *d_gtab = nullptr;
-    void *d_F = nullptr, *d_recip = nullptr, *d_cost = nullptr;
-    void *mu = nullptr, *ds = nullptr, *xo = nullptr, *bt = nullptr, *lref = nullptr;
-    void *ct = nullptr, *xrf = nullptr, *lbt = nullptr, *ubt = nullptr;
-    GraphCache graph;
-    void release() {
-        graph.reset();
-        for (void *p : allocs) cudaFree(p);
-        allocs.clear();
-        ok = false;
-    }
-};
-
-struct opf_batch {
-    opf_handle *h = nullptr;
-    int n = 0;
-    int G = 0, L = 0, S = 0, nrows = 0;
-    std::vector<void *> allocs;
-    double *d_rhs = nullptr, *d_bbar = nullptr, *d_xs = nullptr, *d_lam = nullptr, *d_xref = nullptr;
-    double *d_x = nullptr, *d_obj = nullptr, *d_b0 = nullptr, *d_rcoef = nullptr, *d_stage = nullptr;
-    size_t stage_len = 0;
-    int *d_rsrc = nullptr, *d_c2d = nullptr, *d_bidx = nullptr, *d_flag = nullptr, *d_bad = nullptr;
-    DevStatus *d_st = nullptr, *d_st_save = nullptr;
-    std::vector<DevStatus> h_st;
-    int NB = 0;
-    std::vector<int> h_bidx;
-    BPlan p32, p64;
-    int force_k32 = 0, force_w32 = 0, force_k64 = 0, force_w64 = 0;
-    bool have_x = false;
-    double timing[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaEvent_t eng_ev[2] = {nullptr, nullptr};
-    double engine_ms[2] = {0, 0};        // host-loop runs: engine launches alone (FP32, FP64)
-    long long bodies[2] = {0, 0};        // loop passes of the last solve (FP32, FP64)
-    long long iter_base[2] = {0, 0};     // iteration count at the start of each phase
-    std::vector<double> tune_log;   // (K, W, ms) triples of the last autotune
-};
-
-namespace {
+namespace opf {
+namespace bx {
 
 template <typename T>
 int balloc(std::vector<void *> &list, T **p, size_t n) {
@@ -381,7 +333,7 @@ void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_eve
 }
 
 void enqueue_body_any(opf_batch *b, BPlan &p, double rho, int n_iters, int k, cudaGraphConditionalHandle c,
-                      int use, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
+                      int use, cudaEvent_t e0, cudaEvent_t e1) {
     if (p.dbl) enqueue_body<double>(b, p, rho, n_iters, k, c, use, e0, e1);
     else enqueue_body<float>(b, p, rho, n_iters, k, c, use, e0, e1);
 }
@@ -552,8 +504,14 @@ int after_rhs(opf_batch *b, int first, int count) {
                        b->d_bad, s);
     launch_bbar(first, count, h->L, h->d_meta, h->d_sm, h->d_boff, h->d_pioff, h->d_pinv, b->nrows, b->d_rhs,
                 b->d_bbar, s);
-    launch_binit(first, count, h->L, h->d_gk, h->d_x0, b->d_xs, b->d_lam, b->d_st, 1000000, 1e-8, 1e-4, s);
+    launch_binit(first, count, h->L, h->d_gk, h->d_x0, b->d_xs, b->d_lam, b->d_st, b->init_max_iter,
+                 b->init_eps_rel, b->init_eps_abs, s);
     BCUDA(cudaGetLastError());
+    b->have_x = false;
+    // full-row-rank local systems are consistent for every rhs: nothing to read
+    bool any_rej = false;
+    for (int r : h->h_nrej) any_rej = any_rej || r > 0;
+    if (!any_rej) return OPF_OK;
     std::vector<int> bad(count);
     if (count) BCUDA(cudaMemcpyAsync(bad.data(), b->d_bad + first, count * sizeof(int), cudaMemcpyDeviceToHost, s));
     BCUDA(cudaStreamSynchronize(s));
@@ -566,7 +524,42 @@ int after_rhs(opf_batch *b, int first, int count) {
     return OPF_OK;
 }
 
-}  // namespace
+int write_status(opf_batch *b, int first, int count) {
+    BCUDA(cudaMemcpyAsync(b->d_st + first, b->h_st.data() + first, count * sizeof(DevStatus), cudaMemcpyHostToDevice,
+                          b->h->stream));
+    return OPF_OK;
+}
+
+}  // namespace bx
+}  // namespace opf
+
+int opf::bx::set_loads_impl(opf_batch *b, int first, int count, const double *load_p, const double *load_q,
+                            bool on_device) {
+    BTRY(check_range(b, first, count));
+    if (count == 0) return OPF_OK;
+    opf_handle *h = b->h;
+    const int nl = h->model.n_load;
+    if (nl == 0 || !load_p || !load_q) { set_last_error("batch: loads need a feeder model and both arrays"); return OPF_E_INVALID; }
+    if (h->model.A_depends_on_loads) {
+        set_last_error("batch: a ZIP load exponent makes A_s depend on the load values (one handle per instance)");
+        return OPF_E_INVALID;
+    }
+    BCUDA(cudaSetDevice(h->device));
+    const size_t n = (size_t)count * nl * 3;
+    const double *lp = load_p, *lq = load_q;
+    if (!on_device) {
+        BTRY(stage(b, 2 * n));
+        BCUDA(cudaMemcpyAsync(b->d_stage, load_p, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        BCUDA(cudaMemcpyAsync(b->d_stage + n, load_q, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        lp = b->d_stage;
+        lq = b->d_stage + n;
+    }
+    launch_brhs_loads(first, count, b->nrows, nl, b->d_rsrc, b->d_rcoef, b->d_b0, lp, lq, b->d_rhs, h->stream);
+    BCUDA(cudaGetLastError());
+    return after_rhs(b, first, count);
+}
+
+using namespace opf::bx;
 
 extern "C" {
 
@@ -631,32 +624,6 @@ int opf_batch_set_rhs(opf_batch *b, int32_t first, int32_t count, const double *
     BTRY(stage(b, n));
     BCUDA(cudaMemcpyAsync(b->d_stage, rhs, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     launch_brhs_perm(first, count, b->nrows, b->d_c2d, b->d_stage, b->d_rhs, h->stream);
-    BCUDA(cudaGetLastError());
-    return after_rhs(b, first, count);
-}
-
-static int set_loads_impl(opf_batch *b, int32_t first, int32_t count, const double *load_p, const double *load_q,
-                          bool on_device) {
-    BTRY(check_range(b, first, count));
-    if (count == 0) return OPF_OK;
-    opf_handle *h = b->h;
-    const int nl = h->model.n_load;
-    if (nl == 0 || !load_p || !load_q) { set_last_error("batch: loads need a feeder model and both arrays"); return OPF_E_INVALID; }
-    if (h->model.A_depends_on_loads) {
-        set_last_error("batch: a ZIP load exponent makes A_s depend on the load values (one handle per instance)");
-        return OPF_E_INVALID;
-    }
-    BCUDA(cudaSetDevice(h->device));
-    const size_t n = (size_t)count * nl * 3;
-    const double *lp = load_p, *lq = load_q;
-    if (!on_device) {
-        BTRY(stage(b, 2 * n));
-        BCUDA(cudaMemcpyAsync(b->d_stage, load_p, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        BCUDA(cudaMemcpyAsync(b->d_stage + n, load_q, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        lp = b->d_stage;
-        lq = b->d_stage + n;
-    }
-    launch_brhs_loads(first, count, b->nrows, nl, b->d_rsrc, b->d_rcoef, b->d_b0, lp, lq, b->d_rhs, h->stream);
     BCUDA(cudaGetLastError());
     return after_rhs(b, first, count);
 }

@@ -1,0 +1,80 @@
+// Internal records of the batched engine (shared by the batch C ABI and the
+// request server).
+#pragma once
+
+#include <vector>
+
+#include "handle.h"
+
+// One engine plan: shape, tables and the engine-layout arrays.
+struct BPlan {
+    bool ok = false, dbl = false, fg = false;   // fg: factors read from global memory
+    int K = 0, ks = 0, J = 0, W = 0, nq = 0, threads = 0;
+    int NCH = 0, NB = 0, nF = 0, n_tasks = 0, C = 0;
+    unsigned off_u = 0, off_x = 0, off_red = 0, off_flag = 0, bytes = 0;
+    double rho = -1.0;
+    std::vector<void *> allocs;
+    BatchTask *d_tasks = nullptr;
+    int *d_tmem = nullptr, *d_sch = nullptr, *d_useg = nullptr;
+    int *d_inst = nullptr, *d_ipos = nullptr;
+    int4 *d_chg = nullptr, *d_gtab = nullptr;
+    void *d_F = nullptr, *d_recip = nullptr, *d_cost = nullptr;
+    void *mu = nullptr, *ds = nullptr, *xo = nullptr, *bt = nullptr, *lref = nullptr;
+    void *ct = nullptr, *xrf = nullptr, *lbt = nullptr, *ubt = nullptr;
+    GraphCache graph;
+    void release() {
+        graph.reset();
+        for (void *p : allocs) cudaFree(p);
+        allocs.clear();
+        ok = false;
+    }
+};
+
+struct opf_batch {
+    opf_handle *h = nullptr;
+    int n = 0;
+    int G = 0, L = 0, S = 0, nrows = 0;
+    std::vector<void *> allocs;
+    double *d_rhs = nullptr, *d_bbar = nullptr, *d_xs = nullptr, *d_lam = nullptr, *d_xref = nullptr;
+    double *d_x = nullptr, *d_obj = nullptr, *d_b0 = nullptr, *d_rcoef = nullptr, *d_stage = nullptr;
+    size_t stage_len = 0;
+    int *d_rsrc = nullptr, *d_c2d = nullptr, *d_bidx = nullptr, *d_flag = nullptr, *d_bad = nullptr;
+    DevStatus *d_st = nullptr, *d_st_save = nullptr;
+    std::vector<DevStatus> h_st;
+    int NB = 0;
+    std::vector<int> h_bidx;
+    BPlan p32, p64;
+    int force_k32 = 0, force_w32 = 0, force_k64 = 0, force_w64 = 0;
+    bool have_x = false;
+    double timing[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // test parameters given to an instance when its rhs is set
+    long long init_max_iter = 1000000;
+    double init_eps_rel = 1e-8, init_eps_abs = 1e-4;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t eng_ev[2] = {nullptr, nullptr};
+    double engine_ms[2] = {0, 0};        // host-loop runs: engine launches alone (FP32, FP64)
+    long long bodies[2] = {0, 0};        // loop passes of the last solve (FP32, FP64)
+    long long iter_base[2] = {0, 0};     // iteration count at the start of each phase
+    std::vector<double> tune_log;   // (K, W, ms) triples of the last autotune
+};
+
+namespace opf {
+namespace bx {
+
+// Engine plan for one arithmetic type (built on first use; FP32 autotuned).
+int ensure_plan(opf_batch *b, bool dbl, double rho, int k);
+int plan_set_rho(opf_batch *b, BPlan *p, double rho);
+// One loop pass on the handle's stream: re-centre, n_iters engine iterations
+// (test every k), back to FP64, "still running" flag.
+void enqueue_body_any(opf_batch *b, BPlan &p, double rho, int n_iters, int k, cudaGraphConditionalHandle c,
+                      int use, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
+int read_status(opf_batch *b);
+// Loads of instances [first, first + count) (host or device arrays) into rhs,
+// bbar, start point and fresh status; sync_check reads the consistency flags.
+int set_loads_impl(opf_batch *b, int first, int count, const double *load_p, const double *load_q,
+                   bool on_device);
+// Device -> host status of one instance range, host -> device.
+int write_status(opf_batch *b, int first, int count);
+
+}  // namespace bx
+}  // namespace opf

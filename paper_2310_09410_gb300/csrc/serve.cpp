@@ -1,0 +1,464 @@
+// Request server (C ABI opf_server_*): OPF solves of several feeders and load
+// scenarios arriving over time, served with continuous batching.
+//
+// A model is one feeder topology.  A model whose subsystems fit the batched
+// engine gets a batch whose instances are request slots; every pass of
+// opf_server_step
+//   1. admits queued requests into free slots (slot count bounded by the
+//      device-memory budget given at creation),
+//   2. advances every running slot on the model's own stream: slots in the
+//      FP32 phase by one re-centring interval of FP32 iterations, slots in the
+//      FP64 polish by the same number of FP64 iterations,
+//   3. moves slots whose FP32 test held to the polish and retires slots whose
+//      FP64 test held (or that hit max_iter), freeing them for the next pass.
+// Models run on separate streams, so their work overlaps on the device.  An
+// instance's arithmetic never involves another slot, and its passes start
+// at multiples of the interval from its own admission, so a request gets the
+// same result alone or in any mix.
+// A model whose subsystems exceed the batched engine (the largest feeders)
+// is served by single-instance handles given by the caller, one request per
+// handle at a time, each solved by a worker thread.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "batch_internal.h"
+
+namespace opf {
+void launch_bobjective(int n_inst, int G, const double *c64, const double *x, double *obj, cudaStream_t s);
+}
+
+using namespace opf;
+using namespace opf::bx;
+
+namespace {
+
+double now_s() {
+    using clk = std::chrono::steady_clock;
+    static const clk::time_point t0 = clk::now();
+    return std::chrono::duration<double>(clk::now() - t0).count();
+}
+
+struct Request {
+    int64_t tag;
+    std::vector<double> lp, lq;
+    double t_submit;
+};
+
+struct Done {
+    int64_t tag;
+    int32_t model, converged, iters, status;
+    double objective, t_submit, t_admit, t_done;
+    std::vector<double> x;
+};
+
+struct Worker {                      // single-instance slot
+    opf_handle *h = nullptr;
+    std::thread th;
+    std::atomic<bool> busy{false}, finished{false};
+    Done result;
+};
+
+struct Model {
+    int id = 0;
+    bool batched = false;
+    opf_handle *h = nullptr;
+    opf_batch *b = nullptr;
+    int cap = 0, G = 0, nload = 0;
+    size_t slot_bytes = 0;
+    std::vector<int> state;          // per slot: 0 free, 1 FP32 phase, 2 FP64 polish
+    std::vector<int64_t> tag;
+    std::vector<double> t_submit, t_admit;
+    std::deque<Request> queue;
+    std::vector<std::unique_ptr<Worker>> workers;
+    std::vector<double> obj;
+    int running() const {
+        int n = 0;
+        for (int v : state) n += v != 0;
+        return n;
+    }
+};
+
+#define SCUDA(call)                                                                      \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+            return e_ == cudaErrorMemoryAllocation ? OPF_E_OOM : OPF_E_CUDA;             \
+        }                                                                                \
+    } while (0)
+#define STRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+
+}  // namespace
+
+struct opf_server {
+    opf_server_opts o{};
+    std::vector<std::unique_ptr<Model>> models;
+    std::vector<Done> done;          // finished, not yet polled
+    std::vector<std::pair<int64_t, std::vector<double>>> kept;   // solutions by tag (keep_solutions)
+    std::mutex mu;                   // guards `done` and `kept` (worker threads append)
+    int64_t mem_used = 0;
+    int64_t n_submitted = 0, n_completed = 0, n_passes = 0;
+};
+
+namespace {
+
+// Estimated device bytes of one batch slot: per-instance FP64 arrays and the
+// share of both engines' per-column arrays.
+size_t batch_slot_bytes(opf_handle *h) {
+    const size_t L = h->L, G = h->G, R = h->n_rows;
+    size_t fp64 = 8 * (R + 4 * L + 2 * G) + sizeof(DevStatus) * 2 + 16;
+    size_t eng = (size_t)(1.6 * L) * (4 * 4 + 4 * 8) + G * (3 * 4 + 3 * 8);
+    return fp64 + eng;
+}
+
+// Slot maps of both plans from the slot phases.
+int upload_maps(Model &m) {
+    opf_batch *b = m.b;
+    for (int pi = 0; pi < 2; ++pi) {
+        BPlan &p = pi ? b->p64 : b->p32;
+        const int want = pi ? 2 : 1;
+        std::vector<int> inst((size_t)p.C * p.K, -1), ipos(b->n, -1);
+        for (int i = 0; i < b->n; ++i)
+            if (m.state[i] == want) { inst[i] = i; ipos[i] = i; }
+        SCUDA(cudaMemcpyAsync(p.d_inst, inst.data(), inst.size() * sizeof(int), cudaMemcpyHostToDevice, b->h->stream));
+        SCUDA(cudaMemcpyAsync(p.d_ipos, ipos.data(), ipos.size() * sizeof(int), cudaMemcpyHostToDevice, b->h->stream));
+    }
+    return OPF_OK;
+}
+
+void single_worker(opf_server *s, Model *m, Worker *w, Request req, double t_admit) {
+    const opf_server_opts &o = s->o;
+    Done d;
+    d.tag = req.tag;
+    d.model = m->id;
+    d.t_submit = req.t_submit;
+    d.t_admit = t_admit;
+    d.converged = 0;
+    d.iters = 0;
+    d.objective = NAN;
+    int rc = opf_set_loads(w->h, req.lp.data(), req.lq.data());
+    if (!rc) rc = opf_precompute(w->h);
+    if (!rc) {
+        opf_solve_opts so;
+        memset(&so, 0, sizeof(so));
+        so.rho = o.rho; so.eps_rel = o.eps_rel; so.eps_abs_pres = o.eps_abs_pres; so.max_iter = o.max_iter;
+        so.check_every = o.check_every; so.precision = OPF_PREC_MIXED; so.recenter_every = o.chunk_iters;
+        rc = opf_solve_ex(w->h, &so);
+        d.converged = rc == OPF_OK;
+        if (rc == OPF_OK || rc == OPF_NOT_CONVERGED) {
+            if (o.keep_solutions) d.x.resize(m->G);
+            double obj = 0;
+            opf_get_solution(w->h, o.keep_solutions ? d.x.data() : nullptr, o.keep_solutions ? m->G : 0, &obj);
+            d.objective = obj;
+            double pr, dr, ep, ed;
+            int64_t it = 0;
+            opf_get_residuals(w->h, &pr, &dr, &ep, &ed, &it);
+            d.iters = (int32_t)it;
+            rc = OPF_OK;
+        }
+    }
+    d.status = rc;
+    d.t_done = now_s();
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (o.keep_solutions) s->kept.emplace_back(d.tag, std::move(d.x));
+        s->done.push_back(std::move(d));
+    }
+    w->finished = true;
+}
+
+int step_single(opf_server *s, Model &m) {
+    for (auto &wp : m.workers) {
+        Worker &w = *wp;
+        if (w.busy && w.finished) {
+            w.th.join();
+            w.busy = false;
+            w.finished = false;
+        }
+        if (!w.busy && !m.queue.empty()) {
+            Request r = std::move(m.queue.front());
+            m.queue.pop_front();
+            w.busy = true;
+            w.finished = false;
+            w.th = std::thread(single_worker, s, &m, &w, std::move(r), now_s());
+        }
+    }
+    return OPF_OK;
+}
+
+// Admission and one pass of a batched model (enqueue only).
+int step_batched_enqueue(opf_server *s, Model &m) {
+    opf_batch *b = m.b;
+    for (int i = 0; i < m.cap && !m.queue.empty(); ++i) {
+        if (m.state[i]) continue;
+        Request r = std::move(m.queue.front());
+        m.queue.pop_front();
+        STRY(set_loads_impl(b, i, 1, r.lp.data(), r.lq.data(), false));
+        m.state[i] = 1;
+        m.tag[i] = r.tag;
+        m.t_submit[i] = r.t_submit;
+        m.t_admit[i] = now_s();
+    }
+    if (!m.running()) return OPF_OK;
+    STRY(upload_maps(m));
+    bool any32 = false, any64 = false;
+    for (int v : m.state) { any32 = any32 || v == 1; any64 = any64 || v == 2; }
+    const int R = s->o.chunk_iters, k = s->o.check_every;
+    if (any32) {
+        STRY(plan_set_rho(b, &b->p32, s->o.rho));
+        enqueue_body_any(b, b->p32, s->o.rho, R, k, cudaGraphConditionalHandle{}, 0);
+    }
+    if (any64) {
+        STRY(plan_set_rho(b, &b->p64, s->o.rho));
+        enqueue_body_any(b, b->p64, s->o.rho, R, k, cudaGraphConditionalHandle{}, 0);
+    }
+    launch_bobjective(b->n, b->G, b->h->d_c64, b->d_x, b->d_obj, b->h->stream);
+    SCUDA(cudaGetLastError());
+    return OPF_OK;
+}
+
+// Phase changes and retirement after the model's stream finished the pass.
+int step_batched_collect(opf_server *s, Model &m) {
+    opf_batch *b = m.b;
+    if (!m.running()) return OPF_OK;
+    SCUDA(cudaStreamSynchronize(b->h->stream));
+    STRY(read_status(b));
+    m.obj.resize(b->n);
+    SCUDA(cudaMemcpyAsync(m.obj.data(), b->d_obj, b->n * sizeof(double), cudaMemcpyDeviceToHost, b->h->stream));
+    SCUDA(cudaStreamSynchronize(b->h->stream));
+    bool wrote = false;
+    const double t = now_s();
+    for (int i = 0; i < m.cap; ++i) {
+        DevStatus &st = b->h_st[i];
+        if (!m.state[i] || !st.done) continue;
+        if (m.state[i] == 1 && st.converged && !st.numeric) {
+            // the FP32 test held: continue in FP64 from the same state
+            st.done = 0;
+            st.converged = 0;
+            st.max_iter = std::max<long long>(st.max_iter, st.iter + 2LL * s->o.check_every);
+            m.state[i] = 2;
+            wrote = true;
+            continue;
+        }
+        Done d;
+        d.tag = m.tag[i];
+        d.model = m.id;
+        d.converged = st.converged;
+        d.iters = (int32_t)st.iter;
+        d.status = st.numeric ? OPF_E_NUMERIC : (st.converged ? OPF_OK : OPF_NOT_CONVERGED);
+        d.objective = m.obj[i];
+        d.t_submit = m.t_submit[i];
+        d.t_admit = m.t_admit[i];
+        d.t_done = t;
+        std::vector<double> x;
+        if (s->o.keep_solutions) {
+            x.resize(m.G);
+            SCUDA(cudaMemcpyAsync(x.data(), b->d_x + (size_t)i * m.G, m.G * sizeof(double), cudaMemcpyDeviceToHost,
+                                  b->h->stream));
+            SCUDA(cudaStreamSynchronize(b->h->stream));
+        }
+        {
+            std::lock_guard<std::mutex> g(s->mu);
+            if (s->o.keep_solutions) s->kept.emplace_back(d.tag, std::move(x));
+            s->done.push_back(std::move(d));
+        }
+        m.state[i] = 0;
+    }
+    if (wrote) {
+        STRY(write_status(b, 0, b->n));
+        SCUDA(cudaStreamSynchronize(b->h->stream));
+    }
+    return OPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int opf_server_create(const opf_server_opts *o, opf_server **out) {
+    if (!o || !out || !(o->rho > 0) || o->max_iter < 1 || o->check_every < 2 || (o->check_every & 1) ||
+        o->chunk_iters < o->check_every || o->chunk_iters % o->check_every || o->mem_budget < 0) {
+        set_last_error("server options: rho > 0, max_iter >= 1, even check_every >= 2, chunk_iters a multiple "
+                       "of check_every, mem_budget >= 0");
+        return OPF_E_INVALID;
+    }
+    opf_server *s = new opf_server();
+    s->o = *o;
+    *out = s;
+    return OPF_OK;
+}
+
+int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_handles, int32_t capacity,
+                         int32_t *model_id) {
+    if (!s || !handles || n_handles < 1 || capacity < 1 || !model_id) return OPF_E_INVALID;
+    opf_handle *h = handles[0];
+    if (!h || !h->precomputed) return OPF_E_STATE;
+    if (h->model.n_load == 0) { set_last_error("server: models are feeders (loads per request)"); return OPF_E_INVALID; }
+    if (h->model.A_depends_on_loads) {
+        set_last_error("server: a ZIP load exponent makes A_s depend on the request");
+        return OPF_E_INVALID;
+    }
+    auto m = std::make_unique<Model>();
+    m->id = (int)s->models.size();
+    m->h = h;
+    m->G = h->G;
+    m->nload = h->model.n_load;
+    // batched when both engine plans fit the model
+    const size_t per = batch_slot_bytes(h);
+    int cap = capacity;
+    if (s->o.mem_budget > 0) {
+        const int64_t left = s->o.mem_budget - s->mem_used;
+        cap = (int)std::min<int64_t>(cap, left > 0 ? left / (int64_t)per : 0);
+    }
+    bool batched = false;
+    if (cap >= 1) {
+        // does the batched engine hold this model?  (probe with one slot)
+        opf_batch *probe = nullptr;
+        int rc = opf_batch_create(h, 1, &probe);
+        if (rc == OPF_OK) rc = ensure_plan(probe, false, s->o.rho, s->o.check_every);
+        if (rc == OPF_OK) rc = ensure_plan(probe, true, s->o.rho, s->o.check_every);
+        opf_batch_destroy(probe);
+        if (rc != OPF_OK && rc != OPF_E_CAPACITY) return rc;
+        if (rc == OPF_E_CAPACITY) cap = 0;
+    }
+    if (cap >= 1) {
+        opf_batch *b = nullptr;
+        int rc = opf_batch_create(h, cap, &b);
+        if (rc == OPF_OK) {
+            b->init_max_iter = s->o.max_iter;
+            b->init_eps_rel = s->o.eps_rel;
+            b->init_eps_abs = s->o.eps_abs_pres;
+            rc = ensure_plan(b, false, s->o.rho, s->o.check_every);
+            if (rc == OPF_OK) rc = ensure_plan(b, true, s->o.rho, s->o.check_every);
+        }
+        if (rc == OPF_OK) {
+            m->b = b;
+            batched = true;
+        } else {
+            opf_batch_destroy(b);
+            if (rc != OPF_E_CAPACITY) return rc;
+        }
+    }
+    if (batched) {
+        m->batched = true;
+        m->cap = cap;
+        m->slot_bytes = per;
+        s->mem_used += (int64_t)per * cap;
+        m->state.assign(cap, 0);
+        m->tag.assign(cap, 0);
+        m->t_submit.assign(cap, 0.0);
+        m->t_admit.assign(cap, 0.0);
+    } else {
+        // one request per caller handle at a time
+        const int64_t per1 = (int64_t)h->h2d_bytes * 4 + (int64_t)(h->L + h->G) * 64;
+        int n = n_handles;
+        if (s->o.mem_budget > 0) {
+            const int64_t left = s->o.mem_budget - s->mem_used;
+            n = (int)std::min<int64_t>(n, left > 0 ? left / per1 : 0);
+        }
+        if (n < 1) { set_last_error("server: the memory budget admits no slot of this model"); return OPF_E_CAPACITY; }
+        for (int i = 0; i < n; ++i) {
+            if (!handles[i]) return OPF_E_INVALID;
+            auto w = std::make_unique<Worker>();
+            w->h = handles[i];
+            m->workers.push_back(std::move(w));
+        }
+        m->cap = n;
+        s->mem_used += per1 * n;
+    }
+    *model_id = m->id;
+    s->models.push_back(std::move(m));
+    return OPF_OK;
+}
+
+int opf_server_submit(opf_server *s, int32_t model, const double *load_p, const double *load_q, int64_t tag) {
+    if (!s || model < 0 || model >= (int)s->models.size() || !load_p || !load_q) return OPF_E_INVALID;
+    Model &m = *s->models[model];
+    Request r;
+    r.tag = tag;
+    r.lp.assign(load_p, load_p + (size_t)m.nload * 3);
+    r.lq.assign(load_q, load_q + (size_t)m.nload * 3);
+    r.t_submit = now_s();
+    m.queue.push_back(std::move(r));
+    ++s->n_submitted;
+    return OPF_OK;
+}
+
+int opf_server_step(opf_server *s) {
+    if (!s) return OPF_E_INVALID;
+    for (auto &m : s->models) {
+        if (m->batched) STRY(step_batched_enqueue(s, *m));
+        else STRY(step_single(s, *m));
+    }
+    for (auto &m : s->models)
+        if (m->batched) STRY(step_batched_collect(s, *m));
+    ++s->n_passes;
+    return OPF_OK;
+}
+
+int opf_server_poll(opf_server *s, int64_t *tags, int32_t *converged, double *objective, int32_t *iters,
+                    double *latency_s, int32_t max_n) {
+    if (!s || max_n < 0) return OPF_E_INVALID;
+    std::lock_guard<std::mutex> g(s->mu);
+    const int n = std::min<int>(max_n, (int)s->done.size());
+    for (int i = 0; i < n; ++i) {
+        const Done &d = s->done[i];
+        if (tags) tags[i] = d.tag;
+        if (converged) converged[i] = d.converged;
+        if (objective) objective[i] = d.objective;
+        if (iters) iters[i] = d.iters;
+        if (latency_s) latency_s[i] = d.t_done - d.t_submit;
+    }
+    s->done.erase(s->done.begin(), s->done.begin() + n);
+    s->n_completed += n;
+    return n;
+}
+
+int opf_server_take_solution(opf_server *s, int64_t tag, double *x, int32_t n) {
+    if (!s || !x) return OPF_E_INVALID;
+    std::lock_guard<std::mutex> g(s->mu);
+    for (size_t i = 0; i < s->kept.size(); ++i)
+        if (s->kept[i].first == tag) {
+            if (n < (int)s->kept[i].second.size()) return OPF_E_INVALID;
+            std::copy(s->kept[i].second.begin(), s->kept[i].second.end(), x);
+            s->kept.erase(s->kept.begin() + i);
+            return OPF_OK;
+        }
+    set_last_error("server: no kept solution with this tag");
+    return OPF_E_STATE;
+}
+
+int opf_server_stats(opf_server *s, int64_t *out, int32_t n) {
+    if (!s || !out) return OPF_E_INVALID;
+    int64_t queued = 0, running = 0, slots = 0;
+    for (auto &m : s->models) {
+        queued += (int64_t)m->queue.size();
+        slots += m->cap;
+        if (m->batched) running += m->running();
+        else
+            for (auto &w : m->workers) running += w->busy ? 1 : 0;
+    }
+    const int64_t v[7] = {s->n_submitted, s->n_completed, queued, running, slots, s->n_passes, s->mem_used};
+    for (int i = 0; i < n && i < 7; ++i) out[i] = v[i];
+    return OPF_OK;
+}
+
+void opf_server_destroy(opf_server *s) {
+    if (!s) return;
+    for (auto &m : s->models) {
+        for (auto &w : m->workers)
+            if (w->th.joinable()) w->th.join();
+        if (m->b) opf_batch_destroy(m->b);
+    }
+    delete s;
+}
+
+}  // extern "C"

@@ -64,6 +64,12 @@ class Sizes(C.Structure):
                 ("h2d_bytes", C.c_int64)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("rho", C.c_double), ("eps_rel", C.c_double), ("eps_abs_pres", C.c_double),
+                ("max_iter", C.c_int32), ("check_every", C.c_int32), ("chunk_iters", C.c_int32),
+                ("keep_solutions", C.c_int32), ("mem_budget", C.c_int64)]
+
+
 _lib = None
 
 
@@ -113,6 +119,16 @@ def load(path: str = LIB_PATH):
     lib.opf_batch_get_tune_log.argtypes = [H, _P, C.c_int32]
     lib.opf_batch_destroy.argtypes = [H]
     lib.opf_batch_destroy.restype = None
+    lib.opf_set_loads.argtypes = [H, _P, _P]
+    lib.opf_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(H)]
+    lib.opf_server_add_model.argtypes = [H, _P, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
+    lib.opf_server_submit.argtypes = [H, C.c_int32, _P, _P, C.c_int64]
+    lib.opf_server_step.argtypes = [H]
+    lib.opf_server_poll.argtypes = [H, _P, _P, _P, _P, _P, C.c_int32]
+    lib.opf_server_take_solution.argtypes = [H, C.c_int64, _P, C.c_int32]
+    lib.opf_server_stats.argtypes = [H, _P, C.c_int32]
+    lib.opf_server_destroy.argtypes = [H]
+    lib.opf_server_destroy.restype = None
     for name in ("opf_create", "opf_create_generic", "opf_precompute", "opf_solve", "opf_solve_ex",
                  "opf_step", "opf_reset", "opf_get_solution", "opf_get_residuals", "opf_get_locals",
                  "opf_set_locals", "opf_get_sizes", "opf_get_timing", "opf_global_update_static",
@@ -120,7 +136,9 @@ def load(path: str = LIB_PATH):
                  "opf_batch_solve",
                  "opf_batch_step", "opf_batch_set_shape", "opf_batch_get_shape", "opf_batch_get_solution",
                  "opf_batch_get_status", "opf_batch_get_locals", "opf_batch_get_timing",
-                 "opf_batch_get_tune_log"):
+                 "opf_batch_get_tune_log", "opf_set_loads", "opf_server_create", "opf_server_add_model",
+                 "opf_server_submit", "opf_server_step", "opf_server_poll", "opf_server_take_solution",
+                 "opf_server_stats"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -288,6 +306,12 @@ class Solver:
         lam = np.ascontiguousarray(lam, np.float64)
         _check(load().opf_set_locals(self._h, _ptr(xs), _ptr(lam), len(xs)), "opf_set_locals")
 
+    def set_loads(self, load_p, load_q):
+        """New load values ([n_load, 3] each); precompute() again before iterating."""
+        lp = np.ascontiguousarray(load_p, np.float64)
+        lq = np.ascontiguousarray(load_q, np.float64)
+        _check(load().opf_set_loads(self._h, _ptr(lp), _ptr(lq)), "opf_set_loads")
+
     def timing(self):
         t = np.zeros(6)
         _check(load().opf_get_timing(self._h, _ptr(t), 6), "opf_get_timing")
@@ -404,6 +428,81 @@ class Batch:
         if self._b:
             load().opf_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching request server (wraps an ``opf_server``)."""
+
+    def __init__(self, rho=100.0, eps_rel=1e-8, eps_abs_pres=1e-4, max_iter=1_000_000, check_every=50,
+                 chunk_iters=1000, keep_solutions=False, mem_budget=0):
+        lib = load()
+        o = ServerOpts(rho, eps_rel, eps_abs_pres, int(max_iter), int(check_every), int(chunk_iters),
+                       int(bool(keep_solutions)), int(mem_budget))
+        h = C.c_void_p()
+        _check(lib.opf_server_create(C.byref(o), C.byref(h)), "opf_server_create")
+        self._s = h
+        self._solvers = []             # the server refers to the handles: keep them alive
+        self._n_global = {}
+
+    def add_model(self, solvers, capacity):
+        """solvers: precomputed Solver objects of one feeder topology."""
+        solvers = list(solvers)
+        arr = (C.c_void_p * len(solvers))(*[sv._h.value if isinstance(sv._h, C.c_void_p) else sv._h
+                                            for sv in solvers])
+        mid = C.c_int32()
+        _check(load().opf_server_add_model(self._s, C.cast(arr, C.c_void_p), len(solvers), int(capacity),
+                                           C.byref(mid)), "opf_server_add_model")
+        self._solvers.extend(solvers)
+        self._n_global[mid.value] = solvers[0].sizes()["n_global"]
+        return mid.value
+
+    def submit(self, model, load_p, load_q, tag):
+        lp = np.ascontiguousarray(load_p, np.float64)
+        lq = np.ascontiguousarray(load_q, np.float64)
+        _check(load().opf_server_submit(self._s, int(model), _ptr(lp), _ptr(lq), int(tag)), "opf_server_submit")
+
+    def step(self):
+        _check(load().opf_server_step(self._s), "opf_server_step")
+
+    def poll(self, max_n=4096):
+        tags = np.zeros(max_n, np.int64)
+        conv = np.zeros(max_n, np.int32)
+        obj = np.zeros(max_n)
+        it = np.zeros(max_n, np.int32)
+        lat = np.zeros(max_n)
+        n = load().opf_server_poll(self._s, _ptr(tags), _ptr(conv), _ptr(obj), _ptr(it), _ptr(lat), int(max_n))
+        if n < 0:
+            raise OPFError(n, "opf_server_poll")
+        return [{"tag": int(tags[i]), "converged": bool(conv[i]), "objective": float(obj[i]),
+                 "iters": int(it[i]), "latency_s": float(lat[i])} for i in range(n)]
+
+    def take_solution(self, tag, model):
+        x = np.zeros(self._n_global[model])
+        _check(load().opf_server_take_solution(self._s, int(tag), _ptr(x), len(x)), "opf_server_take_solution")
+        return x
+
+    def stats(self):
+        out = np.zeros(7, np.int64)
+        _check(load().opf_server_stats(self._s, _ptr(out), 7), "opf_server_stats")
+        keys = ("submitted", "polled", "queued", "running", "slots", "passes", "mem_bytes")
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def close(self):
+        if self._s:
+            load().opf_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:

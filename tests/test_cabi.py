@@ -90,3 +90,24 @@ def test_batch_entry_points_reject_bad_handles_on_host(lib):
     assert lib.opf_batch_get_status(None, 0, 1, None, None, None) == opf.OPF_E_INVALID
     assert lib.opf_batch_set_loads(None, 0, 1, None, None) == opf.OPF_E_INVALID
     lib.opf_batch_destroy(None)                      # a no-op
+
+
+def test_server_options_and_handles_checked_on_host(lib):
+    o = opf.ServerOpts(100.0, 1e-8, 1e-4, 1000, 50, 1000, 0, 0)
+    out = ctypes.c_void_p()
+    bad = [opf.ServerOpts(-1.0, 1e-8, 1e-4, 1000, 50, 1000, 0, 0),      # rho
+           opf.ServerOpts(100.0, 1e-8, 1e-4, 1000, 3, 1000, 0, 0),       # odd check interval
+           opf.ServerOpts(100.0, 1e-8, 1e-4, 1000, 50, 1010, 0, 0),      # chunk not a multiple
+           opf.ServerOpts(100.0, 1e-8, 1e-4, 1000, 50, 1000, 0, -5)]     # budget
+    for b in bad:
+        assert lib.opf_server_create(ctypes.byref(b), ctypes.byref(out)) == opf.OPF_E_INVALID
+    assert lib.opf_server_create(ctypes.byref(o), ctypes.byref(out)) == opf.OPF_OK
+    z = np.zeros(3)
+    assert lib.opf_server_submit(out, 0, z.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p),
+                                 7) == opf.OPF_E_INVALID                 # no model 0
+    st = np.zeros(7, np.int64)
+    assert lib.opf_server_stats(out, st.ctypes.data_as(ctypes.c_void_p), 7) == opf.OPF_OK
+    assert list(st[:5]) == [0, 0, 0, 0, 0]
+    assert lib.opf_server_poll(out, None, None, None, None, None, 16) == 0
+    assert lib.opf_server_step(out) == opf.OPF_OK                        # nothing to do
+    lib.opf_server_destroy(out)
