@@ -524,13 +524,135 @@ def run_single(args, rank, world, local):
     return 0
 
 
+SERVE_SIZES = ("13", "34", "123", "8500")
+SERVE_WEIGHTS = (0.4, 0.3, 0.2, 0.1)
+SERVE_FEEDER_SEEDS = {"13": 5013, "34": 5034, "123": 5123, "8500": 5850}
+SERVE_ARRIVAL_SEED, SERVE_REQ_SEED0, SERVE_RATE = 5000, 6000, 2000.0
+
+
+def serve_config(args):
+    return {
+        "workload": "serving: Poisson arrivals (%.0f/s, seed 5000) of solve requests, feeder mix 13/34/123/8500 "
+                    "buses with weights 0.4/0.3/0.2/0.1 (topologies seeds 5013/5034/5123/5850), request r with "
+                    "the load scenario of seed 6000+r; each request FP32 + FP64 polish to eps_rel=1e-8 and "
+                    "pres<=1e-4; %d requests after %d warm-up requests; arrivals stop after the last request, "
+                    "then the server drains for at most %.0f s" % (args.rate, args.requests, args.warm_requests,
+                                                                    args.drain_s),
+        "models": "13/34/123-bus: continuous batching in the batched engine; 8500-bus: %d single-instance "
+                  "handles on worker threads" % args.big_handles,
+        "parallelism": "replicas",
+    }
+
+
+def run_serve(args, rank, world, local):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2310_09410_gb300 import opf, synth
+
+    feeders = {k: synth.preset_feeder(k, SERVE_FEEDER_SEEDS[k]) for k in SERVE_SIZES}
+    solvers = {}
+    srv = opf.Server(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, max_iter=args.max_iter)
+    mid = {}
+    caps = {"13": 1024, "34": 1024, "123": 1024}
+    for k in SERVE_SIZES:
+        hs = []
+        for _ in range(args.big_handles if k == "8500" else 1):
+            sv = opf.Solver.from_feeder(feeders[k], device=local)
+            sv.precompute()
+            hs.append(sv)
+        solvers[k] = hs
+        mid[k] = srv.add_model(hs, caps.get(k, 1))
+    rng = np.random.default_rng(SERVE_ARRIVAL_SEED)
+    n_total = args.requests + args.warm_requests
+    gaps = rng.exponential(1.0 / args.rate, size=n_total)
+    arrival = np.cumsum(gaps)
+    kind = rng.choice(len(SERVE_SIZES), size=n_total, p=SERVE_WEIGHTS)
+    loads = []
+    for r in range(n_total):
+        g = synth.load_scenario(feeders[SERVE_SIZES[kind[r]]], SERVE_REQ_SEED0 + r)
+        loads.append((g["load_a"], g["load_b"]))
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    t0 = time.perf_counter()
+    nxt = 0
+    done_t = {}
+    results = {}
+    drain_deadline = None
+    while True:
+        t_pass = time.perf_counter()
+        now = t_pass - t0
+        while nxt < n_total and arrival[nxt] <= now:
+            srv.submit(mid[SERVE_SIZES[kind[nxt]]], loads[nxt][0], loads[nxt][1], tag=nxt)
+            nxt += 1
+        srv.step()
+        tnow = time.perf_counter() - t0
+        for res in srv.poll():
+            done_t[res["tag"]] = tnow
+            results[res["tag"]] = res
+        if nxt == n_total:
+            if drain_deadline is None:
+                drain_deadline = tnow + args.drain_s
+            if len(results) == n_total or tnow > drain_deadline:
+                break
+        st = srv.stats()
+        if st["running"] == 0 and st["queued"] == 0 and nxt < n_total:
+            time.sleep(max(0.0, min(arrival[nxt] - (time.perf_counter() - t0), 0.01)))
+        elif time.perf_counter() - t_pass < 1e-3:
+            time.sleep(5e-4)            # only worker threads are busy
+    elapsed = time.perf_counter() - t0
+    clocks = sampler.stop()
+    stats = srv.stats()
+    measured = [r for r in range(args.warm_requests, n_total)]
+    lat = {k: [] for k in SERVE_SIZES}
+    conv = {k: 0 for k in SERVE_SIZES}
+    sub = {k: 0 for k in SERVE_SIZES}
+    for r in measured:
+        k = SERVE_SIZES[kind[r]]
+        sub[k] += 1
+        if r in results:
+            lat[k].append(1e3 * (done_t[r] - arrival[r]))
+            conv[k] += int(results[r]["converged"])
+    all_lat = [v for k in SERVE_SIZES for v in lat[k]]
+    t_first = arrival[args.warm_requests]
+    t_last = max((done_t[r] for r in measured if r in done_t), default=elapsed)
+    completed = sum(len(lat[k]) for k in SERVE_SIZES)
+    value = completed / max(t_last - t_first, 1e-9)
+
+    def pct(v, q):
+        return float(np.percentile(v, q)) if v else None
+    per_class = {k: {"submitted": sub[k], "completed": len(lat[k]), "converged": conv[k],
+                     "p50_ms": pct(lat[k], 50), "p99_ms": pct(lat[k], 99)} for k in SERVE_SIZES}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": stats["passes"],
+            "warmup": args.warm_requests, "ms_per_step": 1e3 * elapsed / max(stats["passes"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic", "config": serve_config(args),
+            "latency_ms": {"p50": pct(all_lat, 50), "p99": pct(all_lat, 99),
+                           "note": "from the request's arrival time to the pass that retired it"},
+            "per_class": per_class, "elapsed_s": elapsed, "server": stats, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    srv.close()
+    for hs in solvers.values():
+        for sv in hs:
+            sv.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "single"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "single", "serve"])
+    ap.add_argument("--requests", type=int, default=4000, help="serve: measured requests")
+    ap.add_argument("--warm-requests", type=int, default=200, help="serve: warm-up requests")
+    ap.add_argument("--rate", type=float, default=SERVE_RATE, help="serve: mean arrivals per second")
+    ap.add_argument("--drain-s", type=float, default=30.0, help="serve: longest drain after the last arrival")
+    ap.add_argument("--big-handles", type=int, default=2, help="serve: 8500-bus worker handles")
+    ap.add_argument("--max-iter", type=int, default=1_000_000, help="serve: iteration cap per request")
     ap.add_argument("--instances", type=int, default=N_SCEN)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="single-instance workload only")
@@ -556,6 +678,8 @@ def main():
     try:
         if args.workload == "batch":
             return run_batch(args, rank, world, local)
+        if args.workload == "serve":
+            return run_serve(args, rank, world, local)
         return run_single(args, rank, world, local)
     finally:
         if world > 1:
