@@ -532,14 +532,15 @@ SERVE_ARRIVAL_SEED, SERVE_REQ_SEED0, SERVE_RATE = 5000, 6000, 2000.0
 
 def serve_config(args):
     return {
-        "workload": "serving: Poisson arrivals (%.0f/s, seed 5000) of solve requests, feeder mix 13/34/123/8500 "
-                    "buses with weights 0.4/0.3/0.2/0.1 (topologies seeds 5013/5034/5123/5850), request r with "
-                    "the load scenario of seed 6000+r; each request FP32 + FP64 polish to eps_rel=1e-8 and "
-                    "pres<=1e-4; %d requests after %d warm-up requests; arrivals stop after the last request, "
-                    "then the server drains for at most %.0f s" % (args.rate, args.requests, args.warm_requests,
-                                                                    args.drain_s),
-        "models": "13/34/123-bus: continuous batching in the batched engine; 8500-bus: %d single-instance "
-                  "handles on worker threads" % args.big_handles,
+        "workload": f"serving: Poisson arrivals ({args.rate:.0f}/s, seed 5000) of solve requests, feeder mix "
+                    f"13/34/123/8500 buses with weights {args.mix.replace(',', '/')} (topologies seeds "
+                    f"5013/5034/5123/5850), request r with the load scenario of seed 6000+r; each request FP32 + "
+                    f"FP64 polish to eps_rel=1e-8 and pres<=1e-4; {args.requests} requests after "
+                    f"{args.warm_requests} warm-up requests; arrivals stop after the last request, then the "
+                    f"server drains for at most {args.drain_s:.0f} s",
+        "models": f"13/34/123-bus: continuous batching in the batched engine; 8500-bus: {args.big_handles} "
+                  f"single-instance handles on worker threads; the 8500-bus workers on an SM partition of "
+                  f"{args.big_sms} SMs (green context), the batched models on the remaining SMs",
         "parallelism": "replicas",
     }
 
@@ -550,15 +551,30 @@ def run_serve(args, rank, world, local):
     __graft_entry__.build()
     from paper_2310_09410_gb300 import opf, synth
 
+    weights = np.array([float(w) for w in args.mix.split(",")])
+    weights = weights / weights.sum()
     feeders = {k: synth.preset_feeder(k, SERVE_FEEDER_SEEDS[k]) for k in SERVE_SIZES}
     solvers = {}
     srv = opf.Server(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, max_iter=args.max_iter)
     mid = {}
     caps = {"13": 1024, "34": 1024, "123": 1024}
-    for k in SERVE_SIZES:
+    # SM partitions (green contexts): the single-instance workers of the
+    # 8500-bus feeder on args.big_sms SMs, the batched models on the rest, so
+    # that neither takes the other's SMs
+    parts = []
+    use_big = weights[SERVE_SIZES.index("8500")] > 0
+    if use_big and args.big_sms > 0:
+        parts = [opf.SMPartition(-args.big_sms, device=local)]
+        parts += [opf.SMPartition(args.big_sms, device=local) for _ in range(args.big_handles)]
+    for j, k in enumerate(SERVE_SIZES):
+        if weights[j] == 0:
+            continue
         hs = []
-        for _ in range(args.big_handles if k == "8500" else 1):
-            sv = opf.Solver.from_feeder(feeders[k], device=local)
+        for h in range(args.big_handles if k == "8500" else 1):
+            stream = None
+            if parts:
+                stream = parts[1 + h].stream if k == "8500" else parts[0].stream
+            sv = opf.Solver.from_feeder(feeders[k], device=local, stream=stream)
             sv.precompute()
             hs.append(sv)
         solvers[k] = hs
@@ -567,7 +583,7 @@ def run_serve(args, rank, world, local):
     n_total = args.requests + args.warm_requests
     gaps = rng.exponential(1.0 / args.rate, size=n_total)
     arrival = np.cumsum(gaps)
-    kind = rng.choice(len(SERVE_SIZES), size=n_total, p=SERVE_WEIGHTS)
+    kind = rng.choice(len(SERVE_SIZES), size=n_total, p=weights)
     loads = []
     for r in range(n_total):
         g = synth.load_scenario(feeders[SERVE_SIZES[kind[r]]], SERVE_REQ_SEED0 + r)
@@ -637,6 +653,8 @@ def run_serve(args, rank, world, local):
     for hs in solvers.values():
         for sv in hs:
             sv.close()
+    for p in parts:
+        p.close()
     return 0
 
 
@@ -653,6 +671,8 @@ def main():
     ap.add_argument("--drain-s", type=float, default=30.0, help="serve: longest drain after the last arrival")
     ap.add_argument("--big-handles", type=int, default=2, help="serve: 8500-bus worker handles")
     ap.add_argument("--max-iter", type=int, default=1_000_000, help="serve: iteration cap per request")
+    ap.add_argument("--mix", default="0.4,0.3,0.2,0.1", help="serve: weights of the 13/34/123/8500-bus requests")
+    ap.add_argument("--big-sms", type=int, default=16, help="serve: SMs of the 8500-bus workers' partition (0: none)")
     ap.add_argument("--instances", type=int, default=N_SCEN)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="single-instance workload only")

@@ -368,8 +368,11 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
  * copied) and a caller tag that identifies it in opf_server_poll. */
 int opf_server_submit(opf_server *s, int32_t model, const double *load_p, const double *load_q, int64_t tag);
 
-/* One pass: admit, advance every running request by chunk_iters
- * iterations, retire finished ones.  Blocks until the pass is done. */
+/* Progress without blocking: for each model whose previous pass finished,
+ * retire finished requests, admit queued ones and start the next pass (every
+ * running request advances by chunk_iters iterations per pass); worker
+ * threads of single-instance models start queued requests.  Call it in a
+ * loop; models progress independently of one another. */
 int opf_server_step(opf_server *s);
 
 /* Up to max_n finished requests (in finishing order): tag, converged flag,
@@ -386,6 +389,21 @@ int opf_server_take_solution(opf_server *s, int64_t tag, double *x, int32_t n);
 int opf_server_stats(opf_server *s, int64_t *out, int32_t n);
 
 void opf_server_destroy(opf_server *s);
+
+/* A CUDA stream whose kernels run only on a partition of the device's SMs
+ * (a green context), e.g. to keep the long single-instance solves of large
+ * feeders from taking the SMs the batched engine's resident CTAs need.
+ * n_sm > 0: a partition of n_sm SMs (rounded up to the device's partition
+ * granularity); n_sm < 0: the SMs left after setting -n_sm aside.  The
+ * stream is non-blocking with the given priority; *sm_count receives the
+ * partition's SM count.  Memory of the device is shared as usual.  Solves
+ * on such a stream need OPF_SOLVE_HOST_LOOP (their while-loop graph cannot be
+ * instantiated there).  Release with opf_stream_destroy_partition after the
+ * work on it finished.
+ * OPF_E_CUDA if the driver offers no green contexts. */
+int opf_stream_create_partition(int32_t device, int32_t n_sm, int32_t priority, void **stream,
+                                int32_t *sm_count);
+int opf_stream_destroy_partition(void *stream);
 
 void opf_destroy(opf_handle *h);
 const char *opf_strerror(int code);

@@ -316,7 +316,7 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
 template <typename T>
 void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_every,
                   cudaGraphConditionalHandle cond, int use_cond, cudaEvent_t e0 = nullptr,
-                  cudaEvent_t e1 = nullptr) {
+                  cudaEvent_t e1 = nullptr, int ctas = -1) {
     opf_handle *h = b->h;
     cudaStream_t s = h->stream;
     launch_bref<T>(b->n, h->S, b->G, b->L, p.K, p.ks, p.NCH, p.NB, p.d_ipos, h->d_gseg, h->d_uslot, b->d_bidx,
@@ -325,7 +325,8 @@ void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_eve
                    b->d_bbar, (T *)p.bt, (T *)p.ds, (T *)p.mu, (T *)p.lref, s);
     BatchArgs<T> a = engine_args<T>(b, p, rho);
     if (e0) cudaEventRecord(e0, s);
-    batch_engine_launch<T>(a, p.nq, p.fg, p.C, p.threads, p.bytes, n_iters, check_every, s);
+    const int grid = ctas >= 0 ? std::min(ctas, p.C) : p.C;
+    if (grid > 0) batch_engine_launch<T>(a, p.nq, p.fg, grid, p.threads, p.bytes, n_iters, check_every, s);
     if (e1) cudaEventRecord(e1, s);
     launch_bunshift<T>(b->n, b->G, b->L, p.K, p.ks, p.NCH, p.d_ipos, h->d_gk, p.d_sch, b->d_xref,
                        (const T *)p.ds, (const T *)p.mu, (const T *)p.xo, b->d_st, b->d_xs, b->d_lam, b->d_x, s);
@@ -333,9 +334,9 @@ void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_eve
 }
 
 void enqueue_body_any(opf_batch *b, BPlan &p, double rho, int n_iters, int k, cudaGraphConditionalHandle c,
-                      int use, cudaEvent_t e0, cudaEvent_t e1) {
-    if (p.dbl) enqueue_body<double>(b, p, rho, n_iters, k, c, use, e0, e1);
-    else enqueue_body<float>(b, p, rho, n_iters, k, c, use, e0, e1);
+                      int use, cudaEvent_t e0, cudaEvent_t e1, int ctas) {
+    if (p.dbl) enqueue_body<double>(b, p, rho, n_iters, k, c, use, e0, e1, ctas);
+    else enqueue_body<float>(b, p, rho, n_iters, k, c, use, e0, e1, ctas);
 }
 
 int read_status(opf_batch *b) {

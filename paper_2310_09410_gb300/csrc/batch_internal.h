@@ -66,8 +66,10 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k);
 int plan_set_rho(opf_batch *b, BPlan *p, double rho);
 // One loop pass on the handle's stream: re-centre, n_iters engine iterations
 // (test every k), back to FP64, "still running" flag.
+// ctas >= 0 launches only the first ctas CTAs of the engine (columns packed
+// from the front).
 void enqueue_body_any(opf_batch *b, BPlan &p, double rho, int n_iters, int k, cudaGraphConditionalHandle c,
-                      int use, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
+                      int use, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, int ctas = -1);
 int read_status(opf_batch *b);
 // Loads of instances [first, first + count) (host or device arrays) into rhs,
 // bbar, start point and fresh status; sync_check reads the consistency flags.

@@ -79,6 +79,9 @@ struct Model {
     std::deque<Request> queue;
     std::vector<std::unique_ptr<Worker>> workers;
     std::vector<double> obj;
+    bool inflight = false;           // a pass is enqueued and not yet collected
+    cudaEvent_t ev = nullptr;        // recorded after the pass
+    int n32 = 0, n64 = 0;            // slots in each phase during the pass
     int running() const {
         int n = 0;
         for (int v : state) n += v != 0;
@@ -119,15 +122,19 @@ size_t batch_slot_bytes(opf_handle *h) {
     return fp64 + eng;
 }
 
-// Slot maps of both plans from the slot phases.
+// Engine columns of both plans: the slots of each phase packed from column 0
+// (every pass re-centres from the FP64 state, so a slot may change column
+// between passes); n32 / n64 count them.
 int upload_maps(Model &m) {
     opf_batch *b = m.b;
     for (int pi = 0; pi < 2; ++pi) {
         BPlan &p = pi ? b->p64 : b->p32;
         const int want = pi ? 2 : 1;
         std::vector<int> inst((size_t)p.C * p.K, -1), ipos(b->n, -1);
+        int col = 0;
         for (int i = 0; i < b->n; ++i)
-            if (m.state[i] == want) { inst[i] = i; ipos[i] = i; }
+            if (m.state[i] == want) { inst[col] = i; ipos[i] = col; ++col; }
+        (pi ? m.n64 : m.n32) = col;
         SCUDA(cudaMemcpyAsync(p.d_inst, inst.data(), inst.size() * sizeof(int), cudaMemcpyHostToDevice, b->h->stream));
         SCUDA(cudaMemcpyAsync(p.d_ipos, ipos.data(), ipos.size() * sizeof(int), cudaMemcpyHostToDevice, b->h->stream));
     }
@@ -151,6 +158,9 @@ void single_worker(opf_server *s, Model *m, Worker *w, Request req, double t_adm
         memset(&so, 0, sizeof(so));
         so.rho = o.rho; so.eps_rel = o.eps_rel; so.eps_abs_pres = o.eps_abs_pres; so.max_iter = o.max_iter;
         so.check_every = o.check_every; so.precision = OPF_PREC_MIXED; so.recenter_every = o.chunk_iters;
+        // direct launches: the handle's stream may belong to an SM partition,
+        // where the solve graph of opf_solve_ex cannot be instantiated
+        so.flags = OPF_SOLVE_HOST_LOOP;
         rc = opf_solve_ex(w->h, &so);
         d.converged = rc == OPF_OK;
         if (rc == OPF_OK || rc == OPF_NOT_CONVERGED) {
@@ -209,27 +219,28 @@ int step_batched_enqueue(opf_server *s, Model &m) {
     }
     if (!m.running()) return OPF_OK;
     STRY(upload_maps(m));
-    bool any32 = false, any64 = false;
-    for (int v : m.state) { any32 = any32 || v == 1; any64 = any64 || v == 2; }
     const int R = s->o.chunk_iters, k = s->o.check_every;
-    if (any32) {
+    if (m.n32) {
         STRY(plan_set_rho(b, &b->p32, s->o.rho));
-        enqueue_body_any(b, b->p32, s->o.rho, R, k, cudaGraphConditionalHandle{}, 0);
+        enqueue_body_any(b, b->p32, s->o.rho, R, k, cudaGraphConditionalHandle{}, 0, nullptr, nullptr,
+                         (m.n32 + b->p32.K - 1) / b->p32.K);
     }
-    if (any64) {
+    if (m.n64) {
         STRY(plan_set_rho(b, &b->p64, s->o.rho));
-        enqueue_body_any(b, b->p64, s->o.rho, R, k, cudaGraphConditionalHandle{}, 0);
+        enqueue_body_any(b, b->p64, s->o.rho, R, k, cudaGraphConditionalHandle{}, 0, nullptr, nullptr,
+                         (m.n64 + b->p64.K - 1) / b->p64.K);
     }
     launch_bobjective(b->n, b->G, b->h->d_c64, b->d_x, b->d_obj, b->h->stream);
     SCUDA(cudaGetLastError());
+    SCUDA(cudaEventRecord(m.ev, b->h->stream));
+    m.inflight = true;
     return OPF_OK;
 }
 
 // Phase changes and retirement after the model's stream finished the pass.
 int step_batched_collect(opf_server *s, Model &m) {
     opf_batch *b = m.b;
-    if (!m.running()) return OPF_OK;
-    SCUDA(cudaStreamSynchronize(b->h->stream));
+    m.inflight = false;
     STRY(read_status(b));
     m.obj.resize(b->n);
     SCUDA(cudaMemcpyAsync(m.obj.data(), b->d_obj, b->n * sizeof(double), cudaMemcpyDeviceToHost, b->h->stream));
@@ -348,6 +359,7 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
         }
     }
     if (batched) {
+        SCUDA(cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming));
         m->batched = true;
         m->cap = cap;
         m->slot_bytes = per;
@@ -395,12 +407,20 @@ int opf_server_submit(opf_server *s, int32_t model, const double *load_p, const 
 int opf_server_step(opf_server *s) {
     if (!s) return OPF_E_INVALID;
     for (auto &m : s->models) {
-        if (m->batched) STRY(step_batched_enqueue(s, *m));
-        else STRY(step_single(s, *m));
+        if (!m->batched) {
+            STRY(step_single(s, *m));
+            continue;
+        }
+        // each model advances on its own: collect a finished pass, start the next
+        if (m->inflight) {
+            const cudaError_t q = cudaEventQuery(m->ev);
+            if (q == cudaErrorNotReady) continue;
+            SCUDA(q);
+            STRY(step_batched_collect(s, *m));
+            ++s->n_passes;
+        }
+        STRY(step_batched_enqueue(s, *m));
     }
-    for (auto &m : s->models)
-        if (m->batched) STRY(step_batched_collect(s, *m));
-    ++s->n_passes;
     return OPF_OK;
 }
 
@@ -457,6 +477,7 @@ void opf_server_destroy(opf_server *s) {
         for (auto &w : m->workers)
             if (w->th.joinable()) w->th.join();
         if (m->b) opf_batch_destroy(m->b);
+        if (m->ev) cudaEventDestroy(m->ev);
     }
     delete s;
 }

@@ -129,6 +129,9 @@ def load(path: str = LIB_PATH):
     lib.opf_server_stats.argtypes = [H, _P, C.c_int32]
     lib.opf_server_destroy.argtypes = [H]
     lib.opf_server_destroy.restype = None
+    lib.opf_stream_create_partition.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p),
+                                                C.POINTER(C.c_int32)]
+    lib.opf_stream_destroy_partition.argtypes = [C.c_void_p]
     for name in ("opf_create", "opf_create_generic", "opf_precompute", "opf_solve", "opf_solve_ex",
                  "opf_step", "opf_reset", "opf_get_solution", "opf_get_residuals", "opf_get_locals",
                  "opf_set_locals", "opf_get_sizes", "opf_get_timing", "opf_global_update_static",
@@ -138,7 +141,7 @@ def load(path: str = LIB_PATH):
                  "opf_batch_get_status", "opf_batch_get_locals", "opf_batch_get_timing",
                  "opf_batch_get_tune_log", "opf_set_loads", "opf_server_create", "opf_server_add_model",
                  "opf_server_submit", "opf_server_step", "opf_server_poll", "opf_server_take_solution",
-                 "opf_server_stats"):
+                 "opf_server_stats", "opf_stream_create_partition", "opf_stream_destroy_partition"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -515,3 +518,21 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+class SMPartition:
+    """A stream confined to a subset of the device's SMs (green context).
+    n_sm > 0: that many SMs; n_sm < 0: all but -n_sm SMs."""
+
+    def __init__(self, n_sm, device=0, priority=0):
+        st = C.c_void_p()
+        cnt = C.c_int32()
+        _check(load().opf_stream_create_partition(int(device), int(n_sm), int(priority), C.byref(st), C.byref(cnt)),
+               "opf_stream_create_partition")
+        self.stream = st.value
+        self.sm_count = cnt.value
+
+    def close(self):
+        if self.stream:
+            load().opf_stream_destroy_partition(C.c_void_p(self.stream))
+            self.stream = None
