@@ -659,14 +659,17 @@ __global__ void k_bunshift_globals(int n_inst, int G, int K, int kshift, const i
     }
 }
 
-// Clears the shifted marks; flag = 1 while some instance still runs (and the
-// graph condition, when a conditional node drives the loop).
-__global__ void k_bany(int n_inst, DevStatus *st, int *flag, cudaGraphConditionalHandle cond, int use_cond) {
+// Clears the shifted marks of the plan's instances (ipos >= 0); flag = 1
+// while one of them still runs (and the graph condition, when a conditional
+// node drives the loop).
+__global__ void k_bany(int n_inst, const int *ipos, DevStatus *st, int *flag, cudaGraphConditionalHandle cond,
+                       int use_cond) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
     int mine = 0;
     for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        if (ipos[i] < 0) continue;
         st[i].pad = 0;
         mine |= st[i].done ? 0 : 1;
     }
@@ -853,9 +856,9 @@ template void launch_bunshift<double>(int, int, int, int, int, int, const int *,
                                       const double *, const double *, const double *, const double *,
                                       const DevStatus *, double *, double *, double *, cudaStream_t);
 
-void launch_bany(int n_inst, DevStatus *st, int *flag, cudaGraphConditionalHandle cond, int use_cond,
-                 cudaStream_t s) {
-    k_bany<<<1, 1024, 0, s>>>(n_inst, st, flag, cond, use_cond);
+void launch_bany(int n_inst, const int *ipos, DevStatus *st, int *flag, cudaGraphConditionalHandle cond,
+                 int use_cond, cudaStream_t s) {
+    k_bany<<<1, 1024, 0, s>>>(n_inst, ipos, st, flag, cond, use_cond);
 }
 
 void launch_bobjective(int n_inst, int G, const double *c64, const double *x, double *obj, cudaStream_t s) {

@@ -50,8 +50,8 @@ template <typename T>
 void launch_bunshift(int n_inst, int G, int L, int K, int kshift, int NCH, const int *ipos, const int *gk,
                      const int *sch, const double *xref, const T *ds, const T *mu, const T *xo,
                      const DevStatus *st, double *xsv, double *lam, double *x, cudaStream_t s);
-void launch_bany(int n_inst, DevStatus *st, int *flag, cudaGraphConditionalHandle cond, int use_cond,
-                 cudaStream_t s);
+void launch_bany(int n_inst, const int *ipos, DevStatus *st, int *flag, cudaGraphConditionalHandle cond,
+                 int use_cond, cudaStream_t s);
 void launch_bobjective(int n_inst, int G, const double *c64, const double *x, double *obj, cudaStream_t s);
 void launch_brestart(int n_inst, DevStatus *st, long long add_max, cudaStream_t s);
 template <typename T>
@@ -316,9 +316,9 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
 template <typename T>
 void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_every,
                   cudaGraphConditionalHandle cond, int use_cond, cudaEvent_t e0 = nullptr,
-                  cudaEvent_t e1 = nullptr, int ctas = -1) {
+                  cudaEvent_t e1 = nullptr, int ctas = -1, cudaStream_t stream = nullptr) {
     opf_handle *h = b->h;
-    cudaStream_t s = h->stream;
+    cudaStream_t s = stream ? stream : h->stream;
     launch_bref<T>(b->n, h->S, b->G, b->L, p.K, p.ks, p.NCH, p.NB, p.d_ipos, h->d_gseg, h->d_uslot, b->d_bidx,
                    h->d_c64, h->d_lb64, h->d_ub64, rho, b->d_xs, b->d_lam, b->d_st, b->d_xref, (T *)p.ct,
                    (T *)p.xrf, (T *)p.lbt, (T *)p.ubt, h->d_sub, h->d_sub2, h->d_F64, h->d_gk, p.d_sch,
@@ -330,13 +330,13 @@ void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_eve
     if (e1) cudaEventRecord(e1, s);
     launch_bunshift<T>(b->n, b->G, b->L, p.K, p.ks, p.NCH, p.d_ipos, h->d_gk, p.d_sch, b->d_xref,
                        (const T *)p.ds, (const T *)p.mu, (const T *)p.xo, b->d_st, b->d_xs, b->d_lam, b->d_x, s);
-    launch_bany(b->n, b->d_st, b->d_flag, cond, use_cond, s);
+    launch_bany(b->n, p.d_ipos, b->d_st, p.dbl ? b->d_flag + 1 : b->d_flag, cond, use_cond, s);
 }
 
 void enqueue_body_any(opf_batch *b, BPlan &p, double rho, int n_iters, int k, cudaGraphConditionalHandle c,
-                      int use, cudaEvent_t e0, cudaEvent_t e1, int ctas) {
-    if (p.dbl) enqueue_body<double>(b, p, rho, n_iters, k, c, use, e0, e1, ctas);
-    else enqueue_body<float>(b, p, rho, n_iters, k, c, use, e0, e1, ctas);
+                      int use, cudaEvent_t e0, cudaEvent_t e1, int ctas, cudaStream_t stream) {
+    if (p.dbl) enqueue_body<double>(b, p, rho, n_iters, k, c, use, e0, e1, ctas, stream);
+    else enqueue_body<float>(b, p, rho, n_iters, k, c, use, e0, e1, ctas, stream);
 }
 
 int read_status(opf_batch *b) {
@@ -356,7 +356,8 @@ int run_loop(opf_batch *b, BPlan &p, double rho, int R, int k, bool host_loop) {
             enqueue_body_any(b, p, rho, R, k, cudaGraphConditionalHandle{}, 0, b->eng_ev[0], b->eng_ev[1]);
             BCUDA(cudaGetLastError());
             int flag = 0;
-            BCUDA(cudaMemcpyAsync(&flag, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            BCUDA(cudaMemcpyAsync(&flag, p.dbl ? b->d_flag + 1 : b->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                                  h->stream));
             BCUDA(cudaStreamSynchronize(h->stream));
             float ms = 0;
             cudaEventElapsedTime(&ms, b->eng_ev[0], b->eng_ev[1]);
@@ -581,7 +582,7 @@ int opf_batch_create(opf_handle *h, int32_t n_inst, opf_batch **out) {
     if ((rc = balloc(A, &b->d_rhs, n * R)) || (rc = balloc(A, &b->d_bbar, n * L)) || (rc = balloc(A, &b->d_xs, n * L)) ||
         (rc = balloc(A, &b->d_lam, n * L)) || (rc = balloc(A, &b->d_xref, n * G)) || (rc = balloc(A, &b->d_x, n * G)) ||
         (rc = balloc(A, &b->d_obj, n)) || (rc = balloc(A, &b->d_st, n)) || (rc = balloc(A, &b->d_st_save, n)) ||
-        (rc = balloc(A, &b->d_flag, 1)) || (rc = balloc(A, &b->d_bad, n)))
+        (rc = balloc(A, &b->d_flag, 2)) || (rc = balloc(A, &b->d_bad, n)))
         return fail(rc);
     // rhs sources (device row order) and bounded globals
     std::vector<int> rsrc(R, -1);

@@ -38,7 +38,8 @@ struct opf_batch {
     double *d_rhs = nullptr, *d_bbar = nullptr, *d_xs = nullptr, *d_lam = nullptr, *d_xref = nullptr;
     double *d_x = nullptr, *d_obj = nullptr, *d_b0 = nullptr, *d_rcoef = nullptr, *d_stage = nullptr;
     size_t stage_len = 0;
-    int *d_rsrc = nullptr, *d_c2d = nullptr, *d_bidx = nullptr, *d_flag = nullptr, *d_bad = nullptr;
+    int *d_rsrc = nullptr, *d_c2d = nullptr, *d_bidx = nullptr, *d_bad = nullptr;
+    int *d_flag = nullptr;               // [0] FP32 plan, [1] FP64 plan: an instance still runs
     DevStatus *d_st = nullptr, *d_st_save = nullptr;
     std::vector<DevStatus> h_st;
     int NB = 0;
@@ -69,7 +70,8 @@ int plan_set_rho(opf_batch *b, BPlan *p, double rho);
 // ctas >= 0 launches only the first ctas CTAs of the engine (columns packed
 // from the front).
 void enqueue_body_any(opf_batch *b, BPlan &p, double rho, int n_iters, int k, cudaGraphConditionalHandle c,
-                      int use, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, int ctas = -1);
+                      int use, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, int ctas = -1,
+                      cudaStream_t stream = nullptr);
 int read_status(opf_batch *b);
 // Loads of instances [first, first + count) (host or device arrays) into rhs,
 // bbar, start point and fresh status; sync_check reads the consistency flags.

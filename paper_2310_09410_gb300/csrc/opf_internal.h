@@ -146,6 +146,9 @@ struct WarpLayout {
     unsigned bytes;
 };
 
+// A second non-blocking stream on the same SMs as s (its green context, if any).
+int stream_sibling(cudaStream_t s, cudaStream_t *out);
+
 // ------------------------------------------------------------ batched engine
 // One warp task of the batched engine.  Lanes are (member position jpos,
 // instance column sc), lane = jpos * K + sc, J * K = 32.  A member subsystem

@@ -25,6 +25,7 @@ using PFN_gstream = CUresult (*)(CUstream *, CUgreenCtx, unsigned int, int);
 using PFN_gdestroy = CUresult (*)(CUgreenCtx);
 using PFN_sdestroy = CUresult (*)(CUstream);
 using PFN_devget = CUresult (*)(CUdevice *, int);
+using PFN_sgetg = CUresult (*)(CUstream, CUgreenCtx *);
 
 struct Fns {
     PFN_getRes getRes = nullptr;
@@ -35,6 +36,7 @@ struct Fns {
     PFN_gdestroy gdestroy = nullptr;
     PFN_sdestroy sdestroy = nullptr;
     PFN_devget devget = nullptr;
+    PFN_sgetg sgetg = nullptr;
     bool ok = false;
 };
 
@@ -59,7 +61,8 @@ const Fns &fns() {
         f.ok = entry("cuDeviceGetDevResource", &f.getRes) && entry("cuDevSmResourceSplitByCount", &f.split) &&
                entry("cuDevResourceGenerateDesc", &f.desc) && entry("cuGreenCtxCreate", &f.gctx) &&
                entry("cuGreenCtxStreamCreate", &f.gstream) && entry("cuGreenCtxDestroy", &f.gdestroy) &&
-               entry("cuStreamDestroy", &f.sdestroy) && entry("cuDeviceGet", &f.devget);
+               entry("cuStreamDestroy", &f.sdestroy) && entry("cuDeviceGet", &f.devget) &&
+               entry("cuStreamGetGreenCtx", &f.sgetg);
     });
     return f;
 }
@@ -126,4 +129,18 @@ extern "C" int opf_stream_destroy_partition(void *stream) {
     f.sdestroy((CUstream)stream);
     f.gdestroy(g);
     return OPF_OK;
+}
+
+// A second non-blocking stream on the same SMs as `s`: in s's green context
+// when s belongs to one, else an ordinary stream of the current device.
+int opf::stream_sibling(cudaStream_t s, cudaStream_t *out) {
+    const Fns &f = fns();
+    CUgreenCtx g = nullptr;
+    if (s && f.ok && f.sgetg((CUstream)s, &g) == CUDA_SUCCESS && g) {
+        CUstream st;
+        if (f.gstream(&st, g, CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS) return OPF_E_CUDA;
+        *out = (cudaStream_t)st;
+        return OPF_OK;
+    }
+    return cudaStreamCreateWithFlags(out, cudaStreamNonBlocking) == cudaSuccess ? OPF_OK : OPF_E_CUDA;
 }

@@ -80,7 +80,9 @@ struct Model {
     std::vector<std::unique_ptr<Worker>> workers;
     std::vector<double> obj;
     bool inflight = false;           // a pass is enqueued and not yet collected
-    cudaEvent_t ev = nullptr;        // recorded after the pass
+    cudaEvent_t ev = nullptr;        // recorded after the pass (on the model's stream)
+    cudaStream_t s64 = nullptr;      // FP64 slots' pass, beside the FP32 slots'
+    cudaEvent_t ev64 = nullptr, ev_start = nullptr;
     int n32 = 0, n64 = 0;            // slots in each phase during the pass
     int running() const {
         int n = 0;
@@ -220,6 +222,10 @@ int step_batched_enqueue(opf_server *s, Model &m) {
     if (!m.running()) return OPF_OK;
     STRY(upload_maps(m));
     const int R = s->o.chunk_iters, k = s->o.check_every;
+    // FP32 slots on the model's stream, FP64 slots on a second stream: the
+    // two passes touch disjoint instances and run side by side
+    SCUDA(cudaEventRecord(m.ev_start, b->h->stream));
+    SCUDA(cudaStreamWaitEvent(m.s64, m.ev_start, 0));
     if (m.n32) {
         STRY(plan_set_rho(b, &b->p32, s->o.rho));
         enqueue_body_any(b, b->p32, s->o.rho, R, k, cudaGraphConditionalHandle{}, 0, nullptr, nullptr,
@@ -228,8 +234,10 @@ int step_batched_enqueue(opf_server *s, Model &m) {
     if (m.n64) {
         STRY(plan_set_rho(b, &b->p64, s->o.rho));
         enqueue_body_any(b, b->p64, s->o.rho, R, k, cudaGraphConditionalHandle{}, 0, nullptr, nullptr,
-                         (m.n64 + b->p64.K - 1) / b->p64.K);
+                         (m.n64 + b->p64.K - 1) / b->p64.K, m.s64);
     }
+    SCUDA(cudaEventRecord(m.ev64, m.s64));
+    SCUDA(cudaStreamWaitEvent(b->h->stream, m.ev64, 0));
     launch_bobjective(b->n, b->G, b->h->d_c64, b->d_x, b->d_obj, b->h->stream);
     SCUDA(cudaGetLastError());
     SCUDA(cudaEventRecord(m.ev, b->h->stream));
@@ -360,6 +368,9 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
     }
     if (batched) {
         SCUDA(cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming));
+        SCUDA(cudaEventCreateWithFlags(&m->ev64, cudaEventDisableTiming));
+        SCUDA(cudaEventCreateWithFlags(&m->ev_start, cudaEventDisableTiming));
+        STRY(stream_sibling(h->stream, &m->s64));
         m->batched = true;
         m->cap = cap;
         m->slot_bytes = per;
@@ -478,6 +489,9 @@ void opf_server_destroy(opf_server *s) {
             if (w->th.joinable()) w->th.join();
         if (m->b) opf_batch_destroy(m->b);
         if (m->ev) cudaEventDestroy(m->ev);
+        if (m->ev64) cudaEventDestroy(m->ev64);
+        if (m->ev_start) cudaEventDestroy(m->ev_start);
+        if (m->s64) cudaStreamDestroy(m->s64);
     }
     delete s;
 }
