@@ -390,7 +390,7 @@ def run_batch(args, rank, world, local):
             "note": "instance iterations include the FP64 polish (%d pass(es), under 1%% of them)"
                     % th["fp64_passes"]}
 
-    plain = plain_fp64_reference(opf, f, local, stream)
+    plain = None if args.no_plain_fp64 else plain_fp64_reference(opf, f, local, stream)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -403,7 +403,7 @@ def run_batch(args, rank, world, local):
                                "min": int(np.min(st["iters"]))},
                 "converged": int(np.sum(st["converged"])), "max_pres": float(np.max(st["pres"])),
                 "objective_mean": float(np.mean(objs)),
-                "plain_fp64": dict(plain, speedup=value / plain["value"]),
+                "plain_fp64": dict(plain, speedup=value / plain["value"]) if plain else None,
                 "shape": shape, "tune_log": batch.tune_log(),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
@@ -677,6 +677,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="single-instance workload only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain-fp64", action="store_true",
+                    help="batch: skip the plain single-instance FP64 reference solves (profiling runs)")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the iteration kernels directly instead of one graph with a device WHILE "
                          "node (same kernels and arithmetic; profilers cannot see kernels in such graphs)")
