@@ -201,10 +201,11 @@ int opf_set_locals(opf_handle *h, const double *xs, const double *lam, size_t L)
 int opf_get_sizes(opf_handle *h, opf_sizes *out);
 
 /* New load values for a feeder handle (host arrays [n_load*3] like
- * opf_feeder.load_a / load_b): only the right-hand sides of the load rows
- * change; call opf_precompute again before iterating (OPF_E_STATE until
- * then).  OPF_E_INVALID for generic handles or when a load has a ZIP
- * exponent (A_s would change too). */
+ * opf_feeder.load_a / load_b): the right-hand sides of the load rows change,
+ * and with a ZIP exponent (alpha or beta > 0) also their w coefficients
+ * (VDLM-1..5), so M_s depends on the scenario; call opf_precompute again
+ * before iterating (OPF_E_STATE until then).  A batch created from the handle
+ * must be destroyed first.  OPF_E_INVALID for generic handles. */
 int opf_set_loads(opf_handle *h, const double *load_p, const double *load_q);
 
 /* Statistics of the last precompute/solve (device times from CUDA events on
@@ -359,7 +360,8 @@ int opf_server_create(const opf_server_opts *o, opf_server **out);
  * the batched engine holds the model, handles[0] carries a batch of up to
  * `capacity` request slots (fewer if the memory budget is short); otherwise
  * each handle serves one request at a time on a worker thread (single-
- * instance engines).  model_id receives the model's index.  OPF_E_STATE if
+ * instance engines; also for loads with ZIP exponents, where every request
+ * needs its own factorization).  model_id receives the model's index.  OPF_E_STATE if
  * handles[0] is not precomputed, OPF_E_CAPACITY if the budget admits no slot. */
 int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_handles, int32_t capacity,
                          int32_t *model_id);

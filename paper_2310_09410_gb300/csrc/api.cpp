@@ -199,6 +199,7 @@ static int build_layout(opf_handle *h) {
     }
     soff[h->S] = so;
     h->h_boff = boff;
+    h->dev_to_canon_sub = order;
     {
         std::vector<int> crow0(h->S + 1, 0);
         for (int cs = 0; cs < h->S; ++cs) crow0[cs + 1] = crow0[cs] + M.subs[cs].m;
@@ -1266,23 +1267,38 @@ extern "C" int opf_set_loads(opf_handle *h, const double *load_p, const double *
     if (!h || !load_p || !load_q) return OPF_E_INVALID;
     HostModel &M = h->model;
     if (M.n_load == 0) { g_last_error = "loads: the handle was not built from a feeder"; return OPF_E_INVALID; }
-    if (M.A_depends_on_loads) {
-        g_last_error = "loads: a ZIP load exponent makes A_s depend on the load values";
-        return OPF_E_INVALID;
-    }
-    // right-hand sides of the rows fed by a load value (the others are unchanged)
+    // rows fed by a load value: their rhs and, with a ZIP exponent, their w
+    // coefficient (VDLM-1..5); every other row is unchanged
     std::vector<double> b((size_t)h->nB);
     size_t cr = 0;
+    bool a_changed = false;
     for (HostSub &sub : M.subs)
         for (int i = 0; i < sub.m; ++i, ++cr) {
             if (i < (int)sub.rsrc.size() && sub.rsrc[i] >= 0) {
                 const int src = sub.rsrc[i];
-                sub.b[i] = sub.rcoef[i] * ((src & 1) ? load_q : load_p)[src >> 1];
+                const double val = ((src & 1) ? load_q : load_p)[src >> 1];
+                sub.b[i] = sub.rcoef[i] * val;
+                if (sub.acol[i] >= 0) {
+                    sub.A[(size_t)i * sub.n + sub.acol[i]] = sub.acoef[i] * val;
+                    a_changed = true;
+                }
             }
             b[h->canon_row_to_dev[cr]] = sub.b[i];
         }
     CUDA_TRY(cudaSetDevice(h->device));
     CUDA_TRY(cudaMemcpyAsync(h->d_b, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    std::vector<double> A;
+    if (a_changed) {
+        // A in device subsystem order (the precompute factors it again)
+        A.reserve((size_t)h->nA);
+        std::vector<int> order(h->S);
+        for (int d = 0; d < h->S; ++d) order[d] = h->dev_to_canon_sub[d];
+        for (int d = 0; d < h->S; ++d) {
+            const HostSub &sub = M.subs[order[d]];
+            A.insert(A.end(), sub.A.begin(), sub.A.end());
+        }
+        CUDA_TRY(cudaMemcpyAsync(h->d_A, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    }
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->precomputed = false;
     h->have_pinv = false;

@@ -106,6 +106,7 @@ struct opf_handle {
     WarpPlan w32;
     std::vector<int> h_tpre, h_vpre, h_foff, h_npad, h_pk, h_gk, h_gstart, h_uslot;
     std::vector<int> h_boff;                 // device subsystem -> first row (device row order)
+    std::vector<int> dev_to_canon_sub;       // device subsystem -> canonical subsystem
     std::vector<int> canon_row_to_dev;       // canonical row -> device row
     // A_s^+ and the rejected-row combinations, computed on first use (batches)
     bool have_pinv = false;

@@ -40,6 +40,8 @@ struct Row {
     double rhs = 0.0;
     int src = -1;          // rhs = coef * (load value src), see HostSub::rsrc
     double coef = 0.0;
+    int avar = -1;         // variable whose coefficient is acoef * (load value src)
+    double acoef = 0.0;
     void add(int v, double x) { a.emplace_back(v, x); }
 };
 
@@ -192,9 +194,11 @@ int build_feeder_model(const opf_feeder *f, HostModel *out, std::string *err) {
                 Row r1; r1.add(vload(l, p, PD), 1.0); r1.add(vbus(i, p), -0.5 * a * al * wscale);
                 r1.rhs = a * (1.0 - 0.5 * al);
                 r1.src = 2 * (3 * l + p); r1.coef = 1.0 - 0.5 * al;
+                if (al != 0.0) { r1.avar = vbus(i, p); r1.acoef = -0.5 * al * wscale; }
                 Row r2; r2.add(vload(l, p, QD), 1.0); r2.add(vbus(i, p), -0.5 * b * be * wscale);
                 r2.rhs = b * (1.0 - 0.5 * be);
                 r2.src = 2 * (3 * l + p) + 1; r2.coef = 1.0 - 0.5 * be;
+                if (be != 0.0) { r2.avar = vbus(i, p); r2.acoef = -0.5 * be * wscale; }
                 if (al != 0.0 || be != 0.0) M.A_depends_on_loads = true;
                 rows.push_back(r1); rows.push_back(r2);
             }
@@ -267,6 +271,8 @@ int build_feeder_model(const opf_feeder *f, HostModel *out, std::string *err) {
         s.b.resize(s.m);
         s.rsrc.resize(s.m);
         s.rcoef.resize(s.m);
+        s.acol.assign(s.m, -1);
+        s.acoef.assign(s.m, 0.0);
         std::map<int, int> col;
         for (int k = 0; k < s.n; ++k) col[s.vars[k]] = k;
         for (int r = 0; r < s.m; ++r) {
@@ -274,6 +280,10 @@ int build_feeder_model(const opf_feeder *f, HostModel *out, std::string *err) {
             s.b[r] = rows[r].rhs;
             s.rsrc[r] = rows[r].src;
             s.rcoef[r] = rows[r].coef;
+            if (rows[r].avar >= 0) {
+                s.acol[r] = col.at(rows[r].avar);
+                s.acoef[r] = rows[r].acoef;
+            }
         }
         M.subs.push_back(std::move(s));
     };

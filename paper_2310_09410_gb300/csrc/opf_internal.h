@@ -26,6 +26,10 @@ struct HostSub {
     // (-1: a constant; else 2 * (3 * load + phase) + 0 for a, 1 for b) and the factor
     std::vector<int> rsrc;
     std::vector<double> rcoef;
+    // per row: column of the entry of A proportional to the same load value
+    // (a ZIP exponent's w coefficient; -1: none) and its factor
+    std::vector<int> acol;
+    std::vector<double> acoef;
 };
 
 struct HostModel {

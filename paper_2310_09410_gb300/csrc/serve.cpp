@@ -321,10 +321,7 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
     opf_handle *h = handles[0];
     if (!h || !h->precomputed) return OPF_E_STATE;
     if (h->model.n_load == 0) { set_last_error("server: models are feeders (loads per request)"); return OPF_E_INVALID; }
-    if (h->model.A_depends_on_loads) {
-        set_last_error("server: a ZIP load exponent makes A_s depend on the request");
-        return OPF_E_INVALID;
-    }
+
     auto m = std::make_unique<Model>();
     m->id = (int)s->models.size();
     m->h = h;
@@ -338,6 +335,9 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
         cap = (int)std::min<int64_t>(cap, left > 0 ? left / (int64_t)per : 0);
     }
     bool batched = false;
+    // a ZIP exponent makes A_s (hence M_s) depend on the request's loads: each
+    // request then gets its own factorization on a single-instance handle
+    if (h->model.A_depends_on_loads) cap = 0;
     if (cap >= 1) {
         // does the batched engine hold this model?  (probe with one slot)
         opf_batch *probe = nullptr;
