@@ -130,11 +130,22 @@ __device__ __forceinline__ void st4cg(double *p, const Q4<double> &q) {
 // One warp task with exactly NQT chunks per position.  chg holds g * K per
 // slot (-1: padding); bt holds +bbar~ for members with M = F^T F and -bbar~
 // for M = I - F^T F, so that y = bt + F^T w gives x_s = y or v - y.
+// Shared-memory slot array: chunk ch, slot e, column sc at
+// (ch * 4 + (e ^ (ch & 3))) * K + sc.  Between the two phases of an
+// iteration it holds, at every slot, x of the slot's global (written there by
+// the global update); otherwise u = rho x_s - lambda of the slot.  The
+// swizzle e ^ (ch & 3) puts the four member positions of a warp (consecutive
+// chunks) on distinct banks.  Padding slots hold 0.
+template <int K>
+__device__ __forceinline__ int upos(int ch, int e, int sc) {
+    return (ch * 4 + (e ^ (ch & 3))) * K + sc;
+}
+
 template <typename T, int K, int NQT>
-__device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *us, const T *xs, T *mu_c,
-                                           const T *bt_c, T *ds_c, const T *lr_c, const T *xr_c,
-                                           const int4 *chg, int jpos, int sc, T rho, T inv_rho, bool check,
-                                           bool act, bool wds, double *redw) {
+__device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *us, T *mu_c, const T *bt_c,
+                                           T *ds_c, const T *lr_c, const T *xr_c, const int4 *chg, int jpos,
+                                           int sc, T rho, T inv_rho, bool check, bool act, bool wds,
+                                           double *redw) {
     constexpr int J = 32 / K;
     const int mode1 = (tk.modes >> (jpos >> tk.lp)) & 1;
     T v[4 * NQT], y[4 * NQT];
@@ -144,14 +155,12 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
     for (int q = 0; q < NQT; ++q) {
         const int ch = ch0 + q * J;
         const int off = (ch * K + sc) * 4;
-        const int4 g4 = __ldg(chg + ch);
         const Q4<T> m4 = ld4cg(mu_c + off);
         const Q4<T> b4 = ld4cg(bt_c + off);
-        const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             y[4 * q + e] = b4.v[e];
-            v[4 * q + e] = gg[e] >= 0 ? xs[gg[e] + sc] + m4.v[e] * inv_rho : T(0);
+            v[4 * q + e] = us[upos<K>(ch, e, sc)] + m4.v[e] * inv_rho;
         }
     }
     // x_s = M v + bbar~ over the factor rows, two rows per step
@@ -211,7 +220,6 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
             m4.v[e] = mun;
             u4.v[e] = rho * xsv - mun;
         }
-        st4(us + off, u4);
         if (check) {
             const int4 g4 = __ldg(chg + ch);
             const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
@@ -221,7 +229,7 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (gg[e] < 0) continue;
-                const T d0 = xs[gg[e] + sc] - x4.v[e], d1 = x4.v[e] - o4.v[e];
+                const T d0 = us[upos<K>(ch, e, sc)] - x4.v[e], d1 = x4.v[e] - o4.v[e];
                 const T xa = x4.v[e] + __ldcg(xr_c + gg[e]);
                 const T la = m4.v[e] + l4.v[e];
                 t0 += d0 * d0;
@@ -234,6 +242,8 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
             c3 += (double)t3;
             c4 += (double)t4;
         }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) us[upos<K>(ch, e, sc)] = u4.v[e];
         if (act) {
             st4cg(mu_c + off, m4);
             if (wds) st4cg(ds_c + off, x4);
@@ -264,11 +274,17 @@ __global__ void __launch_bounds__(512, 1)
     k_batch_engine(BatchArgs<T> a, int n_iters, int check_every) {
     constexpr int J = 32 / K;
     constexpr int KS = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : K == 16 ? 4 : 5;
+    constexpr int KQ = K < 4 ? K : 4;          // columns per global-update item
+    constexpr int NQD = K / KQ;                  // items per global
+    constexpr int QS = NQD == 1 ? 0 : NQD == 2 ? 1 : NQD == 4 ? 2 : 3;
+    constexpr int GB = 8;                        // global-update items per thread with loads in flight
     extern __shared__ __align__(16) unsigned char smraw[];
     T *Fsm = reinterpret_cast<T *>(smraw);
     const T *Fs = FG ? a.Fpk : Fsm;
     T *us = reinterpret_cast<T *>(smraw + a.off_u);
-    T *xs = reinterpret_cast<T *>(smraw + a.off_x);
+    int2 *gts = reinterpret_cast<int2 *>(smraw + a.off_gt);      // (first copy | copies << 24, bounded index)
+    T *rcs = reinterpret_cast<T *>(smraw + a.off_rc);            // 1 / (rho N_i)
+    int *usg = reinterpret_cast<int *>(smraw + a.off_useg);      // slot-array row of every copy
     double *red = reinterpret_cast<double *>(smraw + a.off_red);
     int *flags = reinterpret_cast<int *>(smraw + a.off_flag);    // [0,K) running, [K,2K) just finished
     int *tnext = flags + 2 * K;                                    // next task of the dynamic schedule
@@ -286,27 +302,28 @@ __global__ void __launch_bounds__(512, 1)
         for (int q = 0; q < K; ++q) any |= flags[q];
         if (!any) return;
     }
-    // factors into shared memory (nF is a multiple of 4)
+    // factors and the global-update tables into shared memory (nF is a multiple of 4)
     if (!FG)
         for (int i = tid * 4; i < a.nF; i += nthr * 4) st4(Fsm + i, ld4(a.Fpk + i));
+    for (int i = tid; i < a.G; i += nthr) {
+        const int4 gt = __ldg(a.gtab + i);
+        gts[i] = make_int2((int)((unsigned)gt.x | ((unsigned)gt.y << 24)), gt.z);
+        rcs[i] = __ldg(a.recip + i);
+    }
+    for (int k = tid; k < a.L; k += nthr) usg[k] = __ldg(a.useg + k);
     const size_t sb = (size_t)c * a.NCH * K * 4;     // this CTA's slot arrays
     const size_t gb = (size_t)c * a.G * K;           // global arrays
     const size_t bb = (size_t)c * a.NB * K;          // bounded-global arrays
-    const int nsl = a.NCH * K * 4;
     T *mu_c = a.mu + sb, *ds_c = a.ds + sb;
     const T *bt_c = a.bt + sb, *lr_c = a.lref + sb;
-    for (int i = tid * 4; i < nsl; i += nthr * 4) {
-        const Q4<T> d = ld4cg(a.ds + sb + i), m = ld4cg(a.mu + sb + i);
-        Q4<T> u;
+    // u = rho d - mu into the swizzled slot array
+    for (int idx = tid; idx < a.NCH * K; idx += nthr) {
+        const int ch = idx >> KS, col = idx & (K - 1);
+        const Q4<T> d = ld4cg(ds_c + (size_t)idx * 4), m = ld4cg(mu_c + (size_t)idx * 4);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) u.v[e] = a.rho * d.v[e] - m.v[e];
-        st4(us + i, u);
+        for (int e = 0; e < 4; ++e) us[upos<K>(ch, e, col)] = a.rho * d.v[e] - m.v[e];
     }
     __syncthreads();
-    constexpr int KQ = K < 4 ? K : 4;          // columns per global-update item
-    constexpr int NQD = K / KQ;                  // items per global
-    constexpr int QS = NQD == 1 ? 0 : NQD == 2 ? 1 : NQD == 4 ? 2 : 3;
-    const int GQ = a.G * NQD;
     const int sc = tid & (K - 1);
     const int jpos = lane >> KS;
     const T *xr_c = a.xrf + gb + sc;
@@ -315,73 +332,84 @@ __global__ void __launch_bounds__(512, 1)
     const int n_warps = nthr >> 5;
     int last_check = 0;
     const int GK = a.G * K;
+    const int GQ = a.G * NQD;
     for (int it = 0; it < n_iters; ++it) {
         const bool check = check_every > 0 && ((it + 1) % check_every == 0);
-        const bool wds = check || it == n_iters - 1 || (check_every > 0 && ((it + 2) % check_every == 0));
+        const bool last = it == n_iters - 1;
+        const bool wds = check || last || (check_every > 0 && ((it + 2) % check_every == 0));
         const bool act = flags[sc] != 0;
         if (check && lane < K)
 #pragma unroll
             for (int q = 0; q < 6; ++q) redw[lane * 6 + q] = 0.0;
         if (tid == 0) *tnext = 0;
-        // ---- G: global update (Eq. closed_1); a thread item is one global and
-        // KQ of its columns, four items per thread with their loads in flight
-        for (int b0 = tid; b0 < GQ; b0 += 4 * nthr) {
-            int4 gt[4];
-            RowK<T, KQ> cr[4];
+        // ---- G: global update (Eq. closed_1).  An item is one global and KQ of
+        // its columns: sum of u over the copies, shift, scale, clip, and x
+        // stored into every copy's slot; GB items per thread with c~ in flight
+        for (int b0 = tid; b0 < GQ; b0 += GB * nthr) {
+            RowK<T, KQ> cr[GB];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < GB; ++j) {
                 const int item = b0 + j * nthr;
-                gt[j] = make_int4(0, 0, -1, 0);
-                if (item < GQ) {
-                    const int i = item >> QS;
-                    gt[j] = __ldg(a.gtab + i);
-                    load_row<T, KQ, true>(cr[j], a.ct + gb + (size_t)i * K + (item & (NQD - 1)) * KQ);
-                }
+                if (item < GQ)
+                    load_row<T, KQ, true>(cr[j], a.ct + gb + (size_t)(item >> QS) * K + (item & (NQD - 1)) * KQ);
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < GB; ++j) {
                 const int item = b0 + j * nthr;
                 if (item >= GQ) continue;
                 const int i = item >> QS, h = item & (NQD - 1);
+                const int2 gt = gts[i];
+                const int st0 = gt.x & 0xffffff, cnt = (int)((unsigned)gt.x >> 24);
                 RowK<T, KQ> sum;
 #pragma unroll
                 for (int k = 0; k < KQ; ++k) sum.v[k] = T(0);
-                const T rcp = __ldg(a.recip + i);
-                for (int q = 0; q < gt[j].y; ++q) {
-                    const int uo = __ldg(a.useg + gt[j].x + q) + h * KQ * 4;
+                for (int q = 0; q < cnt; ++q) {
+                    RowK<T, KQ> uq;
+                    load_row<T, KQ, false>(uq, us + usg[st0 + q] + h * KQ);
 #pragma unroll
-                    for (int k = 0; k < KQ; ++k) sum.v[k] += us[uo + k * 4];
+                    for (int k = 0; k < KQ; ++k) sum.v[k] += uq.v[k];
                 }
+                const T rcp = rcs[i];
 #pragma unroll
                 for (int k = 0; k < KQ; ++k) sum.v[k] = (sum.v[k] - cr[j].v[k]) * rcp;
-                if (gt[j].z >= 0) {
+                if (gt.y >= 0) {
                     RowK<T, KQ> lo, hi;
-                    load_row<T, KQ, true>(lo, a.lbt + bb + (size_t)gt[j].z * K + h * KQ);
-                    load_row<T, KQ, true>(hi, a.ubt + bb + (size_t)gt[j].z * K + h * KQ);
+                    load_row<T, KQ, true>(lo, a.lbt + bb + (size_t)gt.y * K + h * KQ);
+                    load_row<T, KQ, true>(hi, a.ubt + bb + (size_t)gt.y * K + h * KQ);
 #pragma unroll
                     for (int k = 0; k < KQ; ++k) sum.v[k] = clampT(sum.v[k], lo.v[k], hi.v[k]);
                 }
-                store_row<T, KQ>(xs + (size_t)i * K + h * KQ, sum);
+                for (int q = 0; q < cnt; ++q) store_row<T, KQ>(us + usg[st0 + q] + h * KQ, sum);
             }
         }
         __syncthreads();
-        if (check) {
-            // objective and ||B x||^2 per column (thread column sc = tid % K)
+        if (check || last) {
+            // x of each global (at its first copy): objective and ||B x||^2 per
+            // column on test iterations, and x~ of the running instances for
+            // their results (thread column sc = tid % K)
             double c2 = 0.0, c5 = 0.0;
             for (int item = tid; item < GK; item += nthr) {
                 const int i = item >> KS;
-                const double xa = (double)xs[item] + (double)__ldcg(a.xrf + gb + item);
-                c2 += (double)__ldg(&a.gtab[i].y) * xa * xa;
-                c5 += (double)__ldg(a.cost + i) * xa;
+                const int2 gt = gts[i];
+                const T xv = us[usg[gt.x & 0xffffff] + sc];
+                if (flags[sc]) a.xo[gb + item] = xv;
+                if (check) {
+                    const double xa = (double)xv + (double)__ldcg(a.xrf + gb + item);
+                    c2 += (double)((unsigned)gt.x >> 24) * xa * xa;
+                    c5 += (double)__ldg(a.cost + i) * xa;
+                }
             }
-            for (int o = K; o < 32; o <<= 1) {
-                c2 += __shfl_xor_sync(0xffffffffu, c2, o);
-                c5 += __shfl_xor_sync(0xffffffffu, c5, o);
+            if (check) {
+                for (int o = K; o < 32; o <<= 1) {
+                    c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+                    c5 += __shfl_xor_sync(0xffffffffu, c5, o);
+                }
+                if (lane < K) {
+                    redw[lane * 6 + 2] += c2;
+                    redw[lane * 6 + 5] += c5;
+                }
             }
-            if (lane < K) {
-                redw[lane * 6 + 2] += c2;
-                redw[lane * 6 + 5] += c5;
-            }
+            __syncthreads();      // the slots still hold x: read before phase L overwrites them
         }
         // ---- L: local update (Eq. closed_2) and dual update (Eq. ADMM-3)
         // tasks in decreasing cost; warps take the next one as they finish
@@ -400,17 +428,17 @@ __global__ void __launch_bounds__(512, 1)
                 }
                 const BatchTask tk = a.tasks[t];
                 switch (tk.nq) {
-                    case 1: batch_task<T, K, 1>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
+                    case 1: batch_task<T, K, 1>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
                                                 inv_rho, check, act, wds, redw); break;
-                    case 2: if constexpr (NQ >= 2) batch_task<T, K, 2>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c,
-                                                                       xr_c, a.chg, jpos, sc, rho, inv_rho, check,
-                                                                       act, wds, redw); break;
-                    case 3: if constexpr (NQ >= 3) batch_task<T, K, 3>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c,
-                                                                       xr_c, a.chg, jpos, sc, rho, inv_rho, check,
-                                                                       act, wds, redw); break;
-                    default: if constexpr (NQ >= 4) batch_task<T, K, 4>(tk, Fs, us, xs, mu_c, bt_c, ds_c, lr_c,
-                                                                        xr_c, a.chg, jpos, sc, rho, inv_rho, check,
-                                                                        act, wds, redw); break;
+                    case 2: if constexpr (NQ >= 2) batch_task<T, K, 2>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
+                                                                       a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                       wds, redw); break;
+                    case 3: if constexpr (NQ >= 3) batch_task<T, K, 3>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
+                                                                       a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                       wds, redw); break;
+                    default: if constexpr (NQ >= 4) batch_task<T, K, 4>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
+                                                                        a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                        wds, redw); break;
                 }
                 t = tn;
             }
@@ -433,12 +461,6 @@ __global__ void __launch_bounds__(512, 1)
                 }
             }
             __syncthreads();
-            // x~ of instances that just finished (each thread the entries it wrote)
-            for (int item = tid; item < GQ; item += nthr) {
-                const int i = item >> QS, h = item & (NQD - 1);
-                for (int k = 0; k < KQ; ++k)
-                    if (flags[K + h * KQ + k]) a.xo[gb + (size_t)i * K + h * KQ + k] = xs[(size_t)i * K + h * KQ + k];
-            }
             last_check = it + 1;
             int any = 0;
             for (int q = 0; q < K; ++q) any |= flags[q];
@@ -448,11 +470,6 @@ __global__ void __launch_bounds__(512, 1)
         }
     }
     if (tid < K && flags[tid]) a.st[a.inst[c * K + tid]].iter += n_iters - last_check;
-    for (int item = tid; item < GQ; item += nthr) {
-        const int i = item >> QS, h = item & (NQD - 1);
-        for (int k = 0; k < KQ; ++k)
-            if (flags[h * KQ + k]) a.xo[gb + (size_t)i * K + h * KQ + k] = xs[(size_t)i * K + h * KQ + k];
-    }
 }
 
 // ============================================================ per-instance data

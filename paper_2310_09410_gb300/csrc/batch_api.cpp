@@ -212,17 +212,19 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
         gtab[i] = make_int4(s0, cnt, b->h_bidx[i], 0);
         for (int q = 0; q < cnt; ++q) {
             const int pos = sch[h->h_uslot[s0 + q]];
-            useg[s0 + q] = (pos >> 2) * K * 4 + (pos & 3);
+            const int ch = pos >> 2, e = pos & 3;
+            useg[s0 + q] = (ch * 4 + (e ^ (ch & 3))) * K;
         }
     }
     // shared memory
     p->off_u = fg ? 0u : a16((size_t)p->nF * sz);
-    p->off_x = p->off_u + a16((size_t)p->NCH * K * 4 * sz);
-    p->off_red = p->off_x + a16((size_t)G * K * sz);
+    p->off_gt = p->off_u + a16((size_t)p->NCH * K * 4 * sz);
+    p->off_rc = p->off_gt + a16((size_t)G * sizeof(int2));
+    p->off_useg = p->off_rc + a16((size_t)G * sz);
+    p->off_red = p->off_useg + a16((size_t)L * sizeof(int));
     p->off_flag = p->off_red + a16((size_t)W * K * 6 * sizeof(double));
     p->bytes = p->off_flag + a16((size_t)(2 * K + 1) * sizeof(int));
     if (p->bytes > kMaxSmem) { set_last_error("batch plan: shared memory"); return OPF_E_CAPACITY; }
-    if (G > 8 * p->threads) { set_last_error("batch plan: more than 8 globals per thread"); return OPF_E_CAPACITY; }
     const int rc = dbl ? batch_engine_prepare<double>(K, nq, fg, p->bytes) : batch_engine_prepare<float>(K, nq, fg, p->bytes);
     if (rc) { set_last_error("batch plan: engine attributes"); return OPF_E_CUDA; }
     const int occ = dbl ? batch_engine_max_ctas_per_sm<double>(K, nq, fg, p->threads, p->bytes)
@@ -299,7 +301,9 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
     memset(&a, 0, sizeof(a));
     a.K = p.K; a.kshift = p.ks; a.J = p.J; a.NCH = p.NCH; a.G = b->G; a.NB = p.NB; a.n_tasks = p.n_tasks;
     a.nF = p.nF;
-    a.off_u = p.off_u; a.off_x = p.off_x; a.off_red = p.off_red; a.off_flag = p.off_flag;
+    a.L = b->L;
+    a.off_u = p.off_u; a.off_gt = p.off_gt; a.off_rc = p.off_rc; a.off_useg = p.off_useg;
+    a.off_red = p.off_red; a.off_flag = p.off_flag;
     a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab;
     a.useg = p.d_useg;
     a.Fpk = (const T *)p.d_F; a.recip = (const T *)p.d_recip; a.cost = (const T *)p.d_cost;

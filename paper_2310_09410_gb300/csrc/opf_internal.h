@@ -177,12 +177,12 @@ struct BatchTask {
 //   per bounded   [c][NB][K]       lbt, ubt (bounds - x_ref)
 template <typename T>
 struct BatchArgs {
-    int K, kshift, J, NCH, G, NB, n_tasks, nF;
-    unsigned off_u, off_x, off_red, off_flag;   // shared-memory byte offsets
+    int K, kshift, J, NCH, G, L, NB, n_tasks, nF;
+    unsigned off_u, off_gt, off_rc, off_useg, off_red, off_flag;   // shared-memory byte offsets
     const BatchTask *tasks;    // [n_tasks] in decreasing cost
     const int4 *chg;           // [NCH] g * K of each chunk's 4 slots (-1: padding)
     const int4 *gtab;          // [G] (first copy in useg, copies, bounded index or -1, 0)
-    const int *useg;           // copies of each global: u offset ch * K * 4 + e
+    const int *useg;           // copies of each global: slot-array row (ch * 4 + (e ^ (ch & 3))) * K
     const T *Fpk;              // [nF] factors, task-interleaved
     const T *recip;            // [G] 1 / (rho N_i)
     const T *cost;             // [G] c_i
