@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(512, 1)
     int2 *gts = reinterpret_cast<int2 *>(smraw + a.off_gt);      // (first copy | copies << 24, bounded index)
     T *rcs = reinterpret_cast<T *>(smraw + a.off_rc);            // 1 / (rho N_i)
     int *usg = reinterpret_cast<int *>(smraw + a.off_useg);      // slot-array row of every copy
+    T *bnd = reinterpret_cast<T *>(smraw + a.off_bnd);           // [NB][2][K]: bounds - x_ref
     double *red = reinterpret_cast<double *>(smraw + a.off_red);
     int *flags = reinterpret_cast<int *>(smraw + a.off_flag);    // [0,K) running, [K,2K) just finished
     int *tnext = flags + 2 * K;                                    // next task of the dynamic schedule
@@ -314,6 +315,11 @@ __global__ void __launch_bounds__(512, 1)
     const size_t sb = (size_t)c * a.NCH * K * 4;     // this CTA's slot arrays
     const size_t gb = (size_t)c * a.G * K;           // global arrays
     const size_t bb = (size_t)c * a.NB * K;          // bounded-global arrays
+    for (int idx = tid; idx < a.NB * K; idx += nthr) {
+        const int b = idx >> KS, col = idx & (K - 1);
+        bnd[(b * 2) * K + col] = __ldcg(a.lbt + bb + idx);
+        bnd[(b * 2 + 1) * K + col] = __ldcg(a.ubt + bb + idx);
+    }
     T *mu_c = a.mu + sb, *ds_c = a.ds + sb;
     const T *bt_c = a.bt + sb, *lr_c = a.lref + sb;
     // u = rho d - mu into the swizzled slot array
@@ -374,8 +380,8 @@ __global__ void __launch_bounds__(512, 1)
                 for (int k = 0; k < KQ; ++k) sum.v[k] = (sum.v[k] - cr[j].v[k]) * rcp;
                 if (gt.y >= 0) {
                     RowK<T, KQ> lo, hi;
-                    load_row<T, KQ, true>(lo, a.lbt + bb + (size_t)gt.y * K + h * KQ);
-                    load_row<T, KQ, true>(hi, a.ubt + bb + (size_t)gt.y * K + h * KQ);
+                    load_row<T, KQ, false>(lo, bnd + (gt.y * 2) * K + h * KQ);
+                    load_row<T, KQ, false>(hi, bnd + (gt.y * 2 + 1) * K + h * KQ);
 #pragma unroll
                     for (int k = 0; k < KQ; ++k) sum.v[k] = clampT(sum.v[k], lo.v[k], hi.v[k]);
                 }

@@ -221,7 +221,8 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     p->off_gt = p->off_u + a16((size_t)p->NCH * K * 4 * sz);
     p->off_rc = p->off_gt + a16((size_t)G * sizeof(int2));
     p->off_useg = p->off_rc + a16((size_t)G * sz);
-    p->off_red = p->off_useg + a16((size_t)L * sizeof(int));
+    p->off_bnd = p->off_useg + a16((size_t)L * sizeof(int));
+    p->off_red = p->off_bnd + a16((size_t)b->NB * 2 * K * sz);
     p->off_flag = p->off_red + a16((size_t)W * K * 6 * sizeof(double));
     p->bytes = p->off_flag + a16((size_t)(2 * K + 1) * sizeof(int));
     if (p->bytes > kMaxSmem) { set_last_error("batch plan: shared memory"); return OPF_E_CAPACITY; }
@@ -302,7 +303,7 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
     a.K = p.K; a.kshift = p.ks; a.J = p.J; a.NCH = p.NCH; a.G = b->G; a.NB = p.NB; a.n_tasks = p.n_tasks;
     a.nF = p.nF;
     a.L = b->L;
-    a.off_u = p.off_u; a.off_gt = p.off_gt; a.off_rc = p.off_rc; a.off_useg = p.off_useg;
+    a.off_u = p.off_u; a.off_gt = p.off_gt; a.off_rc = p.off_rc; a.off_useg = p.off_useg; a.off_bnd = p.off_bnd;
     a.off_red = p.off_red; a.off_flag = p.off_flag;
     a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab;
     a.useg = p.d_useg;

@@ -178,7 +178,7 @@ struct BatchTask {
 template <typename T>
 struct BatchArgs {
     int K, kshift, J, NCH, G, L, NB, n_tasks, nF;
-    unsigned off_u, off_gt, off_rc, off_useg, off_red, off_flag;   // shared-memory byte offsets
+    unsigned off_u, off_gt, off_rc, off_useg, off_bnd, off_red, off_flag;   // shared-memory byte offsets
     const BatchTask *tasks;    // [n_tasks] in decreasing cost
     const int4 *chg;           // [NCH] g * K of each chunk's 4 slots (-1: padding)
     const int4 *gtab;          // [G] (first copy in useg, copies, bounded index or -1, 0)
