@@ -121,15 +121,24 @@ typedef struct opf_solve_opts {
     int32_t precision;              /* OPF_PREC_* */
     int32_t recenter_every;         /* OPF_PREC_MIXED: iterations between FP64 re-centrings (0 = default) */
     int32_t engine;                 /* 0 = automatic, 1 = whole-grid kernels, 2 = cluster resident,
-                                       3 = warp per subsystem (FP32, at most 192 subsystems) */
+                                       3 = warp per subsystem (FP32, at most 192 subsystems),
+                                       4 = persistent grid (cooperative launch, instance resident in
+                                       the shared memory of all CTAs, one grid barrier per iteration) */
     int32_t flags;                  /* OPF_SOLVE_* bits */
-    int32_t cluster;                /* engine 2: CTAs per cluster (1, 2, 4, 8, 16; 0 = automatic) */
+    int32_t cluster;                /* engine 2: CTAs per cluster (1, 2, 4, 8, 16; 0 = automatic);
+                                       engine 4: CTAs of the grid (1 .. 2048, at most the resident
+                                       count; 0 = automatic) */
 } opf_solve_opts;
 
 /* opf_solve_opts.flags: drive the iteration chunks from the host (one plain
  * CUDA graph per chunk and a status read after each) instead of one graph
  * with a device-side WHILE node; same arithmetic, slower, profiler-visible. */
 #define OPF_SOLVE_HOST_LOOP 1
+/* Test hook for the failure path of the persistent grid engine (engine 4):
+ * its grid barriers expect one CTA more than the launch has, so the first
+ * bounded wait runs out (about 1 s), every CTA leaves, and the solve returns
+ * OPF_E_TIMEOUT with the handle still usable (reset or re-solve). */
+#define OPF_SOLVE_TEST_BARRIER_TIMEOUT 2
 
 typedef struct opf_sizes {
     int64_t n_global;               /* n: length of x */
@@ -173,7 +182,12 @@ int opf_precompute(opf_handle *h);
 int opf_solve(opf_handle *h, double rho, double eps, int32_t max_iter);
 
 /* Same with every option (NULL = defaults: rho 100, eps_rel 1e-8,
- * eps_abs_pres 1e-4, max_iter 1e6, check_every 50, FP64). */
+ * eps_abs_pres 1e-4, max_iter 1e6, check_every 50, FP64).  Automatic engine
+ * choice: FP32 / mixed iterations on the warp engine, else the cluster
+ * engine, else the persistent grid engine, else whole-grid kernels; FP64
+ * iterations (and the polish) on the persistent grid engine for instances
+ * of more than 4096 slots, else whole-grid kernels.  The persistent engine's grid
+ * barrier waits at most 1 s; past that the solve returns OPF_E_TIMEOUT. */
 int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts);
 
 /* Exactly n_iters FP64 iterations with penalty rho, no stopping test. */

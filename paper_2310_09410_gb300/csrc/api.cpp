@@ -48,6 +48,12 @@ int launch_cluster_engine(const IterArgs<T> &g, const ClusterLayout &lay, const 
                           int n_iters, int check_every, DevStatus *st, double rho,
                           cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
 template <typename T> int cluster_occupancy(const ClusterLayout &lay);
+template <typename T> int prepare_persist_engine(unsigned bytes);
+template <typename T> int persist_occupancy(int threads, unsigned bytes);
+template <typename T>
+int launch_persist_engine(const IterArgs<T> &g, const PersistLayout &lay, const PersistPtrs &pp, T *U,
+                          int bar_extra, int n_iters, int check_every, DevStatus *st, double rho,
+                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
 int prepare_warp_engine(unsigned bytes);
 int launch_warp_engine(const IterArgs<float> &g, const WarpLayout &lay, const int *pr, float *u_glob, int n_iters,
                        int check_every, DevStatus *st, double rho, cudaGraphConditionalHandle cond, int use_cond,
@@ -286,6 +292,14 @@ static int build_layout(opf_handle *h) {
     TRY(dalloc(h, &h->w32.d_klb, h->S + 1));
     TRY(dalloc(h, &h->w32.d_fbig, h->S + 1));
     TRY(dalloc(h, &h->w32.d_F2, h->nF));
+    for (PersistPlan *pp : {&h->p32, &h->p64}) {
+        TRY(dalloc(h, &pp->d_pr, 5 * (kPersistMaxP + 1)));
+        TRY(dalloc(h, &pp->d_srec, h->S + 1));
+        TRY(dalloc(h, &pp->d_items, std::max<long long>(items_cap, 1)));
+        TRY(dalloc(h, &pp->d_meta, h->L));
+        TRY(dalloc(h, &pp->d_part, 6 * kPersistMaxP));
+        TRY(dalloc(h, &pp->d_sync, 1));
+    }
     for (ClusterPlan *cp : {&h->c32, &h->c64}) {
         TRY(dalloc(h, &cp->d_pr, 8 * 17));
         TRY(dalloc(h, &cp->d_srec, h->S + 1));
@@ -486,6 +500,8 @@ extern "C" int opf_precompute(opf_handle *h) {
     TRY(make_tiling(h, &h->t32, 256, 128));
     h->c32.P = h->c64.P = 0;
     h->c32.ok = h->c64.ok = false;
+    h->p32.P = h->p64.P = 0;
+    h->p32.ok = h->p64.ok = h->p32.tried = h->p64.tried = false;
     h->w32.built = h->w32.ok = false;
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->g64.reset();
@@ -697,6 +713,132 @@ static int get_cluster_plan(opf_handle *h, ClusterPlan *cp, int requested, int t
         if (cp->ok || requested > 0) break;
     }
     return OPF_OK;
+}
+
+// Partition the instance over P co-resident CTAs of the persistent grid
+// engine: contiguous subsystem ranges balanced by work (the same cost as the
+// cluster plan), part-relative records, and the shared-memory layout.  Leaves
+// pp->ok false when a part does not fit one CTA or P CTAs cannot be resident.
+template <typename T>
+static int build_persist_plan(opf_handle *h, PersistPlan *pp, int P, int n_sm) {
+    pp->ok = false;
+    pp->P = P;
+    if (P < 1 || P > kPersistMaxP) return OPF_OK;
+    const int S = h->S, L = h->L;
+    std::vector<double> cost(S);
+    double total = 0;
+    for (int s = 0; s < S; ++s) {
+        cost[s] = 6.0 * h->h_sn[s] + (double)h->h_sf[s] * h->h_npad[s] + (double)h->h_sn[s] * h->h_sf[s];
+        total += cost[s];
+    }
+    std::vector<int> sp(P + 1, S);
+    sp[0] = 0;
+    {
+        double acc = 0;
+        int p = 1;
+        for (int s = 0; s < S && p < P; ++s) {
+            acc += cost[s];
+            while (p < P && acc >= total * p / P) sp[p++] = s + 1;
+        }
+        for (int p2 = 1; p2 <= P; ++p2) sp[p2] = std::max(sp[p2], sp[p2 - 1]);
+        sp[P] = S;
+    }
+    const int P1 = P + 1;
+    std::vector<int> pr(5 * P1);
+    auto PR = [&](int field, int p) -> int & { return pr[field * P1 + p]; };
+    for (int p = 0; p <= P; ++p) {
+        const int s = sp[p];
+        PR(0, p) = h->h_soff[s];
+        PR(1, p) = s;
+        PR(2, p) = h->h_tpre[s];
+        PR(3, p) = h->h_foff[s];
+        PR(4, p) = h->h_vpre[s];
+    }
+    std::vector<int4> srec(S + 1, make_int4(0, 0, 0, 0));
+    std::vector<int> items, meta(L);
+    for (int p = 0; p < P; ++p) {
+        for (int s = sp[p]; s < sp[p + 1]; ++s) {
+            srec[s] = make_int4(h->h_foff[s] - PR(3, p), h->h_vpre[s] - PR(4, p), h->h_tpre[s] - PR(2, p),
+                                (h->h_sf[s] << 10) | (h->h_npad[s] << 1) | (h->h_mode[s] & 1));
+            for (int c = 0; c < h->h_sf[s]; ++c) items.push_back(((s - sp[p]) << 8) | c);
+            for (int r = 0; r < h->h_sn[s]; ++r) meta[h->h_soff[s] + r] = ((s - sp[p]) << 8) | r;
+        }
+    }
+    long long mf = 0, ms = 0, mj = 0, mk = 0, mv = 0;
+    for (int p = 0; p < P; ++p) {
+        mk = std::max<long long>(mk, PR(0, p + 1) - PR(0, p));
+        ms = std::max<long long>(ms, PR(1, p + 1) - PR(1, p));
+        mj = std::max<long long>(mj, PR(2, p + 1) - PR(2, p));
+        mf = std::max<long long>(mf, PR(3, p + 1) - PR(3, p));
+        mv = std::max<long long>(mv, PR(4, p + 1) - PR(4, p));
+    }
+    PersistLayout &c = pp->lay;
+    c = PersistLayout{};
+    c.P = P;
+    c.L = L;
+    size_t off = 0;
+    auto take = [&](unsigned *o, size_t bytes) { *o = (unsigned)off; off = align16u(off + bytes); };
+    take(&c.off_F, (size_t)mf * sizeof(T));
+    take(&c.off_srec, (size_t)ms * sizeof(int4));
+    take(&c.off_items, (size_t)mj * sizeof(int));
+    take(&c.off_meta, (size_t)mk * sizeof(int));
+    take(&c.off_segp, (size_t)mk * sizeof(int));
+    take(&c.off_pk, (size_t)mk * sizeof(int));
+    take(&c.off_bt, (size_t)mk * sizeof(T));
+    take(&c.off_ds, (size_t)mk * sizeof(T));
+    take(&c.off_mu, (size_t)mk * sizeof(T));
+    take(&c.off_ct, (size_t)mk * sizeof(T));
+    take(&c.off_lbt, (size_t)mk * sizeof(T));
+    take(&c.off_ubt, (size_t)mk * sizeof(T));
+    take(&c.off_vbx, (size_t)mv * sizeof(T));
+    take(&c.off_vbw, (size_t)mv * sizeof(T));
+    take(&c.off_tb, (size_t)mj * sizeof(T));
+    take(&c.off_recip, 256 * sizeof(T));
+    take(&c.off_xrs, (size_t)mk * sizeof(double));
+    take(&c.off_lrs, (size_t)mk * sizeof(double));
+    take(&c.off_cobj, (size_t)mk * sizeof(double));
+    // flags (16 B), a DevStatus copy, the [32][6] block-sum scratch
+    take(&c.off_misc, 16 + ((sizeof(DevStatus) + 15) & ~(size_t)15) + 32 * 6 * sizeof(double));
+    c.bytes = (unsigned)off;
+    c.threads = (int)std::min<long long>(kPersistMaxThreads, std::max<long long>(64, (std::max(mk, mj) + 31) / 32 * 32));
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if ((long long)c.bytes > optin) return OPF_OK;
+    if (prepare_persist_engine<T>(c.bytes)) { cudaGetLastError(); return OPF_OK; }
+    const int occ = persist_occupancy<T>(c.threads, c.bytes);
+    if ((long long)occ * n_sm < P) { cudaGetLastError(); return OPF_OK; }
+    CUDA_TRY(cudaMemcpyAsync(pp->d_pr, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(pp->d_srec, srec.data(), srec.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
+    if (!items.empty())
+        CUDA_TRY(cudaMemcpyAsync(pp->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 h->stream));
+    CUDA_TRY(cudaMemcpyAsync(pp->d_meta, meta.data(), L * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    pp->ok = true;
+    return OPF_OK;
+}
+
+// CTA count: the requested one, else two per SM of the stream's SMs (one per
+// SM when two do not fit), at most one CTA per 32 slots.
+template <typename T>
+static int get_persist_plan(opf_handle *h, PersistPlan *pp, int requested) {
+    if (pp->tried && pp->req == requested) return OPF_OK;
+    const int n_sm = stream_sm_count(h->stream, h->device);
+    pp->tried = true;
+    pp->req = requested;
+    if (requested > 0) return build_persist_plan<T>(h, pp, requested, n_sm);
+    const int cap = std::max(1, (h->L + 31) / 32);
+    for (int per : {2, 1}) {
+        TRY(build_persist_plan<T>(h, pp, std::min(per * n_sm, cap), n_sm));
+        if (pp->ok) return OPF_OK;
+    }
+    return OPF_OK;
+}
+
+template <typename T>
+static IterArgs<T> with_persist(IterArgs<T> a, const PersistPlan &pp) {
+    a.srec = pp.d_srec; a.citems = pp.d_items; a.cmeta = pp.d_meta;
+    return a;
 }
 
 constexpr int kWarpEngineWarps = 12;
@@ -987,10 +1129,58 @@ static int run_cluster64(opf_handle *h, const opf_solve_opts &o) {
     return OPF_OK;
 }
 
+// Iterations per launch of the persistent engine when it runs to the test
+// (FP64 plain solves and the polish): the host reads the status in between.
+constexpr int kPersistLaunchIters = 20000;
+// Automatic engine choice: FP64 iterations of instances with more slots than
+// this run on the persistent grid engine.
+constexpr int kPersistAutoSlots = 4096;
+
+// Test hook: one arrival more than the grid has, so the first barrier's
+// bounded wait runs out.
+static int bar_extra(const opf_solve_opts &o) { return (o.flags & OPF_SOLVE_TEST_BARRIER_TIMEOUT) ? 1 : 0; }
+
+static int fault_error(opf_handle *h) {
+    if (!h->h_st->fault) return OPF_OK;
+    g_last_error = "persistent grid engine: a grid barrier wait ran out";
+    return OPF_E_TIMEOUT;
+}
+
+// FP64 iterations by the persistent grid engine until the test or max_iter.
+static int run_persist64(opf_handle *h, const opf_solve_opts &o) {
+    const double rho = o.rho;
+    TRY(set_recip(h, rho));
+    launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    const PersistPlan &pp = h->p64;
+    IterArgs<double> a = with_persist(iter_args<double>(h, rho), pp);
+    const int k = o.check_every;
+    const int per = std::max(k, (kPersistLaunchIters / k) * k);
+    for (;;) {
+        if (launch_persist_engine<double>(a, pp.lay, pp.ptrs(), h->d_u64, bar_extra(o), per, k, h->d_st, rho,
+                                          cudaGraphConditionalHandle{}, 0, h->stream)) {
+            g_last_error = std::string("persistent grid engine launch failed: ") +
+                           cudaGetErrorString(cudaGetLastError());
+            return OPF_E_CUDA;
+        }
+        TRY(read_status(h));
+        TRY(fault_error(h));
+        if (h->h_st->done) break;
+    }
+    h->have_prev_u = h->h_st->iter > 0;
+    return OPF_OK;
+}
+
+// FP64 iterations on the engine chosen for the handle: persistent grid when
+// its plan is usable (and not excluded), else whole-grid kernels.
+static int run_fp64(opf_handle *h, const opf_solve_opts &o, bool persistent) {
+    if (persistent && h->p64.ok) return run_persist64(h, o);
+    return run_grid64(h, o);
+}
+
 // FP32 iterations in the shifted frame, re-centred in FP64 every R iterations.
-// eng: 1 whole-grid kernels, 2 cluster engine, 3 warp engine
+// eng: 1 whole-grid kernels, 2 cluster engine, 3 warp engine, 4 persistent grid
 static int run_mixed(opf_handle *h, const opf_solve_opts &o, int eng, bool recenter) {
-    const bool use_cta = eng != 1;
     const double rho = o.rho;
     TRY(set_recip(h, rho));
     const int L = h->L, G = h->G, S = h->S;
@@ -1011,11 +1201,17 @@ static int run_mixed(opf_handle *h, const opf_solve_opts &o, int eng, bool recen
     CUDA_TRY(cudaGetLastError());
 
     const int kind = eng + (recenter ? 0 : 8);
-    const bool hl = (o.flags & OPF_SOLVE_HOST_LOOP) != 0;
-    IterArgs<float> a = eng == 3 ? with_warp_plan(h, iter_args<float>(h, rho), h->w32)
-                                 : with_plan(iter_args<float>(h, rho), h->c32);
+    bool hl = (o.flags & OPF_SOLVE_HOST_LOOP) != 0 || (eng == 4 && h->persist_graph_failed);
+    IterArgs<float> a = eng == 3   ? with_warp_plan(h, iter_args<float>(h, rho), h->w32)
+                        : eng == 4 ? with_persist(iter_args<float>(h, rho), h->p32)
+                                   : with_plan(iter_args<float>(h, rho), h->c32);
+    int launch_rc = 0;
     auto body = [&](cudaGraphConditionalHandle c, int use) {
-            if (eng == 3) {
+            if (eng == 4) {
+                const PersistPlan &pp = h->p32;
+                launch_rc |= launch_persist_engine<float>(a, pp.lay, pp.ptrs(), h->d_u32, bar_extra(o), R, k,
+                                                          h->d_st, rho, c, use, h->stream);
+            } else if (eng == 3) {
                 launch_warp_engine(a, h->w32.lay, h->w32.d_pr, h->d_u32, R, k, h->d_st, rho, c, use, h->stream);
             } else if (eng == 2) {
                 launch_cluster_engine<float>(a, h->c32.lay, h->c32.d_pr, h->d_u32, R, k, h->d_st, rho, c, use,
@@ -1035,13 +1231,28 @@ static int run_mixed(opf_handle *h, const opf_solve_opts &o, int eng, bool recen
             launch_copy_if_running(G, h->d_xr2, h->d_xr, h->d_st, h->stream);
             launch_make_u<float>(L, h->d_pk, h->d_ds32, h->d_mu32, (float)rho, h->d_u32, h->d_st, h->stream);
     };
+    const int planP = eng == 4 ? 10000 + h->p32.P : eng == 3 ? 100 + h->w32.P : eng == 2 ? h->c32.P : 0;
     if (h->gmix.kind != kind || h->gmix.rho != rho || h->gmix.k != k || h->gmix.R != R ||
-        h->gmix.host_loop != hl || h->gmix.P != (eng == 3 ? 100 + h->w32.P : eng == 2 ? h->c32.P : 0)) {
-        TRY(build_while_graph(h, &h->gmix, body, hl));
+        h->gmix.host_loop != hl || h->gmix.P != planP) {
+        int rc = build_while_graph(h, &h->gmix, body, hl);
+        if (rc != OPF_OK && eng == 4 && !hl) {
+            // a cooperative launch that cannot be captured: drive it from the host
+            cudaGetLastError();
+            h->persist_graph_failed = true;
+            hl = true;
+            launch_rc = 0;
+            rc = build_while_graph(h, &h->gmix, body, true);
+        }
+        TRY(rc);
         h->gmix.kind = kind; h->gmix.rho = rho; h->gmix.k = k; h->gmix.R = R;
-        h->gmix.P = eng == 3 ? 100 + h->w32.P : eng == 2 ? h->c32.P : 0;
+        h->gmix.P = planP;
     }
     TRY(run_graph(h, &h->gmix, body));
+    if (launch_rc) {
+        g_last_error = "persistent grid engine launch failed";
+        return OPF_E_CUDA;
+    }
+    TRY(fault_error(h));
     // back to the unshifted FP64 state
     launch_unshift<float>(L, h->d_gk, h->d_xr, h->d_lamr, h->d_ds32, h->d_mu32, h->d_ds64, h->d_mu64, h->stream);
     CUDA_TRY(cudaGetLastError());
@@ -1066,10 +1277,11 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
     if (!h) return OPF_E_INVALID;
     if (!h->precomputed) return OPF_E_STATE;
     opf_solve_opts o = opts ? *opts : default_opts();
+    const bool bad_cluster = o.engine == 4 ? (o.cluster < 0 || o.cluster > kPersistMaxP)
+                                           : (o.cluster < 0 || o.cluster > 16 || (o.cluster & (o.cluster - 1)));
     if (!(o.rho > 0) || o.max_iter < 1 || o.check_every < 2 || (o.check_every & 1) ||
-        o.precision < 0 || o.precision > 2 || o.engine < 0 || o.engine > 3 || o.cluster < 0 ||
-        o.cluster > 16 || (o.cluster & (o.cluster - 1)) || std::isnan(o.eps_rel) ||
-        std::isnan(o.eps_abs_pres)) {
+        o.precision < 0 || o.precision > 2 || o.engine < 0 || o.engine > 4 || bad_cluster ||
+        std::isnan(o.eps_rel) || std::isnan(o.eps_abs_pres)) {
         g_last_error = "solve options: need rho > 0, max_iter >= 1, even check_every >= 2";
         return OPF_E_INVALID;
     }
@@ -1077,6 +1289,14 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
     h->last_rho = o.rho;
     TRY(set_status(h, o, false));
     CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
+    // FP64 iterations (plain solves and the polish) on the persistent grid
+    // engine when asked for, or automatically for large instances
+    bool p64 = false;
+    if (o.engine == 4 || (o.engine == 0 && h->L > kPersistAutoSlots)) {
+        TRY(get_persist_plan<double>(h, &h->p64, o.engine == 4 ? o.cluster : 0));
+        if (!h->p64.ok && o.engine == 4 && o.cluster > 0) TRY(get_persist_plan<double>(h, &h->p64, 0));
+        p64 = h->p64.ok;
+    }
     if (o.precision == OPF_PREC_FP64) {
         bool cl = false;
         if (o.engine == 2) {
@@ -1085,8 +1305,12 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
         }
         if (o.engine == 3) { g_last_error = "the warp engine runs FP32 iterations only"; return OPF_E_INVALID; }
         if (o.engine == 2 && !cl) { g_last_error = "instance does not fit one cluster in FP64"; return OPF_E_CAPACITY; }
+        if (o.engine == 4 && !p64) {
+            g_last_error = "instance does not fit the persistent grid engine in FP64";
+            return OPF_E_CAPACITY;
+        }
         if (cl) TRY(run_cluster64(h, o));
-        else TRY(run_grid64(h, o));
+        else TRY(run_fp64(h, o, p64));
         h->main_iters = h->h_st->iter;
         h->recenters = 0;
         CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
@@ -1101,7 +1325,11 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
             TRY(get_cluster_plan<float>(h, &h->c32, o.cluster, 192));
             if (h->c32.ok) eng = 2;
         }
-        if ((o.engine == 2 || o.engine == 3) && eng != o.engine) {
+        if (eng == 1 && (o.engine == 0 || o.engine == 4)) {
+            TRY(get_persist_plan<float>(h, &h->p32, o.engine == 4 ? o.cluster : 0));
+            if (h->p32.ok) eng = 4;
+        }
+        if ((o.engine == 2 || o.engine == 3 || o.engine == 4) && eng != o.engine) {
             g_last_error = "instance does not fit the requested resident engine";
             return OPF_E_CAPACITY;
         }
@@ -1129,7 +1357,7 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
             st.max_iter = std::max<long long>(o.max_iter, it + o.check_every);
             *h->h_st = st;
             CUDA_TRY(cudaMemcpyAsync(h->d_st, h->h_st, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
-            TRY(run_grid64(h, o));
+            TRY(run_fp64(h, o, p64));
         }
         CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
     }

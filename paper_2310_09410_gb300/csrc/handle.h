@@ -39,6 +39,23 @@ struct ClusterPlan {
     int *d_items = nullptr, *d_meta = nullptr, *d_udst = nullptr, *d_gsegp = nullptr, *d_cdst = nullptr;
 };
 
+// Persistent grid engine plan for one precision: P co-resident CTAs, part
+// ranges, part-relative records, the partial sums and the barrier counter.
+constexpr int kPersistMaxP = 2048;
+struct PersistPlan {
+    int P = 0;
+    bool ok = false;
+    bool tried = false;          // built (ok or not) for the current factors and request
+    int req = 0;                 // requested CTA count of that build (0: automatic)
+    PersistLayout lay{};
+    int *d_pr = nullptr;         // 5 * (kPersistMaxP + 1)
+    int4 *d_srec = nullptr;
+    int *d_items = nullptr, *d_meta = nullptr;
+    double *d_part = nullptr;    // 6 * kPersistMaxP
+    unsigned long long *d_sync = nullptr;
+    PersistPtrs ptrs() const { return PersistPtrs{d_pr, d_part, d_sync}; }
+};
+
 // Warp-engine plan (FP32): subsystem s -> CTA s % P, warp s / P.
 struct WarpPlan {
     int P = 0;
@@ -103,6 +120,8 @@ struct opf_handle {
     long long h2d_bytes = 0;
     GraphCache g64, gmix;
     ClusterPlan c32, c64;
+    PersistPlan p32, p64;
+    bool persist_graph_failed = false;   // the cooperative launch could not be captured in a graph
     WarpPlan w32;
     std::vector<int> h_tpre, h_vpre, h_foff, h_npad, h_pk, h_gk, h_gstart, h_uslot;
     std::vector<int> h_boff;                 // device subsystem -> first row (device row order)

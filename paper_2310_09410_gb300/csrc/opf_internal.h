@@ -107,6 +107,8 @@ struct DevStatus {
     int converged, numeric, done, pad;
     long long max_iter;
     double eps_rel, eps_abs_pres;
+    int fault;             // a bounded wait of an engine ran out (the iterates are not valid)
+    int pad2;
 };
 
 // Per subsystem s (device order): A_s (m x n row-major) at W + aoff[s] and b_s
@@ -143,6 +145,23 @@ struct ClusterLayout {
     unsigned bytes;
 };
 
+// Shared-memory image of one CTA of the persistent grid engine, byte offsets.
+constexpr int kPersistMaxThreads = 512;
+struct PersistLayout {
+    int P, L, threads;
+    unsigned off_F, off_srec, off_items, off_meta, off_segp, off_pk, off_bt, off_ds, off_mu;
+    unsigned off_ct, off_lbt, off_ubt, off_vbx, off_vbw, off_tb, off_recip, off_xrs, off_lrs, off_cobj;
+    unsigned off_misc;
+    unsigned bytes;
+};
+
+// Device arrays of a persistent grid engine plan.
+struct PersistPtrs {
+    const int *pr;                 // part ranges, 5 fields x (P + 1)
+    double *part;                  // Sec. III-C partial sums, P x 6
+    unsigned long long *sync;      // grid barrier counter
+};
+
 // Shared-memory image of one CTA of the warp engine, byte offsets.
 struct WarpLayout {
     int P, L, S, useg_len, fbig_len;
@@ -152,6 +171,8 @@ struct WarpLayout {
 
 // A second non-blocking stream on the same SMs as s (its green context, if any).
 int stream_sibling(cudaStream_t s, cudaStream_t *out);
+// SMs that kernels launched on s may use: its green context's, else the device's.
+int stream_sm_count(cudaStream_t s, int device);
 
 // ------------------------------------------------------------ batched engine
 // One warp task of the batched engine.  Lanes are (member position jpos,

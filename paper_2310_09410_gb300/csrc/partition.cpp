@@ -26,6 +26,7 @@ using PFN_gdestroy = CUresult (*)(CUgreenCtx);
 using PFN_sdestroy = CUresult (*)(CUstream);
 using PFN_devget = CUresult (*)(CUdevice *, int);
 using PFN_sgetg = CUresult (*)(CUstream, CUgreenCtx *);
+using PFN_gres = CUresult (*)(CUgreenCtx, CUdevResource *, CUdevResourceType);
 
 struct Fns {
     PFN_getRes getRes = nullptr;
@@ -37,6 +38,7 @@ struct Fns {
     PFN_sdestroy sdestroy = nullptr;
     PFN_devget devget = nullptr;
     PFN_sgetg sgetg = nullptr;
+    PFN_gres gres = nullptr;
     bool ok = false;
 };
 
@@ -62,7 +64,7 @@ const Fns &fns() {
                entry("cuDevResourceGenerateDesc", &f.desc) && entry("cuGreenCtxCreate", &f.gctx) &&
                entry("cuGreenCtxStreamCreate", &f.gstream) && entry("cuGreenCtxDestroy", &f.gdestroy) &&
                entry("cuStreamDestroy", &f.sdestroy) && entry("cuDeviceGet", &f.devget) &&
-               entry("cuStreamGetGreenCtx", &f.sgetg);
+               entry("cuStreamGetGreenCtx", &f.sgetg) && entry("cuGreenCtxGetDevResource", &f.gres);
     });
     return f;
 }
@@ -143,4 +145,19 @@ int opf::stream_sibling(cudaStream_t s, cudaStream_t *out) {
         return OPF_OK;
     }
     return cudaStreamCreateWithFlags(out, cudaStreamNonBlocking) == cudaSuccess ? OPF_OK : OPF_E_CUDA;
+}
+
+int opf::stream_sm_count(cudaStream_t s, int device) {
+    const Fns &f = fns();
+    CUgreenCtx g = nullptr;
+    if (s && f.ok && f.sgetg((CUstream)s, &g) == CUDA_SUCCESS && g) {
+        CUdevResource r;
+        if (f.gres(g, &r, CU_DEV_RESOURCE_TYPE_SM) == CUDA_SUCCESS && r.sm.smCount > 0) return (int)r.sm.smCount;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n;
 }

@@ -26,9 +26,10 @@ OPF_E_CUDA = -7
 OPF_E_CAPACITY = -8
 
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
-ENGINE_AUTO, ENGINE_GRID, ENGINE_CTA, ENGINE_WARP = 0, 1, 2, 3
+ENGINE_AUTO, ENGINE_GRID, ENGINE_CTA, ENGINE_WARP, ENGINE_PERSISTENT = 0, 1, 2, 3, 4
 ENGINE_CLUSTER = ENGINE_CTA
 SOLVE_HOST_LOOP = 1
+SOLVE_TEST_BARRIER_TIMEOUT = 2
 
 _P = C.c_void_p
 

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path against the CPU oracle through the C ABI.
 
 * FP64 iterates (x, x_s, lambda) after 100 iterations within 1e-10 relative
-  (both engines), on synthetic feeders of every size and on random
+  (whole-grid, cluster and persistent grid engines), on synthetic feeders of every size and on random
   consensus instances (rank-deficient blocks, blocks wider than 64);
 * converged solves (FP64 and mixed precision) reach the LP optimum of the
   oracle within 1e-6 relative with pres <= 1e-4.
@@ -71,7 +71,30 @@ def test_cluster_engine_fp64_matches_oracle(name, seed, cluster):
     assert rel_err(x, ref.x) <= TOL_ITER
 
 
-@pytest.mark.parametrize("engine", [opf.ENGINE_GRID, opf.ENGINE_CLUSTER, opf.ENGINE_WARP])
+@pytest.mark.parametrize("name,seed,ctas", [("13", 1001, 1), ("13", 1001, 32), ("34", 5034, 5),
+                                            ("123", 2001, 3), ("123", 2001, 40), ("123", 2001, 0),
+                                            ("8500", 3001, 0), ("8500", 3001, 152)])
+def test_persistent_engine_fp64_matches_oracle(name, seed, ctas):
+    """The persistent grid engine (one cooperative launch, grid barrier per
+    iteration) with 1 CTA, more CTAs than subsystems, and automatic / fixed
+    grids on the large feeder: FP64 iterates match the oracle."""
+    f = synth.preset_feeder(name, seed)
+    M = lindist.build(f)
+    ref = oracle_iterates(M, 100)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64,
+                engine=opf.ENGINE_PERSISTENT, cluster=ctas)
+        xs, lam = s.locals()
+        x, obj = s.solution()
+        assert s.residuals()["iters"] == 100
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
+    assert abs(obj - ref.objective) <= TOL_ITER * max(1.0, abs(ref.objective))
+
+
+@pytest.mark.parametrize("engine", [opf.ENGINE_GRID, opf.ENGINE_CLUSTER, opf.ENGINE_WARP, opf.ENGINE_PERSISTENT])
 @pytest.mark.parametrize("name,seed", [("13", 1002), ("123", 2001)])
 def test_fp32_engines_track_oracle(name, seed, engine):
     """FP32 iterations without re-centring stay within single-precision
@@ -124,7 +147,9 @@ def test_zip_delta_loads_match_oracle():
 
 
 @pytest.mark.parametrize("precision,engine", [(opf.PREC_FP64, opf.ENGINE_AUTO), (opf.PREC_MIXED, opf.ENGINE_AUTO),
-                                              (opf.PREC_FP64, opf.ENGINE_GRID), (opf.PREC_MIXED, opf.ENGINE_GRID)])
+                                              (opf.PREC_FP64, opf.ENGINE_GRID), (opf.PREC_MIXED, opf.ENGINE_GRID),
+                                              (opf.PREC_FP64, opf.ENGINE_PERSISTENT),
+                                              (opf.PREC_MIXED, opf.ENGINE_PERSISTENT)])
 @pytest.mark.parametrize("name,seed", [("13", 1003), ("123", 2002)])
 def test_converged_objective(name, seed, precision, engine):
     f = synth.preset_feeder(name, seed)

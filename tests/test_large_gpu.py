@@ -1,0 +1,65 @@
+"""The large feeder (8500 buses) solved to convergence, and the failure path
+of the persistent grid engine's bounded barrier wait.
+
+* mixed precision (FP32 iterations in the re-centred frame on the persistent
+  grid engine, FP64 polish) reaches the LP optimum of the oracle within 1e-6
+  relative with pres <= 1e-4;
+* a barrier that can never complete (a test hook asks for one arrival more
+  than the grid has) ends in OPF_E_TIMEOUT after its bounded wait, and the
+  same handle then iterates correctly.
+"""
+import numpy as np
+import pytest
+
+from oracle import admm as oracle_admm, lindist
+from paper_2310_09410_gb300 import opf, synth
+
+pytestmark = pytest.mark.gpu
+
+# Sec. III-C test on the 8500-bus feeder: its norms run over ~1.1e5 local
+# slots, so the relative tolerance that gives a 1e-6 objective is tighter
+# than on the small feeders.
+EPS_REL_LARGE = 2e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
+
+
+def test_large_feeder_mixed_reaches_lp_optimum():
+    f = synth.preset_feeder("8500", 3001)
+    M = lindist.build(f)
+    obj_star, _ = oracle_admm.lp_optimum(M)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        ok = s.solve(precision=opf.PREC_MIXED, eps_rel=EPS_REL_LARGE, max_iter=6_000_000)
+        _, obj = s.solution()
+        r = s.residuals()
+    assert ok, r
+    assert r["pres"] <= 1e-4
+    assert abs(obj - obj_star) <= 1e-6 * abs(obj_star), (obj, obj_star, r)
+
+
+@pytest.mark.parametrize("precision", [opf.PREC_FP64, opf.PREC_MIXED])
+def test_barrier_timeout_is_reported_and_handle_recovers(precision):
+    f = synth.preset_feeder("123", 2001)
+    M = lindist.build(f)
+    ref = oracle_admm.admm(oracle_admm.Prepared(M), rho=100.0, max_iter=100, check_every=0)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        with pytest.raises(opf.OPFError) as e:
+            s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=precision,
+                    engine=opf.ENGINE_PERSISTENT, cluster=8, flags=opf.SOLVE_TEST_BARRIER_TIMEOUT)
+        assert e.value.code == opf.OPF_E_TIMEOUT
+        s.reset()
+        s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64,
+                engine=opf.ENGINE_PERSISTENT, cluster=8)
+        xs, lam = s.locals()
+    assert rel_err(xs, ref.xs) <= 1e-10
+    assert rel_err(lam, ref.lam) <= 1e-10
