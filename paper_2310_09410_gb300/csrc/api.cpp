@@ -754,12 +754,16 @@ static int build_persist_plan(opf_handle *h, PersistPlan *pp, int P, int n_sm) {
         PR(3, p) = h->h_foff[s];
         PR(4, p) = h->h_vpre[s];
     }
+    // factors staged per part with column stride npad (+ 4 when npad % 8 == 0)
     std::vector<int4> srec(S + 1, make_int4(0, 0, 0, 0));
     std::vector<int> items, meta(L);
+    std::vector<long long> fpart(P, 0);
     for (int p = 0; p < P; ++p) {
         for (int s = sp[p]; s < sp[p + 1]; ++s) {
-            srec[s] = make_int4(h->h_foff[s] - PR(3, p), h->h_vpre[s] - PR(4, p), h->h_tpre[s] - PR(2, p),
-                                (h->h_sf[s] << 10) | (h->h_npad[s] << 1) | (h->h_mode[s] & 1));
+            const int npad = h->h_npad[s], cs = npad + ((npad & 7) == 0 ? 4 : 0);
+            srec[s] = make_int4((int)fpart[p], h->h_vpre[s] - PR(4, p), h->h_tpre[s] - PR(2, p),
+                                (h->h_sf[s] << 10) | (npad << 1) | (h->h_mode[s] & 1));
+            fpart[p] += (long long)h->h_sf[s] * cs;
             for (int c = 0; c < h->h_sf[s]; ++c) items.push_back(((s - sp[p]) << 8) | c);
             for (int r = 0; r < h->h_sn[s]; ++r) meta[h->h_soff[s] + r] = ((s - sp[p]) << 8) | r;
         }
@@ -769,7 +773,7 @@ static int build_persist_plan(opf_handle *h, PersistPlan *pp, int P, int n_sm) {
         mk = std::max<long long>(mk, PR(0, p + 1) - PR(0, p));
         ms = std::max<long long>(ms, PR(1, p + 1) - PR(1, p));
         mj = std::max<long long>(mj, PR(2, p + 1) - PR(2, p));
-        mf = std::max<long long>(mf, PR(3, p + 1) - PR(3, p));
+        mf = std::max<long long>(mf, fpart[p]);
         mv = std::max<long long>(mv, PR(4, p + 1) - PR(4, p));
     }
     PersistLayout &c = pp->lay;

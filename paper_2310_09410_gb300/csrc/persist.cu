@@ -117,6 +117,11 @@ __device__ __forceinline__ double dot_fx<double>(const double *__restrict__ f, c
     return a0 + a1;
 }
 
+// Column stride of a staged factor with npad rows: npad, plus 4 words when
+// npad is a multiple of 8, so that the 16-byte column reads of 8 consecutive
+// threads (consecutive columns) fall in distinct bank groups.
+__host__ __device__ __forceinline__ int fstride(int npad) { return npad + ((npad & 7) == 0 ? 4 : 0); }
+
 // Part ranges: pr[field * (P + 1) + rank].
 enum { GR_K = 0, GR_S, GR_J, GR_F, GR_V, GR_NFIELDS };
 
@@ -137,7 +142,6 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
     const int k0 = pr[GR_K * P1 + rank], nk = pr[GR_K * P1 + rank + 1] - k0;
     const int s0 = pr[GR_S * P1 + rank], ns = pr[GR_S * P1 + rank + 1] - s0;
     const int j0 = pr[GR_J * P1 + rank], nj = pr[GR_J * P1 + rank + 1] - j0;
-    const int f0 = pr[GR_F * P1 + rank], nf = pr[GR_F * P1 + rank + 1] - f0;
     const int v0 = pr[GR_V * P1 + rank], nv = pr[GR_V * P1 + rank + 1] - v0;
     T *F = reinterpret_cast<T *>(sm + lay.off_F);
     int4 *srec = reinterpret_cast<int4 *>(sm + lay.off_srec);
@@ -162,7 +166,6 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
     DevStatus *loc = reinterpret_cast<DevStatus *>(sm + lay.off_misc + 16);
     double(*red)[6] = reinterpret_cast<double(*)[6]>(sm + lay.off_misc + 16 + ((sizeof(DevStatus) + 15) & ~15));
 
-    stage<T>(F, g.F + f0, nf);
     stage<int4>(srec, g.srec + s0, ns);
     stage<int>(items, g.citems + j0, nj);
     stage<int>(meta, g.cmeta + k0, nk);
@@ -182,6 +185,17 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
         cobj[k] = (g.pk[k0 + k] == (g.segp[k0 + k] >> 8)) ? g.c64[gi] : 0.0;
     }
     for (int i = threadIdx.x; i < nv; i += blockDim.x) { vbx[i] = (T)0; vbw[i] = (T)0; }
+    __syncthreads();
+    // factors: one warp per own subsystem, columns re-strided
+    for (int i = threadIdx.x >> 5; i < ns; i += blockDim.x >> 5) {
+        const int4 r = srec[i];
+        const int f = r.w >> 10, npad = (r.w >> 1) & 0x1ff, cs = fstride(npad);
+        const T *src = g.F + g.sub2[s0 + i].x;
+        for (int e = threadIdx.x & 31; e < f * npad; e += 32) {
+            const int c = e / npad;
+            F[r.x + c * cs + (e - c * npad)] = src[e];
+        }
+    }
     if (threadIdx.x == 0) {
         flags[0] = 0;
         flags[1] = 0;
@@ -232,7 +246,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
             const int itm = items[j];
             const int4 r = srec[itm >> 8];
             const int c = itm & 255, npad = (r.w >> 1) & 0x1ff;
-            tb[r.z + c] = dot_fx<T>(F + r.x + c * npad, vbx + r.y, vbw + r.y, npad);
+            tb[r.z + c] = dot_fx<T>(F + r.x + c * fstride(npad), vbx + r.y, vbw + r.y, npad);
         }
         __syncthreads();
         // C: projection, dual update, u to the next iteration's buffer
@@ -240,16 +254,16 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
             const int mt = meta[k];
             const int4 r = srec[mt >> 8];
             const int row = mt & 255;
-            const int f = r.w >> 10, npad = (r.w >> 1) & 0x1ff, mode = r.w & 1;
+            const int f = r.w >> 10, cs = fstride((r.w >> 1) & 0x1ff), mode = r.w & 1;
             const T *Fr = F + r.x + row;
             const T *tt = tb + r.z;
             T y0 = 0, y1 = 0;
             int c = 0;
             for (; c + 1 < f; c += 2) {
-                y0 += Fr[c * npad] * tt[c];
-                y1 += Fr[(c + 1) * npad] * tt[c + 1];
+                y0 += Fr[c * cs] * tt[c];
+                y1 += Fr[(c + 1) * cs] * tt[c + 1];
             }
-            if (c < f) y0 += Fr[c * npad] * tt[c];
+            if (c < f) y0 += Fr[c * cs] * tt[c];
             const int pos = r.y + row;
             const T x = vbx[pos];
             const T v = x + vbw[pos];
