@@ -4,6 +4,8 @@ of the persistent grid engine's bounded barrier wait.
 * mixed precision (FP32 iterations in the re-centred frame on the persistent
   grid engine, FP64 polish) reaches the LP optimum of the oracle within 1e-6
   relative with pres <= 1e-4;
+* the persistent engine on an SM partition (green context) sizes its grid to
+  the partition and matches the oracle;
 * a barrier that can never complete (a test hook asks for one arrival more
   than the grid has) ends in OPF_E_TIMEOUT after its bounded wait, and the
   same handle then iterates correctly.
@@ -63,3 +65,25 @@ def test_barrier_timeout_is_reported_and_handle_recovers(precision):
         xs, lam = s.locals()
     assert rel_err(xs, ref.xs) <= 1e-10
     assert rel_err(lam, ref.lam) <= 1e-10
+
+
+def test_persistent_engine_on_sm_partition_matches_oracle():
+    f = synth.preset_feeder("123", 2001)
+    M = lindist.build(f)
+    ref = oracle_admm.admm(oracle_admm.Prepared(M), rho=100.0, max_iter=100, check_every=0)
+    part = opf.SMPartition(32)
+    try:
+        with opf.Solver.from_feeder(f, stream=part.stream) as s:
+            s.precompute()
+            s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64,
+                    engine=opf.ENGINE_PERSISTENT)
+            xs, lam = s.locals()
+            s.reset()
+            assert s.solve(precision=opf.PREC_MIXED, engine=opf.ENGINE_PERSISTENT)
+            _, obj = s.solution()
+    finally:
+        part.close()
+    assert rel_err(xs, ref.xs) <= 1e-10
+    assert rel_err(lam, ref.lam) <= 1e-10
+    obj_star, _ = oracle_admm.lp_optimum(M)
+    assert abs(obj - obj_star) <= 1e-6 * abs(obj_star)
