@@ -618,7 +618,9 @@ def serve_config(args):
                     f"FP64 polish to eps_rel=1e-8 and pres<=1e-4; {args.requests} requests after "
                     f"{args.warm_requests} warm-up requests; arrivals stop after the last request, then the "
                     f"server drains for at most {args.drain_s:.0f} s",
-        "models": f"13/34/123-bus: continuous batching in the batched engine; 8500-bus: {args.big_handles} "
+        "models": f"13/34/123-bus: continuous batching in the batched engine, passes of {args.chunk} FP32 iterations "
+                  f"(slots in the FP64 polish: {args.polish_chunk or 100} FP64 iterations per pass); "
+                  f"8500-bus: {args.big_handles} "
                   f"single-instance handles on worker threads; the 8500-bus workers on an SM partition of "
                   f"{args.big_sms} SMs (green context), the batched models on the remaining SMs",
         "parallelism": "replicas",
@@ -635,7 +637,8 @@ def run_serve(args, rank, world, local):
     weights = weights / weights.sum()
     feeders = {k: synth.preset_feeder(k, SERVE_FEEDER_SEEDS[k]) for k in SERVE_SIZES}
     solvers = {}
-    srv = opf.Server(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, max_iter=args.max_iter)
+    srv = opf.Server(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, max_iter=args.max_iter,
+                     chunk_iters=args.chunk, polish_chunk_iters=args.polish_chunk)
     mid = {}
     caps = {"13": 1024, "34": 1024, "123": 1024}
     # SM partitions (green contexts): the single-instance workers of the
@@ -753,6 +756,10 @@ def main():
     ap.add_argument("--max-iter", type=int, default=1_000_000, help="serve: iteration cap per request")
     ap.add_argument("--mix", default="0.4,0.3,0.2,0.1", help="serve: weights of the 13/34/123/8500-bus requests")
     ap.add_argument("--big-sms", type=int, default=16, help="serve: SMs of the 8500-bus workers' partition (0: none)")
+    ap.add_argument("--chunk", type=int, default=1000,
+                    help="serve: FP32 iterations per pass (and re-centring interval)")
+    ap.add_argument("--polish-chunk", type=int, default=0,
+                    help="serve: FP64 iterations per pass of slots in the polish (0: the library default)")
     ap.add_argument("--instances", type=int, default=N_SCEN)
     ap.add_argument("--feeder", default="123", choices=sorted(SINGLE_SEEDS, key=int),
                     help="single-instance workload: the feeder (13, 123 and 8500 buses are the single-instance "

@@ -365,6 +365,10 @@ typedef struct opf_server_opts {
     int32_t chunk_iters;            /* iterations per pass (a multiple of check_every) */
     int32_t keep_solutions;         /* 1: keep x of finished requests for opf_server_take_solution */
     int64_t mem_budget;             /* device bytes for request slots over all models (0: no limit) */
+    int32_t polish_chunk_iters;     /* FP64 iterations per pass for slots in the polish (a multiple of
+                                       check_every; 0 = 2 x check_every): FP64 iterations cost several
+                                       times FP32 ones, and a model's next pass waits for both */
+    int32_t reserved;               /* 0 */
 } opf_server_opts;
 
 int opf_server_create(const opf_server_opts *o, opf_server **out);

@@ -8,7 +8,8 @@
 //      device-memory budget given at creation),
 //   2. advances every running slot on the model's own stream: slots in the
 //      FP32 phase by one re-centring interval of FP32 iterations, slots in the
-//      FP64 polish by the same number of FP64 iterations,
+//      FP64 polish by a shorter interval of FP64 iterations (an FP64
+//      iteration costs several FP32 ones, and the next pass waits for both),
 //   3. moves slots whose FP32 test held to the polish and retires slots whose
 //      FP64 test held (or that hit max_iter), freeing them for the next pass.
 // Models run on separate streams, so their work overlaps on the device.  An
@@ -222,6 +223,7 @@ int step_batched_enqueue(opf_server *s, Model &m) {
     if (!m.running()) return OPF_OK;
     STRY(upload_maps(m));
     const int R = s->o.chunk_iters, k = s->o.check_every;
+    const int R64 = s->o.polish_chunk_iters;
     // FP32 slots on the model's stream, FP64 slots on a second stream: the
     // two passes touch disjoint instances and run side by side
     SCUDA(cudaEventRecord(m.ev_start, b->h->stream));
@@ -233,7 +235,7 @@ int step_batched_enqueue(opf_server *s, Model &m) {
     }
     if (m.n64) {
         STRY(plan_set_rho(b, &b->p64, s->o.rho));
-        enqueue_body_any(b, b->p64, s->o.rho, R, k, cudaGraphConditionalHandle{}, 0, nullptr, nullptr,
+        enqueue_body_any(b, b->p64, s->o.rho, R64, k, cudaGraphConditionalHandle{}, 0, nullptr, nullptr,
                          (m.n64 + b->p64.K - 1) / b->p64.K, m.s64);
     }
     SCUDA(cudaEventRecord(m.ev64, m.s64));
@@ -304,13 +306,15 @@ extern "C" {
 
 int opf_server_create(const opf_server_opts *o, opf_server **out) {
     if (!o || !out || !(o->rho > 0) || o->max_iter < 1 || o->check_every < 2 || (o->check_every & 1) ||
-        o->chunk_iters < o->check_every || o->chunk_iters % o->check_every || o->mem_budget < 0) {
-        set_last_error("server options: rho > 0, max_iter >= 1, even check_every >= 2, chunk_iters a multiple "
-                       "of check_every, mem_budget >= 0");
+        o->chunk_iters < o->check_every || o->chunk_iters % o->check_every || o->mem_budget < 0 ||
+        o->polish_chunk_iters < 0 || o->polish_chunk_iters % o->check_every) {
+        set_last_error("server options: rho > 0, max_iter >= 1, even check_every >= 2, chunk_iters and "
+                       "polish_chunk_iters multiples of check_every, mem_budget >= 0");
         return OPF_E_INVALID;
     }
     opf_server *s = new opf_server();
     s->o = *o;
+    if (s->o.polish_chunk_iters == 0) s->o.polish_chunk_iters = 2 * o->check_every;
     *out = s;
     return OPF_OK;
 }

@@ -68,7 +68,8 @@ class Sizes(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("rho", C.c_double), ("eps_rel", C.c_double), ("eps_abs_pres", C.c_double),
                 ("max_iter", C.c_int32), ("check_every", C.c_int32), ("chunk_iters", C.c_int32),
-                ("keep_solutions", C.c_int32), ("mem_budget", C.c_int64)]
+                ("keep_solutions", C.c_int32), ("mem_budget", C.c_int64), ("polish_chunk_iters", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -450,10 +451,10 @@ class Server:
     """Continuous-batching request server (wraps an ``opf_server``)."""
 
     def __init__(self, rho=100.0, eps_rel=1e-8, eps_abs_pres=1e-4, max_iter=1_000_000, check_every=50,
-                 chunk_iters=1000, keep_solutions=False, mem_budget=0):
+                 chunk_iters=1000, keep_solutions=False, mem_budget=0, polish_chunk_iters=0):
         lib = load()
         o = ServerOpts(rho, eps_rel, eps_abs_pres, int(max_iter), int(check_every), int(chunk_iters),
-                       int(bool(keep_solutions)), int(mem_budget))
+                       int(bool(keep_solutions)), int(mem_budget), int(polish_chunk_iters), 0)
         h = C.c_void_p()
         _check(lib.opf_server_create(C.byref(o), C.byref(h)), "opf_server_create")
         self._s = h
