@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(512, 1)
     const T *Fs = FG ? a.Fpk : Fsm;
     T *us = reinterpret_cast<T *>(smraw + a.off_u);
     int2 *gts = reinterpret_cast<int2 *>(smraw + a.off_gt);      // (first copy | copies << 24, bounded index)
-    T *rcs = reinterpret_cast<T *>(smraw + a.off_rc);            // 1 / (rho N_i)
+    T *rcs = reinterpret_cast<T *>(smraw + a.off_rc);            // 1 / (rho N) by copy count N
+    BatchTask *tks = reinterpret_cast<BatchTask *>(smraw + a.off_task);   // the warp tasks
     int *usg = reinterpret_cast<int *>(smraw + a.off_useg);      // slot-array row of every copy
     T *bnd = reinterpret_cast<T *>(smraw + a.off_bnd);           // [NB][2][K]: bounds - x_ref
     double *red = reinterpret_cast<double *>(smraw + a.off_red);
@@ -309,8 +310,9 @@ __global__ void __launch_bounds__(512, 1)
     for (int i = tid; i < a.G; i += nthr) {
         const int4 gt = __ldg(a.gtab + i);
         gts[i] = make_int2((int)((unsigned)gt.x | ((unsigned)gt.y << 24)), gt.z);
-        rcs[i] = __ldg(a.recip + i);
     }
+    for (int i = tid; i < kBatchRecip; i += nthr) rcs[i] = __ldg(a.recip + i);
+    for (int i = tid; i < a.n_tasks; i += nthr) tks[i] = a.tasks[i];
     for (int k = tid; k < a.L; k += nthr) usg[k] = __ldg(a.useg + k);
     const size_t sb = (size_t)c * a.NCH * K * 4;     // this CTA's slot arrays
     const size_t gb = (size_t)c * a.G * K;           // global arrays
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
                     for (int k = 0; k < KQ; ++k) sum.v[k] += uq.v[k];
                 }
-                const T rcp = rcs[i];
+                const T rcp = rcs[cnt];
 #pragma unroll
                 for (int k = 0; k < KQ; ++k) sum.v[k] = (sum.v[k] - cr[j].v[k]) * rcp;
                 if (gt.y >= 0) {
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(512, 1)
                     if (lane == 0) tn = atomicAdd(tnext, 1);
                     tn = __shfl_sync(0xffffffffu, tn, 0);
                 }
-                const BatchTask tk = a.tasks[t];
+                const BatchTask tk = tks[t];
                 switch (tk.nq) {
                     case 1: batch_task<T, K, 1>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
                                                 inv_rho, check, act, wds, redw); break;

@@ -220,7 +220,8 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     p->off_u = fg ? 0u : a16((size_t)p->nF * sz);
     p->off_gt = p->off_u + a16((size_t)p->NCH * K * 4 * sz);
     p->off_rc = p->off_gt + a16((size_t)G * sizeof(int2));
-    p->off_useg = p->off_rc + a16((size_t)G * sz);
+    p->off_task = p->off_rc + a16((size_t)kBatchRecip * sz);
+    p->off_useg = p->off_task + a16((size_t)p->n_tasks * sizeof(BatchTask));
     p->off_bnd = p->off_useg + a16((size_t)L * sizeof(int));
     p->off_red = p->off_bnd + a16((size_t)b->NB * 2 * K * sz);
     p->off_flag = p->off_red + a16((size_t)W * K * 6 * sizeof(double));
@@ -254,7 +255,7 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
         return OPF_OK;
     };
     BTRY(arr(&p->d_F, (size_t)p->nF));
-    BTRY(arr(&p->d_recip, (size_t)G));
+    BTRY(arr(&p->d_recip, (size_t)kBatchRecip));
     BTRY(arr(&p->d_cost, (size_t)G));
     BTRY(arr(&p->mu, nslot)); BTRY(arr(&p->ds, nslot)); BTRY(arr(&p->bt, nslot)); BTRY(arr(&p->lref, nslot));
     BTRY(arr(&p->xo, nglob)); BTRY(arr(&p->ct, nglob)); BTRY(arr(&p->xrf, nglob));
@@ -283,12 +284,15 @@ int plan_set_rho(opf_batch *b, BPlan *p, double rho) {
     if (p->rho == rho) return OPF_OK;
     opf_handle *h = b->h;
     const int G = h->G;
-    std::vector<double> r(G);
-    for (int i = 0; i < G; ++i) r[i] = 1.0 / (rho * (h->h_gstart[i + 1] - h->h_gstart[i]));
-    if (p->dbl) BCUDA(cudaMemcpyAsync(p->d_recip, r.data(), G * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    // 1 / (rho N) by copy count N (a global has fewer than kBatchRecip copies)
+    (void)G;
+    std::vector<double> r(kBatchRecip, 0.0);
+    for (int n = 1; n < kBatchRecip; ++n) r[n] = 1.0 / (rho * n);
+    if (p->dbl) BCUDA(cudaMemcpyAsync(p->d_recip, r.data(), kBatchRecip * sizeof(double), cudaMemcpyHostToDevice,
+                                      h->stream));
     else {
         std::vector<float> f(r.begin(), r.end());
-        BCUDA(cudaMemcpyAsync(p->d_recip, f.data(), G * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        BCUDA(cudaMemcpyAsync(p->d_recip, f.data(), kBatchRecip * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     }
     BCUDA(cudaStreamSynchronize(h->stream));
     p->rho = rho;
@@ -303,7 +307,8 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
     a.K = p.K; a.kshift = p.ks; a.J = p.J; a.NCH = p.NCH; a.G = b->G; a.NB = p.NB; a.n_tasks = p.n_tasks;
     a.nF = p.nF;
     a.L = b->L;
-    a.off_u = p.off_u; a.off_gt = p.off_gt; a.off_rc = p.off_rc; a.off_useg = p.off_useg; a.off_bnd = p.off_bnd;
+    a.off_u = p.off_u; a.off_gt = p.off_gt; a.off_rc = p.off_rc; a.off_task = p.off_task; a.off_useg = p.off_useg;
+    a.off_bnd = p.off_bnd;
     a.off_red = p.off_red; a.off_flag = p.off_flag;
     a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab;
     a.useg = p.d_useg;

@@ -11,7 +11,8 @@ struct BPlan {
     bool ok = false, dbl = false, fg = false;   // fg: factors read from global memory
     int K = 0, ks = 0, J = 0, W = 0, nq = 0, threads = 0;
     int NCH = 0, NB = 0, nF = 0, n_tasks = 0, C = 0;
-    unsigned off_u = 0, off_gt = 0, off_rc = 0, off_useg = 0, off_bnd = 0, off_red = 0, off_flag = 0, bytes = 0;
+    unsigned off_u = 0, off_gt = 0, off_rc = 0, off_task = 0, off_useg = 0, off_bnd = 0, off_red = 0, off_flag = 0;
+    unsigned bytes = 0;
     double rho = -1.0;
     std::vector<void *> allocs;
     BatchTask *d_tasks = nullptr;

@@ -181,6 +181,8 @@ int stream_sm_count(cudaStream_t s, int device);
 // (part * nq + q), q < nq, of its member's slots, part = jpos % p, 4 slots
 // per chunk.  Chunk (q, jpos) of the task is chunk ch0 + q * J + jpos of the
 // CTA's chunk array.
+constexpr int kBatchRecip = 256;   // copy counts of a global are below this (the 8-bit count field)
+
 struct BatchTask {
     int ch0;     // first chunk
     int nq;      // chunks per position
@@ -199,13 +201,13 @@ struct BatchTask {
 template <typename T>
 struct BatchArgs {
     int K, kshift, J, NCH, G, L, NB, n_tasks, nF;
-    unsigned off_u, off_gt, off_rc, off_useg, off_bnd, off_red, off_flag;   // shared-memory byte offsets
+    unsigned off_u, off_gt, off_rc, off_task, off_useg, off_bnd, off_red, off_flag;   // shared-memory byte offsets
     const BatchTask *tasks;    // [n_tasks] in decreasing cost
     const int4 *chg;           // [NCH] g * K of each chunk's 4 slots (-1: padding)
     const int4 *gtab;          // [G] (first copy in useg, copies, bounded index or -1, 0)
     const int *useg;           // copies of each global: slot-array row (ch * 4 + (e ^ (ch & 3))) * K
     const T *Fpk;              // [nF] factors, task-interleaved
-    const T *recip;            // [G] 1 / (rho N_i)
+    const T *recip;            // [kBatchRecip] 1 / (rho N) by copy count N
     const T *cost;             // [G] c_i
     T *mu, *ds, *xo;
     const T *bt, *lref, *ct, *xrf, *lbt, *ubt;
