@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(512, 1)
     constexpr int KQ = K < 4 ? K : 4;          // columns per global-update item
     constexpr int NQD = K / KQ;                  // items per global
     constexpr int QS = NQD == 1 ? 0 : NQD == 2 ? 1 : NQD == 4 ? 2 : 3;
-    constexpr int GB = 8;                        // global-update items per thread with loads in flight
+    // global-update items per thread with loads in flight (fewer for FP64 rows of 4: registers)
+    constexpr int GB = (sizeof(T) == 8 && KQ == 4) ? 4 : 8;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *Fsm = reinterpret_cast<T *>(smraw);
     const T *Fs = FG ? a.Fpk : Fsm;
@@ -354,40 +355,74 @@ __global__ void __launch_bounds__(512, 1)
         // its columns: sum of u over the copies, shift, scale, clip, and x
         // stored into every copy's slot; GB items per thread with c~ in flight
         for (int b0 = tid; b0 < GQ; b0 += GB * nthr) {
-            RowK<T, KQ> cr[GB];
+            // the GB items of this thread advance stage by stage, so that the
+            // loads of one stage are in flight together: c~ (L2) and the
+            // table entries, the first two copies' rows, their u; further
+            // copies (vertices of degree > 1) one by one; then the update
+            RowK<T, KQ> cr[GB], sum[GB];
+            int2 gtj[GB];
+            int row0[GB], row1[GB];
 #pragma unroll
             for (int j = 0; j < GB; ++j) {
                 const int item = b0 + j * nthr;
-                if (item < GQ)
+                gtj[j] = make_int2(0, -1);
+                if (item < GQ) {
                     load_row<T, KQ, true>(cr[j], a.ct + gb + (size_t)(item >> QS) * K + (item & (NQD - 1)) * KQ);
+                    gtj[j] = gts[item >> QS];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < GB; ++j) {
+                const int item = b0 + j * nthr;
+                const int st0 = gtj[j].x & 0xffffff, cnt = (int)((unsigned)gtj[j].x >> 24);
+                const int hq = (item & (NQD - 1)) * KQ;
+                row0[j] = cnt > 0 ? usg[st0] + hq : 0;
+                row1[j] = cnt > 1 ? usg[st0 + 1] + hq : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < GB; ++j) {
+                const int cnt = (int)((unsigned)gtj[j].x >> 24);
+#pragma unroll
+                for (int k = 0; k < KQ; ++k) sum[j].v[k] = T(0);
+                if (cnt > 0) {
+                    RowK<T, KQ> u0;
+                    load_row<T, KQ, false>(u0, us + row0[j]);
+#pragma unroll
+                    for (int k = 0; k < KQ; ++k) sum[j].v[k] += u0.v[k];
+                }
+                if (cnt > 1) {
+                    RowK<T, KQ> u1;
+                    load_row<T, KQ, false>(u1, us + row1[j]);
+#pragma unroll
+                    for (int k = 0; k < KQ; ++k) sum[j].v[k] += u1.v[k];
+                }
             }
 #pragma unroll
             for (int j = 0; j < GB; ++j) {
                 const int item = b0 + j * nthr;
                 if (item >= GQ) continue;
-                const int i = item >> QS, h = item & (NQD - 1);
-                const int2 gt = gts[i];
+                const int h = item & (NQD - 1);
+                const int2 gt = gtj[j];
                 const int st0 = gt.x & 0xffffff, cnt = (int)((unsigned)gt.x >> 24);
-                RowK<T, KQ> sum;
-#pragma unroll
-                for (int k = 0; k < KQ; ++k) sum.v[k] = T(0);
-                for (int q = 0; q < cnt; ++q) {
+                for (int q = 2; q < cnt; ++q) {
                     RowK<T, KQ> uq;
                     load_row<T, KQ, false>(uq, us + usg[st0 + q] + h * KQ);
 #pragma unroll
-                    for (int k = 0; k < KQ; ++k) sum.v[k] += uq.v[k];
+                    for (int k = 0; k < KQ; ++k) sum[j].v[k] += uq.v[k];
                 }
                 const T rcp = rcs[cnt];
 #pragma unroll
-                for (int k = 0; k < KQ; ++k) sum.v[k] = (sum.v[k] - cr[j].v[k]) * rcp;
+                for (int k = 0; k < KQ; ++k) sum[j].v[k] = (sum[j].v[k] - cr[j].v[k]) * rcp;
                 if (gt.y >= 0) {
                     RowK<T, KQ> lo, hi;
                     load_row<T, KQ, false>(lo, bnd + (gt.y * 2) * K + h * KQ);
                     load_row<T, KQ, false>(hi, bnd + (gt.y * 2 + 1) * K + h * KQ);
 #pragma unroll
-                    for (int k = 0; k < KQ; ++k) sum.v[k] = clampT(sum.v[k], lo.v[k], hi.v[k]);
+                    for (int k = 0; k < KQ; ++k) sum[j].v[k] = clampT(sum[j].v[k], lo.v[k], hi.v[k]);
                 }
-                for (int q = 0; q < cnt; ++q) store_row<T, KQ>(us + usg[st0 + q] + h * KQ, sum);
+                if (cnt > 0) store_row<T, KQ>(us + row0[j], sum[j]);
+                if (cnt > 1) store_row<T, KQ>(us + row1[j], sum[j]);
+                for (int q = 2; q < cnt; ++q) store_row<T, KQ>(us + usg[st0 + q] + h * KQ, sum[j]);
             }
         }
         __syncthreads();
