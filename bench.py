@@ -682,8 +682,9 @@ def serve_config(args):
         "models": f"13/34/123-bus: continuous batching in the batched engine, passes of {args.chunk} FP32 iterations "
                   f"(slots in the FP64 polish: {args.polish_chunk or 100} FP64 iterations per pass); "
                   f"8500-bus: {args.big_handles} "
-                  f"single-instance handles on worker threads; the 8500-bus workers on an SM partition of "
-                  f"{args.big_sms} SMs (green context), the batched models on the remaining SMs",
+                  f"single-instance handles on worker threads, each on an SM partition of {args.big_sms} SMs "
+                  f"(green context); the batched models on "
+                  + ("the remaining SMs' partition" if args.batched_partition else "ordinary streams"),
         "parallelism": "replicas",
     }
 
@@ -708,7 +709,7 @@ def run_serve(args, rank, world, local):
     parts = []
     use_big = weights[SERVE_SIZES.index("8500")] > 0
     if use_big and args.big_sms > 0:
-        parts = [opf.SMPartition(-args.big_sms, device=local)]
+        parts = [opf.SMPartition(-args.big_sms, device=local) if args.batched_partition else None]
         parts += [opf.SMPartition(args.big_sms, device=local) for _ in range(args.big_handles)]
     for j, k in enumerate(SERVE_SIZES):
         if weights[j] == 0:
@@ -717,7 +718,10 @@ def run_serve(args, rank, world, local):
         for h in range(args.big_handles if k == "8500" else 1):
             stream = None
             if parts:
-                stream = parts[1 + h].stream if k == "8500" else parts[0].stream
+                if k == "8500":
+                    stream = parts[1 + h].stream
+                elif args.batched_partition:
+                    stream = parts[0].stream
             sv = opf.Solver.from_feeder(feeders[k], device=local, stream=stream)
             sv.precompute()
             hs.append(sv)
@@ -798,7 +802,8 @@ def run_serve(args, rank, world, local):
         for sv in hs:
             sv.close()
     for p in parts:
-        p.close()
+        if p is not None:
+            p.close()
     return 0
 
 
@@ -817,6 +822,9 @@ def main():
     ap.add_argument("--max-iter", type=int, default=1_000_000, help="serve: iteration cap per request")
     ap.add_argument("--mix", default="0.4,0.3,0.2,0.1", help="serve: weights of the 13/34/123/8500-bus requests")
     ap.add_argument("--big-sms", type=int, default=16, help="serve: SMs of the 8500-bus workers' partition (0: none)")
+    ap.add_argument("--batched-partition", action="store_true",
+                    help="serve: batched models on a partition of the SMs the 8500-bus workers do not hold "
+                         "(default: ordinary streams; measured sevenfold slower passes on the partition)")
     ap.add_argument("--chunk", type=int, default=1000,
                     help="serve: FP32 iterations per pass (and re-centring interval)")
     ap.add_argument("--polish-chunk", type=int, default=0,
