@@ -98,7 +98,8 @@ def test_server_options_and_handles_checked_on_host(lib):
     bad = [opf.ServerOpts(-1.0, 1e-8, 1e-4, 1000, 50, 1000, 0, 0),      # rho
            opf.ServerOpts(100.0, 1e-8, 1e-4, 1000, 3, 1000, 0, 0),       # odd check interval
            opf.ServerOpts(100.0, 1e-8, 1e-4, 1000, 50, 1010, 0, 0),      # chunk not a multiple
-           opf.ServerOpts(100.0, 1e-8, 1e-4, 1000, 50, 1000, 0, -5)]     # budget
+           opf.ServerOpts(100.0, 1e-8, 1e-4, 1000, 50, 1000, 0, -5),     # budget
+           opf.ServerOpts(100.0, 1e-8, 1e-4, 1000, 50, 1000, 0, 0, 75)]  # polish interval not a multiple
     for b in bad:
         assert lib.opf_server_create(ctypes.byref(b), ctypes.byref(out)) == opf.OPF_E_INVALID
     assert lib.opf_server_create(ctypes.byref(o), ctypes.byref(out)) == opf.OPF_OK

@@ -133,6 +133,54 @@ def test_generic_iterates_match_oracle(seed, kw):
     assert rel_err(x, ref.x) <= TOL_ITER
 
 
+def largest_subsystem_instance(seed=17, n=300):
+    """A consensus instance whose first subsystem has OPF_MAX_NS = 256 slots
+    (rank 120), the others small and overlapping it."""
+    rng = np.random.default_rng(seed)
+    lb, ub = rng.uniform(-2, 0, n), rng.uniform(0.5, 2, n)
+    c, xf = rng.uniform(-1, 1, n), rng.uniform(-0.4, 0.4, n)
+    subs = []
+    idx = np.arange(256, dtype=np.int32)
+    A = rng.normal(size=(120, 256))
+    subs.append({"idx": idx, "A": A, "b": A @ xf[idx]})
+    for start in range(230, n, 15):
+        idx = np.arange(start, min(start + 20, n), dtype=np.int32)
+        A = rng.normal(size=(max(1, len(idx) // 3), len(idx)))
+        subs.append({"idx": idx, "A": A, "b": A @ xf[idx]})
+    return {"c": c, "lb": lb, "ub": ub, "subs": subs}
+
+
+def test_largest_subsystem_matches_oracle():
+    """OPF_MAX_NS slots in one subsystem: FP64 iterates on the whole-grid
+    engine match the oracle, a mixed solve reaches the LP optimum, and the
+    persistent engine, whose CTA cannot hold that factor in FP64, refuses
+    with OPF_E_CAPACITY."""
+    g = largest_subsystem_instance()
+    assert max(len(s["idx"]) for s in g["subs"]) == 256
+    M = lindist.from_generic(g)
+    rho = 3.0
+    ref = oracle_iterates(M, 100, rho=rho)
+    obj_star, _ = oracle_admm.lp_optimum(M)
+    with opf.Solver.from_generic(g["c"], g["lb"], g["ub"], g["subs"]) as s:
+        s.precompute()
+        s.step(100, rho=rho)
+        xs, lam = s.locals()
+        x, _ = s.solution()
+        with pytest.raises(opf.OPFError) as e:
+            s.solve(rho=rho, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64,
+                    engine=opf.ENGINE_PERSISTENT)
+        assert e.value.code == opf.OPF_E_CAPACITY
+        s.reset()
+        assert s.solve(rho=rho, precision=opf.PREC_MIXED, max_iter=2_000_000)
+        _, obj = s.solution()
+        r = s.residuals()
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
+    assert r["pres"] <= TOL_PRES
+    assert abs(obj - obj_star) <= TOL_OBJ * max(1.0, abs(obj_star)), (obj, obj_star, r)
+
+
 def test_zip_delta_loads_match_oracle():
     f = synth.with_zip_delta(synth.preset_feeder("34", 5034), seed=3)
     assert f["load_delta"].sum() > 0
