@@ -220,12 +220,13 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
             const int us = sp >> 8, cnt = sp & 255;
             // the copies' u in flight together, summed in segment order
             T sigma = 0;
-            for (int q0 = 0; q0 < cnt; q0 += 4) {
-                T v[4];
+            constexpr int SEGW = sizeof(T) == 4 ? 8 : 4;    // copies' loads in flight
+            for (int q0 = 0; q0 < cnt; q0 += SEGW) {
+                T v[SEGW];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) v[j] = (q0 + j < cnt) ? __ldcg(Uin + us + q0 + j) : (T)0;
+                for (int j = 0; j < SEGW; ++j) v[j] = (q0 + j < cnt) ? __ldcg(Uin + us + q0 + j) : (T)0;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < SEGW; ++j)
                     if (q0 + j < cnt) sigma += v[j];
             }
             T x = (sigma - kct[k]) * recip[cnt];
