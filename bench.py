@@ -69,7 +69,7 @@ N_SM, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 # profiles/ (None until a capture of the current kernel exists).
 BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 70574080 + 12091392
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 352256 + 1536
-PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = None
+PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8707328 + 355584
 ITERS_PER_LAUNCH = 1000
 
 
