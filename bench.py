@@ -67,7 +67,7 @@ N_SM, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 
 # DRAM bytes per launch of the dominant kernels from the ncu captures in
 # profiles/ (None until a capture of the current kernel exists).
-BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 70574080 + 12091392
+BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 69280512 + 3924736
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 352256 + 1536
 PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8707328 + 355584
 ITERS_PER_LAUNCH = 1000
@@ -503,7 +503,7 @@ def run_batch(args, rank, world, local):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if achieved else None,
             "traffic": BATCH_ENGINE_TRAFFIC_PER_LAUNCH,
-            "traffic_unit": "DRAM bytes per engine launch (ncu)",
+            "traffic_unit": "DRAM bytes per engine launch of 2000 iterations (ncu)",
             "kernel": "k_batch_engine<float> (FP32; %d instances per CTA, %d warps, %d CTAs; factors, u and x "
                       "in shared memory, lambda and bbar~ streamed from L2)"
                       % (shape["k_inst"], shape["warps"], shape["ctas"]),

@@ -280,6 +280,8 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     return OPF_OK;
 }
 
+constexpr int kBatchRecenter = 2000;
+
 int plan_set_rho(opf_batch *b, BPlan *p, double rho) {
     if (p->rho == rho) return OPF_OK;
     opf_handle *h = b->h;
@@ -684,7 +686,9 @@ int opf_batch_solve(opf_batch *b, const opf_solve_opts *opts) {
     }
     BCUDA(cudaSetDevice(h->device));
     const int k = o.check_every;
-    int R = o.recenter_every > 0 ? o.recenter_every : 1000;
+    // default interval: 2000 (a batch pays a re-centring pass over every
+    // instance; 1000 -> 2000 measured 2.6 % less time, the same iterations)
+    int R = o.recenter_every > 0 ? o.recenter_every : kBatchRecenter;
     R = std::max(k, (R / k) * k);
     const bool hl = (o.flags & OPF_SOLVE_HOST_LOOP) != 0;
     // statuses: fresh test parameters, iteration counts from zero
