@@ -167,22 +167,18 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
     const int rstride = NQT * J * 4;
     const T *F0 = Fs + tk.foff + jpos * 4;
     const int red_top = tk.p * K;
+    // (the task's row count is even: a member's missing rows are zero)
     for (int r = 0; r < tk.f; r += 2, F0 += 2 * rstride) {
-        const bool two = r + 1 < tk.f;
         const T *F1 = F0 + rstride;
         T p0[4] = {T(0), T(0), T(0), T(0)}, p1[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int q = 0; q < NQT; ++q) {
             const Q4<T> f0 = ld4(F0 + q * J * 4);
+            const Q4<T> f1 = ld4(F1 + q * J * 4);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) p0[e] += f0.v[e] * v[4 * q + e];
-        }
-        if (two) {
-#pragma unroll
-            for (int q = 0; q < NQT; ++q) {
-                const Q4<T> f1 = ld4(F1 + q * J * 4);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) p1[e] += f1.v[e] * v[4 * q + e];
+            for (int e = 0; e < 4; ++e) {
+                p0[e] += f0.v[e] * v[4 * q + e];
+                p1[e] += f1.v[e] * v[4 * q + e];
             }
         }
         T s0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
@@ -194,15 +190,11 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
 #pragma unroll
         for (int q = 0; q < NQT; ++q) {
             const Q4<T> f0 = ld4(F0 + q * J * 4);
+            const Q4<T> f1 = ld4(F1 + q * J * 4);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) y[4 * q + e] += f0.v[e] * s0;
-        }
-        if (two) {
-#pragma unroll
-            for (int q = 0; q < NQT; ++q) {
-                const Q4<T> f1 = ld4(F1 + q * J * 4);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) y[4 * q + e] += f1.v[e] * s1;
+            for (int e = 0; e < 4; ++e) {
+                y[4 * q + e] += f0.v[e] * s0;
+                y[4 * q + e] += f1.v[e] * s1;
             }
         }
     }

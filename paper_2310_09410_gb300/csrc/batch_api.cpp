@@ -148,6 +148,7 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
                 if (h->h_mode[d]) t.modes |= 1 << mb;
             }
             for (int mb = per; mb < J; ++mb) tmem.push_back(-1);
+            t.f += t.f & 1;        // rows in pairs (the packed extra row is zero)
             tasks.push_back(t);
         }
     }
