@@ -676,7 +676,7 @@ def serve_config(args):
         "workload": f"serving: Poisson arrivals ({args.rate:.0f}/s, seed 5000) of solve requests, feeder mix "
                     f"13/34/123/8500 buses with weights {args.mix.replace(',', '/')} (topologies seeds "
                     f"5013/5034/5123/5850), request r with the load scenario of seed 6000+r; each request FP32 + "
-                    f"FP64 polish to eps_rel=1e-8 and pres<=1e-4; {args.requests} requests after "
+                    f"FP64 polish to eps_rel=1e-8 (8500 buses: 2e-9) and pres<=1e-4; {args.requests} requests after "
                     f"{args.warm_requests} warm-up requests; arrivals stop after the last request, then the "
                     f"server drains for at most {args.drain_s:.0f} s",
         "models": f"13/34/123-bus: continuous batching in the batched engine, passes of {args.chunk} FP32 iterations "
@@ -727,6 +727,8 @@ def run_serve(args, rank, world, local):
             hs.append(sv)
         solvers[k] = hs
         mid[k] = srv.add_model(hs, caps.get(k, 1))
+        if SINGLE_EPS_REL[k] != EPS_REL:
+            srv.set_model_tolerance(mid[k], SINGLE_EPS_REL[k], EPS_ABS)   # the large feeder's stopping rule
     rng = np.random.default_rng(SERVE_ARRIVAL_SEED)
     n_total = args.requests + args.warm_requests
     gaps = rng.exponential(1.0 / args.rate, size=n_total)

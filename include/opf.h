@@ -384,6 +384,12 @@ int opf_server_create(const opf_server_opts *o, opf_server **out);
 int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_handles, int32_t capacity,
                          int32_t *model_id);
 
+/* Stopping test of one model's requests (default: the server's eps_rel and
+ * eps_abs_pres), for requests admitted after the call; e.g. a tighter
+ * eps_rel for a feeder whose norms run over many more slots.  OPF_E_INVALID
+ * for an unknown model or a negative or NaN tolerance. */
+int opf_server_set_model_tolerance(opf_server *s, int32_t model, double eps_rel, double eps_abs_pres);
+
 /* Queues a request of model `model` with its loads (host arrays [n_load*3],
  * copied) and a caller tag that identifies it in opf_server_poll. */
 int opf_server_submit(opf_server *s, int32_t model, const double *load_p, const double *load_q, int64_t tag);

@@ -74,6 +74,7 @@ struct Model {
     opf_batch *b = nullptr;
     int cap = 0, G = 0, nload = 0;
     size_t slot_bytes = 0;
+    double eps_rel = 1e-8, eps_abs = 1e-4;   // stopping test of this model's requests
     std::vector<int> state;          // per slot: 0 free, 1 FP32 phase, 2 FP64 polish
     std::vector<int64_t> tag;
     std::vector<double> t_submit, t_admit;
@@ -159,7 +160,7 @@ void single_worker(opf_server *s, Model *m, Worker *w, Request req, double t_adm
     if (!rc) {
         opf_solve_opts so;
         memset(&so, 0, sizeof(so));
-        so.rho = o.rho; so.eps_rel = o.eps_rel; so.eps_abs_pres = o.eps_abs_pres; so.max_iter = o.max_iter;
+        so.rho = o.rho; so.eps_rel = m->eps_rel; so.eps_abs_pres = m->eps_abs; so.max_iter = o.max_iter;
         so.check_every = o.check_every; so.precision = OPF_PREC_MIXED; so.recenter_every = o.chunk_iters;
         // direct launches: the handle's stream may belong to an SM partition,
         // where the solve graph of opf_solve_ex cannot be instantiated
@@ -331,6 +332,8 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
     m->h = h;
     m->G = h->G;
     m->nload = h->model.n_load;
+    m->eps_rel = s->o.eps_rel;
+    m->eps_abs = s->o.eps_abs_pres;
     // batched when both engine plans fit the model
     const size_t per = batch_slot_bytes(h);
     int cap = capacity;
@@ -403,6 +406,19 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
     }
     *model_id = m->id;
     s->models.push_back(std::move(m));
+    return OPF_OK;
+}
+
+int opf_server_set_model_tolerance(opf_server *s, int32_t model, double eps_rel, double eps_abs_pres) {
+    if (!s || model < 0 || model >= (int)s->models.size() || !(eps_rel >= 0) || !(eps_abs_pres >= 0))
+        return OPF_E_INVALID;
+    Model &m = *s->models[model];
+    m.eps_rel = eps_rel;
+    m.eps_abs = eps_abs_pres;
+    if (m.b) {
+        m.b->init_eps_rel = eps_rel;
+        m.b->init_eps_abs = eps_abs_pres;
+    }
     return OPF_OK;
 }
 

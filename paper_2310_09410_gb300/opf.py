@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
     lib.opf_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(H)]
     lib.opf_server_add_model.argtypes = [H, _P, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
     lib.opf_server_submit.argtypes = [H, C.c_int32, _P, _P, C.c_int64]
+    lib.opf_server_set_model_tolerance.argtypes = [H, C.c_int32, C.c_double, C.c_double]
     lib.opf_server_step.argtypes = [H]
     lib.opf_server_poll.argtypes = [H, _P, _P, _P, _P, _P, C.c_int32]
     lib.opf_server_take_solution.argtypes = [H, C.c_int64, _P, C.c_int32]
@@ -472,6 +473,10 @@ class Server:
         self._solvers.extend(solvers)
         self._n_global[mid.value] = solvers[0].sizes()["n_global"]
         return mid.value
+
+    def set_model_tolerance(self, model, eps_rel, eps_abs_pres=1e-4):
+        _check(load().opf_server_set_model_tolerance(self._s, int(model), float(eps_rel), float(eps_abs_pres)),
+               "opf_server_set_model_tolerance")
 
     def submit(self, model, load_p, load_q, tag):
         lp = np.ascontiguousarray(load_p, np.float64)

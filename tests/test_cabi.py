@@ -111,4 +111,6 @@ def test_server_options_and_handles_checked_on_host(lib):
     assert list(st[:5]) == [0, 0, 0, 0, 0]
     assert lib.opf_server_poll(out, None, None, None, None, None, 16) == 0
     assert lib.opf_server_step(out) == opf.OPF_OK                        # nothing to do
+    lib.opf_server_set_model_tolerance.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double]
+    assert lib.opf_server_set_model_tolerance(out, 0, 1e-9, 1e-4) == opf.OPF_E_INVALID   # no model 0
     lib.opf_server_destroy(out)

@@ -121,6 +121,7 @@ def test_large_model_served_by_workers():
     handles = [solver(f), solver(f)]
     with opf.Server(max_iter=2000) as srv:
         m = srv.add_model(handles, capacity=64)
+        srv.set_model_tolerance(m, 2e-9, 1e-4)           # the large feeder's stopping rule
         assert srv.stats()["slots"] == 2                 # one request per handle
         for r in range(3):
             g = synth.load_scenario(f, 6500 + r)
