@@ -394,10 +394,18 @@ class Batch:
     def step(self, n_iters, rho=100.0):
         _check(load().opf_batch_step(self._b, float(rho), int(n_iters)), "opf_batch_step")
 
-    def solution(self, first=0, count=None):
+    def solution(self, first=0, count=None, out=None):
+        """x [count, n_global] and objectives [count]; out = (x, obj) writes into
+        caller arrays (e.g. views of pinned host memory) instead of new ones."""
         count = self.n - first if count is None else count
-        x = np.zeros((count, self.n_global))
-        obj = np.zeros(count)
+        if out is None:
+            x = np.zeros((count, self.n_global))
+            obj = np.zeros(count)
+        else:
+            x, obj = out
+            if (x.shape != (count, self.n_global) or obj.shape != (count,) or x.dtype != np.float64
+                    or obj.dtype != np.float64 or not x.flags.c_contiguous or not obj.flags.c_contiguous):
+                raise ValueError("out must be C-contiguous float64 arrays [count, n_global] and [count]")
         _check(load().opf_batch_get_solution(self._b, int(first), int(count), _ptr(x), _ptr(obj)),
                "opf_batch_get_solution")
         return x, obj
