@@ -132,3 +132,22 @@ def test_large_model_served_by_workers():
         assert np.isfinite(got[r]["objective"])
     for h in handles:
         h.close()
+
+
+def test_model_tolerance_applies_to_its_requests():
+    f13 = synth.preset_feeder("13", 5013)
+    scen = [synth.load_scenario(f13, 6600 + r) for r in range(3)]
+    iters = {}
+    for eps in (1e-8, 1e-5):
+        s13 = solver(f13)
+        with opf.Server() as srv:
+            m = srv.add_model([s13], capacity=8)
+            if eps != 1e-8:
+                srv.set_model_tolerance(m, eps, 1e-4)
+            for r, g in enumerate(scen):
+                srv.submit(m, g["load_a"], g["load_b"], tag=r)
+            got = drain(srv, list(range(len(scen))))
+        iters[eps] = [got[r]["iters"] for r in range(len(scen))]
+        assert all(got[r]["converged"] for r in range(len(scen)))
+        s13.close()
+    assert all(a < b for a, b in zip(iters[1e-5], iters[1e-8])), iters
