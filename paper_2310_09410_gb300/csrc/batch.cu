@@ -638,35 +638,33 @@ __global__ void k_bref_globals(int n_inst, int G, int L, int K, int kshift, int 
 
 // Per (subsystem, instance), one warp: bbar~ = M (x_ref[g] + lambda_ref / rho)
 // + bbar - x_ref[g], d = x_s - x_ref[g], mu = 0, lambda_ref, in the engine layout.
+// One subsystem of one instance by `nl` lanes starting at lane `l0` of the
+// warp (v and t staged in v[], tt[]): the two FP64 products of the shifted
+// bbar, written in the engine layout.
 template <typename T>
-__global__ void __launch_bounds__(128) k_bref_slots(int S, int n_inst, int G, int L, int K, int kshift, int NCH,
-                                                    const int *ipos, const int4 *sub, const int4 *sub2,
-                                                    const double *F64, const int *gk, const int *sch,
-                                                    double rho, const double *xref, const double *xsv,
-                                                    const double *lam, const double *bbar,
-                                                    const DevStatus *st, T *bt, T *ds, T *mu, T *lref) {
-    __shared__ double buf[4][2][OPF_MAX_NS];
-    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long task = (long long)blockIdx.x * 4 + wl;
-    if (task >= (long long)S * n_inst) return;
-    const int in = (int)(task / S), d = (int)(task % S);
-    if (st[in].done || ipos[in] < 0) return;
-    const int4 h = sub[d], q2 = sub2[d];
+__device__ __forceinline__ void bref_one(int in, bool valid, int d, int l0, int nl, int lane, const int4 h,
+                                         const int4 q2, const double *F64, const int *ipos, const int *gk,
+                                         const int *sch, double rho, const double *xref, const double *xsv,
+                                         const double *lam, const double *bbar, int G, int L, int K, int kshift,
+                                         int NCH, double *v, double *tt, T *bt, T *ds, T *mu, T *lref) {
     const int so = h.x, n = h.y, f = h.z, mode = h.w, npad = q2.y;
     const double *Fs = F64 + q2.x;
+    const int ll = lane - l0;
     const double *xr = xref + (size_t)in * G;
     const double *xi = xsv + (size_t)in * L, *li = lam + (size_t)in * L, *bi = bbar + (size_t)in * L;
-    double *v = buf[wl][0], *tt = buf[wl][1];
-    for (int r = lane; r < n; r += 32) v[r] = xr[gk[so + r]] + li[so + r] / rho;
+    if (valid)
+        for (int r = ll; r < n; r += nl) v[r] = xr[gk[so + r]] + li[so + r] / rho;
     __syncwarp();
-    for (int cc = lane; cc < f; cc += 32) {
-        double acc = 0.0;
-        for (int r = 0; r < n; ++r) acc += Fs[(long long)cc * npad + r] * v[r];
-        tt[cc] = acc;
-    }
+    if (valid)
+        for (int cc = ll; cc < f; cc += nl) {
+            double acc = 0.0;
+            for (int r = 0; r < n; ++r) acc += Fs[(long long)cc * npad + r] * v[r];
+            tt[cc] = acc;
+        }
     __syncwarp();
+    if (!valid) return;
     const int pos = ipos[in], cta = pos >> kshift, sc = pos & (K - 1);
-    for (int r = lane; r < n; r += 32) {
+    for (int r = ll; r < n; r += nl) {
         double yv = 0.0;
         for (int cc = 0; cc < f; ++cc) yv += Fs[(long long)cc * npad + r] * tt[cc];
         const double mv = mode ? yv : v[r] - yv;
@@ -679,6 +677,43 @@ __global__ void __launch_bounds__(128) k_bref_slots(int S, int n_inst, int G, in
         ds[e] = (T)(xi[k] - xg);
         mu[e] = T(0);
         lref[e] = (T)li[k];
+    }
+}
+
+// Per (subsystem, pair of instances), running instances only: bbar~ =
+// M (x_ref[g] + lambda_ref / rho) + bbar - x_ref[g], d = x_s - x_ref[g],
+// mu = 0, lambda_ref, in the engine layout.  A subsystem with at most 16
+// slots and 16 factor columns takes a half-warp per instance (the FP64 pipe
+// issues a warp instruction at the same cost however many lanes are active),
+// a larger one the whole warp for each instance in turn.
+template <typename T>
+__global__ void __launch_bounds__(128) k_bref_slots(int S, int n_inst, int G, int L, int K, int kshift, int NCH,
+                                                    const int *ipos, const int4 *sub, const int4 *sub2,
+                                                    const double *F64, const int *gk, const int *sch,
+                                                    double rho, const double *xref, const double *xsv,
+                                                    const double *lam, const double *bbar,
+                                                    const DevStatus *st, T *bt, T *ds, T *mu, T *lref) {
+    __shared__ double buf[4][2][OPF_MAX_NS];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long task = (long long)blockIdx.x * 4 + wl;
+    const int npair = (n_inst + 1) / 2;
+    if (task >= (long long)S * npair) return;
+    const int pair = (int)(task / S), d = (int)(task % S);
+    const int4 h = sub[d], q2 = sub2[d];
+    if (h.y <= 16 && h.z <= 16) {
+        const int half = lane >> 4, in = 2 * pair + half;
+        const bool valid = in < n_inst && !st[in].done && ipos[in] >= 0;
+        bref_one<T>(in, valid, d, half * 16, 16, lane, h, q2, F64, ipos, gk, sch, rho, xref, xsv, lam, bbar, G, L,
+                    K, kshift, NCH, buf[wl][0] + half * 128, buf[wl][1] + half * 128, bt, ds, mu, lref);
+    } else {
+        for (int q = 0; q < 2; ++q) {
+            const int in = 2 * pair + q;
+            if (in >= n_inst) break;
+            const bool valid = !st[in].done && ipos[in] >= 0;
+            bref_one<T>(in, valid, d, 0, 32, lane, h, q2, F64, ipos, gk, sch, rho, xref, xsv, lam, bbar, G, L, K,
+                        kshift, NCH, buf[wl][0], buf[wl][1], bt, ds, mu, lref);
+            __syncwarp();
+        }
     }
 }
 
@@ -876,7 +911,7 @@ void launch_bref(int n_inst, int S, int G, int L, int K, int kshift, int NCH, in
     k_bref_globals<T><<<bl((long long)n_inst * G, 256), 256, 0, s>>>(n_inst, G, L, K, kshift, NB, ipos, gseg, uslot,
                                                                     bidx, c64, lb, ub, rho, xsv, lam, st, xref,
                                                                     ct, xrf, lbt, ubt);
-    const long long warps = (long long)S * n_inst;
+    const long long warps = (long long)S * ((n_inst + 1) / 2);
     k_bref_slots<T><<<(int)((warps + 3) / 4), 128, 0, s>>>(S, n_inst, G, L, K, kshift, NCH, ipos, sub, sub2, F64,
                                                            gk, sch, rho, xref, xsv, lam, bbar, st, bt, ds, mu, lref);
 }
