@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(512, 1)
         if (check && lane < K)
 #pragma unroll
             for (int q = 0; q < 6; ++q) redw[lane * 6 + q] = 0.0;
-        if (tid == 0) *tnext = 0;
+        if (tid == 0) *tnext = n_warps;
         // ---- G: global update (Eq. closed_1).  An item is one global and KQ of
         // its columns: sum of u over the copies, shift, scale, clip, and x
         // stored into every copy's slot; GB items per thread with c~ in flight
@@ -450,17 +450,13 @@ __global__ void __launch_bounds__(512, 1)
         // tasks in decreasing cost; warps take the next one as they finish
         // (test iterations: task t on warp t % n_warps, a fixed summation order)
         {
+            // each warp's first task is its own (the counter starts at
+            // n_warps); the next task's index is claimed at the start of a
+            // task and read at its end, so the atomic's latency is hidden
             int t = w;
-            if (!check) {
-                if (lane == 0) t = atomicAdd(tnext, 1);
-                t = __shfl_sync(0xffffffffu, t, 0);
-            }
             while (t < a.n_tasks) {
-                int tn = t + n_warps;
-                if (!check) {
-                    if (lane == 0) tn = atomicAdd(tnext, 1);
-                    tn = __shfl_sync(0xffffffffu, tn, 0);
-                }
+                int claim = 0;
+                if (!check && lane == 0) claim = atomicAdd(tnext, 1);
                 const BatchTask tk = tks[t];
                 switch (tk.nq) {
                     case 1: batch_task<T, K, 1>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
@@ -475,7 +471,7 @@ __global__ void __launch_bounds__(512, 1)
                                                                         a.chg, jpos, sc, rho, inv_rho, check, act,
                                                                         wds, redw); break;
                 }
-                t = tn;
+                t = check ? t + n_warps : __shfl_sync(0xffffffffu, claim, 0);
             }
         }
         if (check) {
