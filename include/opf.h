@@ -212,6 +212,8 @@ int opf_get_residuals(opf_handle *h, double *pres, double *dres, double *eps_pri
 int opf_get_locals(opf_handle *h, double *xs, double *lam, size_t L);
 int opf_set_locals(opf_handle *h, const double *xs, const double *lam, size_t L);
 
+/* Sizes of the handle's model (opf_sizes above; sum_nf after opf_precompute).
+ * OPF_E_INVALID for a NULL handle or output. */
 int opf_get_sizes(opf_handle *h, opf_sizes *out);
 
 /* New load values for a feeder handle (host arrays [n_load*3] like
@@ -429,9 +431,14 @@ void opf_server_destroy(opf_server *s);
  * OPF_E_CUDA if the driver offers no green contexts. */
 int opf_stream_create_partition(int32_t device, int32_t n_sm, int32_t priority, void **stream,
                                 int32_t *sm_count);
+/* Destroys a stream made by opf_stream_create_partition and its green
+ * context; OPF_E_INVALID for any other stream. */
 int opf_stream_destroy_partition(void *stream);
 
+/* Frees the handle and all its device memory (NULL is a no-op); destroy its
+ * batches and any server using it first. */
 void opf_destroy(opf_handle *h);
+/* Static name of a status code. */
 const char *opf_strerror(int code);
 /* Message of the last OPF_E_INVALID / OPF_E_CUDA on this thread. */
 const char *opf_last_error(void);
