@@ -133,6 +133,25 @@ def test_generic_iterates_match_oracle(seed, kw):
     assert rel_err(x, ref.x) <= TOL_ITER
 
 
+@pytest.mark.parametrize("seed,kw,ctas", [(1, {}, 2), (4, {"max_n": 40, "n_global": 120}, 3),
+                                          (11, {"p_free": 0.3}, 5)])
+def test_generic_persistent_engine_matches_oracle(seed, kw, ctas):
+    """Rank-deficient blocks, free variables and wide blocks on the
+    persistent grid engine (a few CTAs, so globals span CTAs)."""
+    g, M = generic_model(seed, **kw)
+    rho = 3.0
+    ref = oracle_iterates(M, 100, rho=rho)
+    with opf.Solver.from_generic(g["c"], g["lb"], g["ub"], g["subs"]) as s:
+        s.precompute()
+        s.solve(rho=rho, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64,
+                engine=opf.ENGINE_PERSISTENT, cluster=ctas)
+        xs, lam = s.locals()
+        x, _ = s.solution()
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
+
+
 def largest_subsystem_instance(seed=17, n=300):
     """A consensus instance whose first subsystem has OPF_MAX_NS = 256 slots
     (rank 120), the others small and overlapping it."""
