@@ -516,8 +516,8 @@ def run_batch(args, rank, world, local):
             "launches_timed": passes,
             "engine_ms": th["engine_ms"],
             "peak_source": "FP32 FMA lanes x 2 flops x max SM clock (152 x 128 x 2 x 2070 MHz)",
-            "note": "instance iterations include the FP64 polish (%d pass(es), under 1%% of them)"
-                    % th["fp64_passes"]}
+            "note": "instance iterations include those of the FP64 polish (%d pass(es), about 1%% of them), "
+                    "so achieved is over-stated by about that much" % th["fp64_passes"]}
 
     plain = None if args.no_plain_fp64 else plain_fp64_reference(opf, f, local, stream)
     if rank == 0:
