@@ -364,13 +364,22 @@ def max_over_ranks(value: float, world: int, device) -> float:
     return float(t.item())
 
 
-def count_launches_single(stats, precision, k=50, R=1000, persistent=False, per_launch=20000):
+def warp_engine_fp64(sizes):
+    """The library's automatic choice runs FP64 iterations on the warp engine
+    for instances of at most 64 subsystems of at most 64 slots."""
+    return sizes["n_sub"] <= 64 and sizes["max_ns"] <= 64
+
+
+def count_launches_single(stats, precision, k=50, R=1000, persistent=False, warp64=False, per_launch=20000):
     """Kernels of ours per single-instance step: precompute (3) + solve + objective read (1).
-    FP64 iterations: whole-grid kernels (k + 1 per chunk of k) or, for large
-    instances, the persistent engine (one launch per 20000 iterations)."""
+    FP64 iterations: whole-grid kernels (k + 1 per chunk of k), the warp
+    engine (one launch) for small instances or, for large instances, the
+    persistent engine (one launch per 20000 iterations)."""
     n = 3 + 1
 
     def fp64(iters):
+        if warp64:
+            return 1 + 1
         return 1 + (-(-iters // per_launch) if persistent else (iters // k) * (k + 1))
     if precision == "fp64":
         return n + fp64(stats["main_iters"])
@@ -596,7 +605,8 @@ def run_single(args, rank, world, local):
         iter_ms.append(st["iterate_ms"])
         it_main += st["main_iters"]
         it_pol += st["polish_iters"]
-        launches += count_launches_single(st, args.precision, persistent=solver.sizes()["n_slots"] > 4096)
+        launches += count_launches_single(st, args.precision, persistent=sizes["n_slots"] > 4096,
+                                          warp64=warp_engine_fp64(sizes))
         if not ok:
             raise SystemExit("a timed solve did not converge")
     torch.cuda.synchronize()
@@ -629,13 +639,16 @@ def run_single(args, rank, world, local):
     mixed = args.precision == "mixed"
     big = sizes["n_slots"] > 4096
     if mixed and not big:
-        kern, traffic = ("k_warp_engine (FP32 iterations; one warp per subsystem, factors in registers, "
+        kern, traffic = ("k_warp_engine<float> (FP32 iterations; one warp per subsystem, factors in registers, "
                          "instance resident in one thread-block cluster)"), WARP_ENGINE_TRAFFIC_PER_LAUNCH
     elif big:
         kern = ("k_persist_engine<%s> (%s iterations; cooperative launch over two CTAs per SM, instance "
                 "resident in their shared memory, one grid barrier per iteration)"
                 % (("float", "FP32") if mixed else ("double", "FP64")))
         traffic = PERSIST_ENGINE_TRAFFIC_PER_LAUNCH if mixed else None
+    elif warp_engine_fp64(sizes):
+        kern, traffic = ("k_warp_engine<double> (FP64 iterations; one warp per subsystem, factors in shared "
+                         "memory, instance resident in one thread-block cluster)"), None
     else:
         kern, traffic = "k_tile_iter<double> (FP64 iterations, one CTA per tile)", None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

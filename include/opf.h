@@ -121,7 +121,10 @@ typedef struct opf_solve_opts {
     int32_t precision;              /* OPF_PREC_* */
     int32_t recenter_every;         /* OPF_PREC_MIXED: iterations between FP64 re-centrings (0 = default) */
     int32_t engine;                 /* 0 = automatic, 1 = whole-grid kernels, 2 = cluster resident,
-                                       3 = warp per subsystem (FP32, at most 192 subsystems),
+                                       3 = warp per subsystem (one cluster of at most 16 CTAs: at
+                                           most 192 subsystems of at most 64 slots; FP32 factors
+                                           of at most 32 slots in registers, FP64 factors in
+                                           shared memory),
                                        4 = persistent grid (cooperative launch, instance resident in
                                        the shared memory of all CTAs, one grid barrier per iteration) */
     int32_t flags;                  /* OPF_SOLVE_* bits */
@@ -186,7 +189,8 @@ int opf_solve(opf_handle *h, double rho, double eps, int32_t max_iter);
  * choice: FP32 / mixed iterations on the warp engine, else the cluster
  * engine, else the persistent grid engine, else whole-grid kernels; FP64
  * iterations (and the polish) on the persistent grid engine for instances
- * of more than 4096 slots, else whole-grid kernels.  The persistent engine's grid
+ * of more than 4096 slots, else on the warp engine when the instance fits it
+ * with at most 4 warps per CTA (at most 64 subsystems), else whole-grid kernels.  The persistent engine's grid
  * barrier waits at most 1 s; past that the solve returns OPF_E_TIMEOUT. */
 int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts);
 

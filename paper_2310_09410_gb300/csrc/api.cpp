@@ -54,11 +54,12 @@ template <typename T>
 int launch_persist_engine(const IterArgs<T> &g, const PersistLayout &lay, const PersistPtrs &pp, T *U,
                           int bar_extra, int n_iters, int check_every, DevStatus *st, double rho,
                           cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
-int prepare_warp_engine(unsigned bytes);
-int launch_warp_engine(const IterArgs<float> &g, const WarpLayout &lay, const int *pr, float *u_glob, int n_iters,
+template <typename T> int prepare_warp_engine(unsigned bytes);
+template <typename T>
+int launch_warp_engine(const IterArgs<T> &g, const WarpLayout &lay, const int *pr, T *u_glob, int n_iters,
                        int check_every, DevStatus *st, double rho, cudaGraphConditionalHandle cond, int use_cond,
                        cudaStream_t s);
-int warp_engine_occupancy(const WarpLayout &lay);
+template <typename T> int warp_engine_occupancy(const WarpLayout &lay);
 template <typename T>
 void launch_make_u(int L, const int *pk, const T *ds, const T *mu, T rho, T *u, const DevStatus *st,
                    cudaStream_t s);
@@ -503,6 +504,7 @@ extern "C" int opf_precompute(opf_handle *h) {
     h->p32.P = h->p64.P = 0;
     h->p32.ok = h->p64.ok = h->p32.tried = h->p64.tried = false;
     h->w32.built = h->w32.ok = false;
+    h->w64.built = h->w64.ok = false;
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->g64.reset();
     h->gmix.reset();
@@ -846,16 +848,36 @@ static IterArgs<T> with_persist(IterArgs<T> a, const PersistPlan &pp) {
 }
 
 constexpr int kWarpEngineWarps = 12;
+// FP64 warp engine: warps per CTA when the cluster has room (the FP64 pipe of
+// an SM sub-partition is shared by its warps, so fewer per CTA spread the work)
+constexpr int kWarpEngineWarps64 = 4;
 
-static int build_warp_plan(opf_handle *h) {
-    WarpPlan &wp = h->w32;
+// Warp-engine plan for precision T.  FP32: ceil(S / 12) CTAs of 12 warps,
+// factors of subsystems with n > 32 in shared memory (the rest in registers).
+// FP64: up to 16 CTAs of at least 4 warps, every factor in shared memory.
+template <typename T>
+static int build_warp_plan(opf_handle *h, WarpPlan &wp) {
+    constexpr bool REG = sizeof(T) == 4;
     wp.built = true;
     wp.ok = false;
     const int S = h->S, G = h->G, L = h->L;
-    const int P = (S + kWarpEngineWarps - 1) / kWarpEngineWarps;
+    int P = (S + kWarpEngineWarps - 1) / kWarpEngineWarps;
     if (P < 1 || P > 16 || h->max_ns > 64) return OPF_OK;
     for (int s = 0; s < S; ++s)
         if (h->h_sf[s] > 32) return OPF_OK;
+    if (!REG) P = std::max(P, std::min(16, (S + kWarpEngineWarps64 - 1) / kWarpEngineWarps64));
+    const int warps = (S + P - 1) / P;
+    if (!REG && !wp.d_pr) {
+        TRY(dalloc(h, &wp.d_pr, 8 * 17));
+        TRY(dalloc(h, &wp.d_wrseg, h->L));
+        TRY(dalloc(h, &wp.d_wdsp, h->L));
+        TRY(dalloc(h, &wp.d_wdd, (size_t)h->L * 16));
+        TRY(dalloc(h, &wp.d_wrep, h->L));
+        TRY(dalloc(h, &wp.d_klb, h->S + 1));
+        TRY(dalloc(h, &wp.d_fbig, h->S + 1));
+        TRY(dalloc(h, &wp.d_F2d, h->nF));
+    }
+    auto in_smem = [&](int s) { return !REG || h->h_sn[s] > 32; };
     wp.P = P;
     // local slots (subsystem s lives in CTA s % P, warp s / P)
     std::vector<int> nk(P, 0), klb(S + 1, 0), fb(P, 0), fbig(S + 1, 0);
@@ -863,20 +885,25 @@ static int build_warp_plan(opf_handle *h) {
         const int p = s % P;
         klb[s] = nk[p];
         nk[p] += h->h_sn[s];
-        if (h->h_sn[s] > 32) fb[p] += h->h_sf[s] * h->h_npad[s];
+        if (in_smem(s)) fb[p] += h->h_sf[s] * h->h_npad[s];
     }
     std::vector<int> kb(P + 1, 0), fb0(P + 1, 0);
     for (int p = 0; p < P; ++p) { kb[p + 1] = kb[p] + nk[p]; fb0[p + 1] = fb0[p] + fb[p]; }
     {
         std::vector<int> fill(fb0.begin(), fb0.end() - 1);
         for (int s = 0; s < S; ++s)
-            if (h->h_sn[s] > 32) {
+            if (in_smem(s)) {
                 const int p = s % P;
                 fbig[s] = fill[p];
                 const size_t cnt = (size_t)h->h_sf[s] * h->h_npad[s];
-                if (cnt)
-                    CUDA_TRY(cudaMemcpyAsync(wp.d_F2 + fill[p], h->d_F32 + h->h_foff[s], cnt * sizeof(float),
-                                             cudaMemcpyDeviceToDevice, h->stream));
+                if (cnt) {
+                    if (REG)
+                        CUDA_TRY(cudaMemcpyAsync(wp.d_F2 + fill[p], h->d_F32 + h->h_foff[s], cnt * sizeof(float),
+                                                 cudaMemcpyDeviceToDevice, h->stream));
+                    else
+                        CUDA_TRY(cudaMemcpyAsync(wp.d_F2d + fill[p], h->d_F64 + h->h_foff[s], cnt * sizeof(double),
+                                                 cudaMemcpyDeviceToDevice, h->stream));
+                }
                 fill[p] += (int)cnt;
             }
     }
@@ -944,22 +971,22 @@ static int build_warp_plan(opf_handle *h) {
     }
     WarpLayout &c = wp.lay;
     c = WarpLayout{};
-    c.P = P; c.L = L; c.S = S;
+    c.P = P; c.L = L; c.S = S; c.warps = warps;
     c.useg_len = (mru + 3) & ~3;
     c.fbig_len = (mf + 3) & ~3;
     size_t off = 0;
     auto take = [&](unsigned *o, size_t bytes) { *o = (unsigned)off; off = align16u(off + bytes); };
-    take(&c.off_useg, (size_t)2 * c.useg_len * sizeof(float));
+    take(&c.off_useg, (size_t)2 * c.useg_len * sizeof(T));
     take(&c.off_dd, (size_t)mdd * sizeof(int));
-    take(&c.off_fbig, (size_t)2 * c.fbig_len * sizeof(float));   // column-major factors, then row-major copies
-    take(&c.off_vbig, (size_t)kWarpEngineWarps * 64 * sizeof(float));
+    take(&c.off_fbig, (size_t)2 * c.fbig_len * sizeof(T));   // column-major factors, then row-major copies
+    take(&c.off_vbig, (size_t)warps * 64 * sizeof(T));
     take(&c.off_red, 16 * 6 * sizeof(double) + 16);
     c.bytes = (unsigned)off;
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if ((long long)c.bytes + 4096 > optin) return OPF_OK;
-    if (prepare_warp_engine(c.bytes)) { cudaGetLastError(); return OPF_OK; }
-    if (warp_engine_occupancy(c) < 1) { cudaGetLastError(); return OPF_OK; }
+    if (prepare_warp_engine<T>(c.bytes)) { cudaGetLastError(); return OPF_OK; }
+    if (warp_engine_occupancy<T>(c) < 1) { cudaGetLastError(); return OPF_OK; }
     if ((size_t)wdd.size() > (size_t)h->L * 16 || wrep.size() > (size_t)h->L) return OPF_OK;
     CUDA_TRY(cudaMemcpyAsync(wp.d_pr, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(cudaMemcpyAsync(wp.d_klb, klb.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -979,6 +1006,13 @@ static IterArgs<float> with_warp_plan(opf_handle *h, IterArgs<float> a, const Wa
     a.klb = wp.d_klb; a.fbig = wp.d_fbig; a.F2 = wp.d_F2;
     a.wrseg = wp.d_wrseg; a.wdsp = wp.d_wdsp; a.wdd = wp.d_wdd; a.wrep = wp.d_wrep;
     a.u_prev_out = h->d_u32 + h->L;
+    return a;
+}
+
+static IterArgs<double> with_warp_plan(opf_handle *h, IterArgs<double> a, const WarpPlan &wp) {
+    a.klb = wp.d_klb; a.fbig = wp.d_fbig; a.F2 = wp.d_F2d;
+    a.wrseg = wp.d_wrseg; a.wdsp = wp.d_wdsp; a.wdd = wp.d_wdd; a.wrep = wp.d_wrep;
+    a.u_prev_out = h->d_u64 + h->L;
     return a;
 }
 
@@ -1175,10 +1209,29 @@ static int run_persist64(opf_handle *h, const opf_solve_opts &o) {
     return OPF_OK;
 }
 
-// FP64 iterations on the engine chosen for the handle: persistent grid when
-// its plan is usable (and not excluded), else whole-grid kernels.
-static int run_fp64(opf_handle *h, const opf_solve_opts &o, bool persistent) {
-    if (persistent && h->p64.ok) return run_persist64(h, o);
+// FP64 iterations by the warp engine (the instance in one cluster, factors in
+// shared memory), one launch up to max_iter.
+static int run_warp64(opf_handle *h, const opf_solve_opts &o) {
+    const double rho = o.rho;
+    TRY(set_recip(h, rho));
+    launch_make_u<double>(h->L, h->d_pk, h->d_ds64, h->d_mu64, rho, h->d_u64, nullptr, h->stream);
+    IterArgs<double> a = with_warp_plan(h, iter_args<double>(h, rho), h->w64);
+    if (launch_warp_engine<double>(a, h->w64.lay, h->w64.d_pr, h->d_u64, o.max_iter, o.check_every, h->d_st, rho,
+                                   cudaGraphConditionalHandle{}, 0, h->stream)) {
+        g_last_error = std::string("warp engine launch failed: ") + cudaGetErrorString(cudaGetLastError());
+        return OPF_E_CUDA;
+    }
+    CUDA_TRY(cudaGetLastError());
+    TRY(read_status(h));
+    h->have_prev_u = h->h_st->iter > 0;
+    return OPF_OK;
+}
+
+// FP64 iterations on the engine chosen for the solve: 4 persistent grid,
+// 3 warp engine, else whole-grid kernels.
+static int run_fp64(opf_handle *h, const opf_solve_opts &o, int e64) {
+    if (e64 == 4 && h->p64.ok) return run_persist64(h, o);
+    if (e64 == 3 && h->w64.ok) return run_warp64(h, o);
     return run_grid64(h, o);
 }
 
@@ -1216,7 +1269,7 @@ static int run_mixed(opf_handle *h, const opf_solve_opts &o, int eng, bool recen
                 launch_rc |= launch_persist_engine<float>(a, pp.lay, pp.ptrs(), h->d_u32, bar_extra(o), R, k,
                                                           h->d_st, rho, c, use, h->stream);
             } else if (eng == 3) {
-                launch_warp_engine(a, h->w32.lay, h->w32.d_pr, h->d_u32, R, k, h->d_st, rho, c, use, h->stream);
+                launch_warp_engine<float>(a, h->w32.lay, h->w32.d_pr, h->d_u32, R, k, h->d_st, rho, c, use, h->stream);
             } else if (eng == 2) {
                 launch_cluster_engine<float>(a, h->c32.lay, h->c32.d_pr, h->d_u32, R, k, h->d_st, rho, c, use,
                                              h->stream);
@@ -1301,20 +1354,29 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
         if (!h->p64.ok && o.engine == 4 && o.cluster > 0) TRY(get_persist_plan<double>(h, &h->p64, 0));
         p64 = h->p64.ok;
     }
+    // else on the warp engine when the instance fits one cluster of it with at
+    // most 4 warps per CTA (automatic choice; with more, the warps of an SM
+    // queue on its FP64 pipe and whole-grid kernels are faster)
+    bool w64 = false;
+    if (!p64 && o.precision != OPF_PREC_FP32 && (o.engine == 0 || o.engine == 3)) {
+        if (!h->w64.built) TRY(build_warp_plan<double>(h, h->w64));
+        w64 = h->w64.ok && (o.engine == 3 || h->w64.lay.warps <= kWarpEngineWarps64);
+    }
+    const int e64 = p64 ? 4 : w64 ? 3 : 1;
     if (o.precision == OPF_PREC_FP64) {
         bool cl = false;
         if (o.engine == 2) {
             TRY(get_cluster_plan<double>(h, &h->c64, o.cluster, 96));
             cl = h->c64.ok;
         }
-        if (o.engine == 3) { g_last_error = "the warp engine runs FP32 iterations only"; return OPF_E_INVALID; }
+        if (o.engine == 3 && !w64) { g_last_error = "instance does not fit the warp engine in FP64"; return OPF_E_CAPACITY; }
         if (o.engine == 2 && !cl) { g_last_error = "instance does not fit one cluster in FP64"; return OPF_E_CAPACITY; }
         if (o.engine == 4 && !p64) {
             g_last_error = "instance does not fit the persistent grid engine in FP64";
             return OPF_E_CAPACITY;
         }
         if (cl) TRY(run_cluster64(h, o));
-        else TRY(run_fp64(h, o, p64));
+        else TRY(run_fp64(h, o, e64));
         h->main_iters = h->h_st->iter;
         h->recenters = 0;
         CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
@@ -1322,7 +1384,7 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
     } else {
         int eng = 1;
         if (o.engine == 0 || o.engine == 3) {
-            if (!h->w32.built) TRY(build_warp_plan(h));
+            if (!h->w32.built) TRY(build_warp_plan<float>(h, h->w32));
             if (h->w32.ok) eng = 3;
         }
         if (eng == 1 && (o.engine == 0 || o.engine == 2)) {
@@ -1361,7 +1423,7 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
             st.max_iter = std::max<long long>(o.max_iter, it + o.check_every);
             *h->h_st = st;
             CUDA_TRY(cudaMemcpyAsync(h->d_st, h->h_st, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
-            TRY(run_fp64(h, o, p64));
+            TRY(run_fp64(h, o, e64));
         }
         CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
     }

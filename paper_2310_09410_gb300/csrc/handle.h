@@ -56,7 +56,7 @@ struct PersistPlan {
     PersistPtrs ptrs() const { return PersistPtrs{d_pr, d_part, d_sync}; }
 };
 
-// Warp-engine plan (FP32): subsystem s -> CTA s % P, warp s / P.
+// Warp-engine plan for one precision: subsystem s -> CTA s % P, warp s / P.
 struct WarpPlan {
     int P = 0;
     bool built = false, ok = false;
@@ -64,7 +64,8 @@ struct WarpPlan {
     int *d_pr = nullptr, *d_klb = nullptr, *d_fbig = nullptr;
     int *d_wrseg = nullptr, *d_wdsp = nullptr, *d_wdd = nullptr;
     int3 *d_wrep = nullptr;
-    float *d_F2 = nullptr;
+    float *d_F2 = nullptr;     // FP32 plan: factors of the subsystems with n > 32
+    double *d_F2d = nullptr;   // FP64 plan: every factor
 };
 
 // Grid tiling for one precision: tile t covers subsystems [s0[t], s0[t+1]).
@@ -122,7 +123,7 @@ struct opf_handle {
     ClusterPlan c32, c64;
     PersistPlan p32, p64;
     bool persist_graph_failed = false;   // the cooperative launch could not be captured in a graph
-    WarpPlan w32;
+    WarpPlan w32, w64;
     std::vector<int> h_tpre, h_vpre, h_foff, h_npad, h_pk, h_gk, h_gstart, h_uslot;
     std::vector<int> h_boff;                 // device subsystem -> first row (device row order)
     std::vector<int> dev_to_canon_sub;       // device subsystem -> canonical subsystem

@@ -758,13 +758,16 @@ __global__ void __launch_bounds__(1024) k_cluster_engine(IterArgs<T> g, ClusterL
 }
 
 // ============================================================ warp engine
-// FP32 persistent engine for instances of at most 16 x 12 subsystems: a
-// cluster of P CTAs, one warp per subsystem for the whole solve (subsystem
-// s = warp * P + rank, so every CTA gets a mix of sizes); lane l owns local
-// rows l and l + 32.  A subsystem with n <= 32 keeps its factor F in
-// registers (lane c: column c for t = F^T v; lane r: row r for y = F t), so
-// both mat-vecs are chains of warp shuffles and FMAs; a larger one (n <= 64)
-// reads F from shared memory.  For one iteration:
+// Persistent engine for instances of at most 16 x 12 subsystems: a cluster of
+// P CTAs, one warp per subsystem for the whole solve (subsystem s = warp * P +
+// rank, so every CTA gets a mix of sizes); lane l owns local rows l and l + 32.
+// In FP32 a subsystem with n <= 32 keeps its factor F in registers (lane c:
+// column c for t = F^T v; lane r: row r for y = F t), so both mat-vecs are
+// chains of warp shuffles and FMAs; a larger one (n <= 64) reads F from shared
+// memory.  In FP64 every factor is read from shared memory (two copies,
+// column- and row-major), and t = F^T v splits the rows over the two half-warps
+// when f <= 16: a warp FP64 instruction costs the same whatever its active
+// lanes, so the dependent chain is what sets the time.  For one iteration:
 //   x = clip((sum of u over the global's copies - c~) / (rho N), lb~, ub~)   (Eq. closed_1)
 //   v = x + mu / rho;  t = F^T v;  y = F t
 //   x_s = (v - y or y) + bbar~  (Eq. closed_2),  mu += rho (x - x_s) (Eq. ADMM-3)
@@ -782,9 +785,14 @@ __device__ __forceinline__ void we_barrier(cg::cluster_group &cl, int P) {
     else cl.sync();
 }
 
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename T>
 __global__ void __launch_bounds__(32 * WE_WARPS, 1)
-k_warp_engine(IterArgs<float> g, WarpLayout lay, const int *pr, float *u_glob, int n_iters, int check_every,
+k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_iters, int check_every,
               DevStatus *st, double rho_d, cudaGraphConditionalHandle cond, int use_cond) {
+    constexpr bool REG = sizeof(T) == 4;   // register-resident factors (FP32 only)
     extern __shared__ __align__(16) unsigned char sm[];
     cg::cluster_group cl = cg::this_cluster();
     const int P = lay.P, P1 = P + 1;
@@ -794,56 +802,59 @@ k_warp_engine(IterArgs<float> g, WarpLayout lay, const int *pr, float *u_glob, i
         return;
     }
     const int kb = pr[PR_K * P1 + rank];                                              // local slots
-    const int fb0 = pr[PR_F * P1 + rank], nfb = pr[PR_F * P1 + rank + 1] - fb0;       // big factors
+    const int fb0 = pr[PR_F * P1 + rank], nfb = pr[PR_F * P1 + rank + 1] - fb0;       // shared-memory factors
     const int db0 = pr[PR_J * P1 + rank], ndb = pr[PR_J * P1 + rank + 1] - db0;       // u destinations
     const int rb0 = pr[PR_V * P1 + rank], nrb = pr[PR_V * P1 + rank + 1] - rb0;       // replica segments
-    float *ubuf[2] = {reinterpret_cast<float *>(sm + lay.off_useg),
-                      reinterpret_cast<float *>(sm + lay.off_useg) + lay.useg_len};   // read t % 2, write the other
+    T *ubuf[2] = {reinterpret_cast<T *>(sm + lay.off_useg),
+                  reinterpret_cast<T *>(sm + lay.off_useg) + lay.useg_len};           // read t % 2, write the other
     int *dd = reinterpret_cast<int *>(sm + lay.off_dd);
-    float *Fbig = reinterpret_cast<float *>(sm + lay.off_fbig);
-    float *vbig = reinterpret_cast<float *>(sm + lay.off_vbig);    // 64 floats per warp
+    T *Fbig = reinterpret_cast<T *>(sm + lay.off_fbig);
+    T *vbig = reinterpret_cast<T *>(sm + lay.off_vbig);    // 64 entries per warp
     double *red = reinterpret_cast<double *>(sm + lay.off_red);
     int *stop = reinterpret_cast<int *>(sm + lay.off_red + 16 * 6 * sizeof(double));
-    copy_in<float>(dd, g.wdd + db0, (size_t)ndb * sizeof(int));
-    copy_in<float>(Fbig, g.F2 + fb0, (size_t)nfb * sizeof(float));
+    copy_in<T>(dd, g.wdd + db0, (size_t)ndb * sizeof(int));
+    copy_in<T>(Fbig, g.F2 + fb0, (size_t)nfb * sizeof(T));
     for (int i = threadIdx.x; i < nrb; i += blockDim.x) {
         const int3 r = g.wrep[rb0 + i];
         for (int q = 0; q < r.z; ++q) ubuf[0][r.x + q] = u_glob[r.y + q];
     }
     if (threadIdx.x == 0) *stop = 0;
-    const float rho = g.rho, inv_rho = g.inv_rho;
+    __syncthreads();   // the factors copied in by the whole CTA are read per warp below
+    const T rho = g.rho, inv_rho = g.inv_rho;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // ---- per-warp subsystem and per-lane row state (registers)
     const int s = warp * P + rank;
     const bool have = s < lay.S;
     int n = 0, f = 0, mode = 0, soff = 0, big = 0, npad = 0;
-    const float *Fs = nullptr;
-    float *Frm = nullptr;
-    float Fc[WE_NREG], Fr[WE_FREG];
+    const T *Fs = nullptr;
+    T *Frm = nullptr;
+    T Fc[REG ? WE_NREG : 1], Fr[REG ? WE_FREG : 1];
 #pragma unroll
-    for (int r = 0; r < WE_NREG; ++r) Fc[r] = 0.0f;
+    for (int r = 0; r < (REG ? WE_NREG : 1); ++r) Fc[r] = T(0);
 #pragma unroll
-    for (int c = 0; c < WE_FREG; ++c) Fr[c] = 0.0f;
-    float bt[2] = {0, 0}, ds[2] = {0, 0}, mu[2] = {0, 0}, ct[2] = {0, 0}, lo[2] = {0, 0}, hi[2] = {0, 0};
-    float rcp[2] = {0, 0};
+    for (int c = 0; c < (REG ? WE_FREG : 1); ++c) Fr[c] = T(0);
+    T bt[2] = {0, 0}, ds[2] = {0, 0}, mu[2] = {0, 0}, ct[2] = {0, 0}, lo[2] = {0, 0}, hi[2] = {0, 0};
+    T rcp[2] = {0, 0};
     int rseg[2] = {0, 0}, dsp[2] = {0, 0}, qk[2] = {0, 0}, pk[2] = {0, 0};
     int ndr = 0;
-    float *dptr[WE_DREG];
+    T *dptr[WE_DREG];
 #pragma unroll
     for (int e = 0; e < WE_DREG; ++e) dptr[e] = nullptr;
     if (have) {
         const int4 h = g.sub[s], q = g.sub2[s];
         soff = h.x; n = h.y; f = h.z; mode = h.w;
         npad = q.y;
-        big = n > 32;
+        big = REG ? n > 32 : 1;
         if (!big) {
-            const float *Fg = g.F + q.x;
+            if constexpr (REG) {
+                const T *Fg = g.F + q.x;
 #pragma unroll
-            for (int r = 0; r < WE_NREG; ++r)
-                if (lane < f && r < n) Fc[r] = Fg[lane * npad + r];
+                for (int r = 0; r < WE_NREG; ++r)
+                    if (lane < f && r < n) Fc[r] = Fg[lane * npad + r];
 #pragma unroll
-            for (int c = 0; c < WE_FREG; ++c)
-                if (c < f && lane < n) Fr[c] = Fg[c * npad + lane];
+                for (int c = 0; c < WE_FREG; ++c)
+                    if (c < f && lane < n) Fr[c] = Fg[c * npad + lane];
+            }
         } else {
             Fs = Fbig + (g.fbig[s] - fb0);                      // column-major, column stride npad
             Frm = Fbig + lay.fbig_len + (g.fbig[s] - fb0);      // row-major copy, row stride f
@@ -893,21 +904,21 @@ k_warp_engine(IterArgs<float> g, WarpLayout lay, const int *pr, float *u_glob, i
     for (int it = 0; it < n_iters; ++it) {
         const bool chk = ((it + 1) % check_every) == 0 || it == n_iters - 1;
         double acc[6] = {0, 0, 0, 0, 0, 0};
-        const float *useg = ubuf[par];
+        const T *useg = ubuf[par];
         const int nxt = (par ^ 1) * lay.useg_len;      // offset of the buffer written this iteration
         if (have) {
-            float x[2] = {0.0f, 0.0f}, v[2] = {0.0f, 0.0f};
+            T x[2] = {0, 0}, v[2] = {0, 0};
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int row = lane + 32 * j;
                 if (row < n) {
                     const int base = rseg[j] >> 8, cnt = rseg[j] & 255;
-                    float sg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    T sg[4] = {0, 0, 0, 0};
 #pragma unroll
                     for (int qq = 0; qq < 8; ++qq)
                         if (qq < cnt) sg[qq & 3] += useg[base + qq];
                     for (int qq = 8; qq < cnt; ++qq) sg[qq & 3] += useg[base + qq];
-                    float xv = ((sg[0] + sg[1]) + (sg[2] + sg[3]) - ct[j]) * rcp[j];
+                    T xv = ((sg[0] + sg[1]) + (sg[2] + sg[3]) - ct[j]) * rcp[j];
                     if (xv < lo[j]) xv = lo[j];
                     if (xv > hi[j]) xv = hi[j];
                     x[j] = xv;
@@ -921,74 +932,107 @@ k_warp_engine(IterArgs<float> g, WarpLayout lay, const int *pr, float *u_glob, i
                     }
                 }
             }
-            float t = 0.0f, y[2] = {0.0f, 0.0f};
+            T t = 0, y[2] = {0, 0};
             if (!big) {
-                // t_c (lane c) = sum_r F[r][c] v_r, then y_r (lane r) = sum_c F[r][c] t_c;
-                // warp-uniform bounds: n shuffles for t and f for y
-                float t1 = 0.0f;
+                if constexpr (REG) {
+                    // t_c (lane c) = sum_r F[r][c] v_r, then y_r (lane r) = sum_c F[r][c] t_c;
+                    // warp-uniform bounds: n shuffles for t and f for y
+                    T t1 = 0;
 #pragma unroll
-                for (int r = 0; r < WE_NREG; r += 2) {
-                    if (r >= n) break;
-                    t = fmaf(Fc[r], __shfl_sync(0xffffffffu, v[0], r), t);
-                    t1 = fmaf(Fc[r + 1], __shfl_sync(0xffffffffu, v[0], r + 1), t1);
-                }
-                t += t1;
-                float y1 = 0.0f;
+                    for (int r = 0; r < WE_NREG; r += 2) {
+                        if (r >= n) break;
+                        t = fma_t(Fc[r], __shfl_sync(0xffffffffu, v[0], r), t);
+                        t1 = fma_t(Fc[r + 1], __shfl_sync(0xffffffffu, v[0], r + 1), t1);
+                    }
+                    t += t1;
+                    T y1 = 0;
 #pragma unroll
-                for (int c = 0; c < WE_FREG; c += 2) {
-                    if (c >= f) break;
-                    y[0] = fmaf(Fr[c], __shfl_sync(0xffffffffu, t, c), y[0]);
-                    y1 = fmaf(Fr[c + 1], __shfl_sync(0xffffffffu, t, c + 1), y1);
+                    for (int c = 0; c < WE_FREG; c += 2) {
+                        if (c >= f) break;
+                        y[0] = fma_t(Fr[c], __shfl_sync(0xffffffffu, t, c), y[0]);
+                        y1 = fma_t(Fr[c + 1], __shfl_sync(0xffffffffu, t, c + 1), y1);
+                    }
+                    y[0] += y1;
                 }
-                y[0] += y1;
             } else {
-                float *vb = vbig + warp * 64;
+                T *vb = vbig + warp * 64;
                 vb[lane] = v[0];
                 vb[lane + 32] = v[1];
                 __syncwarp();
-                if (lane < f) {
-                    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+                if (!REG && f <= 16) {
+                    // FP64: half-warp h sums rows h, h + 2, ... of column c = lane % 16
+                    const int c = lane & 15, h = lane >> 4;
+                    T a0 = 0, a1 = 0;
+                    if (c < f) {
+                        int r = h;
+                        for (; r + 2 < n; r += 4) {
+                            a0 = fma_t(Frm[r * f + c], vb[r], a0);
+                            a1 = fma_t(Frm[(r + 2) * f + c], vb[r + 2], a1);
+                        }
+                        for (; r < n; r += 2) a0 = fma_t(Frm[r * f + c], vb[r], a0);
+                    }
+                    t = a0 + a1;
+                    t += __shfl_xor_sync(0xffffffffu, t, 16);
+                } else if (lane < f) {
+                    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
                     int r = 0;
                     for (; r + 3 < n; r += 4) {
-                        a0 = fmaf(Frm[(r + 0) * f + lane], vb[r + 0], a0);
-                        a1 = fmaf(Frm[(r + 1) * f + lane], vb[r + 1], a1);
-                        a2 = fmaf(Frm[(r + 2) * f + lane], vb[r + 2], a2);
-                        a3 = fmaf(Frm[(r + 3) * f + lane], vb[r + 3], a3);
+                        a0 = fma_t(Frm[(r + 0) * f + lane], vb[r + 0], a0);
+                        a1 = fma_t(Frm[(r + 1) * f + lane], vb[r + 1], a1);
+                        a2 = fma_t(Frm[(r + 2) * f + lane], vb[r + 2], a2);
+                        a3 = fma_t(Frm[(r + 3) * f + lane], vb[r + 3], a3);
                     }
-                    for (; r < n; ++r) a0 = fmaf(Frm[r * f + lane], vb[r], a0);
+                    for (; r < n; ++r) a0 = fma_t(Frm[r * f + lane], vb[r], a0);
                     t = (a0 + a1) + (a2 + a3);
                 }
                 __syncwarp();
-                const int r2 = lane + 32 < npad ? lane + 32 : lane;   // stays inside the column
-                float b0 = 0.0f, b1 = 0.0f, e0 = 0.0f, e1 = 0.0f;
-                int c = 0;
-                for (; c + 1 < f; c += 2) {
-                    const float ta = __shfl_sync(0xffffffffu, t, c);
-                    const float tb2 = __shfl_sync(0xffffffffu, t, c + 1);
-                    b0 = fmaf(Fs[c * npad + lane], ta, b0);
-                    b1 = fmaf(Fs[(c + 1) * npad + lane], tb2, b1);
-                    e0 = fmaf(Fs[c * npad + r2], ta, e0);
-                    e1 = fmaf(Fs[(c + 1) * npad + r2], tb2, e1);
+                if (!REG && n <= 16) {
+                    // FP64: half-warp h sums columns h, h + 2, ... for row lane % 16
+                    const int h = lane >> 4, rr = (lane & 15) < npad ? (lane & 15) : 0;
+                    const int nc = (f + 1) >> 1;
+                    T b0 = 0;
+                    for (int i = 0; i < nc; ++i) {
+                        const int c = 2 * i + h;
+                        const T tc = __shfl_sync(0xffffffffu, t, c < f ? c : 0);
+                        if (c < f) b0 = fma_t(Fs[c * npad + rr], tc, b0);
+                    }
+                    y[0] = b0 + __shfl_xor_sync(0xffffffffu, b0, 16);
+                } else {
+                    const bool two = REG || n > 32;   // a second row per lane
+                    const int r1 = (REG || lane < npad) ? lane : 0;
+                    const int r2 = lane + 32 < npad ? lane + 32 : lane;   // stays inside the column
+                    T b0 = 0, b1 = 0, e0 = 0, e1 = 0;
+                    int c = 0;
+                    for (; c + 1 < f; c += 2) {
+                        const T ta = __shfl_sync(0xffffffffu, t, c);
+                        const T tb2 = __shfl_sync(0xffffffffu, t, c + 1);
+                        b0 = fma_t(Fs[c * npad + r1], ta, b0);
+                        b1 = fma_t(Fs[(c + 1) * npad + r1], tb2, b1);
+                        if (two) {
+                            e0 = fma_t(Fs[c * npad + r2], ta, e0);
+                            e1 = fma_t(Fs[(c + 1) * npad + r2], tb2, e1);
+                        }
+                    }
+                    if (c < f) {
+                        const T ta = __shfl_sync(0xffffffffu, t, c);
+                        b0 = fma_t(Fs[c * npad + r1], ta, b0);
+                        if (two) e0 = fma_t(Fs[c * npad + r2], ta, e0);
+                    }
+                    y[0] = b0 + b1;
+                    y[1] = e0 + e1;   // used only when lane + 32 < n
                 }
-                if (c < f) {
-                    const float ta = __shfl_sync(0xffffffffu, t, c);
-                    b0 = fmaf(Fs[c * npad + lane], ta, b0);
-                    e0 = fmaf(Fs[c * npad + r2], ta, e0);
-                }
-                y[0] = b0 + b1;
-                y[1] = e0 + e1;   // used only when lane + 32 < n
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int row = lane + 32 * j;
                 if (row < n) {
-                    const float xm = (mode ? y[j] : v[j] - y[j]) + bt[j];
-                    const float res = x[j] - xm;
-                    const float mu_new = mu[j] + rho * res;
-                    const float d_old = ds[j];
+                    const T xm = (mode ? y[j] : v[j] - y[j]) + bt[j];
+                    const T res = x[j] - xm;
+                    const T mu_new = mu[j] + rho * res;
+                    const T d_old = ds[j];
                     ds[j] = xm;
                     mu[j] = mu_new;
-                    const float un = rho * xm - mu_new;
+                    const T un = rho * xm - mu_new;
                     const int d0 = dsp[j] >> 8, nd = dsp[j] & 255;
                     int e0 = 0;
                     if (j == 0) {
@@ -1000,7 +1044,7 @@ k_warp_engine(IterArgs<float> g, WarpLayout lay, const int *pr, float *u_glob, i
                     for (int e = e0; e < nd; ++e) {
                         const int d = dd[d0 + e];
                         const int ro = d >> 24, up = d & 0xffffff;
-                        float *ud = (ro == rank) ? ubuf[par ^ 1] : cl.map_shared_rank(ubuf[par ^ 1], ro);
+                        T *ud = (ro == rank) ? ubuf[par ^ 1] : cl.map_shared_rank(ubuf[par ^ 1], ro);
                         ud[up] = un;
                     }
                     if (chk) {
@@ -1056,10 +1100,11 @@ k_warp_engine(IterArgs<float> g, WarpLayout lay, const int *pr, float *u_glob, i
     if (use_cond && rank == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, *stop ? 0u : 1u);
 }
 
+template <typename T>
 int prepare_warp_engine(unsigned bytes) {
-    if (cudaFuncSetAttribute(k_warp_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_warp_engine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return -1;
-    if (cudaFuncSetAttribute(k_warp_engine, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_warp_engine<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
         return -1;
     return 0;
 }
@@ -1079,25 +1124,38 @@ static void fill_cluster_cfg(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr,
     cfg->numAttrs = 1;
 }
 
-int launch_warp_engine(const IterArgs<float> &g, const WarpLayout &lay, const int *pr, float *u_glob, int n_iters,
+template <typename T>
+int launch_warp_engine(const IterArgs<T> &g, const WarpLayout &lay, const int *pr, T *u_glob, int n_iters,
                        int check_every, DevStatus *st, double rho, cudaGraphConditionalHandle cond, int use_cond,
                        cudaStream_t s) {
+    if (lay.warps < 1 || lay.warps > WE_WARPS) return -1;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    fill_cluster_cfg(&cfg, attr, lay.P, 32 * WE_WARPS, lay.bytes, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_warp_engine, g, lay, pr, u_glob, n_iters, check_every, st, rho,
+    fill_cluster_cfg(&cfg, attr, lay.P, 32 * lay.warps, lay.bytes, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_warp_engine<T>, g, lay, pr, u_glob, n_iters, check_every, st, rho,
                                        cond, use_cond);
     return e == cudaSuccess ? 0 : -1;
 }
 
+template <typename T>
 int warp_engine_occupancy(const WarpLayout &lay) {
+    if (lay.warps < 1 || lay.warps > WE_WARPS) return 0;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    fill_cluster_cfg(&cfg, attr, lay.P, 32 * WE_WARPS, lay.bytes, 0);
+    fill_cluster_cfg(&cfg, attr, lay.P, 32 * lay.warps, lay.bytes, 0);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_warp_engine, &cfg) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_warp_engine<T>, &cfg) != cudaSuccess) return 0;
     return n;
 }
+
+template int prepare_warp_engine<float>(unsigned);
+template int prepare_warp_engine<double>(unsigned);
+template int launch_warp_engine<float>(const IterArgs<float> &, const WarpLayout &, const int *, float *, int, int,
+                                       DevStatus *, double, cudaGraphConditionalHandle, int, cudaStream_t);
+template int launch_warp_engine<double>(const IterArgs<double> &, const WarpLayout &, const int *, double *, int,
+                                        int, DevStatus *, double, cudaGraphConditionalHandle, int, cudaStream_t);
+template int warp_engine_occupancy<float>(const WarpLayout &);
+template int warp_engine_occupancy<double>(const WarpLayout &);
 
 // ============================================================ small kernels
 // u[pk[k]] = rho * ds[k] - mu[k]

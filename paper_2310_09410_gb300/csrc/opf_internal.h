@@ -165,6 +165,7 @@ struct PersistPtrs {
 // Shared-memory image of one CTA of the warp engine, byte offsets.
 struct WarpLayout {
     int P, L, S, useg_len, fbig_len;
+    int warps;                     // warps per CTA (subsystem s: CTA s % P, warp s / P)
     unsigned off_useg, off_dd, off_fbig, off_vbig, off_red;
     unsigned bytes;
 };

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path against the CPU oracle through the C ABI.
 
 * FP64 iterates (x, x_s, lambda) after 100 iterations within 1e-10 relative
-  (whole-grid, cluster and persistent grid engines), on synthetic feeders of every size and on random
+  (whole-grid, cluster, warp and persistent grid engines), on synthetic feeders of every size and on random
   consensus instances (rank-deficient blocks, blocks wider than 64);
 * converged solves (FP64 and mixed precision) reach the LP optimum of the
   oracle within 1e-6 relative with pres <= 1e-4.
@@ -94,8 +94,28 @@ def test_persistent_engine_fp64_matches_oracle(name, seed, ctas):
     assert abs(obj - ref.objective) <= TOL_ITER * max(1.0, abs(ref.objective))
 
 
+@pytest.mark.parametrize("name,seed", [("13", 1001), ("13", 1002), ("34", 5034), ("123", 2001)])
+def test_warp_engine_fp64_matches_oracle(name, seed):
+    """The FP64 warp engine (one cluster, a warp per subsystem, factors in
+    shared memory, half-warp splits of the mat-vecs of small blocks; blocks of
+    up to 51 slots here, so every branch runs): FP64 iterates match the oracle."""
+    f = synth.preset_feeder(name, seed)
+    M = lindist.build(f)
+    ref = oracle_iterates(M, 100)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64, engine=opf.ENGINE_WARP)
+        xs, lam = s.locals()
+        x, obj = s.solution()
+        assert s.residuals()["iters"] == 100
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
+    assert abs(obj - ref.objective) <= TOL_ITER * max(1.0, abs(ref.objective))
+
+
 @pytest.mark.parametrize("engine", [opf.ENGINE_GRID, opf.ENGINE_CLUSTER, opf.ENGINE_WARP, opf.ENGINE_PERSISTENT])
-@pytest.mark.parametrize("name,seed", [("13", 1002), ("123", 2001)])
+@pytest.mark.parametrize("name,seed", [("13", 1002), ("34", 5034), ("123", 2001)])
 def test_fp32_engines_track_oracle(name, seed, engine):
     """FP32 iterations without re-centring stay within single-precision
     distance of the FP64 oracle over 100 iterations, on every engine."""
@@ -150,6 +170,38 @@ def test_generic_persistent_engine_matches_oracle(seed, kw, ctas):
     assert rel_err(xs, ref.xs) <= TOL_ITER
     assert rel_err(lam, ref.lam) <= TOL_ITER
     assert rel_err(x, ref.x) <= TOL_ITER
+
+
+@pytest.mark.parametrize("seed,kw", [(1, {}), (4, {"max_n": 40, "n_global": 120}), (11, {"p_free": 0.3})])
+def test_generic_warp_engine_fp64_matches_oracle(seed, kw):
+    """Rank-deficient blocks and free variables on the FP64 warp engine."""
+    g, M = generic_model(seed, **kw)
+    rho = 3.0
+    ref = oracle_iterates(M, 100, rho=rho)
+    with opf.Solver.from_generic(g["c"], g["lb"], g["ub"], g["subs"]) as s:
+        s.precompute()
+        s.solve(rho=rho, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64,
+                engine=opf.ENGINE_WARP)
+        xs, lam = s.locals()
+        x, _ = s.solution()
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
+
+
+def test_warp_engine_refuses_wide_blocks():
+    """A block of 94 slots does not fit a warp: the FP64 warp engine refuses
+    with OPF_E_CAPACITY and the automatic choice still solves the instance."""
+    g, M = generic_model(9, max_n=100, n_global=160, n_sub=5)
+    with opf.Solver.from_generic(g["c"], g["lb"], g["ub"], g["subs"]) as s:
+        s.precompute()
+        with pytest.raises(opf.OPFError) as e:
+            s.solve(rho=3.0, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64,
+                    engine=opf.ENGINE_WARP)
+        assert e.value.code == opf.OPF_E_CAPACITY
+        s.reset()
+        s.solve(rho=3.0, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64)
+        assert s.residuals()["iters"] == 100
 
 
 def largest_subsystem_instance(seed=17, n=300):
@@ -215,6 +267,7 @@ def test_zip_delta_loads_match_oracle():
 
 @pytest.mark.parametrize("precision,engine", [(opf.PREC_FP64, opf.ENGINE_AUTO), (opf.PREC_MIXED, opf.ENGINE_AUTO),
                                               (opf.PREC_FP64, opf.ENGINE_GRID), (opf.PREC_MIXED, opf.ENGINE_GRID),
+                                              (opf.PREC_FP64, opf.ENGINE_WARP), (opf.PREC_MIXED, opf.ENGINE_WARP),
                                               (opf.PREC_FP64, opf.ENGINE_PERSISTENT),
                                               (opf.PREC_MIXED, opf.ENGINE_PERSISTENT)])
 @pytest.mark.parametrize("name,seed", [("13", 1003), ("123", 2002)])
