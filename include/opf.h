@@ -129,6 +129,8 @@ typedef struct opf_solve_opts {
                                        the shared memory of all CTAs, one grid barrier per iteration) */
     int32_t flags;                  /* OPF_SOLVE_* bits */
     int32_t cluster;                /* engine 2: CTAs per cluster (1, 2, 4, 8, 16; 0 = automatic);
+                                       engine 3: CTAs of the cluster (1 .. 16, at most 12
+                                       subsystems per CTA; 0 = automatic);
                                        engine 4: CTAs of the grid (1 .. 2048, at most the resident
                                        count; 0 = automatic) */
 } opf_solve_opts;

@@ -59,6 +59,7 @@ struct PersistPlan {
 // Warp-engine plan for one precision: subsystem s -> CTA s % P, warp s / P.
 struct WarpPlan {
     int P = 0;
+    int req = 0;               // CTA count asked for when built (0 = automatic)
     bool built = false, ok = false;
     WarpLayout lay{};
     int *d_pr = nullptr, *d_klb = nullptr, *d_fbig = nullptr;

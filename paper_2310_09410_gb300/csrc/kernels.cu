@@ -765,9 +765,10 @@ __global__ void __launch_bounds__(1024) k_cluster_engine(IterArgs<T> g, ClusterL
 // column c for t = F^T v; lane r: row r for y = F t), so both mat-vecs are
 // chains of warp shuffles and FMAs; a larger one (n <= 64) reads F from shared
 // memory.  In FP64 every factor is read from shared memory (two copies,
-// column- and row-major), and t = F^T v splits the rows over the two half-warps
-// when f <= 16: a warp FP64 instruction costs the same whatever its active
-// lanes, so the dependent chain is what sets the time.  For one iteration:
+// column- and row-major), t = F^T v splits the rows over 2 or 4 lane groups
+// when f <= 16 and y = F t the columns when n <= 16: a warp FP64 instruction
+// occupies the FP64 pipe the same whatever its active lanes, so the count of
+// them on the largest subsystem's warp sets the time.  For one iteration:
 //   x = clip((sum of u over the global's copies - c~) / (rho N), lb~, ub~)   (Eq. closed_1)
 //   v = x + mu / rho;  t = F^T v;  y = F t
 //   x_s = (v - y or y) + bbar~  (Eq. closed_2),  mu += rho (x - x_s) (Eq. ADMM-3)
@@ -913,12 +914,19 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
                 const int row = lane + 32 * j;
                 if (row < n) {
                     const int base = rseg[j] >> 8, cnt = rseg[j] & 255;
-                    T sg[4] = {0, 0, 0, 0};
+                    T sum;
+                    if constexpr (REG) {   // four chains for latency
+                        T sg[4] = {0, 0, 0, 0};
 #pragma unroll
-                    for (int qq = 0; qq < 8; ++qq)
-                        if (qq < cnt) sg[qq & 3] += useg[base + qq];
-                    for (int qq = 8; qq < cnt; ++qq) sg[qq & 3] += useg[base + qq];
-                    T xv = ((sg[0] + sg[1]) + (sg[2] + sg[3]) - ct[j]) * rcp[j];
+                        for (int qq = 0; qq < 8; ++qq)
+                            if (qq < cnt) sg[qq & 3] += useg[base + qq];
+                        for (int qq = 8; qq < cnt; ++qq) sg[qq & 3] += useg[base + qq];
+                        sum = (sg[0] + sg[1]) + (sg[2] + sg[3]);
+                    } else {               // FP64: cnt - 1 adds, no padding adds on the FP64 pipe
+                        sum = useg[base];
+                        for (int qq = 1; qq < cnt; ++qq) sum += useg[base + qq];
+                    }
+                    T xv = (sum - ct[j]) * rcp[j];
                     if (xv < lo[j]) xv = lo[j];
                     if (xv > hi[j]) xv = hi[j];
                     x[j] = xv;
@@ -960,19 +968,21 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
                 vb[lane + 32] = v[1];
                 __syncwarp();
                 if (!REG && f <= 16) {
-                    // FP64: half-warp h sums rows h, h + 2, ... of column c = lane % 16
-                    const int c = lane & 15, h = lane >> 4;
+                    // FP64: G = 2 or 4 lane groups; group h sums rows h, h + G, ...
+                    // of column c = lane % (32 / G), then the groups are added
+                    const int lg = f <= 8 ? 3 : 4, G = 32 >> lg;
+                    const int c = lane & ((1 << lg) - 1), h = lane >> lg;
                     T a0 = 0, a1 = 0;
                     if (c < f) {
                         int r = h;
-                        for (; r + 2 < n; r += 4) {
+                        for (; r + G < n; r += 2 * G) {
                             a0 = fma_t(Frm[r * f + c], vb[r], a0);
-                            a1 = fma_t(Frm[(r + 2) * f + c], vb[r + 2], a1);
+                            a1 = fma_t(Frm[(r + G) * f + c], vb[r + G], a1);
                         }
-                        for (; r < n; r += 2) a0 = fma_t(Frm[r * f + c], vb[r], a0);
+                        for (; r < n; r += G) a0 = fma_t(Frm[r * f + c], vb[r], a0);
                     }
                     t = a0 + a1;
-                    t += __shfl_xor_sync(0xffffffffu, t, 16);
+                    for (int o = 1 << lg; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
                 } else if (lane < f) {
                     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
                     int r = 0;
@@ -987,16 +997,20 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
                 }
                 __syncwarp();
                 if (!REG && n <= 16) {
-                    // FP64: half-warp h sums columns h, h + 2, ... for row lane % 16
-                    const int h = lane >> 4, rr = (lane & 15) < npad ? (lane & 15) : 0;
-                    const int nc = (f + 1) >> 1;
+                    // FP64: G = 2 or 4 lane groups; group h sums columns h, h + G, ...
+                    // for row lane % (32 / G), then the groups are added
+                    const int lg = n <= 8 ? 3 : 4, G = 32 >> lg;
+                    const int rl = lane & ((1 << lg) - 1), h = lane >> lg;
+                    const int rr = rl < npad ? rl : 0;
+                    const int nc = (f + G - 1) / G;
                     T b0 = 0;
                     for (int i = 0; i < nc; ++i) {
-                        const int c = 2 * i + h;
+                        const int c = i * G + h;
                         const T tc = __shfl_sync(0xffffffffu, t, c < f ? c : 0);
                         if (c < f) b0 = fma_t(Fs[c * npad + rr], tc, b0);
                     }
-                    y[0] = b0 + __shfl_xor_sync(0xffffffffu, b0, 16);
+                    for (int o = 1 << lg; o < 32; o <<= 1) b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+                    y[0] = b0;
                 } else {
                     const bool two = REG || n > 32;   // a second row per lane
                     const int r1 = (REG || lane < npad) ? lane : 0;
