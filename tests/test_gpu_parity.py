@@ -192,6 +192,24 @@ def test_generic_warp_engine_fp64_matches_oracle(seed, kw):
     assert rel_err(x, ref.x) <= TOL_ITER
 
 
+def test_warp_engine_cta_count_limits():
+    """engine 3 takes 1 to 16 CTAs holding at most 12 subsystems each: 17 is
+    invalid, one CTA cannot hold the 188 subsystems of the 123-bus feeder."""
+    f = synth.preset_feeder("123", 2001)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        for prec in (opf.PREC_FP64, opf.PREC_FP32):
+            with pytest.raises(opf.OPFError) as e:
+                s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=prec, engine=opf.ENGINE_WARP, cluster=17)
+            assert e.value.code == opf.OPF_E_INVALID
+            with pytest.raises(opf.OPFError) as e:
+                s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=prec, engine=opf.ENGINE_WARP, cluster=1)
+            assert e.value.code == opf.OPF_E_CAPACITY
+        s.reset()
+        s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64, engine=opf.ENGINE_WARP, cluster=16)
+        assert s.residuals()["iters"] == 100
+
+
 def test_warp_engine_refuses_wide_blocks():
     """A block of 94 slots does not fit a warp: the FP64 warp engine refuses
     with OPF_E_CAPACITY and the automatic choice still solves the instance."""
@@ -286,6 +304,23 @@ def test_converged_objective(name, seed, precision, engine):
     assert ok
     assert r["pres"] <= TOL_PRES
     assert abs(obj - obj_star) <= TOL_OBJ * abs(obj_star), (obj, obj_star, r)
+
+
+@pytest.mark.parametrize("name,seed", [("13", 1001), ("34", 5034), ("123", 2001)])
+def test_fp32_reaches_paper_tolerance_in_fp64_iterations(name, seed):
+    """Sec. V-C / Table V: with the paper's default eps_rel = 1e-3 (the
+    Sec. III-C test alone, no absolute gate) FP32 iterations stop at the same
+    or nearly the same iteration as FP64 ones (tested every 2 iterations)."""
+    f = synth.preset_feeder(name, seed)
+    its = {}
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        for prec in (opf.PREC_FP64, opf.PREC_FP32):
+            s.reset()
+            assert s.solve(eps_rel=1e-3, eps_abs_pres=1e30, max_iter=200_000, check_every=2, precision=prec)
+            its[prec] = s.residuals()["iters"]
+    it64, it32 = its[opf.PREC_FP64], its[opf.PREC_FP32]
+    assert abs(it32 - it64) <= max(4, 0.02 * it64), its
 
 
 def test_step_then_getters_and_errors():
