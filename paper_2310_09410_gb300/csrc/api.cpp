@@ -853,10 +853,15 @@ constexpr int kWarpEngineWarps = 12;
 // or an issue slot (FP32: 5 % faster than 12 warps on the 13- and 34-bus feeders)
 constexpr int kWarpEngineWarps64 = 4;
 
-// Warp-engine plan for precision T: max(ceil(S / 12), min(16, ceil(S / 4)))
-// CTAs unless req_P asks for a count.  FP32: factors of subsystems with
-// n > 32 in shared memory (the rest in registers); FP64: every factor in
-// shared memory.
+// Warp-engine plan for precision T.  Work items are warps: one per subsystem,
+// or in FP64 two for the largest subsystems of more than 16 slots, as many as
+// keep 4 warps per CTA (each takes half of its rows; the two sit in warp
+// slots 2k, 2k + 1 of one CTA, on different SM sub-partitions, and add their
+// halves of t = F^T v through shared memory).
+// W items go to max(ceil(W / 12), min(16, ceil(W / 4))) CTAs unless req_P asks
+// for a count: pairs first, round-robin over the CTAs, then single warps,
+// round-robin in subsystem order.  FP32: factors of subsystems with n > 32 in
+// shared memory (the rest in registers); FP64: every factor in shared memory.
 template <typename T>
 static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
     constexpr bool REG = sizeof(T) == 4;
@@ -864,16 +869,66 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
     wp.ok = false;
     wp.req = req_P;
     const int S = h->S, G = h->G, L = h->L;
-    int P = (S + kWarpEngineWarps - 1) / kWarpEngineWarps;
-    if (P < 1 || P > 16 || h->max_ns > 64) return OPF_OK;
+    if (h->max_ns > 64) return OPF_OK;
     for (int s = 0; s < S; ++s)
         if (h->h_sf[s] > 32) return OPF_OK;
-    P = std::max(P, std::min(16, (S + kWarpEngineWarps64 - 1) / kWarpEngineWarps64));
+    // FP64: split the largest subsystems of more than 16 slots while the
+    // warps stay within 4 per CTA of the cluster (16 CTAs, or req_P)
+    std::vector<int> nparts(S, 1);
+    if (!REG) {
+        std::vector<int> big_first;
+        for (int s = 0; s < S; ++s)
+            if (h->h_sn[s] > 16) big_first.push_back(s);
+        std::stable_sort(big_first.begin(), big_first.end(), [&](int x, int y) {
+            return h->h_sn[x] * (h->h_sf[x] + 4) > h->h_sn[y] * (h->h_sf[y] + 4);
+        });
+        const int budget = (req_P > 0 ? req_P : 16) * kWarpEngineWarps64 - S;
+        for (int i = 0; i < (int)big_first.size() && i < budget; ++i) nparts[big_first[i]] = 2;
+    }
+    int W = 0;
+    for (int s = 0; s < S; ++s) W += nparts[s];
+    int P = (W + kWarpEngineWarps - 1) / kWarpEngineWarps;
+    if (P < 1 || P > 16) return OPF_OK;
+    P = std::max(P, std::min(16, (W + kWarpEngineWarps64 - 1) / kWarpEngineWarps64));
     if (req_P > 0) {
-        if (req_P > 16 || (S + req_P - 1) / req_P > kWarpEngineWarps) return OPF_OK;
+        if (req_P > 16) return OPF_OK;
         P = req_P;
     }
-    const int warps = (S + P - 1) / P;
+    // place the items: cta_of[s], first warp slot slot_of[s]
+    std::vector<int> cta_of(S, 0), slot_of(S, 0);
+    auto place = [&](int wpc) -> bool {
+        std::vector<char> used((size_t)P * wpc, 0);
+        int k = 0;
+        for (int s = 0; s < S; ++s) {
+            if (nparts[s] != 2) continue;
+            const int p = k % P, sl = 2 * (k / P);
+            if (sl + 1 >= wpc) return false;
+            used[(size_t)p * wpc + sl] = used[(size_t)p * wpc + sl + 1] = 1;
+            cta_of[s] = p; slot_of[s] = sl;
+            ++k;
+        }
+        int i = 0;
+        for (int s = 0; s < S; ++s) {
+            if (nparts[s] != 1) continue;
+            bool done = false;
+            for (int t = 0; t < P && !done; ++t) {
+                const int p = (i + t) % P;
+                for (int sl = 0; sl < wpc; ++sl)
+                    if (!used[(size_t)p * wpc + sl]) {
+                        used[(size_t)p * wpc + sl] = 1;
+                        cta_of[s] = p; slot_of[s] = sl;
+                        done = true;
+                        break;
+                    }
+            }
+            if (!done) return false;
+            ++i;
+        }
+        return true;
+    };
+    int warps = (W + P - 1) / P;
+    while (warps <= kWarpEngineWarps && !place(warps)) ++warps;
+    if (warps > kWarpEngineWarps) return OPF_OK;
     if (!REG && !wp.d_pr) {
         TRY(dalloc(h, &wp.d_pr, 8 * 17));
         TRY(dalloc(h, &wp.d_wrseg, h->L));
@@ -884,12 +939,17 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
         TRY(dalloc(h, &wp.d_fbig, h->S + 1));
         TRY(dalloc(h, &wp.d_F2d, h->nF));
     }
+    if (!wp.d_wmap) TRY(dalloc(h, &wp.d_wmap, 16 * kWarpEngineWarps));
+    std::vector<int> wmap((size_t)P * warps, -1);
+    for (int s = 0; s < S; ++s)
+        for (int q = 0; q < nparts[s]; ++q)
+            wmap[(size_t)cta_of[s] * warps + slot_of[s] + q] = (s << 8) | (q << 4) | nparts[s];
     auto in_smem = [&](int s) { return !REG || h->h_sn[s] > 32; };
     wp.P = P;
-    // local slots (subsystem s lives in CTA s % P, warp s / P)
+    // local slots of each CTA, in subsystem order
     std::vector<int> nk(P, 0), klb(S + 1, 0), fb(P, 0), fbig(S + 1, 0);
     for (int s = 0; s < S; ++s) {
-        const int p = s % P;
+        const int p = cta_of[s];
         klb[s] = nk[p];
         nk[p] += h->h_sn[s];
         if (in_smem(s)) fb[p] += h->h_sf[s] * h->h_npad[s];
@@ -900,7 +960,7 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
         std::vector<int> fill(fb0.begin(), fb0.end() - 1);
         for (int s = 0; s < S; ++s)
             if (in_smem(s)) {
-                const int p = s % P;
+                const int p = cta_of[s];
                 fbig[s] = fill[p];
                 const size_t cnt = (size_t)h->h_sf[s] * h->h_npad[s];
                 if (cnt) {
@@ -920,7 +980,7 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
     std::vector<int> nru(P, 0);
     std::vector<std::map<int, int>> seg_of(P);
     for (int s = 0; s < S; ++s) {
-        const int p = s % P;
+        const int p = cta_of[s];
         for (int r = 0; r < h->h_sn[s]; ++r) {
             const int gi = h->h_gk[h->h_soff[s] + r];
             if (seg_of[p].count(gi)) continue;
@@ -939,7 +999,7 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
     std::vector<int> db(P + 1, 0);
     std::vector<std::vector<int>> dd(P);
     for (int s = 0; s < S; ++s) {
-        const int p = s % P;
+        const int p = cta_of[s];
         for (int r = 0; r < h->h_sn[s]; ++r) {
             const int k = h->h_soff[s] + r;
             const int gi = h->h_gk[k];
@@ -987,6 +1047,7 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
     take(&c.off_dd, (size_t)mdd * sizeof(int));
     take(&c.off_fbig, (size_t)2 * c.fbig_len * sizeof(T));   // column-major factors, then row-major copies
     take(&c.off_vbig, (size_t)warps * 64 * sizeof(T));
+    take(&c.off_tpart, (size_t)(warps / 2 + 1) * 64 * sizeof(T));   // per warp pair: two halves of t
     take(&c.off_red, 16 * 6 * sizeof(double) + 16);
     c.bytes = (unsigned)off;
     int optin = 0;
@@ -996,6 +1057,7 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
     if (warp_engine_occupancy<T>(c) < 1) { cudaGetLastError(); return OPF_OK; }
     if ((size_t)wdd.size() > (size_t)h->L * 16 || wrep.size() > (size_t)h->L) return OPF_OK;
     CUDA_TRY(cudaMemcpyAsync(wp.d_pr, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(wp.d_wmap, wmap.data(), wmap.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(cudaMemcpyAsync(wp.d_klb, klb.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(cudaMemcpyAsync(wp.d_fbig, fbig.data(), (S + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(cudaMemcpyAsync(wp.d_wrseg, wrseg.data(), L * sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -1010,6 +1072,7 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
 }
 
 static IterArgs<float> with_warp_plan(opf_handle *h, IterArgs<float> a, const WarpPlan &wp) {
+    a.wmap = wp.d_wmap;
     a.klb = wp.d_klb; a.fbig = wp.d_fbig; a.F2 = wp.d_F2;
     a.wrseg = wp.d_wrseg; a.wdsp = wp.d_wdsp; a.wdd = wp.d_wdd; a.wrep = wp.d_wrep;
     a.u_prev_out = h->d_u32 + h->L;
@@ -1017,6 +1080,7 @@ static IterArgs<float> with_warp_plan(opf_handle *h, IterArgs<float> a, const Wa
 }
 
 static IterArgs<double> with_warp_plan(opf_handle *h, IterArgs<double> a, const WarpPlan &wp) {
+    a.wmap = wp.d_wmap;
     a.klb = wp.d_klb; a.fbig = wp.d_fbig; a.F2 = wp.d_F2d;
     a.wrseg = wp.d_wrseg; a.wdsp = wp.d_wdsp; a.wdd = wp.d_wdd; a.wrep = wp.d_wrep;
     a.u_prev_out = h->d_u64 + h->L;

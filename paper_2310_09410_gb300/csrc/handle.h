@@ -56,7 +56,7 @@ struct PersistPlan {
     PersistPtrs ptrs() const { return PersistPtrs{d_pr, d_part, d_sync}; }
 };
 
-// Warp-engine plan for one precision: subsystem s -> CTA s % P, warp s / P.
+// Warp-engine plan for one precision: warp slots of the CTAs of one cluster.
 struct WarpPlan {
     int P = 0;
     int req = 0;               // CTA count asked for when built (0 = automatic)
@@ -64,6 +64,7 @@ struct WarpPlan {
     WarpLayout lay{};
     int *d_pr = nullptr, *d_klb = nullptr, *d_fbig = nullptr;
     int *d_wrseg = nullptr, *d_wdsp = nullptr, *d_wdd = nullptr;
+    int *d_wmap = nullptr;     // per (CTA, warp slot): (subsystem << 8) | (part << 4) | parts, or -1
     int3 *d_wrep = nullptr;
     float *d_F2 = nullptr;     // FP32 plan: factors of the subsystems with n > 32
     double *d_F2d = nullptr;   // FP64 plan: every factor

@@ -811,6 +811,7 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
     int *dd = reinterpret_cast<int *>(sm + lay.off_dd);
     T *Fbig = reinterpret_cast<T *>(sm + lay.off_fbig);
     T *vbig = reinterpret_cast<T *>(sm + lay.off_vbig);    // 64 entries per warp
+    T *tpart = reinterpret_cast<T *>(sm + lay.off_tpart);  // per warp pair: its two halves of t
     double *red = reinterpret_cast<double *>(sm + lay.off_red);
     int *stop = reinterpret_cast<int *>(sm + lay.off_red + 16 * 6 * sizeof(double));
     copy_in<T>(dd, g.wdd + db0, (size_t)ndb * sizeof(int));
@@ -823,10 +824,12 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
     __syncthreads();   // the factors copied in by the whole CTA are read per warp below
     const T rho = g.rho, inv_rho = g.inv_rho;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // ---- per-warp subsystem and per-lane row state (registers)
-    const int s = warp * P + rank;
-    const bool have = s < lay.S;
-    int n = 0, f = 0, mode = 0, soff = 0, big = 0, npad = 0;
+    // ---- per-warp subsystem, its rows [r0, r0 + nr) and per-lane row state (registers)
+    const int wm = g.wmap[rank * lay.warps + warp];
+    const int s = wm >= 0 ? (wm >> 8) : lay.S;
+    const int part = (wm >> 4) & 15, nparts = wm & 15;   // nparts 2: rows split with warp slot warp ^ 1
+    const bool have = wm >= 0 && s < lay.S;
+    int n = 0, f = 0, mode = 0, soff = 0, big = 0, npad = 0, r0 = 0, nr = 0;
     const T *Fs = nullptr;
     T *Frm = nullptr;
     T Fc[REG ? WE_NREG : 1], Fr[REG ? WE_FREG : 1];
@@ -845,6 +848,9 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
         const int4 h = g.sub[s], q = g.sub2[s];
         soff = h.x; n = h.y; f = h.z; mode = h.w;
         npad = q.y;
+        const int hn = (n + 1) >> 1;
+        r0 = (nparts == 2 && part) ? hn : 0;
+        nr = nparts == 2 ? (part ? n - hn : hn) : n;
         big = REG ? n > 32 : 1;
         if (!big) {
             if constexpr (REG) {
@@ -859,7 +865,7 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
         } else {
             Fs = Fbig + (g.fbig[s] - fb0);                      // column-major, column stride npad
             Frm = Fbig + lay.fbig_len + (g.fbig[s] - fb0);      // row-major copy, row stride f
-            for (int i = lane; i < f * n; i += 32) {
+            for (int i = r0 * f + lane; i < (r0 + nr) * f; i += 32) {   // this warp's rows
                 const int r = i / f, c = i - r * f;
                 Frm[i] = Fs[c * npad + r];
             }
@@ -867,8 +873,8 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
         const int kl0 = g.klb[s];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int row = lane + 32 * j;
-            if (row < n) {
+            const int lr = lane + 32 * j, row = r0 + lr;
+            if (lr < nr) {
                 const int kg = soff + row;
                 const int gi = g.gk[kg];
                 bt[j] = g.bt[kg];
@@ -887,7 +893,7 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
         }
         // first row: up to WE_DREG destinations resolved to pointers (buffer 0;
         // the parity offset is added per iteration)
-        if (lane < n) {
+        if (lane < nr) {
             const int d0 = dsp[0] >> 8, nd = dsp[0] & 255;
             ndr = nd < WE_DREG ? nd : WE_DREG;
 #pragma unroll
@@ -911,8 +917,8 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
             T x[2] = {0, 0}, v[2] = {0, 0};
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int row = lane + 32 * j;
-                if (row < n) {
+                const int lr = lane + 32 * j, row = r0 + lr;
+                if (lr < nr) {
                     const int base = rseg[j] >> 8, cnt = rseg[j] & 255;
                     T sum;
                     if constexpr (REG) {   // four chains for latency
@@ -963,9 +969,9 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
                     y[0] += y1;
                 }
             } else {
-                T *vb = vbig + warp * 64;
-                vb[lane] = v[0];
-                vb[lane + 32] = v[1];
+                T *vb = vbig + warp * 64;   // indexed by subsystem row; this warp's rows only
+                if (lane < nr) vb[r0 + lane] = v[0];
+                if (lane + 32 < nr) vb[r0 + lane + 32] = v[1];
                 __syncwarp();
                 if (!REG && f <= 16) {
                     // FP64: G = 2 or 4 lane groups; group h sums rows h, h + G, ...
@@ -974,34 +980,43 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
                     const int c = lane & ((1 << lg) - 1), h = lane >> lg;
                     T a0 = 0, a1 = 0;
                     if (c < f) {
-                        int r = h;
-                        for (; r + G < n; r += 2 * G) {
+                        const int re = r0 + nr;
+                        int r = r0 + h;
+                        for (; r + G < re; r += 2 * G) {
                             a0 = fma_t(Frm[r * f + c], vb[r], a0);
                             a1 = fma_t(Frm[(r + G) * f + c], vb[r + G], a1);
                         }
-                        for (; r < n; r += G) a0 = fma_t(Frm[r * f + c], vb[r], a0);
+                        for (; r < re; r += G) a0 = fma_t(Frm[r * f + c], vb[r], a0);
                     }
                     t = a0 + a1;
                     for (int o = 1 << lg; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
                 } else if (lane < f) {
                     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-                    int r = 0;
-                    for (; r + 3 < n; r += 4) {
+                    const int re = r0 + nr;
+                    int r = r0;
+                    for (; r + 3 < re; r += 4) {
                         a0 = fma_t(Frm[(r + 0) * f + lane], vb[r + 0], a0);
                         a1 = fma_t(Frm[(r + 1) * f + lane], vb[r + 1], a1);
                         a2 = fma_t(Frm[(r + 2) * f + lane], vb[r + 2], a2);
                         a3 = fma_t(Frm[(r + 3) * f + lane], vb[r + 3], a3);
                     }
-                    for (; r < n; ++r) a0 = fma_t(Frm[r * f + lane], vb[r], a0);
+                    for (; r < re; ++r) a0 = fma_t(Frm[r * f + lane], vb[r], a0);
                     t = (a0 + a1) + (a2 + a3);
                 }
                 __syncwarp();
-                if (!REG && n <= 16) {
+                if (!REG && nparts == 2) {
+                    // the pair's halves of t, added in the same order by both warps
+                    T *tp = tpart + (warp >> 1) * 64;
+                    if (lane < f) tp[part * 32 + lane] = t;
+                    asm volatile("bar.sync %0, 64;" ::"r"(1 + (warp >> 1)) : "memory");
+                    if (lane < f) t = tp[lane] + tp[32 + lane];
+                }
+                if (!REG && nr <= 16) {
                     // FP64: G = 2 or 4 lane groups; group h sums columns h, h + G, ...
-                    // for row lane % (32 / G), then the groups are added
-                    const int lg = n <= 8 ? 3 : 4, G = 32 >> lg;
+                    // for row r0 + lane % (32 / G), then the groups are added
+                    const int lg = nr <= 8 ? 3 : 4, G = 32 >> lg;
                     const int rl = lane & ((1 << lg) - 1), h = lane >> lg;
-                    const int rr = rl < npad ? rl : 0;
+                    const int rr = r0 + rl < npad ? r0 + rl : 0;
                     const int nc = (f + G - 1) / G;
                     T b0 = 0;
                     for (int i = 0; i < nc; ++i) {
@@ -1012,9 +1027,9 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
                     for (int o = 1 << lg; o < 32; o <<= 1) b0 += __shfl_xor_sync(0xffffffffu, b0, o);
                     y[0] = b0;
                 } else {
-                    const bool two = REG || n > 32;   // a second row per lane
-                    const int r1 = (REG || lane < npad) ? lane : 0;
-                    const int r2 = lane + 32 < npad ? lane + 32 : lane;   // stays inside the column
+                    const bool two = REG || nr > 32;   // a second row per lane
+                    const int r1 = (REG || r0 + lane < npad) ? r0 + lane : 0;
+                    const int r2 = lane + 32 < npad ? lane + 32 : lane;   // stays inside the column (r0 = 0 here)
                     T b0 = 0, b1 = 0, e0 = 0, e1 = 0;
                     int c = 0;
                     for (; c + 1 < f; c += 2) {
@@ -1038,8 +1053,8 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int row = lane + 32 * j;
-                if (row < n) {
+                const int lr = lane + 32 * j, row = r0 + lr;
+                if (lr < nr) {
                     const T xm = (mode ? y[j] : v[j] - y[j]) + bt[j];
                     const T res = x[j] - xm;
                     const T mu_new = mu[j] + rho * res;
@@ -1102,8 +1117,8 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
     if (have) {
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int row = lane + 32 * j;
-            if (row < n) {
+            const int lr = lane + 32 * j, row = r0 + lr;
+            if (lr < nr) {
                 g.mu[soff + row] = mu[j];
                 g.ds[soff + row] = ds[j];
                 u_glob[pk[j]] = ubuf[par][(rseg[j] >> 8) + qk[j]];

@@ -91,6 +91,7 @@ struct IterArgs {
     // ((offset << 8) | count) of its u; destinations ((rank << 24) | position);
     // replica list (local start, start in u, copies) per CTA
     const T *F2;
+    const int *wmap;      // per (CTA, warp slot): (subsystem << 8) | (part << 4) | parts, or -1
     const int *fbig;
     const int *klb;
     const int *wrseg, *wdsp, *wdd;
@@ -166,7 +167,7 @@ struct PersistPtrs {
 struct WarpLayout {
     int P, L, S, useg_len, fbig_len;
     int warps;                     // warps per CTA (subsystem s: CTA s % P, warp s / P)
-    unsigned off_useg, off_dd, off_fbig, off_vbig, off_red;
+    unsigned off_useg, off_dd, off_fbig, off_vbig, off_tpart, off_red;
     unsigned bytes;
 };
 
