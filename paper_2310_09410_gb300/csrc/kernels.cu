@@ -759,8 +759,9 @@ __global__ void __launch_bounds__(1024) k_cluster_engine(IterArgs<T> g, ClusterL
 
 // ============================================================ warp engine
 // Persistent engine for instances of at most 16 x 12 subsystems: a cluster of
-// P CTAs, one warp per subsystem for the whole solve (subsystem s = warp * P +
-// rank, so every CTA gets a mix of sizes); lane l owns local rows l and l + 32.
+// P CTAs, one warp per subsystem for the whole solve (the plan's warp map
+// spreads the sizes over the CTAs), or in FP64 two warps for a large one, each
+// owning half of its rows; lane l owns the warp's rows r0 + l and r0 + l + 32.
 // In FP32 a subsystem with n <= 32 keeps its factor F in registers (lane c:
 // column c for t = F^T v; lane r: row r for y = F t), so both mat-vecs are
 // chains of warp shuffles and FMAs; a larger one (n <= 64) reads F from shared
