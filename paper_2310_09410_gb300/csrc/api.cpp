@@ -872,17 +872,21 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
     if (h->max_ns > 64) return OPF_OK;
     for (int s = 0; s < S; ++s)
         if (h->h_sf[s] > 32) return OPF_OK;
-    // FP64: split the largest subsystems of more than 16 slots while the
-    // warps stay within 4 per CTA of the cluster (16 CTAs, or req_P)
+    // split the largest subsystems over two warps while the warps stay within
+    // 4 per CTA of the cluster (16 CTAs, or req_P): in FP64 those of more than
+    // 16 slots; in FP32 those of more than 32 (the ones whose factor is in
+    // shared memory), up to 12 warps per CTA
     std::vector<int> nparts(S, 1);
-    if (!REG) {
+    {
+        const int min_n = REG ? 32 : 16;
         std::vector<int> big_first;
         for (int s = 0; s < S; ++s)
-            if (h->h_sn[s] > 16) big_first.push_back(s);
+            if (h->h_sn[s] > min_n) big_first.push_back(s);
         std::stable_sort(big_first.begin(), big_first.end(), [&](int x, int y) {
             return h->h_sn[x] * (h->h_sf[x] + 4) > h->h_sn[y] * (h->h_sf[y] + 4);
         });
-        const int budget = (req_P > 0 ? req_P : 16) * kWarpEngineWarps64 - S;
+        const int per_cta = REG ? kWarpEngineWarps : kWarpEngineWarps64;
+        const int budget = (req_P > 0 ? req_P : 16) * per_cta - S;
         for (int i = 0; i < (int)big_first.size() && i < budget; ++i) nparts[big_first[i]] = 2;
     }
     int W = 0;

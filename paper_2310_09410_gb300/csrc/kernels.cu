@@ -760,8 +760,8 @@ __global__ void __launch_bounds__(1024) k_cluster_engine(IterArgs<T> g, ClusterL
 // ============================================================ warp engine
 // Persistent engine for instances of at most 16 x 12 subsystems: a cluster of
 // P CTAs, one warp per subsystem for the whole solve (the plan's warp map
-// spreads the sizes over the CTAs), or in FP64 two warps for a large one, each
-// owning half of its rows; lane l owns the warp's rows r0 + l and r0 + l + 32.
+// spreads the sizes over the CTAs), or two warps for a large one, each owning
+// half of its rows; lane l owns the warp's rows r0 + l and r0 + l + 32.
 // In FP32 a subsystem with n <= 32 keeps its factor F in registers (lane c:
 // column c for t = F^T v; lane r: row r for y = F t), so both mat-vecs are
 // chains of warp shuffles and FMAs; a larger one (n <= 64) reads F from shared
@@ -852,7 +852,7 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
         const int hn = (n + 1) >> 1;
         r0 = (nparts == 2 && part) ? hn : 0;
         nr = nparts == 2 ? (part ? n - hn : hn) : n;
-        big = REG ? n > 32 : 1;
+        big = REG ? (n > 32 || nparts == 2) : 1;
         if (!big) {
             if constexpr (REG) {
                 const T *Fg = g.F + q.x;
@@ -1005,7 +1005,7 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
                     t = (a0 + a1) + (a2 + a3);
                 }
                 __syncwarp();
-                if (!REG && nparts == 2) {
+                if (nparts == 2) {
                     // the pair's halves of t, added in the same order by both warps
                     T *tp = tpart + (warp >> 1) * 64;
                     if (lane < f) tp[part * 32 + lane] = t;
@@ -1028,9 +1028,9 @@ k_warp_engine(IterArgs<T> g, WarpLayout lay, const int *pr, T *u_glob, int n_ite
                     for (int o = 1 << lg; o < 32; o <<= 1) b0 += __shfl_xor_sync(0xffffffffu, b0, o);
                     y[0] = b0;
                 } else {
-                    const bool two = REG || nr > 32;   // a second row per lane
-                    const int r1 = (REG || r0 + lane < npad) ? r0 + lane : 0;
-                    const int r2 = lane + 32 < npad ? lane + 32 : lane;   // stays inside the column (r0 = 0 here)
+                    const bool two = nr > 32;   // a second row per lane (only when r0 = 0)
+                    const int r1 = r0 + lane < npad ? r0 + lane : 0;     // stays inside the column
+                    const int r2 = lane + 32 < npad ? lane + 32 : lane;
                     T b0 = 0, b1 = 0, e0 = 0, e1 = 0;
                     int c = 0;
                     for (; c + 1 < f; c += 2) {
