@@ -68,7 +68,7 @@ N_SM, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 # DRAM bytes per launch of the dominant kernels from the ncu captures in
 # profiles/ (None until a capture of the current kernel exists).
 BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 83461632 + 33740800
-WARP_ENGINE_TRAFFIC_PER_LAUNCH = 352256 + 1536
+WARP_ENGINE_TRAFFIC_PER_LAUNCH = 516864 + 768
 PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8707328 + 355584
 ITERS_PER_LAUNCH = 1000
 
