@@ -84,35 +84,31 @@ __device__ __forceinline__ void stage(T *dst, const T *src, int n) {
 }
 
 template <typename T>
-__device__ __forceinline__ T dot_fx(const T *__restrict__ f, const T *__restrict__ x, const T *__restrict__ w,
-                                    int npad);
+__device__ __forceinline__ T dot_fv(const T *__restrict__ f, const T *__restrict__ v, int npad);
 
 template <>
-__device__ __forceinline__ float dot_fx<float>(const float *__restrict__ f, const float *__restrict__ x,
-                                               const float *__restrict__ w, int npad) {
+__device__ __forceinline__ float dot_fv<float>(const float *__restrict__ f, const float *__restrict__ v, int npad) {
     float a0 = 0.0f, a1 = 0.0f;
     for (int r = 0; r < npad; r += 4) {
         const float4 a = *reinterpret_cast<const float4 *>(f + r);
-        const float4 b = *reinterpret_cast<const float4 *>(x + r);
-        const float4 c = *reinterpret_cast<const float4 *>(w + r);
-        a0 = fmaf(a.x, b.x + c.x, a0);
-        a1 = fmaf(a.y, b.y + c.y, a1);
-        a0 = fmaf(a.z, b.z + c.z, a0);
-        a1 = fmaf(a.w, b.w + c.w, a1);
+        const float4 b = *reinterpret_cast<const float4 *>(v + r);
+        a0 = fmaf(a.x, b.x, a0);
+        a1 = fmaf(a.y, b.y, a1);
+        a0 = fmaf(a.z, b.z, a0);
+        a1 = fmaf(a.w, b.w, a1);
     }
     return a0 + a1;
 }
 
 template <>
-__device__ __forceinline__ double dot_fx<double>(const double *__restrict__ f, const double *__restrict__ x,
-                                                 const double *__restrict__ w, int npad) {
+__device__ __forceinline__ double dot_fv<double>(const double *__restrict__ f, const double *__restrict__ v,
+                                                 int npad) {
     double a0 = 0.0, a1 = 0.0;
     for (int r = 0; r < npad; r += 2) {
         const double2 a = *reinterpret_cast<const double2 *>(f + r);
-        const double2 b = *reinterpret_cast<const double2 *>(x + r);
-        const double2 c = *reinterpret_cast<const double2 *>(w + r);
-        a0 = fma(a.x, b.x + c.x, a0);
-        a1 = fma(a.y, b.y + c.y, a1);
+        const double2 b = *reinterpret_cast<const double2 *>(v + r);
+        a0 = fma(a.x, b.x, a0);
+        a1 = fma(a.y, b.y, a1);
     }
     return a0 + a1;
 }
@@ -234,7 +230,9 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
             if (x < lo) x = lo;
             if (x > hi) x = hi;
             const int mt = meta[k];
-            vbx[srec[mt >> 8].y + (mt & 255)] = x;
+            const int pos = srec[mt >> 8].y + (mt & 255);
+            vbx[pos] = x;
+            vbw[pos] = x + vbw[pos];   // v = x + lambda / rho until phase C
             if (chk) {
                 const double xd = xrs[k] + (double)x;
                 acc[2] += xd * xd;
@@ -242,12 +240,12 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
             }
         }
         __syncthreads();
-        // B: t = F^T (x + w) per own factor column
+        // B: t = F^T v per own factor column
         for (int j = threadIdx.x; j < nj; j += blockDim.x) {
             const int itm = items[j];
             const int4 r = srec[itm >> 8];
             const int c = itm & 255, npad = (r.w >> 1) & 0x1ff;
-            tb[r.z + c] = dot_fx<T>(F + r.x + c * fstride(npad), vbx + r.y, vbw + r.y, npad);
+            tb[r.z + c] = dot_fv<T>(F + r.x + c * fstride(npad), vbw + r.y, npad);
         }
         __syncthreads();
         // C: projection, dual update, u to the next iteration's buffer
@@ -267,7 +265,7 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
             if (c < f) y0 += Fr[c * cs] * tt[c];
             const int pos = r.y + row;
             const T x = vbx[pos];
-            const T v = x + vbw[pos];
+            const T v = vbw[pos];
             const T xm = (mode ? (y0 + y1) : v - (y0 + y1)) + bt[k];
             const T res = x - xm;
             const T mu_new = mu[k] + rho * res;
