@@ -69,7 +69,7 @@ N_SM, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 # profiles/ (None until a capture of the current kernel exists).
 BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 83461632 + 33740800
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 516864 + 768
-PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8707328 + 355584
+PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8708352 + 313088
 ITERS_PER_LAUNCH = 1000
 
 
