@@ -767,9 +767,11 @@ __global__ void __launch_bounds__(1024) k_cluster_engine(IterArgs<T> g, ClusterL
 // chains of warp shuffles and FMAs; a larger one (n <= 64) reads F from shared
 // memory.  In FP64 every factor is read from shared memory (two copies,
 // column- and row-major), t = F^T v splits the rows over 2 or 4 lane groups
-// when f <= 16 and y = F t the columns when n <= 16: a warp FP64 instruction
-// occupies the FP64 pipe the same whatever its active lanes, so the count of
-// them on the largest subsystem's warp sets the time.  For one iteration:
+// when f <= 16 and y = F t the columns when the warp has at most 16 rows: a
+// warp FP64 instruction occupies the FP64 pipe the same whatever its active
+// lanes, so the count of them on the slowest warp sets the time.  The two
+// warps of a split subsystem add their halves of t through shared memory
+// behind a two-warp named barrier.  For one iteration:
 //   x = clip((sum of u over the global's copies - c~) / (rho N), lb~, ub~)   (Eq. closed_1)
 //   v = x + mu / rho;  t = F^T v;  y = F t
 //   x_s = (v - y or y) + bbar~  (Eq. closed_2),  mu += rho (x - x_s) (Eq. ADMM-3)
