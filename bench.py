@@ -372,9 +372,9 @@ def warp_engine_fp64(sizes):
 
 def count_launches_single(stats, precision, k=50, R=1000, persistent=False, warp64=False, per_launch=20000):
     """Kernels of ours per single-instance step: precompute (3) + solve + objective read (1).
-    FP64 iterations: whole-grid kernels (k + 1 per chunk of k), the warp
-    engine (one launch) for small instances or, for large instances, the
-    persistent engine (one launch per 20000 iterations)."""
+    FP64 iterations: the warp engine (one launch) for small instances, else the
+    persistent engine (one launch per 20000 iterations); whole-grid kernels
+    (k + 1 per chunk of k) only where neither holds the instance."""
     n = 3 + 1
 
     def fp64(iters):
@@ -416,7 +416,8 @@ def plain_fp64_reference(opf, f, device, stream, n=2):
     iters = s.residuals()["iters"]
     s.close()
     return {"value": 1e3 * len(times) / sum(times), "unit": UNIT, "iterations": int(iters),
-            "path": "single instance, FP64 iterations on the grid engine (opf_solve_ex, engine auto)"}
+            "path": "single instance, FP64 iterations on the engine opf_solve_ex picks (warp engine up to 64 "
+                    "subsystems, else the persistent grid engine)"}
 
 
 def run_batch(args, rank, world, local):
@@ -605,7 +606,7 @@ def run_single(args, rank, world, local):
         iter_ms.append(st["iterate_ms"])
         it_main += st["main_iters"]
         it_pol += st["polish_iters"]
-        launches += count_launches_single(st, args.precision, persistent=sizes["n_slots"] > 4096,
+        launches += count_launches_single(st, args.precision, persistent=not warp_engine_fp64(sizes),
                                           warp64=warp_engine_fp64(sizes))
         if not ok:
             raise SystemExit("a timed solve did not converge")
@@ -650,7 +651,8 @@ def run_single(args, rank, world, local):
         kern, traffic = ("k_warp_engine<double> (FP64 iterations; one warp per subsystem, factors in shared "
                          "memory, instance resident in one thread-block cluster)"), None
     else:
-        kern, traffic = "k_tile_iter<double> (FP64 iterations, one CTA per tile)", None
+        kern, traffic = ("k_persist_engine<double> (FP64 iterations; cooperative launch, instance resident in "
+                         "the CTAs' shared memory, one grid barrier per iteration)"), None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
             "traffic": traffic,

@@ -190,9 +190,9 @@ int opf_solve(opf_handle *h, double rho, double eps, int32_t max_iter);
  * eps_abs_pres 1e-4, max_iter 1e6, check_every 50, FP64).  Automatic engine
  * choice: FP32 / mixed iterations on the warp engine, else the cluster
  * engine, else the persistent grid engine, else whole-grid kernels; FP64
- * iterations (and the polish) on the persistent grid engine for instances
- * of more than 4096 slots, else on the warp engine when the instance fits it
- * with at most 4 warps per CTA (at most 64 subsystems), else whole-grid kernels.  The persistent engine's grid
+ * iterations (and the polish) on the warp engine when the instance fits it
+ * with at most 4 warps per CTA (at most 64 subsystems), else on the
+ * persistent grid engine when its plan fits, else whole-grid kernels.  The persistent engine's grid
  * barrier waits at most 1 s; past that the solve returns OPF_E_TIMEOUT. */
 int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts);
 

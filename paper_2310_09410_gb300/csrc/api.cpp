@@ -1245,9 +1245,6 @@ static int run_cluster64(opf_handle *h, const opf_solve_opts &o) {
 // Iterations per launch of the persistent engine when it runs to the test
 // (FP64 plain solves and the polish): the host reads the status in between.
 constexpr int kPersistLaunchIters = 20000;
-// Automatic engine choice: FP64 iterations of instances with more slots than
-// this run on the persistent grid engine.
-constexpr int kPersistAutoSlots = 4096;
 
 // Test hook: one arrival more than the grid has, so the first barrier's
 // bounded wait runs out.
@@ -1422,24 +1419,24 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
     h->last_rho = o.rho;
     TRY(set_status(h, o, false));
     CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
-    // FP64 iterations (plain solves and the polish) on the persistent grid
-    // engine when asked for, or automatically for large instances
-    bool p64 = false;
-    if (o.engine == 4 || (o.engine == 0 && h->L > kPersistAutoSlots)) {
-        TRY(get_persist_plan<double>(h, &h->p64, o.engine == 4 ? o.cluster : 0));
-        if (!h->p64.ok && o.engine == 4 && o.cluster > 0) TRY(get_persist_plan<double>(h, &h->p64, 0));
-        p64 = h->p64.ok;
-    }
-    // else on the warp engine when the instance fits one cluster of it with at
-    // most 4 warps per CTA (automatic choice; with more, the warps of an SM
-    // queue on its FP64 pipe and whole-grid kernels are faster)
-    bool w64 = false;
-    if (!p64 && o.precision != OPF_PREC_FP32 && (o.engine == 0 || o.engine == 3)) {
+    // FP64 iterations (plain solves and the polish): on the warp engine when
+    // asked for, or automatically when the instance fits one cluster of it
+    // with at most 4 warps per CTA (with more, the warps of an SM queue on its
+    // FP64 pipe); else on the persistent grid engine when asked for, or
+    // automatically when its plan fits (123 buses: 5.5 us per iteration
+    // against 7.3 us for whole-grid kernels); else whole-grid kernels
+    bool w64 = false, p64 = false;
+    if (o.precision != OPF_PREC_FP32 && (o.engine == 0 || o.engine == 3)) {
         const int req = o.engine == 3 ? o.cluster : 0;
         if (!h->w64.built || h->w64.req != req) TRY(build_warp_plan<double>(h, h->w64, req));
         w64 = h->w64.ok && (o.engine == 3 || h->w64.lay.warps <= kWarpEngineWarps64);
     }
-    const int e64 = p64 ? 4 : w64 ? 3 : 1;
+    if (!w64 && (o.engine == 4 || (o.engine == 0 && o.precision != OPF_PREC_FP32))) {
+        TRY(get_persist_plan<double>(h, &h->p64, o.engine == 4 ? o.cluster : 0));
+        if (!h->p64.ok && o.engine == 4 && o.cluster > 0) TRY(get_persist_plan<double>(h, &h->p64, 0));
+        p64 = h->p64.ok;
+    }
+    const int e64 = w64 ? 3 : p64 ? 4 : 1;
     if (o.precision == OPF_PREC_FP64) {
         bool cl = false;
         if (o.engine == 2) {

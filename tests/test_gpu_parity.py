@@ -212,17 +212,25 @@ def test_warp_engine_cta_count_limits():
 
 def test_warp_engine_refuses_wide_blocks():
     """A block of 94 slots does not fit a warp: the FP64 warp engine refuses
-    with OPF_E_CAPACITY and the automatic choice still solves the instance."""
+    with OPF_E_CAPACITY, and the automatic choice (the persistent grid engine)
+    iterates to oracle parity."""
     g, M = generic_model(9, max_n=100, n_global=160, n_sub=5)
+    rho = 3.0
+    ref = oracle_iterates(M, 100, rho=rho)
     with opf.Solver.from_generic(g["c"], g["lb"], g["ub"], g["subs"]) as s:
         s.precompute()
         with pytest.raises(opf.OPFError) as e:
-            s.solve(rho=3.0, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64,
+            s.solve(rho=rho, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64,
                     engine=opf.ENGINE_WARP)
         assert e.value.code == opf.OPF_E_CAPACITY
         s.reset()
-        s.solve(rho=3.0, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64)
+        s.solve(rho=rho, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64)
         assert s.residuals()["iters"] == 100
+        xs, lam = s.locals()
+        x, _ = s.solution()
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
 
 
 def largest_subsystem_instance(seed=17, n=300):
