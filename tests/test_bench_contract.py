@@ -1,0 +1,48 @@
+"""bench.py's JSON line, checked on the CPU through the reference arm (the
+oracle timed on the host cores) and the host-side helpers of the GPU arm."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+        "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e")
+
+
+def test_reference_arm_prints_one_json_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "single",
+                          "--feeder", "13", "--steps", "2", "--warmup", "1"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    for k in KEYS:
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
+
+
+def test_fp64_engine_rule_and_launch_counts():
+    """The launch counts bench.py claims follow the library's automatic FP64
+    engine: the warp engine (one launch per solve) up to 64 subsystems of at
+    most 64 slots, else the persistent engine (one launch per 20000
+    iterations)."""
+    small = {"n_sub": 18, "max_ns": 36}
+    large = {"n_sub": 188, "max_ns": 51}
+    assert bench.warp_engine_fp64(small) and not bench.warp_engine_fp64(large)
+    assert not bench.warp_engine_fp64({"n_sub": 12, "max_ns": 94})
+    st = {"main_iters": 3150, "polish_iters": 0}
+    # precompute (3) + objective read (1) + u (1) + the engine
+    assert bench.count_launches_single(st, "fp64", warp64=True) == 3 + 1 + 1 + 1
+    st = {"main_iters": 26000, "polish_iters": 0}
+    assert bench.count_launches_single(st, "fp64", persistent=True) == 3 + 1 + 1 + 2
