@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "opf_internal.h"
+#include "warp_place.h"
 
 namespace opf {
 
@@ -899,40 +900,9 @@ static int build_warp_plan(opf_handle *h, WarpPlan &wp, int req_P) {
         P = req_P;
     }
     // place the items: cta_of[s], first warp slot slot_of[s]
-    std::vector<int> cta_of(S, 0), slot_of(S, 0);
-    auto place = [&](int wpc) -> bool {
-        std::vector<char> used((size_t)P * wpc, 0);
-        int k = 0;
-        for (int s = 0; s < S; ++s) {
-            if (nparts[s] != 2) continue;
-            const int p = k % P, sl = 2 * (k / P);
-            if (sl + 1 >= wpc) return false;
-            used[(size_t)p * wpc + sl] = used[(size_t)p * wpc + sl + 1] = 1;
-            cta_of[s] = p; slot_of[s] = sl;
-            ++k;
-        }
-        int i = 0;
-        for (int s = 0; s < S; ++s) {
-            if (nparts[s] != 1) continue;
-            bool done = false;
-            for (int t = 0; t < P && !done; ++t) {
-                const int p = (i + t) % P;
-                for (int sl = 0; sl < wpc; ++sl)
-                    if (!used[(size_t)p * wpc + sl]) {
-                        used[(size_t)p * wpc + sl] = 1;
-                        cta_of[s] = p; slot_of[s] = sl;
-                        done = true;
-                        break;
-                    }
-            }
-            if (!done) return false;
-            ++i;
-        }
-        return true;
-    };
-    int warps = (W + P - 1) / P;
-    while (warps <= kWarpEngineWarps && !place(warps)) ++warps;
-    if (warps > kWarpEngineWarps) return OPF_OK;
+    std::vector<int> cta_of, slot_of;
+    const int warps = place_warp_items_min(nparts, P, kWarpEngineWarps, &cta_of, &slot_of);
+    if (warps == 0) return OPF_OK;
     if (!REG && !wp.d_pr) {
         TRY(dalloc(h, &wp.d_pr, 8 * 17));
         TRY(dalloc(h, &wp.d_wrseg, h->L));
