@@ -395,3 +395,32 @@ def test_init_point_rule():
             assert x0[k] == pytest.approx(0.5 * (M.lb[k] + M.ub[k]))
         elif nm[0] in ("load", "line") or (nm[0] == "gen" and nm[1] == 0):
             assert x0[k] == 0.0
+
+
+# --- Sec. III-C quantities against the iterates ---------------------------
+
+def test_residual_history_matches_the_iterates():
+    """The quantities the oracle records after iteration t + 1, against the
+    states of separate runs of t and t + 1 iterations: pres equals
+    |lambda^{t+1} - lambda^t| / rho (the dual update, Eq. ADMM-3), dres is rho
+    |x_s^{t+1} - x_s^t|, the norms behind eps_prim and eps_dual are those of
+    B x^{t+1}, x_s^{t+1} and lambda^{t+1}, and the objective is c^T x^{t+1}
+    (an off-by-one in the oracle's bookkeeping of the previous state fails)."""
+    M = lindist.build(synth.preset_feeder("13", 1001))
+    P = admm.Prepared(M)
+    rho = 100.0
+    rec = admm.admm(P, rho=rho, max_iter=40, check_every=0, record=True)
+    for t in (0, 1, 9, 39):
+        if t == 0:
+            lam_t, xs_t = np.zeros(len(P.gidx)), P.x0[P.gidx]
+        else:
+            a = admm.admm(P, rho=rho, max_iter=t, check_every=0)
+            lam_t, xs_t = a.lam, a.xs
+        b = admm.admm(P, rho=rho, max_iter=t + 1, check_every=0)
+        pres, dres, eprim, edual, obj = rec.hist[t]
+        assert pres == pytest.approx(np.linalg.norm(b.lam - lam_t) / rho, rel=1e-9)
+        assert pres == pytest.approx(np.linalg.norm(b.x[P.gidx] - b.xs), rel=1e-12)
+        assert dres == pytest.approx(rho * np.linalg.norm(b.xs - xs_t), rel=1e-12)
+        assert eprim == pytest.approx(max(np.linalg.norm(b.x[P.gidx]), np.linalg.norm(b.xs)), rel=1e-12)
+        assert edual == pytest.approx(np.linalg.norm(b.lam), rel=1e-12)
+        assert obj == pytest.approx(M.c @ b.x, rel=1e-12)
