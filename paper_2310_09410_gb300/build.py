@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libopf.so")
-SOURCES = ["kernels.cu", "api.cpp", "model.cpp", "static_update.cu", "batch.cu", "batch_api.cpp", "serve.cpp", "partition.cpp", "persist.cu"]
+SOURCES = ["kernels.cu", "api.cpp", "model.cpp", "static_update.cu", "batch.cu", "batch_api.cpp", "serve.cpp", "partition.cpp", "persist.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fPIC,-O2,-fno-strict-aliasing", "-I" + os.path.join(ROOT, "include")]
@@ -50,8 +50,6 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if ptxas_info and src.endswith(".cu"):
             cmd.insert(1, "-Xptxas=-v")
-        if src.endswith(".cpp"):
-            cmd += ["-x", "cu"] if False else []
         procs.append((src, cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, cmd, p in procs:

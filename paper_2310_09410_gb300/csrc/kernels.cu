@@ -8,14 +8,18 @@
 //                 Q itself (mode 0, M = I - F F^T) or an orthonormal null-space
 //                 basis N from pivoted Gram-Schmidt on the columns of I - Q^T Q
 //                 (mode 1, M = F F^T).
-//  k_iterate      one ADMM iteration of Algorithm 1 over all subsystems:
-//                 global update (Eq. closed_1) recomputed per slot from the
-//                 slot's segment of u = rho x_s - lambda of the previous
-//                 iteration, local update (Eq. closed_2) x_s = M_s v + bbar_s
-//                 with v = x_g + lambda/rho, dual update (Eq. ADMM-3), and on
-//                 tested iterations the Sec. III-C sums in FP64.
-//  k_cta_engine   the same iteration run by one CTA for many iterations with
-//                 the whole instance resident in shared memory.
+//  k_tile_iter    one ADMM iteration of Algorithm 1, one CTA per tile of
+//                 consecutive subsystems: global update (Eq. closed_1)
+//                 recomputed per slot from the slot's segment of
+//                 u = rho x_s - lambda of the previous iteration, local update
+//                 (Eq. closed_2) x_s = M_s v + bbar_s with v = x_g + lambda/rho,
+//                 dual update (Eq. ADMM-3), and on tested iterations the
+//                 Sec. III-C sums in FP64 (k_check applies the test).
+//  k_cluster_engine  the same iterations run by one thread-block cluster for
+//                 many iterations with the whole instance resident in the
+//                 cluster's shared memory (globals exchanged through DSMEM).
+//  k_warp_engine  one warp per subsystem for a whole solve, factors in
+//                 registers or shared memory, one barrier per iteration.
 //
 // Every quantity may be shifted by an FP64 reference point (x_ref per global,
 // lambda_ref per slot): the kernels iterate on d = x_s - x_ref[g] and
