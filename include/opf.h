@@ -237,12 +237,12 @@ int opf_set_loads(opf_handle *h, const double *load_p, const double *load_q);
 int opf_get_timing(opf_handle *h, double *ms, int n);
 
 /* Allocation-free global update, for callers that cannot allocate device
- * memory: work enqueued while a CUDA stream is being captured (cudaMalloc
- * cannot be captured), control loops that forbid allocation once running, and
- * hosts whose device memory comes only from their own allocator.  The paper
- * has no counterpart: this is the global update of Eq. closed_1 and the
- * objective c^T x (what opf_get_solution returns) over caller device arrays,
- * without a handle.
+ * memory: control loops that forbid allocation once they run (an allocation
+ * may block, or fail when memory is short, at any moment), and hosts whose
+ * device memory is handed out only by their own allocator (a framework's
+ * caching allocator that owns the whole device).  The paper has no
+ * counterpart: this is the global update and the objective c^T x (what
+ * opf_get_solution returns) over caller device arrays, without a handle.
  *   n          number of globals, 1 <= n <= OPF_STATIC_MAX_GLOBALS
  *   seg_off    device, n + 1 int32 offsets: the local copies of global i are
  *              u[seg_off[i] .. seg_off[i+1]) (at least one each)
@@ -256,12 +256,13 @@ int opf_get_timing(opf_handle *h, double *ms, int n);
  *              enqueues work, synchronise the stream before reading outputs.
  * Scratch is a fixed device array of OPF_STATIC_MAX_BLOCKS doubles, one per
  * block of 256 globals, held by every device that loads the library until
- * the process exits.  The first call on a device (with that device current)
- * looks up the array's address, which needs no allocation; make that first
- * call before any stream capture.  Every call on a device shares the array:
- * calls that may overlap on the GPU (different streams without ordering)
- * race and must be serialised by the caller.  Each call writes every entry
- * it reads, so stale contents from an earlier call are never used.
+ * the process exits.  The first call in a CUDA context (the stream's; a
+ * stream of an SM partition has its own) looks up the array's address in
+ * that context, which needs no allocation; make that first call before any
+ * stream capture.  Every call in a context shares the array: calls that may
+ * overlap on the GPU (different streams without ordering) race and must be
+ * serialised by the caller.  Each call writes every entry it reads, so stale
+ * contents from an earlier call are never used.
  * Returns OPF_OK, OPF_E_INVALID (null pointer, n < 1, rho <= 0),
  * OPF_E_CAPACITY (n above the limit; message in opf_last_error), OPF_E_CUDA. */
 #define OPF_STATIC_MAX_BLOCKS 8192
@@ -334,8 +335,10 @@ int opf_batch_get_shape(opf_batch *b, int32_t precision, int32_t *out, int32_t n
  * output may be NULL. */
 int opf_batch_get_solution(opf_batch *b, int32_t first, int32_t count, double *x, double *objective);
 
-/* Per instance: res[4 i ..] = pres, dres, eps_prim, eps_dual of its last test,
- * iterations, converged flag (any output may be NULL). */
+/* Per instance: res[4 i ..] = pres, dres, eps_prim, eps_dual of its last
+ * test (eps_prim and eps_dual for epsilon_rel = 1, i.e. the two norms the
+ * test scales, as opf_get_residuals), iterations, converged flag (any output
+ * may be NULL). */
 int opf_batch_get_status(opf_batch *b, int32_t first, int32_t count, double *res, int32_t *iters,
                          int32_t *converged);
 
@@ -398,8 +401,22 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
  * for an unknown model or a negative or NaN tolerance. */
 int opf_server_set_model_tolerance(opf_server *s, int32_t model, double eps_rel, double eps_abs_pres);
 
+/* Admission policy of one model (default: no bounds).  max_queue > 0 bounds
+ * the requests waiting for a slot; max_wait_s > 0 bounds the seconds a
+ * request may wait for one: at submit the wait is predicted from the
+ * requests ahead (queued and running, served `slots` at a time) and the
+ * model's mean service time so far, and a queued request that has waited
+ * longer is shed by opf_server_step, reported by opf_server_poll_ex with
+ * status OPF_E_TIMEOUT.  With both bounds set every request is served,
+ * refused at submit or shed, so none stays pending without a status when
+ * the arrivals exceed what the model can serve.  OPF_E_INVALID for an
+ * unknown model or a negative bound. */
+int opf_server_set_admission(opf_server *s, int32_t model, int32_t max_queue, double max_wait_s);
+
 /* Queues a request of model `model` with its loads (host arrays [n_load*3],
- * copied) and a caller tag that identifies it in opf_server_poll. */
+ * copied) and a caller tag that identifies it in opf_server_poll.  Returns
+ * OPF_E_CAPACITY, with the request counted as refused and not queued, when
+ * the model's admission policy turns it away (message in opf_last_error). */
 int opf_server_submit(opf_server *s, int32_t model, const double *load_p, const double *load_q, int64_t tag);
 
 /* Progress without blocking: for each model whose previous pass finished,
@@ -414,15 +431,35 @@ int opf_server_step(opf_server *s);
  * (any array may be NULL).  Returns how many were written (>= 0). */
 int opf_server_poll(opf_server *s, int64_t *tags, int32_t *converged, double *objective, int32_t *iters,
                     double *latency_s, int32_t max_n);
+/* Same with each request's status: OPF_OK (served; converged or not as the
+ * flag says), OPF_E_NUMERIC, OPF_E_TIMEOUT (shed by the admission policy:
+ * never ran, objective NaN) or the error of a failed single-instance solve. */
+int opf_server_poll_ex(opf_server *s, int64_t *tags, int32_t *status, int32_t *converged, double *objective,
+                       int32_t *iters, double *latency_s, int32_t max_n);
 
 /* x (n_global doubles) of a finished request when keep_solutions is set. */
 int opf_server_take_solution(opf_server *s, int64_t tag, double *x, int32_t n);
 
-/* [0] submitted, [1] polled, [2] queued, [3] running, [4] slots, [5] passes,
- * [6] device bytes held for slots. */
+/* [0] submitted (refused ones included), [1] polled, [2] queued,
+ * [3] running, [4] slots, [5] passes, [6] device bytes held for slots. */
 int opf_server_stats(opf_server *s, int64_t *out, int32_t n);
+/* Per model: [0] submitted, [1] served (finished after running), [2] of
+ * those converged, [3] refused at submit, [4] shed from the queue,
+ * [5] queued, [6] running, [7] slots, [8] mean service time in microseconds.
+ * submitted = served + refused + shed + queued + running. */
+int opf_server_model_stats(opf_server *s, int32_t model, int64_t *out, int32_t n);
 
 void opf_server_destroy(opf_server *s);
+
+/* Measurement helper, not part of the method: enqueues a kernel of
+ * `blocks` x `threads` threads (threads a multiple of 32, at most 1024) in
+ * which every thread runs 8 independent FP32 FMA chains for 16 * iters steps,
+ * writing one float per thread to the device buffer out (blocks * threads
+ * floats, caller-owned).  *flops (may be NULL) receives the launch's flop
+ * count (2 per FMA); time the launch with events on `stream` for the FP32
+ * FMA throughput of the device at its current clocks, the denominator of the
+ * batched engine's roofline.  OPF_E_INVALID for bad sizes, OPF_E_CUDA. */
+int opf_probe_fma(int32_t blocks, int32_t threads, int32_t iters, float *out, void *stream, double *flops);
 
 /* A CUDA stream whose kernels run only on a partition of the device's SMs
  * (a green context), e.g. to keep the long single-instance solves of large

@@ -795,7 +795,7 @@ int opf_batch_get_status(opf_batch *b, int32_t first, int32_t count, double *res
     BTRY(read_status(b));
     for (int i = 0; i < count; ++i) {
         const DevStatus &s = b->h_st[first + i];
-        if (res) { res[4 * i] = s.pres; res[4 * i + 1] = s.dres; res[4 * i + 2] = s.eprim * s.eps_rel; res[4 * i + 3] = s.edual * s.eps_rel; }
+        if (res) { res[4 * i] = s.pres; res[4 * i + 1] = s.dres; res[4 * i + 2] = s.eprim; res[4 * i + 3] = s.edual; }
         if (iters) iters[i] = (int32_t)s.iter;
         if (converged) converged[i] = s.converged;
     }

@@ -5,7 +5,8 @@
 * FP32 iterations stay within single-precision distance of the oracle;
 * mixed-precision solves reach each instance's LP optimum within 1e-6 relative
   with pres <= 1e-4, on small batches and on the full 1024-scenario batch
-  (sampled instances checked against the oracle one by one).
+  (every instance checked against the oracle's LP optimum, computed on a
+  pool of host processes).
 """
 import numpy as np
 import pytest
@@ -139,12 +140,31 @@ def test_batch_converged_objective(name, seed, n_scen):
         assert abs(obj[j] - obj_star) <= TOL_OBJ * abs(obj_star), (j, obj[j], obj_star)
 
 
-def test_full_batch_sampled_against_oracle():
+def _lp_optimum_of_scenario(args):
+    """Oracle LP optimum of load scenario `seed` of a preset feeder (runs in
+    a worker process)."""
+    name, fseed, seed = args
+    f = synth.preset_feeder(name, fseed)
+    return oracle_admm.lp_optimum(lindist.build(synth.load_scenario(f, seed)))[0]
+
+
+def oracle_lp_optima(name, fseed, seeds):
+    """LP optima of many scenarios on a spawn pool (safe after CUDA is up)."""
+    import multiprocessing as mp
+    import os
+    n = max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(n) as pool:
+        return np.array(pool.map(_lp_optimum_of_scenario, [(name, fseed, sd) for sd in seeds],
+                                 chunksize=max(1, len(seeds) // (4 * n))))
+
+
+def test_full_batch_all_instances_against_oracle():
     """The 1024-scenario batch of the 123-bus feeder as the benchmark runs it;
-    sampled instances are checked against the oracle's LP optimum."""
+    every instance's objective is checked against the oracle's LP optimum."""
     f = synth.preset_feeder("123", 2001)
     n = 1024
-    fs = scenarios(f, [4000 + j for j in range(n)])
+    seeds = [4000 + j for j in range(n)]
+    fs = scenarios(f, seeds)
     with opf.Solver.from_feeder(f) as s:
         s.precompute()
         with opf.Batch(s, n) as b:
@@ -154,9 +174,9 @@ def test_full_batch_sampled_against_oracle():
             _, obj = b.solution()
     assert ok
     assert np.all(st["converged"]) and np.all(st["pres"] <= TOL_PRES)
-    for j in (0, 1, 517, 1023):
-        obj_star, _ = oracle_admm.lp_optimum(lindist.build(fs[j]))
-        assert abs(obj[j] - obj_star) <= TOL_OBJ * abs(obj_star), (j, obj[j], obj_star)
+    obj_star = oracle_lp_optima("123", 2001, seeds)
+    rel = np.abs(obj - obj_star) / np.abs(obj_star)
+    assert np.all(rel <= TOL_OBJ), (int(np.argmax(rel)), float(rel.max()))
 
 
 def test_batch_errors():
