@@ -258,6 +258,32 @@ def with_zip_delta(feeder, seed: int, p_delta=0.5):
     return f
 
 
+def with_shunts_and_taps(feeder, seed: int, g_max=2e-3, b_max=4e-3, tap_dev=0.03):
+    """Copy of ``feeder`` with shunt admittances and off-nominal taps: every
+    bus phase gets g^sh U[0, g_max] and b^sh U[-b_max, b_max] (p.u.), every
+    line phase gets from- and to-side g^s U[0, g_max], b^s U[0, b_max] (line
+    charging) and a squared-voltage tap ratio tau U[1 - tap_dev, 1 + tap_dev].
+    Phases a bus or line does not have keep zeros and tau = 1."""
+    rng = np.random.default_rng(seed)
+    f = dict(feeder)
+    nb, nl = int(feeder["n_bus"]), len(feeder["line_from"])
+
+    def masked(mask_arr, n, lo, hi, fill):
+        v = rng.uniform(lo, hi, size=(n, 3))
+        on = np.array([[(int(m) >> p) & 1 for p in range(3)] for m in mask_arr], dtype=bool)
+        return np.where(on, v, fill)
+
+    f["bus_gsh"] = masked(feeder["bus_phases"], nb, 0.0, g_max, 0.0)
+    f["bus_bsh"] = masked(feeder["bus_phases"], nb, -b_max, b_max, 0.0)
+    f["line_gs_from"] = masked(feeder["line_phases"], nl, 0.0, g_max, 0.0)
+    f["line_bs_from"] = masked(feeder["line_phases"], nl, 0.0, b_max, 0.0)
+    f["line_gs_to"] = masked(feeder["line_phases"], nl, 0.0, g_max, 0.0)
+    f["line_bs_to"] = masked(feeder["line_phases"], nl, 0.0, b_max, 0.0)
+    f["line_tap"] = masked(feeder["line_phases"], nl, 1.0 - tap_dev, 1.0 + tap_dev, 1.0)
+    f["meta"] = dict(feeder["meta"], shunt_tap_seed=seed)
+    return f
+
+
 def random_generic(seed: int, n_global=40, n_sub=12, max_n=9, p_free=0.0):
     """Random instance of the consensus LP form (c, bounds, {A_s, b_s, idx_s}).
 

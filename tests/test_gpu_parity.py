@@ -3,6 +3,7 @@
 * FP64 iterates (x, x_s, lambda) after 100 iterations within 1e-10 relative
   (whole-grid, cluster, warp and persistent grid engines), on synthetic feeders of every size and on random
   consensus instances (rank-deficient blocks, blocks wider than 64);
+  also with non-zero shunts and off-nominal taps on every bus and line;
 * converged solves (FP64 and mixed precision) reach the LP optimum of the
   oracle within 1e-6 relative with pres <= 1e-4.
 """
@@ -292,6 +293,26 @@ def test_zip_delta_loads_match_oracle():
         xs, lam = s.locals()
     assert rel_err(xs, ref.xs) <= TOL_ITER
     assert rel_err(lam, ref.lam) <= TOL_ITER
+
+
+@pytest.mark.parametrize("name,seed,engine", [("34", 5034, opf.ENGINE_AUTO), ("123", 2001, opf.ENGINE_AUTO),
+                                              ("123", 2001, opf.ENGINE_GRID), ("13", 1001, opf.ENGINE_PERSISTENT)])
+def test_shunts_and_taps_match_oracle(name, seed, engine):
+    """Non-zero g^sh, b^sh (Eq. balance_eqns), g^s, b^s at both line ends and
+    taps tau != 1 (Eq. power_flow_eqns) on every bus and line: the library's
+    own LP rows give the oracle's FP64 iterates over 100 iterations."""
+    f = synth.with_shunts_and_taps(synth.preset_feeder(name, seed), seed=77)
+    M = lindist.build(f)
+    ref = oracle_iterates(M, 100)
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        s.solve(eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP64, engine=engine)
+        xs, lam = s.locals()
+        x, obj = s.solution()
+    assert rel_err(xs, ref.xs) <= TOL_ITER
+    assert rel_err(lam, ref.lam) <= TOL_ITER
+    assert rel_err(x, ref.x) <= TOL_ITER
+    assert abs(obj - ref.objective) <= TOL_ITER * max(1.0, abs(ref.objective))
 
 
 @pytest.mark.parametrize("precision,engine", [(opf.PREC_FP64, opf.ENGINE_AUTO), (opf.PREC_MIXED, opf.ENGINE_AUTO),

@@ -122,6 +122,158 @@ def test_lp_matches_exact_ac_flow_to_first_order(ph):
     assert errs[1] < errs[0] / 50.0
 
 
+def chain_feeder(zs, ph, loads, ysh, yi, yj, tau):
+    """Buses 0 - 1 - ... - n-1 in a chain, every line on phase set ``ph``;
+    bus 0 is the source (w = 1), bus k >= 1 has load loads[k-1] (complex, per
+    phase) and shunt ysh[k-1] = g^sh + j b^sh; line k has impedance zs[k],
+    from-side and to-side shunts yi[k], yj[k] = g^s + j b^s and squared-voltage
+    tap ratio tau[k] (per phase)."""
+    n = len(zs) + 1
+    f = two_bus(zs[0].real, zs[0].imag, ph=ph, load=loads[0])
+    f.update({
+        "n_bus": n,
+        "bus_phases": np.array([7] + [ph] * (n - 1), dtype=np.uint8),
+        "bus_wmin": np.array([[1.0] * 3] + [[0.5] * 3] * (n - 1)),
+        "bus_wmax": np.array([[1.0] * 3] + [[1.5] * 3] * (n - 1)),
+        "bus_gsh": np.vstack([np.zeros(3)] + [y.real for y in ysh]),
+        "bus_bsh": np.vstack([np.zeros(3)] + [y.imag for y in ysh]),
+        "line_from": np.arange(n - 1, dtype=np.int32), "line_to": np.arange(1, n, dtype=np.int32),
+        "line_phases": np.full(n - 1, ph, dtype=np.uint8),
+        "line_r": np.array([z.real for z in zs]), "line_x": np.array([z.imag for z in zs]),
+        "line_gs_from": np.array([y.real for y in yi]), "line_bs_from": np.array([y.imag for y in yi]),
+        "line_gs_to": np.array([y.real for y in yj]), "line_bs_to": np.array([y.imag for y in yj]),
+        "line_tap": np.array(tau),
+        "load_bus": np.arange(1, n, dtype=np.int32), "load_phases": np.full(n - 1, ph, dtype=np.uint8),
+        "load_delta": np.zeros(n - 1, dtype=np.uint8),
+        "load_a": np.array([l.real for l in loads]), "load_b": np.array([l.imag for l in loads]),
+        "load_alpha": np.zeros((n - 1, 3)), "load_beta": np.zeros((n - 1, 3)),
+    })
+    return f
+
+
+def ac_chain_flow(zs, ph, loads, ysh, yi, yj, tau, sweeps=400):
+    """Exact unbalanced AC power flow of the chain: each line is a pi model
+    (shunt yi at the from end, series impedance Z, an ideal transformer whose
+    primary voltage is sqrt(tau) times the secondary's, shunt yj at the to
+    end); a shunt admittance y at squared voltage w draws w conj(y); loads
+    have constant power.  Backward/forward sweeps from a flat start.
+    Returns w per bus and the complex power entering each line at its from
+    end (S_ij) and at its to end (S_ji), on the phases of ``ph``."""
+    idx = [p for p in range(3) if (ph >> p) & 1]
+    n = len(zs) + 1
+    t = [np.sqrt(np.asarray(tk)[idx]) for tk in tau]
+    v = [np.exp(1j * THETA[idx])]
+    for k in range(n - 1):
+        v.append(v[-1] / t[k])
+    for _ in range(sweeps):
+        s_into = None                     # power bus k+1 sends into line k+1
+        ip, s_ij, s_ji = [None] * (n - 1), [None] * (n - 1), [None] * (n - 1)
+        for k in range(n - 2, -1, -1):
+            j = k + 1
+            wj = np.abs(v[j]) ** 2
+            s_del = loads[j - 1][idx] + wj * np.conj(ysh[j - 1][idx]) + (0 if s_into is None else s_into)
+            s_t = s_del + wj * np.conj(yj[k][idx])
+            ip[k] = np.conj(s_t / v[j]) / t[k]
+            s_ji[k] = -s_del
+            s_ij[k] = v[k] * np.conj(ip[k]) + np.abs(v[k]) ** 2 * np.conj(yi[k][idx])
+            s_into = s_ij[k]
+        for k in range(n - 1):
+            zz = zs[k][np.ix_(idx, idx)]
+            v[k + 1] = (v[k] - zz @ ip[k]) / t[k]
+    w = [np.abs(vk) ** 2 for vk in v]
+    return w, s_ij, s_ji
+
+
+def chain_case(rng, ph, n_lines=2):
+    zs, loads, ysh, yi, yj, tau = [], [], [], [], [], []
+    for _ in range(n_lines):
+        r, x = rand_z(rng, 0.05)
+        zs.append(r + 1j * x)
+        loads.append(rng.uniform(0.2, 1.0, 3) + 1j * rng.uniform(0.05, 0.4, 3))
+        ysh.append(rng.uniform(0.05, 0.3, 3) + 1j * rng.uniform(-0.4, 0.4, 3))
+        yi.append(rng.uniform(0.05, 0.3, 3) + 1j * rng.uniform(0.1, 0.5, 3))
+        yj.append(rng.uniform(0.05, 0.3, 3) + 1j * rng.uniform(0.1, 0.5, 3))
+        # one tap per line on multi-phase lines: the model's drop term takes the
+        # phase voltages as balanced in magnitude, which unequal taps break at
+        # first order; per-phase values where one phase is on
+        tau.append(rng.uniform(0.95, 1.05, 3) if ph in (1, 2, 4) else np.full(3, rng.uniform(0.95, 1.05)))
+    return zs, loads, ysh, yi, yj, tau
+
+
+def chain_errors(ph, seed):
+    """LP optimum of the chain against the exact AC flow with loads and
+    shunts scaled by 0.1 and 0.01 (taps fixed): max errors of w, line flows
+    and objective at each scale, and the size of the first-order effects
+    (the voltage deviation from the no-load profile and the largest flow)."""
+    rng = np.random.default_rng(seed)
+    zs, loads, ysh, yi, yj, tau = chain_case(rng, ph)
+    idx = [p for p in range(3) if (ph >> p) & 1]
+    out = []
+    for scale in (0.1, 0.01):
+        sc = [[y * scale for y in arr] for arr in (loads, ysh, yi, yj)]
+        f = chain_feeder(zs, ph, sc[0], sc[1], sc[2], sc[3], tau)
+        M = lindist.build(f)
+        obj, xs = admm.lp_optimum(M)
+        w_ex, s_ij, s_ji = ac_chain_flow(zs, ph, sc[0], sc[1], sc[2], sc[3], tau)
+        w0 = [np.ones(len(idx))]
+        for k in range(len(zs)):
+            w0.append(w0[-1] / np.asarray(tau[k])[idx])      # no-load profile
+        ew, ef, dev, big = 0.0, 0.0, 0.0, 0.0
+        for k, nm in enumerate(M.names):
+            if nm[0] == "bus" and nm[1] >= 1:
+                pos = idx.index(nm[2])
+                ew = max(ew, abs(xs[k] - w_ex[nm[1]][pos]))
+                dev = max(dev, abs(w_ex[nm[1]][pos] - w0[nm[1]][pos]))
+            if nm[0] == "line":
+                pos = idx.index(nm[2])
+                ex = {"pij": s_ij[nm[1]].real, "qij": s_ij[nm[1]].imag,
+                      "pji": s_ji[nm[1]].real, "qji": s_ji[nm[1]].imag}[nm[3]][pos]
+                ef = max(ef, abs(xs[k] - ex))
+                big = max(big, abs(ex))
+        eo = abs(obj - float(np.sum(s_ij[0].real)))
+        out.append((ew, ef, eo, dev, big))
+    return out
+
+
+def chain_pin_holds(errs):
+    (w1, f1, o1, _, _), (w2, f2, o2, dev2, big2) = errs
+    quadratic = w2 < w1 / 50.0 and f2 < f1 / 50.0 and o2 < o1 / 50.0
+    small = w2 < 0.05 * dev2 and f2 < 0.05 * big2
+    return quadratic and small
+
+
+@pytest.mark.parametrize("ph", [7, 3, 6, 1, 2, 4])
+def test_shunts_and_taps_match_exact_ac_flow_to_first_order(ph):
+    """Eq. balance_eqns (g^sh, b^sh) and Eq. power_flow_eqns (g^s, b^s at both
+    ends, tap tau): on a three-bus chain (a bus subsystem with loads, shunts
+    and two lines, a line subsystem, a leaf) the LP's voltages, line flows
+    and objective approach the exact pi-model AC power flow quadratically as
+    the loads and shunt admittances shrink, with off-nominal taps held."""
+    assert chain_pin_holds(chain_errors(ph, 200 + ph))
+
+
+MUTATIONS = {
+    # a sign error in one shunt term, or the tap on the wrong side of the line
+    "bus g^sh sign": ("_bus_rows", lambda f: dict(f, bus_gsh=-f["bus_gsh"])),
+    "bus b^sh sign": ("_bus_rows", lambda f: dict(f, bus_bsh=-f["bus_bsh"])),
+    "from g^s sign": ("_line_rows", lambda f: dict(f, line_gs_from=-f["line_gs_from"])),
+    "from b^s sign": ("_line_rows", lambda f: dict(f, line_bs_from=-f["line_bs_from"])),
+    "to g^s sign": ("_line_rows", lambda f: dict(f, line_gs_to=-f["line_gs_to"])),
+    "to b^s sign": ("_line_rows", lambda f: dict(f, line_bs_to=-f["line_bs_to"])),
+    "tap inverted": ("_line_rows", lambda f: dict(f, line_tap=1.0 / f["line_tap"])),
+}
+
+
+@pytest.mark.parametrize("mutation", sorted(MUTATIONS))
+def test_shunt_tap_pin_catches_planted_errors(monkeypatch, mutation):
+    """The pin above fails when one shunt or tap term of the oracle's rows is
+    planted with a plausible mistake."""
+    fn, change = MUTATIONS[mutation]
+    orig = getattr(lindist, fn)
+    monkeypatch.setattr(lindist, fn, lambda f, *a, **k: orig(change(f), *a, **k))
+    assert not chain_pin_holds(chain_errors(7, 207))
+
+
 # --- Sec. II-A: load model -----------------------------------------------
 
 @pytest.mark.parametrize("alpha", [0.0, 1.0, 2.0])
