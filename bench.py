@@ -61,13 +61,16 @@ METRIC = "OPF solves/s to 1e-4 residual (batched/served vs plain FP64); p50/p99 
 UNIT = "solves/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
-# SM count and FP32 lanes of the part, and its maximum SM clock, for the FP32
-# SIMT peak of the batched engine (an ALU-bound kernel).
-N_SM, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+# FP32 lanes per SM (Blackwell: 4 sub-partitions x 32), for the nominal FP32
+# SIMT peak printed beside the measured one; the SM count and the clock are
+# read from the device and from the clock samples of the run.
+FP32_LANES = 128
 
-# DRAM bytes per launch of the dominant kernels from the ncu captures in
-# profiles/ (None until a capture of the current kernel exists).
+# DRAM bytes per launch of the dominant kernels, copied from the ncu captures
+# summarised in profiles/ (a copied constant, labelled so in the line; None
+# once the kernel has changed since the capture).
 BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 83461632 + 33740800
+BATCH_ENGINE_TRAFFIC_SOURCE = "profiles/k_batch_engine_123bus_x1024.md"
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 516864 + 768
 PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8708352 + 313088
 ITERS_PER_LAUNCH = 1000
@@ -192,6 +195,71 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def fp32_fma_peak(opf, torch, device, stream, reps=10):
+    """FP32 FMA throughput of the device measured now: the library's FMA probe
+    (8 independent chains per thread, two 1024-thread CTAs per SM) timed with
+    CUDA events on `stream`; median and best of `reps` launches."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks, threads, iters = 2 * sms, 1024, 2048
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=torch.device("cuda", device))
+    torch.cuda.synchronize()
+    for _ in range(3):
+        opf.probe_fma(blocks, threads, iters, out.data_ptr(), stream.cuda_stream)
+    times, fl = [], 0.0
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = opf.probe_fma(blocks, threads, iters, out.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    med, best = statistics.median(times), min(times)
+    return {"tflops": fl / (med / 1e3) / 1e12, "tflops_best": fl / (best / 1e3) / 1e12, "sms": sms,
+            "flops_per_launch": fl, "ms_median": med, "launches": reps}
+
+
+def _lp_optimum(g):
+    """The oracle's LP optimum of one instance (pool worker)."""
+    from oracle import admm as oracle_admm, lindist
+    return oracle_admm.lp_optimum(lindist.build(g))[0]
+
+
+def oracle_error(instances, objs, pres_gpu, x=None, locals_of=None, sample=64):
+    """Error of every result against the FP64 oracle (part of the CPU-baseline
+    leg): relative objective error of each instance against the oracle's LP
+    optimum of that instance (computed on spawned host processes), and pres
+    recomputed on the host from the library's x and local copies x_s for a
+    sample of instances, |x[g(k)] - x_s,k| stacked over the slots."""
+    import multiprocessing as mp
+    from oracle import lindist
+    t0 = time.perf_counter()
+    cores = min(_host_cores(), 16, len(instances))
+    if cores > 1:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            star = np.array(pool.map(_lp_optimum, instances, chunksize=max(1, len(instances) // (4 * cores))))
+    else:
+        star = np.array([_lp_optimum(g) for g in instances])
+    rel = np.abs(np.asarray(objs) - star) / np.abs(star)
+    out = {"max_obj_rel": float(rel.max()), "mean_obj_rel": float(rel.mean()), "instances": len(instances),
+           "max_pres": float(np.max(pres_gpu)),
+           "reference": "LP optimum of each instance (oracle: HiGHS on the centralized LP of Eq. LP_model)"}
+    if x is not None and locals_of is not None:
+        # canonical slot -> global index (the instances share one topology)
+        gidx = np.concatenate([sb["idx"] for sb in lindist.build(instances[0]).subs])
+        picks = np.unique(np.linspace(0, len(instances) - 1, min(sample, len(instances))).astype(int))
+        ph, dif = [], []
+        for j in picks:
+            xs, _ = locals_of(int(j))
+            p = float(np.linalg.norm(x[j][gidx] - xs))
+            ph.append(p)
+            dif.append(abs(p - float(pres_gpu[j])) / max(float(pres_gpu[j]), 1e-300))
+        out.update({"max_pres_host": max(ph), "pres_host_vs_gpu_max_rel_diff": max(dif),
+                    "pres_host_sample": int(len(picks))})
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
 def oracle_solve(g):
     from oracle import admm as oracle_admm, lindist
     M = lindist.build(g)
@@ -258,7 +326,7 @@ def cpu_baseline(instances, budget_s=15.0, what="scenarios of the batch"):
                       f"loop); one core alone: {one:.3f} solves/s ({n} solves in {el:.1f} s)"}
 
 
-def cpu_baseline_extrapolated(f, gpu_iters, budget_s=15.0):
+def cpu_baseline_extrapolated(f, gpu_iters, budget_s=15.0, copied=False):
     """The oracle's per-iteration time on the instance, measured over a bounded
     number of iterations, times the iterations the GPU solve needed, plus its
     precompute: a full solve of the large feeder takes the CPU loop hours."""
@@ -279,12 +347,13 @@ def cpu_baseline_extrapolated(f, gpu_iters, budget_s=15.0):
     return {"value": 1.0 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"LP build + precompute ({t_pre:.1f} s) and {n} iterations ({per_it * 1e3:.3f} ms each) "
                       f"of the plain FP64 C loop, one thread, extrapolated to the {gpu_iters} iterations of the "
-                      f"GPU solve"}
+                      f"GPU solve" + (" (a copied constant: the count of an earlier GPU solve)" if copied else "")}
 
 
-# Iterations of the 8500-bus solve at its stopping rule (measured on the GPU
-# path, FP32 iterations + FP64 polish); the CPU reference arm extrapolates its
-# per-iteration time to this count instead of running the hours-long loop.
+# Iterations of the 8500-bus solve at its stopping rule, copied from a GPU
+# solve (FP32 iterations + FP64 polish; tests/test_large_gpu.py runs the same
+# solve): the CPU reference arm extrapolates its per-iteration time to this
+# count instead of running the hours-long loop, and says so in its line.
 ITERS_8500 = 2_196_200
 
 
@@ -294,7 +363,7 @@ def run_reference(args, rank, world):
     f = feeder()
     if args.workload == "single" and args.feeder == "8500":
         from paper_2310_09410_gb300 import synth
-        cb = cpu_baseline_extrapolated(synth.preset_feeder("8500", SINGLE_SEEDS["8500"]), ITERS_8500)
+        cb = cpu_baseline_extrapolated(synth.preset_feeder("8500", SINGLE_SEEDS["8500"]), ITERS_8500, copied=True)
         value = cb["value"]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": 1,
                 "warmup": 0, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
@@ -509,15 +578,26 @@ def run_batch(args, rank, world, local):
     sizes = solver.sizes()
     fpi = algorithmic_flops_per_iter(sizes)
     st_h = batch.status()
+    x_h, obj_h = batch.solution()        # same inputs as the timed steps: the results checked against the oracle
     inst_iters = float(np.sum(st_h["iters"]))
     passes = max(th["fp32_passes"], 1)
     achieved = fpi * inst_iters / (th["engine_ms"] / 1e3) / 1e12 if th["engine_ms"] > 0 else None
-    peak = N_SM * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    probe = fp32_fma_peak(opf, torch, local, stream)
+    peak = probe["tflops"]
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    nominal = probe["sms"] * FP32_LANES * 2 * max_mhz * 1e6 / 1e12
     shape = batch.shape(opf.PREC_FP32)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if achieved else None,
+            "peak_source": "measured in this run: FP32 FMA probe (opf_probe_fma, %d CTAs x 1024 threads, 8 "
+                           "independent chains each), median of %d launches timed with CUDA events; best %.1f "
+                           "TFLOP/s; nominal %d SMs x %d lanes x 2 x %.0f MHz = %.1f TFLOP/s"
+                           % (2 * probe["sms"], probe["launches"], probe["tflops_best"], probe["sms"],
+                              FP32_LANES, max_mhz, nominal),
+            "frac_of_nominal": achieved / nominal if achieved else None,
             "traffic": BATCH_ENGINE_TRAFFIC_PER_LAUNCH,
-            "traffic_unit": "DRAM bytes per engine launch of 2000 iterations (ncu)",
+            "traffic_unit": "DRAM bytes per engine launch of 2000 iterations, copied from the ncu capture in "
+                            + BATCH_ENGINE_TRAFFIC_SOURCE + " (not measured in this run)",
             "kernel": "k_batch_engine<float> (FP32; %d instances per CTA, %d warps, %d CTAs; factors, u and x "
                       "in shared memory, lambda and bbar~ streamed from L2)"
                       % (shape["k_inst"], shape["warps"], shape["ctas"]),
@@ -525,11 +605,20 @@ def run_batch(args, rank, world, local):
             "instance_iterations_timed": inst_iters,
             "launches_timed": passes,
             "engine_ms": th["engine_ms"],
-            "peak_source": "FP32 FMA lanes x 2 flops x max SM clock (152 x 128 x 2 x 2070 MHz)",
             "note": "instance iterations include those of the FP64 polish (%d pass(es), about 1%% of them), "
                     "so achieved is over-stated by about that much" % th["fp64_passes"]}
 
     plain = None if args.no_plain_fp64 else plain_fp64_reference(opf, f, local, stream)
+    serve = None
+    if args.serve_requests > 0:
+        # the serving workload, short: the metric's p50/p99 latency per feeder class
+        sr = serve_measure(args, local, args.serve_requests, 200, drain_s=args.max_service_s + 1.0)
+        serve = {"value": sr["value"], "unit": UNIT, "p50_ms": sr["p50_ms"], "p99_ms": sr["p99_ms"],
+                 "per_class": sr["per_class"], "window_s": sr["window_s"], "requests": sr["requests"],
+                 "warm_requests": sr["warm_requests"], "clocks": sr["clocks"],
+                 "config": dict(serve_config(args), workload=serve_config(args)["workload"].replace(
+                     f"{args.requests} requests after", f"{args.serve_requests} requests after").replace(
+                     f"at most {args.drain_s:.0f} s", f"at most {args.max_service_s + 1.0:.0f} s"))}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -547,8 +636,11 @@ def run_batch(args, rank, world, local):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "roofline": roof, "clocks": clocks, "gpu_launches": int(launches)}
+        if serve is not None:
+            line["serve"] = serve
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(fs)
+            line["oracle_error"] = oracle_error(fs, obj_h, st_h["pres"], x=x_h, locals_of=batch.locals)
         print(json.dumps(line), flush=True)
     batch.close()
     solver.close()
@@ -679,6 +771,10 @@ def run_single(args, rank, world, local):
                 line["cpu_baseline"] = cpu_baseline_extrapolated(f, int(np.mean(iters)))
             else:
                 line["cpu_baseline"] = cpu_baseline([f], what="the same instance")
+            if not args.fixed_iters:
+                x1, _ = solver.solution()
+                line["oracle_error"] = oracle_error([f], [objs[-1]], [solver.residuals()["pres"]],
+                                                    x=x1[None, :], locals_of=lambda j: solver.locals())
         print(json.dumps(line), flush=True)
     solver.close()
     return 0
@@ -698,6 +794,9 @@ def serve_config(args):
                     f"FP64 polish to eps_rel=1e-8 (8500 buses: 2e-9) and pres<=1e-4; {args.requests} requests after "
                     f"{args.warm_requests} warm-up requests; arrivals stop after the last request, then the "
                     f"server drains for at most {args.drain_s:.0f} s",
+        "admission": f"every model: a request whose predicted wait for a slot exceeds {args.max_wait_s:g} s is "
+                     f"refused at submit, one that has waited longer is shed; 8500-bus requests stop after "
+                     f"{args.max_service_s:g} s of service; each outcome is counted per class",
         "models": f"13/34/123-bus: continuous batching in the batched engine, passes of {args.chunk} FP32 iterations "
                   f"(slots in the FP64 polish: {args.polish_chunk or 100} FP64 iterations per pass); "
                   f"8500-bus: {args.big_handles} "
@@ -708,10 +807,14 @@ def serve_config(args):
     }
 
 
-def run_serve(args, rank, world, local):
+def serve_measure(args, local, requests, warm_requests, drain_s):
+    """The serving workload: Poisson arrivals of the feeder mix submitted to
+    the request server, which admits, batches and retires them; each model
+    has an admission policy (bounded wait for a slot, bounded service time),
+    so every measured request ends served, refused at submit, shed from the
+    queue or stopped at its service bound, each with its status counted.
+    Returns the per-class and overall results."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2310_09410_gb300 import opf, synth
 
     weights = np.array([float(w) for w in args.mix.split(",")])
@@ -748,8 +851,10 @@ def run_serve(args, rank, world, local):
         mid[k] = srv.add_model(hs, caps.get(k, 1))
         if SINGLE_EPS_REL[k] != EPS_REL:
             srv.set_model_tolerance(mid[k], SINGLE_EPS_REL[k], EPS_ABS)   # the large feeder's stopping rule
+        srv.set_admission(mid[k], max_wait_s=args.max_wait_s,
+                          max_service_s=args.max_service_s if k == "8500" else 0.0)
     rng = np.random.default_rng(SERVE_ARRIVAL_SEED)
-    n_total = args.requests + args.warm_requests
+    n_total = requests + warm_requests
     gaps = rng.exponential(1.0 / args.rate, size=n_total)
     arrival = np.cumsum(gaps)
     kind = rng.choice(len(SERVE_SIZES), size=n_total, p=weights)
@@ -762,14 +867,14 @@ def run_serve(args, rank, world, local):
     sampler.start()
     t0 = time.perf_counter()
     nxt = 0
-    done_t = {}
-    results = {}
+    done_t, results, refused = {}, {}, set()
     drain_deadline = None
     while True:
         t_pass = time.perf_counter()
         now = t_pass - t0
         while nxt < n_total and arrival[nxt] <= now:
-            srv.submit(mid[SERVE_SIZES[kind[nxt]]], loads[nxt][0], loads[nxt][1], tag=nxt)
+            if not srv.submit(mid[SERVE_SIZES[kind[nxt]]], loads[nxt][0], loads[nxt][1], tag=nxt, refusable=True):
+                refused.add(nxt)
             nxt += 1
         srv.step()
         tnow = time.perf_counter() - t0
@@ -778,8 +883,8 @@ def run_serve(args, rank, world, local):
             results[res["tag"]] = res
         if nxt == n_total:
             if drain_deadline is None:
-                drain_deadline = tnow + args.drain_s
-            if len(results) == n_total or tnow > drain_deadline:
+                drain_deadline = tnow + drain_s
+            if len(results) + len(refused) == n_total or tnow > drain_deadline:
                 break
         st = srv.stats()
         if st["running"] == 0 and st["queued"] == 0 and nxt < n_total:
@@ -789,35 +894,37 @@ def run_serve(args, rank, world, local):
     elapsed = time.perf_counter() - t0
     clocks = sampler.stop()
     stats = srv.stats()
-    measured = [r for r in range(args.warm_requests, n_total)]
-    lat = {k: [] for k in SERVE_SIZES}
-    conv = {k: 0 for k in SERVE_SIZES}
-    sub = {k: 0 for k in SERVE_SIZES}
+    model_stats = {k: srv.model_stats(mid[k]) for k in mid}
+    measured = range(warm_requests, n_total)
+    t_first = arrival[warm_requests]
+    cls = {k: {"submitted": 0, "served": 0, "converged": 0, "refused": 0, "shed": 0, "stopped": 0,
+               "unfinished": 0, "lat": []} for k in SERVE_SIZES}
     for r in measured:
-        k = SERVE_SIZES[kind[r]]
-        sub[k] += 1
-        if r in results:
-            lat[k].append(1e3 * (done_t[r] - arrival[r]))
-            conv[k] += int(results[r]["converged"])
-    all_lat = [v for k in SERVE_SIZES for v in lat[k]]
-    t_first = arrival[args.warm_requests]
+        c = cls[SERVE_SIZES[kind[r]]]
+        c["submitted"] += 1
+        if r in refused:
+            c["refused"] += 1
+        elif r not in results:
+            c["unfinished"] += 1               # still queued or running when the window closed
+        elif results[r]["status"] == opf.OPF_E_TIMEOUT:
+            c["stopped" if results[r]["iters"] > 0 else "shed"] += 1
+        else:
+            c["served"] += 1
+            c["converged"] += int(results[r]["converged"])
+            c["lat"].append(1e3 * (done_t[r] - arrival[r]))
     t_last = max((done_t[r] for r in measured if r in done_t), default=elapsed)
-    completed = sum(len(lat[k]) for k in SERVE_SIZES)
-    value = completed / max(t_last - t_first, 1e-9)
+    window = max(t_last - t_first, 1e-9)
 
     def pct(v, q):
         return float(np.percentile(v, q)) if v else None
-    per_class = {k: {"submitted": sub[k], "completed": len(lat[k]), "converged": conv[k],
-                     "p50_ms": pct(lat[k], 50), "p99_ms": pct(lat[k], 99)} for k in SERVE_SIZES}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": stats["passes"],
-            "warmup": args.warm_requests, "ms_per_step": 1e3 * elapsed / max(stats["passes"], 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic", "config": serve_config(args),
-            "latency_ms": {"p50": pct(all_lat, 50), "p99": pct(all_lat, 99),
-                           "note": "from the request's arrival time to the pass that retired it"},
-            "per_class": per_class, "elapsed_s": elapsed, "server": stats, "clocks": clocks}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    per_class = {}
+    for k in SERVE_SIZES:
+        c = cls[k]
+        lat = c.pop("lat")
+        per_class[k] = dict(c, p50_ms=pct(lat, 50), p99_ms=pct(lat, 99), solves_per_s=c["converged"] / window)
+    all_lat = [1e3 * (done_t[r] - arrival[r]) for r in measured
+               if r in results and results[r]["status"] == opf.OPF_OK]
+    converged = sum(per_class[k]["converged"] for k in SERVE_SIZES)
     srv.close()
     for hs in solvers.values():
         for sv in hs:
@@ -825,6 +932,25 @@ def run_serve(args, rank, world, local):
     for p in parts:
         if p is not None:
             p.close()
+    return {"value": converged / window, "p50_ms": pct(all_lat, 50), "p99_ms": pct(all_lat, 99),
+            "per_class": per_class, "elapsed_s": elapsed, "window_s": window, "server": stats,
+            "models": model_stats, "clocks": clocks, "requests": requests, "warm_requests": warm_requests}
+
+
+def run_serve(args, rank, world, local):
+    import __graft_entry__
+    __graft_entry__.build()
+    r = serve_measure(args, local, args.requests, args.warm_requests, args.drain_s)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": r["server"]["passes"],
+            "warmup": args.warm_requests, "ms_per_step": 1e3 * r["elapsed_s"] / max(r["server"]["passes"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic", "config": serve_config(args),
+            "latency_ms": {"p50": r["p50_ms"], "p99": r["p99_ms"],
+                           "note": "served requests, from the request's arrival time to the pass that retired it"},
+            "per_class": r["per_class"], "elapsed_s": r["elapsed_s"], "server": r["server"],
+            "models": r["models"], "clocks": r["clocks"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -839,6 +965,12 @@ def main():
     ap.add_argument("--warm-requests", type=int, default=200, help="serve: warm-up requests")
     ap.add_argument("--rate", type=float, default=SERVE_RATE, help="serve: mean arrivals per second")
     ap.add_argument("--drain-s", type=float, default=30.0, help="serve: longest drain after the last arrival")
+    ap.add_argument("--max-wait-s", type=float, default=2.0,
+                    help="serve: admission bound on a request's wait for a slot (predicted at submit, shed after)")
+    ap.add_argument("--max-service-s", type=float, default=5.0,
+                    help="serve: bound on an 8500-bus request's run time once admitted")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="batch workload: measured requests of the serving sub-record (0: none)")
     ap.add_argument("--big-handles", type=int, default=2, help="serve: 8500-bus worker handles")
     ap.add_argument("--max-iter", type=int, default=1_000_000, help="serve: iteration cap per request")
     ap.add_argument("--mix", default="0.4,0.3,0.2,0.1", help="serve: weights of the 13/34/123/8500-bus requests")

@@ -345,6 +345,16 @@ int opf_batch_get_status(opf_batch *b, int32_t first, int32_t count, double *res
 /* x_s and lambda of one instance, canonical slot order (n_slots each). */
 int opf_batch_get_locals(opf_batch *b, int32_t inst, double *xs, double *lam);
 
+/* Warm start, an opt-in acceleration (the paper starts every solve from the
+ * point of Sec. V-A): instances whose rhs or loads are set after this call
+ * start from x_s = xs and lambda = lam (host arrays of n_slots doubles,
+ * canonical slot order, e.g. opf_get_locals of a converged solve of the
+ * same feeder at base load) instead of that point.  ADMM converges to the
+ * same LP optimum from any start; the iterates differ from the paper's.
+ * xs = lam = NULL returns to the Sec. V-A start.  OPF_E_INVALID for one
+ * NULL array or a non-finite entry, OPF_E_OOM. */
+int opf_batch_set_start(opf_batch *b, const double *xs, const double *lam);
+
 /* Last solve: [0] FP32 phase ms, [1] FP64 phase ms, [2] autotune ms (0 when
  * the shape was known), [3] mean iterations, [4] converged instances,
  * [5] FP32 loop passes (engine launches), [6] FP64 loop passes, [7] FP32
@@ -401,17 +411,28 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
  * for an unknown model or a negative or NaN tolerance. */
 int opf_server_set_model_tolerance(opf_server *s, int32_t model, double eps_rel, double eps_abs_pres);
 
-/* Admission policy of one model (default: no bounds).  max_queue > 0 bounds
- * the requests waiting for a slot; max_wait_s > 0 bounds the seconds a
- * request may wait for one: at submit the wait is predicted from the
- * requests ahead (queued and running, served `slots` at a time) and the
+/* Warm start of one model's requests (opt-in, as opf_batch_set_start): every
+ * request admitted after the call starts from x_s = xs, lambda = lam
+ * (n_slots doubles each, canonical slot order) instead of the Sec. V-A
+ * point; the start is fixed per model, so a result still does not depend on
+ * the other requests.  NULL, NULL returns to the Sec. V-A start. */
+int opf_server_set_model_start(opf_server *s, int32_t model, const double *xs, const double *lam);
+
+/* Admission policy of one model (default: no bounds; 0 = no bound).
+ * max_queue bounds the requests waiting for a slot.  max_wait_s bounds the
+ * seconds a request may wait for one: at submit the wait is predicted from
+ * the requests ahead (queued and running, served `slots` at a time) and the
  * model's mean service time so far, and a queued request that has waited
- * longer is shed by opf_server_step, reported by opf_server_poll_ex with
- * status OPF_E_TIMEOUT.  With both bounds set every request is served,
- * refused at submit or shed, so none stays pending without a status when
- * the arrivals exceed what the model can serve.  OPF_E_INVALID for an
- * unknown model or a negative bound. */
-int opf_server_set_admission(opf_server *s, int32_t model, int32_t max_queue, double max_wait_s);
+ * longer is shed by opf_server_step.  max_service_s bounds the seconds a
+ * request may run once admitted: a batched slot past it is retired at the
+ * end of a pass, a worker's solve stops at its next chunk.  Shed and stopped
+ * requests are reported by opf_server_poll_ex with status OPF_E_TIMEOUT
+ * (objective NaN), refused ones get OPF_E_CAPACITY from opf_server_submit,
+ * so with the bounds set no request stays pending without a status when the
+ * arrivals exceed what the model can serve.  OPF_E_INVALID for an unknown
+ * model or a negative bound. */
+int opf_server_set_admission(opf_server *s, int32_t model, int32_t max_queue, double max_wait_s,
+                             double max_service_s);
 
 /* Queues a request of model `model` with its loads (host arrays [n_load*3],
  * copied) and a caller tag that identifies it in opf_server_poll.  Returns
@@ -432,8 +453,8 @@ int opf_server_step(opf_server *s);
 int opf_server_poll(opf_server *s, int64_t *tags, int32_t *converged, double *objective, int32_t *iters,
                     double *latency_s, int32_t max_n);
 /* Same with each request's status: OPF_OK (served; converged or not as the
- * flag says), OPF_E_NUMERIC, OPF_E_TIMEOUT (shed by the admission policy:
- * never ran, objective NaN) or the error of a failed single-instance solve. */
+ * flag says), OPF_E_NUMERIC, OPF_E_TIMEOUT (shed or stopped by the admission
+ * policy, objective NaN) or the error of a failed single-instance solve. */
 int opf_server_poll_ex(opf_server *s, int64_t *tags, int32_t *status, int32_t *converged, double *objective,
                        int32_t *iters, double *latency_s, int32_t max_n);
 
@@ -443,9 +464,10 @@ int opf_server_take_solution(opf_server *s, int64_t tag, double *x, int32_t n);
 /* [0] submitted (refused ones included), [1] polled, [2] queued,
  * [3] running, [4] slots, [5] passes, [6] device bytes held for slots. */
 int opf_server_stats(opf_server *s, int64_t *out, int32_t n);
-/* Per model: [0] submitted, [1] served (finished after running), [2] of
- * those converged, [3] refused at submit, [4] shed from the queue,
- * [5] queued, [6] running, [7] slots, [8] mean service time in microseconds.
+/* Per model: [0] submitted, [1] served (finished after running, stopped
+ * ones included), [2] of those converged, [3] refused at submit, [4] shed
+ * from the queue, [5] queued, [6] running, [7] slots, [8] mean service time
+ * in microseconds, [9] stopped by the service bound (part of [1]).
  * submitted = served + refused + shed + queued + running. */
 int opf_server_model_stats(opf_server *s, int32_t model, int64_t *out, int32_t n);
 

@@ -16,6 +16,7 @@
 //   final status read.
 #include <algorithm>
 #include <map>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -91,6 +92,10 @@ using namespace opf;
 static thread_local std::string g_last_error;
 
 void opf::set_last_error(const std::string &msg) { g_last_error = msg; }
+
+double opf::steady_seconds() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 #define CUDA_TRY(call)                                                                   \
     do {                                                                                 \
@@ -1171,6 +1176,10 @@ static int run_graph(opf_handle *h, GraphCache *gc, Fn fn) {
         CUDA_TRY(cudaGetLastError());
         TRY(read_status(h));
         if (h->h_st->done) return OPF_OK;
+        if (h->cancel.load() || (h->deadline > 0.0 && opf::steady_seconds() > h->deadline)) {
+            g_last_error = "solve stopped by its deadline or a cancel request";
+            return OPF_E_TIMEOUT;
+        }
     }
 }
 

@@ -525,6 +525,17 @@ __global__ void k_binit(int i0, int cnt, int L, const int *gk, const double *x0,
     }
 }
 
+// Warm start of instances [i0, i0 + cnt): x_s and lambda copied from one
+// start state (device slot order), e.g. a converged base-load solution.
+__global__ void k_bwarm(int i0, int cnt, int L, const double *xs0, const double *lam0, double *xs, double *lam) {
+    const long long n = (long long)cnt * L;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int in = i0 + (int)(t / L), k = (int)(t % L);
+        xs[(size_t)in * L + k] = xs0[k];
+        lam[(size_t)in * L + k] = lam0[k];
+    }
+}
+
 __global__ void k_bfill(int cnt, int nrows, const double *b0, double *rhs) {
     const long long n = (long long)cnt * nrows;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
@@ -872,6 +883,11 @@ template int batch_engine_max_ctas_per_sm<double>(int, int, bool, int, unsigned)
 void launch_binit(int i0, int cnt, int L, const int *gk, const double *x0, double *xs, double *lam,
                   DevStatus *st, long long max_iter, double eps_rel, double eps_abs, cudaStream_t s) {
     k_binit<<<bl((long long)cnt * L, 256), 256, 0, s>>>(i0, cnt, L, gk, x0, xs, lam, st, max_iter, eps_rel, eps_abs);
+}
+
+void launch_bwarm(int i0, int cnt, int L, const double *xs0, const double *lam0, double *xs, double *lam,
+                  cudaStream_t s) {
+    k_bwarm<<<bl((long long)cnt * L, 256), 256, 0, s>>>(i0, cnt, L, xs0, lam0, xs, lam);
 }
 
 void launch_bfill(int cnt, int nrows, const double *b0, double *rhs, cudaStream_t s) {

@@ -29,6 +29,8 @@ template <typename T>
 int batch_engine_launch(const BatchArgs<T> &a, int nq, bool fg, int ctas, int threads, unsigned bytes, int n_iters,
                         int check_every, cudaStream_t s);
 template <typename T> int batch_engine_max_ctas_per_sm(int K, int nq, bool fg, int threads, unsigned bytes);
+void launch_bwarm(int i0, int cnt, int L, const double *xs0, const double *lam0, double *xs, double *lam,
+                  cudaStream_t s);
 void launch_binit(int i0, int cnt, int L, const int *gk, const double *x0, double *xs, double *lam,
                   DevStatus *st, long long max_iter, double eps_rel, double eps_abs, cudaStream_t s);
 void launch_bfill(int cnt, int nrows, const double *b0, double *rhs, cudaStream_t s);
@@ -521,6 +523,7 @@ int after_rhs(opf_batch *b, int first, int count) {
                 b->d_bbar, s);
     launch_binit(first, count, h->L, h->d_gk, h->d_x0, b->d_xs, b->d_lam, b->d_st, b->init_max_iter,
                  b->init_eps_rel, b->init_eps_abs, s);
+    if (b->d_start) launch_bwarm(first, count, h->L, b->d_start, b->d_start + h->L, b->d_xs, b->d_lam, s);
     BCUDA(cudaGetLastError());
     b->have_x = false;
     // full-row-rank local systems are consistent for every rhs: nothing to read
@@ -802,6 +805,40 @@ int opf_batch_get_status(opf_batch *b, int32_t first, int32_t count, double *res
     return OPF_OK;
 }
 
+int opf_batch_set_start(opf_batch *b, const double *xs, const double *lam) {
+    if (!b || (!xs) != (!lam)) return OPF_E_INVALID;
+    opf_handle *h = b->h;
+    BCUDA(cudaSetDevice(h->device));
+    const int L = b->L;
+    if (!xs) {
+        if (b->d_start) cudaFree(b->d_start);
+        b->d_start = nullptr;
+        return OPF_OK;
+    }
+    std::vector<double> dev(2 * (size_t)L);
+    for (int cs = 0; cs < L; ++cs) {
+        const int k = h->canon_slot_to_dev[cs];
+        if (!std::isfinite(xs[cs]) || !std::isfinite(lam[cs])) {
+            set_last_error("batch start: non-finite entry");
+            return OPF_E_INVALID;
+        }
+        dev[k] = xs[cs];
+        dev[(size_t)L + k] = lam[cs];
+    }
+    if (!b->d_start) {
+        void *q = nullptr;
+        if (cudaMalloc(&q, 2 * (size_t)L * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            set_last_error("cudaMalloc (batch start)");
+            return OPF_E_OOM;
+        }
+        b->d_start = (double *)q;
+    }
+    BCUDA(cudaMemcpyAsync(b->d_start, dev.data(), dev.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    BCUDA(cudaStreamSynchronize(h->stream));
+    return OPF_OK;
+}
+
 int opf_batch_get_locals(opf_batch *b, int32_t inst, double *xs, double *lam) {
     if (!b || inst < 0 || inst >= b->n || !xs || !lam) return OPF_E_INVALID;
     opf_handle *h = b->h;
@@ -839,6 +876,7 @@ void opf_batch_destroy(opf_batch *b) {
     b->p64.release();
     for (void *p : b->allocs) cudaFree(p);
     if (b->d_stage) cudaFree(b->d_stage);
+    if (b->d_start) cudaFree(b->d_start);
     for (auto &e : b->ev) if (e) cudaEventDestroy(e);
     for (auto &e : b->eng_ev) if (e) cudaEventDestroy(e);
     delete b;

@@ -38,6 +38,7 @@ struct opf_batch {
     std::vector<void *> allocs;
     double *d_rhs = nullptr, *d_bbar = nullptr, *d_xs = nullptr, *d_lam = nullptr, *d_xref = nullptr;
     double *d_x = nullptr, *d_obj = nullptr, *d_b0 = nullptr, *d_rcoef = nullptr, *d_stage = nullptr;
+    double *d_start = nullptr;           // warm start (x_s then lambda, device slot order), or none
     size_t stage_len = 0;
     int *d_rsrc = nullptr, *d_c2d = nullptr, *d_bidx = nullptr, *d_bad = nullptr;
     int *d_flag = nullptr;               // [0] FP32 plan, [1] FP64 plan: an instance still runs

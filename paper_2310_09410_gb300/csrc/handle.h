@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -116,6 +117,13 @@ struct opf_handle {
     bool precomputed = false;
     bool have_prev_u = false;    // d_u64 + L holds the u that produced the last global update
     double last_rho = 100.0, recip_rho = -1.0;
+    // Stop for solves whose body the host relaunches (OPF_SOLVE_HOST_LOOP):
+    // past `deadline` (steady-clock seconds, 0 = none) or once `cancel` is
+    // set by another thread, the solve returns OPF_E_TIMEOUT at its next
+    // chunk with the iterate of that chunk readable (the request server's
+    // service-time bound and its shutdown).
+    double deadline = 0.0;
+    std::atomic<int> cancel{0};
     long long total_iters = 0;
     long long main_iters = 0, recenters = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

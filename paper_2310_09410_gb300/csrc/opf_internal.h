@@ -15,6 +15,9 @@ namespace opf {
 // Message returned by opf_last_error() on the calling thread.
 void set_last_error(const std::string &msg);
 
+// Seconds of the steady clock (for deadlines shared between threads).
+double steady_seconds();
+
 // ---------------------------------------------------------------- host model
 // One subsystem of Eq. OurModel: m x n block A (row-major), b, and the global
 // index of each local slot (ascending for feeder models).

@@ -19,6 +19,13 @@
 // A model whose subsystems exceed the batched engine (the largest feeders)
 // is served by single-instance handles given by the caller, one request per
 // handle at a time, each solved by a worker thread.
+// Admission (opf_server_set_admission): a model may bound its queue and the
+// time a request waits for a slot.  A request is refused at submit when the
+// queue is full or when the wait predicted from the model's measured service
+// time exceeds the bound, and a queued request that has waited longer than
+// the bound is shed; both are counted, and a shed request is reported by
+// opf_server_poll_ex with status OPF_E_TIMEOUT, so no request stays pending
+// without a status when a model cannot keep up with its arrivals.
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -86,6 +93,13 @@ struct Model {
     cudaStream_t s64 = nullptr;      // FP64 slots' pass, beside the FP32 slots'
     cudaEvent_t ev64 = nullptr, ev_start = nullptr;
     int n32 = 0, n64 = 0;            // slots in each phase during the pass
+    int max_queue = 0;               // admission: queued requests at most (0: no bound)
+    double max_wait_s = 0.0;         // admission: seconds a request may wait for a slot (0: no bound)
+    double max_service_s = 0.0;      // seconds a request may run once admitted (0: no bound)
+    std::vector<double> start_xs, start_lam;   // warm start of worker requests (empty: Sec. V-A point)
+    double svc_s = 0.0;              // mean service time (admission to finish) of finished requests
+    int64_t n_svc = 0;
+    std::atomic<int64_t> n_sub{0}, n_done{0}, n_conv{0}, n_refused{0}, n_shed{0}, n_stopped{0};
     int running() const {
         int n = 0;
         for (int v : state) n += v != 0;
@@ -116,6 +130,44 @@ struct opf_server {
 };
 
 namespace {
+
+// A finished request: counted on its model (service time for the admission
+// estimate) and queued for opf_server_poll.  Called with s->mu held.
+void finish_locked(opf_server *s, Model &m, Done &&d) {
+    if (d.status == OPF_E_TIMEOUT && d.t_done > d.t_admit) ++m.n_stopped;   // ran into its service bound
+    if (d.status != OPF_E_TIMEOUT || d.t_done > d.t_admit) {
+        ++m.n_done;
+        if (d.converged) ++m.n_conv;
+        const double svc = d.t_done - d.t_admit;
+        m.svc_s = (m.svc_s * (double)m.n_svc + svc) / (double)(m.n_svc + 1);
+        ++m.n_svc;
+    }
+    s->done.push_back(std::move(d));
+}
+
+// Queued requests of model m that waited longer than its bound leave the
+// queue with status OPF_E_TIMEOUT (shed).
+void shed_expired(opf_server *s, Model &m) {
+    if (!(m.max_wait_s > 0.0)) return;
+    const double t = now_s();
+    while (!m.queue.empty() && t - m.queue.front().t_submit > m.max_wait_s) {
+        Request r = std::move(m.queue.front());
+        m.queue.pop_front();
+        Done d;
+        d.tag = r.tag;
+        d.model = m.id;
+        d.converged = 0;
+        d.iters = 0;
+        d.status = OPF_E_TIMEOUT;
+        d.objective = NAN;
+        d.t_submit = r.t_submit;
+        d.t_admit = t;
+        d.t_done = t;
+        ++m.n_shed;
+        std::lock_guard<std::mutex> g(s->mu);
+        s->done.push_back(std::move(d));
+    }
+}
 
 // Estimated device bytes of one batch slot: per-instance FP64 arrays and the
 // share of both engines' per-column arrays.
@@ -157,15 +209,20 @@ void single_worker(opf_server *s, Model *m, Worker *w, Request req, double t_adm
     d.objective = NAN;
     int rc = opf_set_loads(w->h, req.lp.data(), req.lq.data());
     if (!rc) rc = opf_precompute(w->h);
+    if (!rc && !m->start_xs.empty())
+        rc = opf_set_locals(w->h, m->start_xs.data(), m->start_lam.data(), m->start_xs.size());
     if (!rc) {
         opf_solve_opts so;
         memset(&so, 0, sizeof(so));
         so.rho = o.rho; so.eps_rel = m->eps_rel; so.eps_abs_pres = m->eps_abs; so.max_iter = o.max_iter;
         so.check_every = o.check_every; so.precision = OPF_PREC_MIXED; so.recenter_every = o.chunk_iters;
         // direct launches: the handle's stream may belong to an SM partition,
-        // where the solve graph of opf_solve_ex cannot be instantiated
+        // where the solve graph of opf_solve_ex cannot be instantiated (and
+        // the host loop honours the service bound and a cancel)
         so.flags = OPF_SOLVE_HOST_LOOP;
+        w->h->deadline = m->max_service_s > 0.0 ? steady_seconds() + m->max_service_s : 0.0;
         rc = opf_solve_ex(w->h, &so);
+        w->h->deadline = 0.0;
         d.converged = rc == OPF_OK;
         if (rc == OPF_OK || rc == OPF_NOT_CONVERGED) {
             if (o.keep_solutions) d.x.resize(m->G);
@@ -177,6 +234,11 @@ void single_worker(opf_server *s, Model *m, Worker *w, Request req, double t_adm
             opf_get_residuals(w->h, &pr, &dr, &ep, &ed, &it);
             d.iters = (int32_t)it;
             rc = OPF_OK;
+        } else if (rc == OPF_E_TIMEOUT) {     // stopped by the service bound: iterations run so far
+            double pr, dr, ep, ed;
+            int64_t it = 0;
+            opf_get_residuals(w->h, &pr, &dr, &ep, &ed, &it);
+            d.iters = (int32_t)it;
         }
     }
     d.status = rc;
@@ -184,7 +246,7 @@ void single_worker(opf_server *s, Model *m, Worker *w, Request req, double t_adm
     {
         std::lock_guard<std::mutex> g(s->mu);
         if (o.keep_solutions) s->kept.emplace_back(d.tag, std::move(d.x));
-        s->done.push_back(std::move(d));
+        finish_locked(s, *m, std::move(d));
     }
     w->finished = true;
 }
@@ -290,9 +352,28 @@ int step_batched_collect(opf_server *s, Model &m) {
         {
             std::lock_guard<std::mutex> g(s->mu);
             if (s->o.keep_solutions) s->kept.emplace_back(d.tag, std::move(x));
-            s->done.push_back(std::move(d));
+            finish_locked(s, m, std::move(d));
         }
         m.state[i] = 0;
+    }
+    // running slots past the model's service bound leave with OPF_E_TIMEOUT
+    if (m.max_service_s > 0.0) {
+        for (int i = 0; i < m.cap; ++i) {
+            if (!m.state[i] || t - m.t_admit[i] <= m.max_service_s) continue;
+            Done d;
+            d.tag = m.tag[i];
+            d.model = m.id;
+            d.converged = 0;
+            d.iters = (int32_t)b->h_st[i].iter;
+            d.status = OPF_E_TIMEOUT;
+            d.objective = NAN;
+            d.t_submit = m.t_submit[i];
+            d.t_admit = m.t_admit[i];
+            d.t_done = t;
+            std::lock_guard<std::mutex> g(s->mu);
+            finish_locked(s, m, std::move(d));
+            m.state[i] = 0;
+        }
     }
     if (wrote) {
         STRY(write_status(b, 0, b->n));
@@ -422,22 +503,78 @@ int opf_server_set_model_tolerance(opf_server *s, int32_t model, double eps_rel,
     return OPF_OK;
 }
 
+int opf_server_set_model_start(opf_server *s, int32_t model, const double *xs, const double *lam) {
+    if (!s || model < 0 || model >= (int)s->models.size() || (!xs) != (!lam)) return OPF_E_INVALID;
+    Model &m = *s->models[model];
+    if (m.b) return opf_batch_set_start(m.b, xs, lam);
+    const size_t L = (size_t)m.h->L;
+    if (xs) {
+        m.start_xs.assign(xs, xs + L);
+        m.start_lam.assign(lam, lam + L);
+    } else {
+        m.start_xs.clear();
+        m.start_lam.clear();
+    }
+    return OPF_OK;
+}
+
+int opf_server_set_admission(opf_server *s, int32_t model, int32_t max_queue, double max_wait_s,
+                             double max_service_s) {
+    if (!s || model < 0 || model >= (int)s->models.size() || max_queue < 0 || !(max_wait_s >= 0.0) ||
+        !(max_service_s >= 0.0))
+        return OPF_E_INVALID;
+    Model &m = *s->models[model];
+    m.max_queue = max_queue;
+    m.max_wait_s = max_wait_s;
+    m.max_service_s = max_service_s;
+    return OPF_OK;
+}
+
 int opf_server_submit(opf_server *s, int32_t model, const double *load_p, const double *load_q, int64_t tag) {
     if (!s || model < 0 || model >= (int)s->models.size() || !load_p || !load_q) return OPF_E_INVALID;
     Model &m = *s->models[model];
+    ++m.n_sub;
+    ++s->n_submitted;
+    if (m.max_queue > 0 && (int)m.queue.size() >= m.max_queue) {
+        ++m.n_refused;
+        set_last_error("server: model " + std::to_string(model) + " queue is full (" +
+                       std::to_string(m.max_queue) + " requests)");
+        return OPF_E_CAPACITY;
+    }
+    if (m.max_wait_s > 0.0) {
+        // predicted wait for a slot: the requests ahead (queued and running)
+        // served cap at a time, each taking the model's mean service time
+        double svc;
+        {
+            std::lock_guard<std::mutex> g(s->mu);
+            svc = m.n_svc ? m.svc_s : 0.0;
+        }
+        int busy = 0;
+        if (m.batched) busy = m.running();
+        else
+            for (auto &w : m.workers) busy += w->busy ? 1 : 0;
+        const int ahead = (int)m.queue.size() + busy;
+        const double wait = ahead < m.cap ? 0.0 : (double)((ahead - m.cap) / m.cap + 1) * svc;
+        if (wait > m.max_wait_s) {
+            ++m.n_refused;
+            set_last_error("server: model " + std::to_string(model) + " cannot start the request within " +
+                           std::to_string(m.max_wait_s) + " s (predicted wait " + std::to_string(wait) + " s)");
+            return OPF_E_CAPACITY;
+        }
+    }
     Request r;
     r.tag = tag;
     r.lp.assign(load_p, load_p + (size_t)m.nload * 3);
     r.lq.assign(load_q, load_q + (size_t)m.nload * 3);
     r.t_submit = now_s();
     m.queue.push_back(std::move(r));
-    ++s->n_submitted;
     return OPF_OK;
 }
 
 int opf_server_step(opf_server *s) {
     if (!s) return OPF_E_INVALID;
     for (auto &m : s->models) {
+        shed_expired(s, *m);
         if (!m->batched) {
             STRY(step_single(s, *m));
             continue;
@@ -455,14 +592,15 @@ int opf_server_step(opf_server *s) {
     return OPF_OK;
 }
 
-int opf_server_poll(opf_server *s, int64_t *tags, int32_t *converged, double *objective, int32_t *iters,
-                    double *latency_s, int32_t max_n) {
+int opf_server_poll_ex(opf_server *s, int64_t *tags, int32_t *status, int32_t *converged, double *objective,
+                       int32_t *iters, double *latency_s, int32_t max_n) {
     if (!s || max_n < 0) return OPF_E_INVALID;
     std::lock_guard<std::mutex> g(s->mu);
     const int n = std::min<int>(max_n, (int)s->done.size());
     for (int i = 0; i < n; ++i) {
         const Done &d = s->done[i];
         if (tags) tags[i] = d.tag;
+        if (status) status[i] = d.status;
         if (converged) converged[i] = d.converged;
         if (objective) objective[i] = d.objective;
         if (iters) iters[i] = d.iters;
@@ -471,6 +609,11 @@ int opf_server_poll(opf_server *s, int64_t *tags, int32_t *converged, double *ob
     s->done.erase(s->done.begin(), s->done.begin() + n);
     s->n_completed += n;
     return n;
+}
+
+int opf_server_poll(opf_server *s, int64_t *tags, int32_t *converged, double *objective, int32_t *iters,
+                    double *latency_s, int32_t max_n) {
+    return opf_server_poll_ex(s, tags, nullptr, converged, objective, iters, latency_s, max_n);
 }
 
 int opf_server_take_solution(opf_server *s, int64_t tag, double *x, int32_t n) {
@@ -502,11 +645,34 @@ int opf_server_stats(opf_server *s, int64_t *out, int32_t n) {
     return OPF_OK;
 }
 
+int opf_server_model_stats(opf_server *s, int32_t model, int64_t *out, int32_t n) {
+    if (!s || !out || model < 0 || model >= (int)s->models.size()) return OPF_E_INVALID;
+    Model &m = *s->models[model];
+    int64_t running = 0;
+    if (m.batched) running = m.running();
+    else
+        for (auto &w : m.workers) running += w->busy ? 1 : 0;
+    double svc;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        svc = m.n_svc ? m.svc_s : 0.0;
+    }
+    const int64_t v[10] = {m.n_sub.load(), m.n_done.load(), m.n_conv.load(), m.n_refused.load(), m.n_shed.load(),
+                           (int64_t)m.queue.size(), running, (int64_t)m.cap, (int64_t)(svc * 1e6),
+                           m.n_stopped.load()};
+    for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
+    return OPF_OK;
+}
+
 void opf_server_destroy(opf_server *s) {
     if (!s) return;
+    for (auto &m : s->models)           // running worker solves stop at their next chunk
+        for (auto &w : m->workers) w->h->cancel = 1;
     for (auto &m : s->models) {
-        for (auto &w : m->workers)
+        for (auto &w : m->workers) {
             if (w->th.joinable()) w->th.join();
+            w->h->cancel = 0;
+        }
         if (m->b) opf_batch_destroy(m->b);
         if (m->ev) cudaEventDestroy(m->ev);
         if (m->ev64) cudaEventDestroy(m->ev64);

@@ -128,6 +128,11 @@ def load(path: str = LIB_PATH):
     lib.opf_server_set_model_tolerance.argtypes = [H, C.c_int32, C.c_double, C.c_double]
     lib.opf_server_step.argtypes = [H]
     lib.opf_server_poll.argtypes = [H, _P, _P, _P, _P, _P, C.c_int32]
+    lib.opf_server_poll_ex.argtypes = [H, _P, _P, _P, _P, _P, _P, C.c_int32]
+    lib.opf_batch_set_start.argtypes = [H, _P, _P]
+    lib.opf_server_set_model_start.argtypes = [H, C.c_int32, _P, _P]
+    lib.opf_server_set_admission.argtypes = [H, C.c_int32, C.c_int32, C.c_double, C.c_double]
+    lib.opf_server_model_stats.argtypes = [H, C.c_int32, _P, C.c_int32]
     lib.opf_server_take_solution.argtypes = [H, C.c_int64, _P, C.c_int32]
     lib.opf_server_stats.argtypes = [H, _P, C.c_int32]
     lib.opf_server_destroy.argtypes = [H]
@@ -135,6 +140,7 @@ def load(path: str = LIB_PATH):
     lib.opf_stream_create_partition.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p),
                                                 C.POINTER(C.c_int32)]
     lib.opf_stream_destroy_partition.argtypes = [C.c_void_p]
+    lib.opf_probe_fma.argtypes = [C.c_int32, C.c_int32, C.c_int32, _P, _P, C.POINTER(C.c_double)]
     for name in ("opf_create", "opf_create_generic", "opf_precompute", "opf_solve", "opf_solve_ex",
                  "opf_step", "opf_reset", "opf_get_solution", "opf_get_residuals", "opf_get_locals",
                  "opf_set_locals", "opf_get_sizes", "opf_get_timing", "opf_global_update_static",
@@ -144,7 +150,9 @@ def load(path: str = LIB_PATH):
                  "opf_batch_get_status", "opf_batch_get_locals", "opf_batch_get_timing",
                  "opf_batch_get_tune_log", "opf_set_loads", "opf_server_create", "opf_server_add_model",
                  "opf_server_submit", "opf_server_step", "opf_server_poll", "opf_server_take_solution",
-                 "opf_server_stats", "opf_stream_create_partition", "opf_stream_destroy_partition"):
+                 "opf_server_stats", "opf_stream_create_partition", "opf_stream_destroy_partition",
+                 "opf_probe_fma", "opf_server_poll_ex", "opf_server_set_admission", "opf_server_model_stats",
+                 "opf_batch_set_start", "opf_server_set_model_start"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -173,6 +181,14 @@ def global_update_static(n, seg_off_ptr, u_ptr, c_ptr, lb_ptr, ub_ptr, rho, x_pt
     """Allocation-free global update on caller device pointers (see include/opf.h)."""
     _check(load().opf_global_update_static(int(n), seg_off_ptr, u_ptr, c_ptr, lb_ptr, ub_ptr, float(rho),
                                            x_ptr, obj_ptr, stream), "opf_global_update_static")
+
+
+def probe_fma(blocks, threads, iters, out_ptr, stream=None):
+    """Enqueue the FP32 FMA throughput probe (see include/opf.h); returns its flop count."""
+    fl = C.c_double()
+    _check(load().opf_probe_fma(int(blocks), int(threads), int(iters), out_ptr, stream, C.byref(fl)),
+           "opf_probe_fma")
+    return fl.value
 
 
 class Solver:
@@ -420,6 +436,15 @@ class Batch:
         return {"pres": res[:, 0], "dres": res[:, 1], "eps_prim": res[:, 2], "eps_dual": res[:, 3],
                 "iters": it, "converged": conv.astype(bool)}
 
+    def set_start(self, xs=None, lam=None):
+        """Warm start of instances set afterwards (None: the Sec. V-A point)."""
+        if xs is None:
+            _check(load().opf_batch_set_start(self._b, None, None), "opf_batch_set_start")
+            return
+        xs = np.ascontiguousarray(xs, np.float64)
+        lam = np.ascontiguousarray(lam, np.float64)
+        _check(load().opf_batch_set_start(self._b, _ptr(xs), _ptr(lam)), "opf_batch_set_start")
+
     def locals(self, inst):
         xs, lam = np.zeros(self.n_slots), np.zeros(self.n_slots)
         _check(load().opf_batch_get_locals(self._b, int(inst), _ptr(xs), _ptr(lam)), "opf_batch_get_locals")
@@ -486,10 +511,29 @@ class Server:
         _check(load().opf_server_set_model_tolerance(self._s, int(model), float(eps_rel), float(eps_abs_pres)),
                "opf_server_set_model_tolerance")
 
-    def submit(self, model, load_p, load_q, tag):
+    def set_model_start(self, model, xs=None, lam=None):
+        if xs is None:
+            _check(load().opf_server_set_model_start(self._s, int(model), None, None), "opf_server_set_model_start")
+            return
+        xs = np.ascontiguousarray(xs, np.float64)
+        lam = np.ascontiguousarray(lam, np.float64)
+        _check(load().opf_server_set_model_start(self._s, int(model), _ptr(xs), _ptr(lam)),
+               "opf_server_set_model_start")
+
+    def set_admission(self, model, max_queue=0, max_wait_s=0.0, max_service_s=0.0):
+        _check(load().opf_server_set_admission(self._s, int(model), int(max_queue), float(max_wait_s),
+                                               float(max_service_s)), "opf_server_set_admission")
+
+    def submit(self, model, load_p, load_q, tag, refusable=False):
+        """Queue a request; with refusable=True a refusal by the model's
+        admission policy returns False instead of raising."""
         lp = np.ascontiguousarray(load_p, np.float64)
         lq = np.ascontiguousarray(load_q, np.float64)
-        _check(load().opf_server_submit(self._s, int(model), _ptr(lp), _ptr(lq), int(tag)), "opf_server_submit")
+        rc = load().opf_server_submit(self._s, int(model), _ptr(lp), _ptr(lq), int(tag))
+        if refusable and rc == OPF_E_CAPACITY:
+            return False
+        _check(rc, "opf_server_submit")
+        return True
 
     def step(self):
         _check(load().opf_server_step(self._s), "opf_server_step")
@@ -500,11 +544,13 @@ class Server:
         obj = np.zeros(max_n)
         it = np.zeros(max_n, np.int32)
         lat = np.zeros(max_n)
-        n = load().opf_server_poll(self._s, _ptr(tags), _ptr(conv), _ptr(obj), _ptr(it), _ptr(lat), int(max_n))
+        sts = np.zeros(max_n, np.int32)
+        n = load().opf_server_poll_ex(self._s, _ptr(tags), _ptr(sts), _ptr(conv), _ptr(obj), _ptr(it), _ptr(lat),
+                                      int(max_n))
         if n < 0:
-            raise OPFError(n, "opf_server_poll")
-        return [{"tag": int(tags[i]), "converged": bool(conv[i]), "objective": float(obj[i]),
-                 "iters": int(it[i]), "latency_s": float(lat[i])} for i in range(n)]
+            raise OPFError(n, "opf_server_poll_ex")
+        return [{"tag": int(tags[i]), "status": int(sts[i]), "converged": bool(conv[i]),
+                 "objective": float(obj[i]), "iters": int(it[i]), "latency_s": float(lat[i])} for i in range(n)]
 
     def take_solution(self, tag, model):
         x = np.zeros(self._n_global[model])
@@ -516,6 +562,15 @@ class Server:
         _check(load().opf_server_stats(self._s, _ptr(out), 7), "opf_server_stats")
         keys = ("submitted", "polled", "queued", "running", "slots", "passes", "mem_bytes")
         return {k: int(v) for k, v in zip(keys, out)}
+
+    def model_stats(self, model):
+        out = np.zeros(10, np.int64)
+        _check(load().opf_server_model_stats(self._s, int(model), _ptr(out), 10), "opf_server_model_stats")
+        keys = ("submitted", "served", "converged", "refused", "shed", "queued", "running", "slots")
+        d = {k: int(v) for k, v in zip(keys, out)}
+        d["service_s"] = float(out[8]) / 1e6
+        d["stopped"] = int(out[9])
+        return d
 
     def close(self):
         if self._s:

@@ -5,7 +5,9 @@
   scenarios;
 * served results reach each request's LP optimum within 1e-6 relative;
 * admission is bounded by the device-memory budget;
-* models too large for the batched engine are served by worker threads.
+* models too large for the batched engine are served by worker threads;
+* a model's admission policy serves, refuses at submit or sheds every
+  request with a counted status (none is left pending).
 """
 import numpy as np
 import pytest
@@ -151,3 +153,94 @@ def test_model_tolerance_applies_to_its_requests():
         assert all(got[r]["converged"] for r in range(len(scen)))
         s13.close()
     assert all(a < b for a, b in zip(iters[1e-5], iters[1e-8])), iters
+
+
+def test_flooded_worker_model_serves_or_refuses_every_request():
+    """A model served by worker threads (ZIP loads: a factorization per
+    request) with a bounded queue: every request of a burst is either served
+    or refused at submit with a status, and none is left pending."""
+    fz = synth.with_zip_delta(synth.preset_feeder("34", 5034), seed=11)
+    h = solver(fz)
+    n = 10
+    with opf.Server() as srv:
+        m = srv.add_model([h], capacity=4)
+        srv.set_admission(m, max_queue=2)
+        accepted = []
+        for r in range(n):
+            g = synth.load_scenario(fz, 6700 + r)
+            if srv.submit(m, g["load_a"], g["load_b"], tag=r, refusable=True):
+                accepted.append(r)
+        assert 2 <= len(accepted) < n
+        got = drain(srv, accepted)
+        st = srv.model_stats(m)
+    assert st["submitted"] == n
+    assert st["refused"] == n - len(accepted)
+    assert st["served"] == len(accepted) and st["shed"] == 0
+    assert st["queued"] == 0 and st["running"] == 0
+    for r in accepted:
+        assert got[r]["status"] == opf.OPF_OK and got[r]["converged"]
+    h.close()
+
+
+def test_waiting_requests_are_shed_then_refused_by_predicted_wait():
+    """max_wait_s: queued requests that wait longer are shed with
+    OPF_E_TIMEOUT; once the model has a measured service time, a request
+    whose predicted wait exceeds the bound is refused at submit."""
+    fz = synth.with_zip_delta(synth.preset_feeder("123", 5123), seed=12)
+    h = solver(fz)
+    scen = [synth.load_scenario(fz, 6800 + r) for r in range(8)]
+    with opf.Server() as srv:
+        m = srv.add_model([h], capacity=4)
+        srv.set_admission(m, max_wait_s=0.02)
+        assert srv.submit(m, scen[0]["load_a"], scen[0]["load_b"], tag=0, refusable=True)
+        srv.step()                                          # the worker takes request 0
+        for r in range(1, 4):                               # no service time yet: queued
+            assert srv.submit(m, scen[r]["load_a"], scen[r]["load_b"], tag=r, refusable=True)
+        got = drain(srv, list(range(4)))
+        st = srv.model_stats(m)
+        assert got[0]["status"] == opf.OPF_OK and got[0]["converged"]
+        shed = [r for r in range(1, 4) if got[r]["status"] == opf.OPF_E_TIMEOUT]
+        assert shed, got                                    # one worker, 20 ms bound, solves take longer
+        for r in shed:
+            assert not got[r]["converged"] and np.isnan(got[r]["objective"])
+        assert st["service_s"] > 0.02
+        # a free worker admits one request; the next would wait a service time
+        assert srv.submit(m, scen[4]["load_a"], scen[4]["load_b"], tag=4, refusable=True)
+        assert not srv.submit(m, scen[5]["load_a"], scen[5]["load_b"], tag=5, refusable=True)
+        got.update(drain(srv, [4]))
+        st = srv.model_stats(m)
+    assert st["submitted"] == 6 and st["refused"] == 1
+    assert st["served"] + st["shed"] + st["refused"] == st["submitted"]
+    assert st["queued"] == 0 and st["running"] == 0
+    assert got[4]["status"] == opf.OPF_OK
+    h.close()
+
+
+def test_service_bound_stops_running_requests_with_a_status():
+    """max_service_s: a worker's solve stops at its next chunk and a batched
+    slot is retired at the end of a pass once the bound has passed; both are
+    reported with OPF_E_TIMEOUT and counted as stopped."""
+    fz = synth.with_zip_delta(synth.preset_feeder("123", 5123), seed=13)
+    f13 = synth.preset_feeder("13", 5013)
+    hz, h13 = solver(fz), solver(f13)
+    with opf.Server() as srv:
+        mz = srv.add_model([hz], capacity=4)
+        m13 = srv.add_model([h13], capacity=8)
+        srv.set_admission(mz, max_service_s=1e-3)
+        srv.set_admission(m13, max_service_s=1e-6)
+        g = synth.load_scenario(fz, 6900)
+        srv.submit(mz, g["load_a"], g["load_b"], tag=0)
+        for r in range(3):
+            g = synth.load_scenario(f13, 6910 + r)
+            srv.submit(m13, g["load_a"], g["load_b"], tag=1 + r)
+        got = drain(srv, [0, 1, 2, 3])
+        stz, st13 = srv.model_stats(mz), srv.model_stats(m13)
+    for r in range(4):
+        assert got[r]["status"] == opf.OPF_E_TIMEOUT and not got[r]["converged"]
+        assert np.isnan(got[r]["objective"])
+    assert stz["stopped"] == 1 and stz["served"] == 1 and stz["converged"] == 0
+    assert st13["stopped"] == 3 and st13["served"] == 3
+    for st in (stz, st13):
+        assert st["queued"] == 0 and st["running"] == 0
+    hz.close()
+    h13.close()
