@@ -599,8 +599,10 @@ def run_batch(args, rank, world, local):
             "traffic_unit": "DRAM bytes per engine launch of 2000 iterations, copied from the ncu capture in "
                             + BATCH_ENGINE_TRAFFIC_SOURCE + " (not measured in this run)",
             "kernel": "k_batch_engine<float> (FP32; %d instances per CTA, %d warps, %d CTAs; factors, u and x "
-                      "in shared memory, lambda and bbar~ streamed from L2)"
-                      % (shape["k_inst"], shape["warps"], shape["ctas"]),
+                      "in shared memory, lambda and bbar~ %s)"
+                      % (shape["k_inst"], shape["warps"], shape["ctas"],
+                         "in tensor memory (%d TMEM columns per CTA)" % shape["tmem_cols"] if shape["tmem"]
+                         else "streamed from L2"),
             "flops_per_instance_iteration": fpi,
             "instance_iterations_timed": inst_iters,
             "launches_timed": passes,

@@ -326,9 +326,18 @@ int opf_batch_step(opf_batch *b, double rho, int32_t n_iters);
  * instances per CTA (power of two <= 32) and warps per CTA (<= 16); 0 = pick
  * (FP32: the fastest of the candidate shapes timed on the batch; FP64: the
  * largest k_inst <= 4 that fits).  out (get): ok, k_inst, warps, chunks per
- * lane, tasks, chunks per CTA, shared bytes, CTAs. */
+ * lane, tasks, chunks per CTA, shared bytes, CTAs, lambda and bbar~ in
+ * tensor memory (1/0), tensor-memory columns per CTA. */
 int opf_batch_set_shape(opf_batch *b, int32_t precision, int32_t k_inst, int32_t warps);
 int opf_batch_get_shape(opf_batch *b, int32_t precision, int32_t *out, int32_t n_out);
+
+/* FP32 engine storage (default 1): with 1, a plan whose warp count is a
+ * multiple of 4 keeps lambda and bbar~ of its CTA's instances in tensor
+ * memory (tcgen05 TMEM, allocated per CTA for each launch) when they fit in
+ * 512 columns per lane quadrant, instead of streaming them from L2 every
+ * iteration; 0 streams them.  The arithmetic and the iterates are the same
+ * either way.  The FP32 plan is rebuilt at the next solve. */
+int opf_batch_set_tmem(opf_batch *b, int32_t enable);
 
 /* Global x (count * n_global doubles, canonical order) and objective c^T x of
  * instances [first, first + count) after the last solve or step; either
@@ -472,6 +481,70 @@ int opf_server_stats(opf_server *s, int64_t *out, int32_t n);
 int opf_server_model_stats(opf_server *s, int32_t model, int64_t *out, int32_t n);
 
 void opf_server_destroy(opf_server *s);
+
+/* ------------------------------------------------------------------ shards
+ * One instance split over several GPUs (one shard per GPU), the multi-GPU
+ * form of the server/agent exchange of Sec. IV reduced to what Algorithm 1
+ * needs: a shard holds a subset of the subsystems; the global update of
+ * Eq. closed_1 for a global whose copies lie on several shards (a cut
+ * global) needs the sum over all shards of sigma_i = sum_k (rho x_k -
+ * lambda_k), which the caller exchanges (an all-reduce over the cut) between
+ * opf_shard_partial and opf_shard_step.  The cut is the same list on every
+ * shard (every global with copies on more than one part, ascending), so the
+ * exchange is a plain sum of equal-length arrays.  Every shard then computes the same
+ * x_i, so the iterates equal the unsharded instance's.  FP64 iterations.
+ * A shard is not thread-safe; all its work is ordered on its stream. */
+typedef struct opf_shard opf_shard;
+
+/* Part of every subsystem (n_sub = subsystem count of the feeder's model,
+ * canonical order): the buses in depth-first order from the substation cut
+ * into n_parts contiguous ranges of balanced work (n_s^2 summed over the
+ * subsystems anchored at a bus: a bus subsystem at its bus, a line subsystem
+ * at its to-bus), so each part is a run of whole subtrees.  Host only.
+ * OPF_E_INVALID for a malformed feeder or a wrong n_sub. */
+int opf_partition(const opf_feeder *f, int32_t n_parts, int32_t *sub_part, int32_t n_sub);
+
+/* Shard `part` of the feeder under the partition sub_part (n_sub entries):
+ * its subsystems over the globals they touch (local globals, ascending global
+ * index); the cut (n_cut entries, the same on every shard) lists the globals
+ * with copies on more than one part; the objective counts a global on the
+ * lowest part holding it.  The feeder arrays are
+ * copied.  OPF_E_INVALID if the part is empty. */
+int opf_shard_create(const opf_feeder *f, const int32_t *sub_part, int32_t n_sub, int32_t part,
+                     const opf_options *o, opf_shard **out);
+/* FP64 precompute of the shard's subsystems; the iterate goes to the
+ * Sec. V-A start. */
+int opf_shard_precompute(opf_shard *sh);
+/* Local globals, cut globals (of all shards), local copies (slots). */
+int opf_shard_sizes(opf_shard *sh, int32_t *n_global, int32_t *n_cut, int32_t *n_slots);
+/* Global index (whole instance) of every local global, and of every cut
+ * global in the order of the sigma arrays (host arrays; either may be NULL). */
+int opf_shard_maps(opf_shard *sh, int32_t *global_of_local, int32_t *cut_global);
+/* Enqueues on the shard's stream: sig[j] = this shard's part of sigma of cut
+ * global j from the current iterate, 0 where it holds no copy (device array
+ * of n_cut doubles). */
+int opf_shard_partial(opf_shard *sh, double rho, double *sig);
+/* Enqueues one FP64 iteration with sig_tot (device, n_cut doubles: sigma
+ * summed over all shards, as opf_shard_partial produced before this step).
+ * sums (device, 6 doubles, or NULL): this shard's part of the Sec. III-C sums
+ * of the iteration, |x_g(k) - x_s,k|^2, |x_s - x_s,old|^2, |x_g(k)|^2,
+ * |x_s|^2 over its slots, |lambda|^2 and its share of c^T x; add them over
+ * the shards and apply opf_test_rule.  OPF_E_STATE without a preceding
+ * opf_shard_partial at the same rho. */
+int opf_shard_step(opf_shard *sh, double rho, const double *sig_tot, double *sums);
+/* x per local global after the last step (host array), and x_s, lambda of the
+ * shard's slots (as opf_get_locals on its subsystems). */
+int opf_shard_get_x(opf_shard *sh, double *x);
+int opf_shard_get_locals(opf_shard *sh, double *xs, double *lam, size_t n);
+/* The cudaStream_t the shard's work is ordered on. */
+void *opf_shard_stream(opf_shard *sh);
+void opf_shard_destroy(opf_shard *sh);
+
+/* The Sec. III-C test on summed squares (host): sums as opf_shard_step,
+ * out (may be NULL) = pres, dres, eps_prim / eps_rel, eps_dual / eps_rel,
+ * objective.  Returns 1 when pres <= eps_rel eps_prim, dres <= eps_rel
+ * eps_dual and pres <= eps_abs_pres, 0 when not, OPF_E_NUMERIC on NaN. */
+int opf_test_rule(const double *sums, double rho, double eps_rel, double eps_abs_pres, double *out);
 
 /* Measurement helper, not part of the method: enqueues a kernel of
  * `blocks` x `threads` threads (threads a multiple of 32, at most 1024) in

@@ -141,22 +141,109 @@ __device__ __forceinline__ int upos(int ch, int e, int sc) {
     return (ch * 4 + (e ^ (ch & 3))) * K + sc;
 }
 
-template <typename T, int K, int NQT>
+// ---- tensor memory (tcgen05): lambda and bbar~ of the tasks, 32-bit columns.
+// A warp w reaches the 32 lanes of quadrant w % 4; a lane of the warp reads
+// and writes its own tensor-memory lane.  Address = (lane << 16) | column.
+__device__ __forceinline__ void tm_alloc(unsigned *dst_smem, int cols) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(a), "r"(cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(unsigned taddr, int cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// 8 consecutive columns of the lane: lambda (4) then bbar~ (4) of one chunk
+__device__ __forceinline__ void tm_ld8(unsigned taddr, Q4<float> &m, Q4<float> &b) {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        m.v[e] = __uint_as_float(r[e]);
+        b.v[e] = __uint_as_float(r[4 + e]);
+    }
+}
+__device__ __forceinline__ void tm_st8(unsigned taddr, const Q4<float> &m, const Q4<float> &b) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(__float_as_uint(m.v[0])), "r"(__float_as_uint(m.v[1])), "r"(__float_as_uint(m.v[2])),
+                 "r"(__float_as_uint(m.v[3])), "r"(__float_as_uint(b.v[0])), "r"(__float_as_uint(b.v[1])),
+                 "r"(__float_as_uint(b.v[2])), "r"(__float_as_uint(b.v[3]))
+                 : "memory");
+}
+__device__ __forceinline__ void tm_st4(unsigned taddr, const Q4<float> &m) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+                 "r"(__float_as_uint(m.v[0])), "r"(__float_as_uint(m.v[1])), "r"(__float_as_uint(m.v[2])),
+                 "r"(__float_as_uint(m.v[3]))
+                 : "memory");
+}
+__device__ __forceinline__ void tm_ld4(unsigned taddr, Q4<float> &m) {
+    unsigned r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int e = 0; e < 4; ++e) m.v[e] = __uint_as_float(r[e]);
+}
+
+// Tensor-memory staging of one task (TMTASK): at the start of a launch
+// lambda and bbar~ from the engine arrays into the task's columns; at a
+// freeze or the end lambda back to the engine array for the columns flagged
+// in `wcols` (bit sc), after the lanes' own loads.
+template <int K, int NQT>
+__device__ __forceinline__ void tm_stage_in(const BatchTask &tk, unsigned tl, const float *mu_c, const float *bt_c,
+                                            int jpos, int sc) {
+    constexpr int J = 32 / K;
+    const unsigned col = (unsigned)(tk.tm >> 2);
+#pragma unroll
+    for (int q = 0; q < NQT; ++q) {
+        const int off = ((tk.ch0 + jpos + q * J) * K + sc) * 4;
+        tm_st8(tl + col + 8 * q, ld4cg(mu_c + off), ld4cg(bt_c + off));
+    }
+}
+template <int K, int NQT>
+__device__ __forceinline__ void tm_stage_out(const BatchTask &tk, unsigned tl, float *mu_c, int jpos, int sc,
+                                             bool write) {
+    constexpr int J = 32 / K;
+    const unsigned col = (unsigned)(tk.tm >> 2);
+#pragma unroll
+    for (int q = 0; q < NQT; ++q) {
+        Q4<float> m;
+        tm_ld4(tl + col + 8 * q, m);
+        tm_wait_ld();
+        if (write) st4cg(mu_c + ((tk.ch0 + jpos + q * J) * K + sc) * 4, m);
+    }
+}
+
+template <typename T, int K, int NQT, bool TM>
 __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *us, T *mu_c, const T *bt_c,
                                            T *ds_c, const T *lr_c, const T *xr_c, const int4 *chg, int jpos,
                                            int sc, T rho, T inv_rho, bool check, bool act, bool wds,
-                                           double *redw) {
+                                           double *redw, unsigned tl) {
     constexpr int J = 32 / K;
     const int mode1 = (tk.modes >> (jpos >> tk.lp)) & 1;
     T v[4 * NQT], y[4 * NQT];
     double c0 = 0.0, c1 = 0.0, c3 = 0.0, c4 = 0.0;
     const int ch0 = tk.ch0 + jpos;
+    const unsigned tcol = tl + (unsigned)(tk.tm >> 2);
 #pragma unroll
     for (int q = 0; q < NQT; ++q) {
         const int ch = ch0 + q * J;
         const int off = (ch * K + sc) * 4;
-        const Q4<T> m4 = ld4cg(mu_c + off);
-        const Q4<T> b4 = ld4cg(bt_c + off);
+        Q4<T> m4, b4;
+        if constexpr (TM) {
+            tm_ld8(tcol + 8 * q, m4, b4);
+            tm_wait_ld();
+        } else {
+            m4 = ld4cg(mu_c + off);
+            b4 = ld4cg(bt_c + off);
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             y[4 * q + e] = b4.v[e];
@@ -236,7 +323,12 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) us[upos<K>(ch, e, sc)] = u4.v[e];
-        if (act) {
+        if constexpr (TM) {
+            // every lane (a frozen column keeps iterating in tensor memory;
+            // its lambda went to the engine array when it froze)
+            tm_st4(tcol + 8 * q, m4);
+            if (act && wds) st4cg(ds_c + off, x4);
+        } else if (act) {
             st4cg(mu_c + off, m4);
             if (wds) st4cg(ds_c + off, x4);
         }
@@ -261,7 +353,10 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
 // K: instance columns per CTA (compile time), J = 32 / K member positions.
 // NQ: chunks of 4 slots a lane can hold (registers v and y: 2 * 4 * NQ).
 // FG: factors read from global memory (L1/L2) instead of shared memory.
-template <typename T, int K, int NQ, bool FG>
+// TM (FP32 only): lambda and bbar~ of the tasks in tensor memory for the
+// launch instead of streamed from L2; the tasks of lane quadrant q run on the
+// warps w with w % 4 == q (a dynamic schedule per quadrant).
+template <typename T, int K, int NQ, bool FG, bool TM>
 __global__ void __launch_bounds__(512, 1)
     k_batch_engine(BatchArgs<T> a, int n_iters, int check_every) {
     constexpr int J = 32 / K;
@@ -282,7 +377,8 @@ __global__ void __launch_bounds__(512, 1)
     T *bnd = reinterpret_cast<T *>(smraw + a.off_bnd);           // [NB][2][K]: bounds - x_ref
     double *red = reinterpret_cast<double *>(smraw + a.off_red);
     int *flags = reinterpret_cast<int *>(smraw + a.off_flag);    // [0,K) running, [K,2K) just finished
-    int *tnext = flags + 2 * K;                                    // next task of the dynamic schedule
+    int *tnext = flags + 2 * K;                                    // next task of the dynamic schedule (per quadrant)
+    __shared__ unsigned tm_base;                                   // tensor-memory address of the allocation
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int nthr = blockDim.x;
     const int c = blockIdx.x;
@@ -324,14 +420,36 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
         for (int e = 0; e < 4; ++e) us[upos<K>(ch, e, col)] = a.rho * d.v[e] - m.v[e];
     }
-    __syncthreads();
     const int sc = tid & (K - 1);
     const int jpos = lane >> KS;
+    const int n_warps = nthr >> 5;
+    const int qd = w & 3, wq = w >> 2, nwq = n_warps >> 2;     // quadrant, warp in it, warps per quadrant
+    unsigned tl = 0;                                             // this warp's tensor-memory lane base
+    if constexpr (TM) {
+        if (w == 0) tm_alloc(&tm_base, a.tm_cols);
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        tl = tm_base + ((unsigned)(32 * qd) << 16);
+        for (int t = a.qstart[qd] + wq; t < a.qstart[qd + 1]; t += nwq) {
+            const BatchTask tk = a.tasks[t];
+            switch (tk.nq) {
+                case 1: tm_stage_in<K, 1>(tk, tl, mu_c, bt_c, jpos, sc); break;
+                case 2: tm_stage_in<K, 2>(tk, tl, mu_c, bt_c, jpos, sc); break;
+                case 3: tm_stage_in<K, 3>(tk, tl, mu_c, bt_c, jpos, sc); break;
+                default: tm_stage_in<K, 4>(tk, tl, mu_c, bt_c, jpos, sc); break;
+            }
+        }
+        tm_wait_st();
+        tm_fence_before();
+    }
+    __syncthreads();
+    if constexpr (TM) tm_fence_after();
     const T *xr_c = a.xrf + gb + sc;
     const T rho = a.rho, inv_rho = a.inv_rho;
     double *redw = red + (size_t)w * K * 6;      // this warp's test sums per column
-    const int n_warps = nthr >> 5;
     int last_check = 0;
+    bool all_done = false;
     const int GK = a.G * K;
     const int GQ = a.G * NQD;
     for (int it = 0; it < n_iters; ++it) {
@@ -342,7 +460,11 @@ __global__ void __launch_bounds__(512, 1)
         if (check && lane < K)
 #pragma unroll
             for (int q = 0; q < 6; ++q) redw[lane * 6 + q] = 0.0;
-        if (tid == 0) *tnext = n_warps;
+        if constexpr (TM) {
+            if (tid < 4) tnext[tid] = a.qstart[tid] + nwq;
+        } else if (tid == 0) {
+            *tnext = n_warps;
+        }
         // ---- G: global update (Eq. closed_1).  An item is one global and KQ of
         // its columns: sum of u over the copies, shift, scale, clip, and x
         // stored into every copy's slot; GB items per thread with c~ in flight
@@ -453,29 +575,38 @@ __global__ void __launch_bounds__(512, 1)
             // each warp's first task is its own (the counter starts at
             // n_warps); the next task's index is claimed at the start of a
             // task and read at its end, so the atomic's latency is hidden
-            int t = w;
-            while (t < a.n_tasks) {
+            // (tensor-memory plans: the same within the warp's quadrant)
+            int t = TM ? a.qstart[qd] + wq : w;
+            const int t_end = TM ? a.qstart[qd + 1] : a.n_tasks;
+            const int t_step = TM ? nwq : n_warps;
+            int *cnt = TM ? tnext + qd : tnext;
+            while (t < t_end) {
                 int claim = 0;
-                if (!check && lane == 0) claim = atomicAdd(tnext, 1);
+                if (!check && lane == 0) claim = atomicAdd(cnt, 1);
                 const BatchTask tk = tks[t];
                 switch (tk.nq) {
-                    case 1: batch_task<T, K, 1>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
-                                                inv_rho, check, act, wds, redw); break;
-                    case 2: if constexpr (NQ >= 2) batch_task<T, K, 2>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                       a.chg, jpos, sc, rho, inv_rho, check, act,
-                                                                       wds, redw); break;
-                    case 3: if constexpr (NQ >= 3) batch_task<T, K, 3>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                       a.chg, jpos, sc, rho, inv_rho, check, act,
-                                                                       wds, redw); break;
-                    default: if constexpr (NQ >= 4) batch_task<T, K, 4>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                        a.chg, jpos, sc, rho, inv_rho, check, act,
-                                                                        wds, redw); break;
+                    case 1: batch_task<T, K, 1, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
+                                                    inv_rho, check, act, wds, redw, tl); break;
+                    case 2: if constexpr (NQ >= 2) batch_task<T, K, 2, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
+                                                                           a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                           wds, redw, tl); break;
+                    case 3: if constexpr (NQ >= 3) batch_task<T, K, 3, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
+                                                                           a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                           wds, redw, tl); break;
+                    default: if constexpr (NQ >= 4) batch_task<T, K, 4, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
+                                                                            a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                            wds, redw, tl); break;
                 }
-                t = check ? t + n_warps : __shfl_sync(0xffffffffu, claim, 0);
+                t = check ? t + t_step : __shfl_sync(0xffffffffu, claim, 0);
+            }
+            if constexpr (TM) {
+                tm_wait_st();
+                tm_fence_before();
             }
         }
         if (check) {
             __syncthreads();
+            if constexpr (TM) tm_fence_after();
             if (tid < K) {
                 flags[K + tid] = 0;
                 if (flags[tid]) {
@@ -493,14 +624,52 @@ __global__ void __launch_bounds__(512, 1)
             }
             __syncthreads();
             last_check = it + 1;
+            if constexpr (TM) {
+                // lambda of the columns that just finished, to the engine array
+                int fin = 0;
+                for (int q = 0; q < K; ++q) fin |= flags[K + q];
+                if (fin)
+                    for (int t = a.qstart[qd] + wq; t < a.qstart[qd + 1]; t += nwq) {
+                        const BatchTask tk = tks[t];
+                        const bool wr = flags[K + sc] != 0;
+                        switch (tk.nq) {
+                            case 1: tm_stage_out<K, 1>(tk, tl, (float *)mu_c, jpos, sc, wr); break;
+                            case 2: tm_stage_out<K, 2>(tk, tl, (float *)mu_c, jpos, sc, wr); break;
+                            case 3: tm_stage_out<K, 3>(tk, tl, (float *)mu_c, jpos, sc, wr); break;
+                            default: tm_stage_out<K, 4>(tk, tl, (float *)mu_c, jpos, sc, wr); break;
+                        }
+                    }
+            }
             int any = 0;
             for (int q = 0; q < K; ++q) any |= flags[q];
-            if (!any) return;
+            if (!any) {
+                all_done = true;
+                break;
+            }
         } else {
             __syncthreads();
+            if constexpr (TM) tm_fence_after();
         }
     }
-    if (tid < K && flags[tid]) a.st[a.inst[c * K + tid]].iter += n_iters - last_check;
+    if (!all_done && tid < K && flags[tid]) a.st[a.inst[c * K + tid]].iter += n_iters - last_check;
+    if constexpr (TM) {
+        // lambda of the columns still running, then the allocation is freed
+        if (!all_done)
+            for (int t = a.qstart[qd] + wq; t < a.qstart[qd + 1]; t += nwq) {
+                const BatchTask tk = tks[t];
+                const bool wr = flags[sc] != 0;
+                switch (tk.nq) {
+                    case 1: tm_stage_out<K, 1>(tk, tl, (float *)mu_c, jpos, sc, wr); break;
+                    case 2: tm_stage_out<K, 2>(tk, tl, (float *)mu_c, jpos, sc, wr); break;
+                    case 3: tm_stage_out<K, 3>(tk, tl, (float *)mu_c, jpos, sc, wr); break;
+                    default: tm_stage_out<K, 4>(tk, tl, (float *)mu_c, jpos, sc, wr); break;
+                }
+            }
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        if (w == 0) tm_dealloc(tm_base, a.tm_cols);
+    }
 }
 
 // ============================================================ per-instance data
@@ -797,10 +966,10 @@ __global__ void k_brestart(int n_inst, DevStatus *st, long long add_max) {
 }
 
 // Factors packed per task: element (r, q, jpos, e) of task t from the FP64
-// factor of member mb = jpos >> lp (tmem[t * J + mb], -1: none), slot
+// factor of member mb = jpos >> lp (memb[t * J + mb], -1: none), slot
 // c = ((jpos & (p-1)) * nq + q) * 4 + e.
 template <typename T>
-__global__ void k_bpack(int n_tasks, int J, const BatchTask *tasks, const int *tmem, const int4 *sub,
+__global__ void k_bpack(int n_tasks, int J, const BatchTask *tasks, const int *memb, const int4 *sub,
                         const int4 *sub2, const double *F64, T *dst) {
     const int t = blockIdx.x;
     if (t >= n_tasks) return;
@@ -809,7 +978,7 @@ __global__ void k_bpack(int n_tasks, int J, const BatchTask *tasks, const int *t
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
         const int e = x & 3, jpos = (x >> 2) % J, q = (x / (4 * J)) % tk.nq, r = x / (4 * J * tk.nq);
         const int mb = jpos >> tk.lp, part = jpos & (tk.p - 1);
-        const int d = tmem[t * J + mb];
+        const int d = memb[t * J + mb];
         double v = 0.0;
         if (d >= 0) {
             const int4 h = sub[d], q2 = sub2[d];
@@ -828,27 +997,31 @@ static inline int bl(long long n, int t) {
     return (int)b;
 }
 
-// Instantiated shapes: FP32 with factors in shared memory (K = 2, 4, 8; NQ = 4);
-// FP64 (NQ = 2, K = 1, 2, 4) with factors in shared or global memory.
+// Instantiated shapes: FP32 with factors in shared memory (K = 2, 4, 8; NQ = 4),
+// lambda and bbar~ in tensor memory or streamed from L2; FP64 (NQ = 2,
+// K = 1, 2, 4) with factors in shared or global memory.
 template <typename T>
-static const void *engine_fn(int K, int nq, bool fg) {
+static const void *engine_fn(int K, int nq, bool fg, bool tm) {
     if constexpr (sizeof(T) == 4) {
         if (fg || nq != 4) return nullptr;
-        if (K == 2) return (const void *)k_batch_engine<float, 2, 4, false>;
-        if (K == 4) return (const void *)k_batch_engine<float, 4, 4, false>;
-        if (K == 8) return (const void *)k_batch_engine<float, 8, 4, false>;
+        if (K == 2) return tm ? (const void *)k_batch_engine<float, 2, 4, false, true>
+                              : (const void *)k_batch_engine<float, 2, 4, false, false>;
+        if (K == 4) return tm ? (const void *)k_batch_engine<float, 4, 4, false, true>
+                              : (const void *)k_batch_engine<float, 4, 4, false, false>;
+        if (K == 8) return tm ? (const void *)k_batch_engine<float, 8, 4, false, true>
+                              : (const void *)k_batch_engine<float, 8, 4, false, false>;
     } else {
-        if (nq != 2) return nullptr;
-        if (K == 1) return fg ? (const void *)k_batch_engine<double, 1, 2, true> : (const void *)k_batch_engine<double, 1, 2, false>;
-        if (K == 2) return fg ? (const void *)k_batch_engine<double, 2, 2, true> : (const void *)k_batch_engine<double, 2, 2, false>;
-        if (K == 4) return fg ? (const void *)k_batch_engine<double, 4, 2, true> : (const void *)k_batch_engine<double, 4, 2, false>;
+        if (nq != 2 || tm) return nullptr;
+        if (K == 1) return fg ? (const void *)k_batch_engine<double, 1, 2, true, false> : (const void *)k_batch_engine<double, 1, 2, false, false>;
+        if (K == 2) return fg ? (const void *)k_batch_engine<double, 2, 2, true, false> : (const void *)k_batch_engine<double, 2, 2, false, false>;
+        if (K == 4) return fg ? (const void *)k_batch_engine<double, 4, 2, true, false> : (const void *)k_batch_engine<double, 4, 2, false, false>;
     }
     return nullptr;
 }
 
 template <typename T>
-int batch_engine_prepare(int K, int nq, bool fg, unsigned bytes) {
-    const void *fn = engine_fn<T>(K, nq, fg);
+int batch_engine_prepare(int K, int nq, bool fg, bool tm, unsigned bytes) {
+    const void *fn = engine_fn<T>(K, nq, fg, tm);
     if (!fn) return -1;
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess ? 0 : -1;
 }
@@ -856,7 +1029,7 @@ int batch_engine_prepare(int K, int nq, bool fg, unsigned bytes) {
 template <typename T>
 int batch_engine_launch(const BatchArgs<T> &a, int nq, bool fg, int ctas, int threads, unsigned bytes, int n_iters,
                         int check_every, cudaStream_t s) {
-    const void *fn = engine_fn<T>(a.K, nq, fg);
+    const void *fn = engine_fn<T>(a.K, nq, fg, a.tm != 0);
     if (!fn) return -1;
     BatchArgs<T> aa = a;
     void *args[] = {(void *)&aa, (void *)&n_iters, (void *)&check_every};
@@ -864,21 +1037,21 @@ int batch_engine_launch(const BatchArgs<T> &a, int nq, bool fg, int ctas, int th
 }
 
 template <typename T>
-int batch_engine_max_ctas_per_sm(int K, int nq, bool fg, int threads, unsigned bytes) {
-    const void *fn = engine_fn<T>(K, nq, fg);
+int batch_engine_max_ctas_per_sm(int K, int nq, bool fg, bool tm, int threads, unsigned bytes) {
+    const void *fn = engine_fn<T>(K, nq, fg, tm);
     if (!fn) return -1;
     int n = 0;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, bytes) == cudaSuccess ? n : -1;
 }
 
-template int batch_engine_prepare<float>(int, int, bool, unsigned);
-template int batch_engine_prepare<double>(int, int, bool, unsigned);
+template int batch_engine_prepare<float>(int, int, bool, bool, unsigned);
+template int batch_engine_prepare<double>(int, int, bool, bool, unsigned);
 template int batch_engine_launch<float>(const BatchArgs<float> &, int, bool, int, int, unsigned, int, int,
                                         cudaStream_t);
 template int batch_engine_launch<double>(const BatchArgs<double> &, int, bool, int, int, unsigned, int, int,
                                          cudaStream_t);
-template int batch_engine_max_ctas_per_sm<float>(int, int, bool, int, unsigned);
-template int batch_engine_max_ctas_per_sm<double>(int, int, bool, int, unsigned);
+template int batch_engine_max_ctas_per_sm<float>(int, int, bool, bool, int, unsigned);
+template int batch_engine_max_ctas_per_sm<double>(int, int, bool, bool, int, unsigned);
 
 void launch_binit(int i0, int cnt, int L, const int *gk, const double *x0, double *xs, double *lam,
                   DevStatus *st, long long max_iter, double eps_rel, double eps_abs, cudaStream_t s) {
@@ -969,9 +1142,9 @@ void launch_brestart(int n_inst, DevStatus *st, long long add_max, cudaStream_t 
 }
 
 template <typename T>
-void launch_bpack(int n_tasks, int J, const BatchTask *tasks, const int *tmem, const int4 *sub, const int4 *sub2,
+void launch_bpack(int n_tasks, int J, const BatchTask *tasks, const int *memb, const int4 *sub, const int4 *sub2,
                   const double *F64, T *dst, cudaStream_t s) {
-    if (n_tasks > 0) k_bpack<T><<<n_tasks, 256, 0, s>>>(n_tasks, J, tasks, tmem, sub, sub2, F64, dst);
+    if (n_tasks > 0) k_bpack<T><<<n_tasks, 256, 0, s>>>(n_tasks, J, tasks, memb, sub, sub2, F64, dst);
 }
 template void launch_bpack<float>(int, int, const BatchTask *, const int *, const int4 *, const int4 *,
                                   const double *, float *, cudaStream_t);

@@ -24,11 +24,11 @@
 #include "batch_internal.h"
 
 namespace opf {
-template <typename T> int batch_engine_prepare(int K, int nq, bool fg, unsigned bytes);
+template <typename T> int batch_engine_prepare(int K, int nq, bool fg, bool tm, unsigned bytes);
 template <typename T>
 int batch_engine_launch(const BatchArgs<T> &a, int nq, bool fg, int ctas, int threads, unsigned bytes, int n_iters,
                         int check_every, cudaStream_t s);
-template <typename T> int batch_engine_max_ctas_per_sm(int K, int nq, bool fg, int threads, unsigned bytes);
+template <typename T> int batch_engine_max_ctas_per_sm(int K, int nq, bool fg, bool tm, int threads, unsigned bytes);
 void launch_bwarm(int i0, int cnt, int L, const double *xs0, const double *lam0, double *xs, double *lam,
                   cudaStream_t s);
 void launch_binit(int i0, int cnt, int L, const int *gk, const double *x0, double *xs, double *lam,
@@ -57,7 +57,7 @@ void launch_bany(int n_inst, const int *ipos, DevStatus *st, int *flag, cudaGrap
 void launch_bobjective(int n_inst, int G, const double *c64, const double *x, double *obj, cudaStream_t s);
 void launch_brestart(int n_inst, DevStatus *st, long long add_max, cudaStream_t s);
 template <typename T>
-void launch_bpack(int n_tasks, int J, const BatchTask *tasks, const int *tmem, const int4 *sub, const int4 *sub2,
+void launch_bpack(int n_tasks, int J, const BatchTask *tasks, const int *memb, const int4 *sub, const int4 *sub2,
                   const double *F64, T *dst, cudaStream_t s);
 }  // namespace opf
 
@@ -128,7 +128,7 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     }
     // tasks: per class p, J / p members of similar shape
     std::vector<BatchTask> tasks;
-    std::vector<int> tmem;
+    std::vector<int> memb;
     for (int q = 1; q <= J; q <<= 1) {
         std::vector<int> cls;
         for (int d = 0; d < S; ++d) if (pd[d] == q) cls.push_back(d);
@@ -143,13 +143,13 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
             t.p = q; t.lp = ilog2(q);
             for (int mb = 0; mb < per; ++mb) {
                 const int d = i + mb < cls.size() ? cls[i + mb] : -1;
-                tmem.push_back(d);
+                memb.push_back(d);
                 if (d < 0) continue;
                 t.nq = std::max(t.nq, nqd[d]);
                 t.f = std::max(t.f, h->h_sf[d]);
                 if (h->h_mode[d]) t.modes |= 1 << mb;
             }
-            for (int mb = per; mb < J; ++mb) tmem.push_back(-1);
+            for (int mb = per; mb < J; ++mb) memb.push_back(-1);
             t.f += t.f & 1;        // rows in pairs (the packed extra row is zero)
             tasks.push_back(t);
         }
@@ -166,10 +166,54 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
         std::vector<int> m2;
         for (int t : ord) {
             t2.push_back(tasks[t]);
-            m2.insert(m2.end(), tmem.begin() + (size_t)t * J, tmem.begin() + (size_t)(t + 1) * J);
+            m2.insert(m2.end(), memb.begin() + (size_t)t * J, memb.begin() + (size_t)(t + 1) * J);
         }
         tasks.swap(t2);
-        tmem.swap(m2);
+        memb.swap(m2);
+    }
+    // FP32 plans with a warp count divisible by 4: lambda and bbar~ of each
+    // task in tensor memory, in the lane quadrant of the warps that run it
+    // (a warp w reaches lanes 32 (w % 4) .. + 31 only).  Longest-first list
+    // scheduling of the tasks over the 4 quadrants by cost, 8 nq columns per
+    // task (per chunk 4 of lambda then 4 of bbar~), at most 512 per quadrant.
+    p->tm = false;
+    if (!dbl && b->allow_tmem && W % 4 == 0) {
+        std::vector<double> load(4, 0.0);
+        std::vector<int> used(4, 0), quad(tasks.size(), -1);
+        bool fits = true;
+        for (size_t t = 0; t < tasks.size() && fits; ++t) {
+            const double cost = tasks[t].nq * (tasks[t].f * (6.0 * 4 + 4 + 2 * tasks[t].lp) + 40.0) + 30.0;
+            int best = -1;
+            for (int q = 0; q < 4; ++q)
+                if (used[q] + 8 * tasks[t].nq <= 512 && (best < 0 || load[q] < load[best])) best = q;
+            if (best < 0) { fits = false; break; }
+            quad[t] = best;
+            load[best] += cost;
+            used[best] += 8 * tasks[t].nq;
+        }
+        if (fits) {
+            std::vector<BatchTask> t2;
+            std::vector<int> m2;
+            int cols[4] = {0, 0, 0, 0};
+            for (int q = 0; q < 4; ++q) {
+                p->qstart[q] = (int)t2.size();
+                for (size_t t = 0; t < tasks.size(); ++t) {
+                    if (quad[t] != q) continue;
+                    BatchTask tk = tasks[t];
+                    tk.tm = (cols[q] << 2) | q;
+                    cols[q] += 8 * tk.nq;
+                    t2.push_back(tk);
+                    m2.insert(m2.end(), memb.begin() + t * J, memb.begin() + (t + 1) * J);
+                }
+            }
+            p->qstart[4] = (int)t2.size();
+            tasks.swap(t2);
+            memb.swap(m2);
+            int mx = std::max(std::max(cols[0], cols[1]), std::max(cols[2], cols[3]));
+            p->tm_cols = 32;
+            while (p->tm_cols < mx) p->tm_cols <<= 1;
+            p->tm = true;
+        }
     }
     // chunk / factor offsets and slot tables
     int ch = 0, fo = 0;
@@ -182,7 +226,7 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
         chg.resize((size_t)ch + (size_t)tk.nq * J, make_int4(-1, -1, -1, -1));
         for (int jpos = 0; jpos < J; ++jpos) {
             const int mb = jpos >> tk.lp, part = jpos & (tk.p - 1);
-            const int d = tmem[t * J + mb];
+            const int d = memb[t * J + mb];
             if (d < 0) continue;
             const int so = h->h_soff[d], n = h->h_sn[d];
             for (int q = 0; q < tk.nq; ++q) {
@@ -228,12 +272,13 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     p->off_bnd = p->off_useg + a16((size_t)L * sizeof(int));
     p->off_red = p->off_bnd + a16((size_t)b->NB * 2 * K * sz);
     p->off_flag = p->off_red + a16((size_t)W * K * 6 * sizeof(double));
-    p->bytes = p->off_flag + a16((size_t)(2 * K + 1) * sizeof(int));
+    p->bytes = p->off_flag + a16((size_t)(2 * K + 4) * sizeof(int));
     if (p->bytes > kMaxSmem) { set_last_error("batch plan: shared memory"); return OPF_E_CAPACITY; }
-    const int rc = dbl ? batch_engine_prepare<double>(K, nq, fg, p->bytes) : batch_engine_prepare<float>(K, nq, fg, p->bytes);
+    const int rc = dbl ? batch_engine_prepare<double>(K, nq, fg, p->tm, p->bytes)
+                       : batch_engine_prepare<float>(K, nq, fg, p->tm, p->bytes);
     if (rc) { set_last_error("batch plan: engine attributes"); return OPF_E_CUDA; }
-    const int occ = dbl ? batch_engine_max_ctas_per_sm<double>(K, nq, fg, p->threads, p->bytes)
-                        : batch_engine_max_ctas_per_sm<float>(K, nq, fg, p->threads, p->bytes);
+    const int occ = dbl ? batch_engine_max_ctas_per_sm<double>(K, nq, fg, p->tm, p->threads, p->bytes)
+                        : batch_engine_max_ctas_per_sm<float>(K, nq, fg, p->tm, p->threads, p->bytes);
     if (occ < 1) { set_last_error("batch plan: the engine does not fit an SM"); return OPF_E_CAPACITY; }
     // columns
     p->C = (b->n + K - 1) / K;
@@ -242,7 +287,7 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     // device tables
     std::vector<void *> &A = p->allocs;
     BTRY(bupload(A, &p->d_tasks, tasks, st));
-    BTRY(bupload(A, &p->d_tmem, tmem, st));
+    BTRY(bupload(A, &p->d_memb, memb, st));
     BTRY(bupload(A, &p->d_sch, sch, st));
     BTRY(bupload(A, &p->d_useg, useg, st));
     BTRY(bupload(A, &p->d_chg, chg, st));
@@ -263,9 +308,9 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     BTRY(arr(&p->mu, nslot)); BTRY(arr(&p->ds, nslot)); BTRY(arr(&p->bt, nslot)); BTRY(arr(&p->lref, nslot));
     BTRY(arr(&p->xo, nglob)); BTRY(arr(&p->ct, nglob)); BTRY(arr(&p->xrf, nglob));
     BTRY(arr(&p->lbt, nbnd)); BTRY(arr(&p->ubt, nbnd));
-    if (dbl) launch_bpack<double>(p->n_tasks, J, p->d_tasks, p->d_tmem, h->d_sub, h->d_sub2, h->d_F64,
+    if (dbl) launch_bpack<double>(p->n_tasks, J, p->d_tasks, p->d_memb, h->d_sub, h->d_sub2, h->d_F64,
                                   (double *)p->d_F, st);
-    else launch_bpack<float>(p->n_tasks, J, p->d_tasks, p->d_tmem, h->d_sub, h->d_sub2, h->d_F64,
+    else launch_bpack<float>(p->n_tasks, J, p->d_tasks, p->d_memb, h->d_sub, h->d_sub2, h->d_F64,
                              (float *)p->d_F, st);
     BCUDA(cudaGetLastError());
     {
@@ -323,6 +368,9 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
     a.lbt = (const T *)p.lbt; a.ubt = (const T *)p.ubt;
     a.inst = p.d_inst; a.st = b->d_st;
     a.rho = (T)rho; a.inv_rho = (T)(1.0 / rho); a.rho_d = rho;
+    a.tm = p.tm ? 1 : 0;
+    a.tm_cols = p.tm_cols;
+    for (int q = 0; q < 5; ++q) a.qstart[q] = p.qstart[q];
     return a;
 }
 
@@ -667,11 +715,19 @@ int opf_batch_set_shape(opf_batch *b, int32_t precision, int32_t k_inst, int32_t
     return OPF_OK;
 }
 
+int opf_batch_set_tmem(opf_batch *b, int32_t enable) {
+    if (!b) return OPF_E_INVALID;
+    b->allow_tmem = enable != 0;
+    b->p32.release();
+    return OPF_OK;
+}
+
 int opf_batch_get_shape(opf_batch *b, int32_t precision, int32_t *out, int32_t n_out) {
     if (!b || !out || n_out < 1) return OPF_E_INVALID;
     const BPlan &p = precision == OPF_PREC_FP64 ? b->p64 : b->p32;
-    const int32_t v[8] = {p.ok ? 1 : 0, p.K, p.W, p.nq, p.n_tasks, p.NCH, (int32_t)p.bytes, p.C};
-    for (int i = 0; i < n_out && i < 8; ++i) out[i] = v[i];
+    const int32_t v[10] = {p.ok ? 1 : 0, p.K, p.W, p.nq, p.n_tasks, p.NCH, (int32_t)p.bytes, p.C, p.tm ? 1 : 0,
+                           p.tm_cols};
+    for (int i = 0; i < n_out && i < 10; ++i) out[i] = v[i];
     return OPF_OK;
 }
 

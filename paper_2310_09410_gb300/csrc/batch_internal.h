@@ -11,12 +11,14 @@ struct BPlan {
     bool ok = false, dbl = false, fg = false;   // fg: factors read from global memory
     int K = 0, ks = 0, J = 0, W = 0, nq = 0, threads = 0;
     int NCH = 0, NB = 0, nF = 0, n_tasks = 0, C = 0;
+    bool tm = false;                  // lambda and bbar~ in tensor memory (FP32 plans)
+    int tm_cols = 0, qstart[5] = {0, 0, 0, 0, 0};
     unsigned off_u = 0, off_gt = 0, off_rc = 0, off_task = 0, off_useg = 0, off_bnd = 0, off_red = 0, off_flag = 0;
     unsigned bytes = 0;
     double rho = -1.0;
     std::vector<void *> allocs;
     BatchTask *d_tasks = nullptr;
-    int *d_tmem = nullptr, *d_sch = nullptr, *d_useg = nullptr;
+    int *d_memb = nullptr, *d_sch = nullptr, *d_useg = nullptr;
     int *d_inst = nullptr, *d_ipos = nullptr;
     int4 *d_chg = nullptr, *d_gtab = nullptr;
     void *d_F = nullptr, *d_recip = nullptr, *d_cost = nullptr;
@@ -48,6 +50,7 @@ struct opf_batch {
     std::vector<int> h_bidx;
     BPlan p32, p64;
     int force_k32 = 0, force_w32 = 0, force_k64 = 0, force_w64 = 0;
+    bool allow_tmem = true;              // FP32 plans may keep lambda and bbar~ in tensor memory
     bool have_x = false;
     double timing[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // test parameters given to an instance when its rhs is set

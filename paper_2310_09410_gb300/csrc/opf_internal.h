@@ -195,7 +195,7 @@ struct BatchTask {
     int foff;    // factor element (r, q, jpos, e) at foff + ((r * nq + q) * J + jpos) * 4 + e
     int p, lp;   // positions per member and log2(p)
     int modes;   // bit mb: member mb uses M = F^T F (1) or M = I - F^T F (0)
-    int pad;
+    int tm;      // tensor-memory plans: (first column << 2) | lane quadrant of the task's lambda / bbar~
 };
 
 // Arguments of one batched-engine launch.  Instance column sc of CTA c holds
@@ -207,6 +207,10 @@ template <typename T>
 struct BatchArgs {
     int K, kshift, J, NCH, G, L, NB, n_tasks, nF;
     unsigned off_u, off_gt, off_rc, off_task, off_useg, off_bnd, off_red, off_flag;   // shared-memory byte offsets
+    // Tensor-memory plans (FP32): lambda and bbar~ of every task stay in
+    // tensor memory for the launch; the tasks of lane quadrant q are
+    // [qstart[q], qstart[q + 1]) and run only on warps w with w % 4 == q.
+    int tm, tm_cols, qstart[5];
     const BatchTask *tasks;    // [n_tasks] in decreasing cost
     const int4 *chg;           // [NCH] g * K of each chunk's 4 slots (-1: padding)
     const int4 *gtab;          // [G] (first copy in useg, copies, bounded index or -1, 0)

@@ -191,6 +191,56 @@ def probe_fma(blocks, threads, iters, out_ptr, stream=None):
     return fl.value
 
 
+def _feeder_struct(f):
+    """opf_feeder over numpy copies of the feeder dict's arrays (kept alive
+    by the returned dict)."""
+    keep = {}
+
+    def arr(name, dtype, shape=None):
+        a = np.ascontiguousarray(f[name], dtype=dtype)
+        if shape is not None:
+            a = a.reshape(shape)
+        keep[name] = a
+        return _ptr(a)
+
+    nb, nl, nd, ng = int(f["n_bus"]), len(f["line_from"]), len(f["load_bus"]), len(f["gen_bus"])
+    fd = Feeder()
+    fd.n_bus = nb
+    fd.bus_phases = arr("bus_phases", np.uint8)
+    fd.bus_wmin = arr("bus_wmin", np.float64, (nb * 3,))
+    fd.bus_wmax = arr("bus_wmax", np.float64, (nb * 3,))
+    fd.bus_gsh = arr("bus_gsh", np.float64, (nb * 3,))
+    fd.bus_bsh = arr("bus_bsh", np.float64, (nb * 3,))
+    fd.n_line = nl
+    fd.line_from = arr("line_from", np.int32)
+    fd.line_to = arr("line_to", np.int32)
+    fd.line_phases = arr("line_phases", np.uint8)
+    fd.line_r = arr("line_r", np.float64, (nl * 9,))
+    fd.line_x = arr("line_x", np.float64, (nl * 9,))
+    fd.line_gs_from = arr("line_gs_from", np.float64, (nl * 3,))
+    fd.line_bs_from = arr("line_bs_from", np.float64, (nl * 3,))
+    fd.line_gs_to = arr("line_gs_to", np.float64, (nl * 3,))
+    fd.line_bs_to = arr("line_bs_to", np.float64, (nl * 3,))
+    fd.line_tap = arr("line_tap", np.float64, (nl * 3,))
+    fd.n_load = nd
+    fd.load_bus = arr("load_bus", np.int32)
+    fd.load_phases = arr("load_phases", np.uint8)
+    fd.load_delta = arr("load_delta", np.uint8)
+    fd.load_a = arr("load_a", np.float64, (nd * 3,))
+    fd.load_b = arr("load_b", np.float64, (nd * 3,))
+    fd.load_alpha = arr("load_alpha", np.float64, (nd * 3,))
+    fd.load_beta = arr("load_beta", np.float64, (nd * 3,))
+    fd.n_gen = ng
+    fd.gen_bus = arr("gen_bus", np.int32)
+    fd.gen_phases = arr("gen_phases", np.uint8)
+    fd.gen_pmin = arr("gen_pmin", np.float64, (ng * 3,))
+    fd.gen_pmax = arr("gen_pmax", np.float64, (ng * 3,))
+    fd.gen_qmin = arr("gen_qmin", np.float64, (ng * 3,))
+    fd.gen_qmax = arr("gen_qmax", np.float64, (ng * 3,))
+    fd.gen_cost = arr("gen_cost", np.float64)
+    return fd, keep
+
+
 class Solver:
     """One problem instance on one device (wraps an ``opf_handle``)."""
 
@@ -202,50 +252,7 @@ class Solver:
     @classmethod
     def from_feeder(cls, f, device=0, stream=None):
         lib = load()
-        keep = {}
-
-        def arr(name, dtype, shape=None):
-            a = np.ascontiguousarray(f[name], dtype=dtype)
-            if shape is not None:
-                a = a.reshape(shape)
-            keep[name] = a
-            return _ptr(a)
-
-        nb, nl, nd, ng = int(f["n_bus"]), len(f["line_from"]), len(f["load_bus"]), len(f["gen_bus"])
-        fd = Feeder()
-        fd.n_bus = nb
-        fd.bus_phases = arr("bus_phases", np.uint8)
-        fd.bus_wmin = arr("bus_wmin", np.float64, (nb * 3,))
-        fd.bus_wmax = arr("bus_wmax", np.float64, (nb * 3,))
-        fd.bus_gsh = arr("bus_gsh", np.float64, (nb * 3,))
-        fd.bus_bsh = arr("bus_bsh", np.float64, (nb * 3,))
-        fd.n_line = nl
-        fd.line_from = arr("line_from", np.int32)
-        fd.line_to = arr("line_to", np.int32)
-        fd.line_phases = arr("line_phases", np.uint8)
-        fd.line_r = arr("line_r", np.float64, (nl * 9,))
-        fd.line_x = arr("line_x", np.float64, (nl * 9,))
-        fd.line_gs_from = arr("line_gs_from", np.float64, (nl * 3,))
-        fd.line_bs_from = arr("line_bs_from", np.float64, (nl * 3,))
-        fd.line_gs_to = arr("line_gs_to", np.float64, (nl * 3,))
-        fd.line_bs_to = arr("line_bs_to", np.float64, (nl * 3,))
-        fd.line_tap = arr("line_tap", np.float64, (nl * 3,))
-        fd.n_load = nd
-        fd.load_bus = arr("load_bus", np.int32)
-        fd.load_phases = arr("load_phases", np.uint8)
-        fd.load_delta = arr("load_delta", np.uint8)
-        fd.load_a = arr("load_a", np.float64, (nd * 3,))
-        fd.load_b = arr("load_b", np.float64, (nd * 3,))
-        fd.load_alpha = arr("load_alpha", np.float64, (nd * 3,))
-        fd.load_beta = arr("load_beta", np.float64, (nd * 3,))
-        fd.n_gen = ng
-        fd.gen_bus = arr("gen_bus", np.int32)
-        fd.gen_phases = arr("gen_phases", np.uint8)
-        fd.gen_pmin = arr("gen_pmin", np.float64, (ng * 3,))
-        fd.gen_pmax = arr("gen_pmax", np.float64, (ng * 3,))
-        fd.gen_qmin = arr("gen_qmin", np.float64, (ng * 3,))
-        fd.gen_qmax = arr("gen_qmax", np.float64, (ng * 3,))
-        fd.gen_cost = arr("gen_cost", np.float64)
+        fd, keep = _feeder_struct(f)
         opts = Options(int(device), C.c_void_p(stream) if stream else None)
         h = C.c_void_p()
         _check(lib.opf_create(C.byref(fd), C.byref(opts), C.byref(h)), "opf_create")
@@ -394,10 +401,15 @@ class Batch:
         _check(load().opf_batch_set_shape(self._b, int(precision), int(k_inst), int(warps)), "opf_batch_set_shape")
 
     def shape(self, precision=PREC_FP32):
-        out = np.zeros(8, np.int32)
-        _check(load().opf_batch_get_shape(self._b, int(precision), _ptr(out), 8), "opf_batch_get_shape")
-        keys = ("ok", "k_inst", "warps", "chunks_per_lane", "tasks", "chunks", "smem_bytes", "ctas")
+        out = np.zeros(10, np.int32)
+        _check(load().opf_batch_get_shape(self._b, int(precision), _ptr(out), 10), "opf_batch_get_shape")
+        keys = ("ok", "k_inst", "warps", "chunks_per_lane", "tasks", "chunks", "smem_bytes", "ctas", "tmem",
+                "tmem_cols")
         return {k: int(v) for k, v in zip(keys, out)}
+
+    def set_tmem(self, enable):
+        """FP32 engine: lambda and bbar~ in tensor memory (True) or streamed from L2."""
+        _check(load().opf_batch_set_tmem(self._b, int(bool(enable))), "opf_batch_set_tmem")
 
     def solve(self, rho=100.0, eps_rel=1e-8, eps_abs_pres=1e-4, max_iter=1_000_000, check_every=50,
               precision=PREC_MIXED, recenter_every=0, flags=0):
@@ -606,3 +618,81 @@ class SMPartition:
         if self.stream:
             load().opf_stream_destroy_partition(C.c_void_p(self.stream))
             self.stream = None
+
+
+def partition(f, n_parts, n_sub):
+    """Part of each of the feeder model's n_sub subsystems (opf_partition)."""
+    fd, keep = _feeder_struct(f)
+    out = np.zeros(n_sub, np.int32)
+    _check(load().opf_partition(C.byref(fd), int(n_parts), _ptr(out), int(n_sub)), "opf_partition")
+    return out
+
+
+def apply_test_rule(sums, rho, eps_rel, eps_abs_pres):
+    """Sec. III-C test on summed squares (opf_test_rule): (converged, [pres,
+    dres, eps_prim / eps_rel, eps_dual / eps_rel, objective])."""
+    sm = np.ascontiguousarray(sums, np.float64)
+    out = np.zeros(5)
+    rc = load().opf_test_rule(_ptr(sm), float(rho), float(eps_rel), float(eps_abs_pres), _ptr(out))
+    if rc < 0:
+        raise OPFError(rc, "opf_test_rule")
+    return bool(rc), out
+
+
+class Shard:
+    """One part of a sharded instance (wraps an ``opf_shard``); the caller
+    exchanges the cut sums between partial() and step()."""
+
+    def __init__(self, f, sub_part, part, device=0, stream=None):
+        fd, self._keep = _feeder_struct(f)
+        sp = np.ascontiguousarray(sub_part, np.int32)
+        self._keep["sub_part"] = sp
+        opts = Options(int(device), C.c_void_p(stream) if stream else None)
+        h = C.c_void_p()
+        _check(load().opf_shard_create(C.byref(fd), _ptr(sp), len(sp), int(part), C.byref(opts), C.byref(h)),
+               "opf_shard_create")
+        self._s = h
+        g, c, l = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().opf_shard_sizes(h, C.byref(g), C.byref(c), C.byref(l)), "opf_shard_sizes")
+        self.n_global, self.n_cut, self.n_slots = g.value, c.value, l.value
+        self.global_of_local = np.zeros(self.n_global, np.int32)
+        self.cut_global = np.zeros(max(self.n_cut, 1), np.int32)
+        _check(load().opf_shard_maps(h, _ptr(self.global_of_local), _ptr(self.cut_global)), "opf_shard_maps")
+        self.cut_global = self.cut_global[:self.n_cut]
+        self.stream = load().opf_shard_stream(h)
+
+    def precompute(self):
+        _check(load().opf_shard_precompute(self._s), "opf_shard_precompute")
+
+    def partial(self, rho, sig_ptr):
+        _check(load().opf_shard_partial(self._s, float(rho), sig_ptr), "opf_shard_partial")
+
+    def step(self, rho, sig_tot_ptr, sums_ptr=None):
+        _check(load().opf_shard_step(self._s, float(rho), sig_tot_ptr, sums_ptr), "opf_shard_step")
+
+    def x(self):
+        out = np.zeros(self.n_global)
+        _check(load().opf_shard_get_x(self._s, _ptr(out)), "opf_shard_get_x")
+        return out
+
+    def locals(self):
+        xs, lam = np.zeros(self.n_slots), np.zeros(self.n_slots)
+        _check(load().opf_shard_get_locals(self._s, _ptr(xs), _ptr(lam), self.n_slots), "opf_shard_get_locals")
+        return xs, lam
+
+    def close(self):
+        if self._s:
+            load().opf_shard_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -140,6 +140,55 @@ def test_batch_converged_objective(name, seed, n_scen):
         assert abs(obj[j] - obj_star) <= TOL_OBJ * abs(obj_star), (j, obj[j], obj_star)
 
 
+@pytest.mark.parametrize("name,seed,n,k,w", [("123", 2001, 24, 8, 16), ("123", 2001, 10, 4, 12),
+                                             ("13", 1001, 12, 8, 8), ("34", 5034, 9, 2, 16)])
+def test_fp32_engine_tensor_memory_matches_l2_streaming(name, seed, n, k, w):
+    """The FP32 engine with lambda and bbar~ held in tensor memory gives
+    bit-identical iterates to the same engine shape streaming them from L2
+    (the arithmetic is the same; only where the two arrays live differs)."""
+    f = synth.preset_feeder(name, seed)
+    fs = scenarios(f, [4700 + j for j in range(n)])
+    out = {}
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        with opf.Batch(s, n) as b:
+            for tm in (True, False):
+                b.set_tmem(tm)
+                b.set_shape(opf.PREC_FP32, k, w)
+                b.set_loads(0, *load_arrays(fs))
+                b.solve(eps_rel=0.0, max_iter=400, check_every=50, precision=opf.PREC_FP32)
+                sh = b.shape(opf.PREC_FP32)
+                assert sh["tmem"] == (1 if tm else 0) and sh["k_inst"] == k and sh["warps"] == w
+                out[tm] = [b.locals(j) for j in range(n)]
+                assert np.all(b.status()["iters"] == 400)
+    for j in range(n):
+        assert np.array_equal(out[True][j][0], out[False][j][0]), j
+        assert np.array_equal(out[True][j][1], out[False][j][1]), j
+
+
+def test_fp32_engine_tensor_memory_freezes_finished_instances():
+    """Instances that stop at different test iterations inside one launch:
+    each keeps the lambda of its stopping iteration (written from tensor
+    memory when it froze), so results equal the L2-streaming engine's."""
+    f = synth.preset_feeder("13", 1001)
+    fs = scenarios(f, [4800 + j for j in range(16)])
+    res = {}
+    with opf.Solver.from_feeder(f) as s:
+        s.precompute()
+        with opf.Batch(s, len(fs)) as b:
+            for tm in (True, False):
+                b.set_tmem(tm)
+                b.set_shape(opf.PREC_FP32, 8, 16)
+                b.set_loads(0, *load_arrays(fs))
+                assert b.solve(eps_rel=1e-5, precision=opf.PREC_FP32, recenter_every=4000)
+                st = b.status()
+                res[tm] = (st["iters"].copy(), [b.locals(j) for j in range(len(fs))])
+    assert len(set(res[True][0].tolist())) > 1          # the instances stopped at different iterations
+    assert np.array_equal(res[True][0], res[False][0])
+    for j in range(len(fs)):
+        assert np.array_equal(res[True][1][j][1], res[False][1][j][1]), j
+
+
 def _lp_optimum_of_scenario(args):
     """Oracle LP optimum of load scenario `seed` of a preset feeder (runs in
     a worker process)."""
