@@ -55,7 +55,8 @@ struct opf_shard {
     unsigned char *d_own = nullptr;       // per local global: 1 if this shard counts it in the objective
     int *d_cut_local = nullptr;
     double *d_x = nullptr;                // x per local global after the last step
-    double *d_part = nullptr;             // per tile: 6 partial sums
+    double *d_part = nullptr;             // per tile: 6 partial sums (n_tiles known after the precompute)
+    int part_cap = 0;                     // tiles d_part holds
     int parity = 0;                       // u of the last iteration at d_u64 + parity * L
     bool started = false;
     double rho = -1.0;
@@ -346,7 +347,6 @@ int opf_shard_create(const opf_feeder *f, const int32_t *sub_part, int32_t n_sub
     }
     sh->n_cut = (int)sh->cut_local.size();
     opf_handle *h = sh->h;
-    sh->n_tiles = h->t64.n_tiles;
     auto up = [&](auto **dst, const auto &v) -> int {
         using E = typename std::decay<decltype(v[0])>::type;
         void *p = nullptr;
@@ -358,9 +358,9 @@ int opf_shard_create(const opf_feeder *f, const int32_t *sub_part, int32_t n_sub
         *dst = reinterpret_cast<std::remove_reference_t<decltype(**dst)> *>(p);
         return OPF_OK;
     };
-    std::vector<double> zx(G, 0.0), zp((size_t)std::max(sh->n_tiles, 1) * 6, 0.0);
+    std::vector<double> zx(G, 0.0);
     if ((rc = up(&sh->d_cutj, cutj)) || (rc = up(&sh->d_ntot, nt)) || (rc = up(&sh->d_own, own)) ||
-        (rc = up(&sh->d_cut_local, sh->cut_local)) || (rc = up(&sh->d_x, zx)) || (rc = up(&sh->d_part, zp))) {
+        (rc = up(&sh->d_cut_local, sh->cut_local)) || (rc = up(&sh->d_x, zx))) {
         opf_shard_destroy(sh);
         return fail(rc, "shard: device allocation");
     }
@@ -372,7 +372,19 @@ int opf_shard_precompute(opf_shard *sh) {
     if (!sh) return OPF_E_INVALID;
     const int rc = opf_precompute(sh->h);
     sh->started = false;
-    return rc;
+    if (rc != OPF_OK) return rc;
+    // the tiling of the shard's subsystems exists from here on: room for the
+    // per-tile test sums
+    opf_handle *h = sh->h;
+    sh->n_tiles = h->t64.n_tiles;
+    if (sh->n_tiles > sh->part_cap) {
+        if (sh->d_part) cudaFree(sh->d_part);
+        sh->d_part = nullptr;
+        sh->part_cap = 0;
+        SH_CUDA(cudaMalloc(&sh->d_part, (size_t)sh->n_tiles * 6 * sizeof(double)));
+        sh->part_cap = sh->n_tiles;
+    }
+    return OPF_OK;
 }
 
 int opf_shard_sizes(opf_shard *sh, int32_t *n_global, int32_t *n_cut, int32_t *n_slots) {
@@ -414,8 +426,8 @@ int opf_shard_partial(opf_shard *sh, double rho, double *sig) {
 int opf_shard_step(opf_shard *sh, double rho, const double *sig_tot, double *sums) {
     if (!sh || !(rho > 0) || (!sig_tot && sh->n_cut)) return OPF_E_INVALID;
     opf_handle *h = sh->h;
-    if (!h->precomputed || !sh->started || sh->rho != rho) {
-        set_last_error("shard: call opf_shard_partial with the same rho before each step");
+    if (!h->precomputed || !sh->started || sh->rho != rho || h->t64.n_tiles > sh->part_cap) {
+        set_last_error("shard: call opf_shard_precompute, then opf_shard_partial with the same rho before each step");
         return OPF_E_STATE;
     }
     SH_CUDA(cudaSetDevice(h->device));
@@ -463,7 +475,10 @@ void *opf_shard_stream(opf_shard *sh) { return sh ? (void *)sh->h->stream : null
 
 void opf_shard_destroy(opf_shard *sh) {
     if (!sh) return;
-    opf_destroy(sh->h);      // frees the shard's device arrays with the handle's
+    if (sh->h) cudaSetDevice(sh->h->device);
+    if (sh->h) cudaStreamSynchronize(sh->h->stream);
+    if (sh->d_part) cudaFree(sh->d_part);
+    opf_destroy(sh->h);      // frees the shard's other device arrays with the handle's
     delete sh;
 }
 

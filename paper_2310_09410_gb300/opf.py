@@ -141,6 +141,21 @@ def load(path: str = LIB_PATH):
                                                 C.POINTER(C.c_int32)]
     lib.opf_stream_destroy_partition.argtypes = [C.c_void_p]
     lib.opf_probe_fma.argtypes = [C.c_int32, C.c_int32, C.c_int32, _P, _P, C.POINTER(C.c_double)]
+    lib.opf_batch_set_tmem.argtypes = [H, C.c_int32]
+    lib.opf_partition.argtypes = [C.POINTER(Feeder), C.c_int32, _P, C.c_int32]
+    lib.opf_shard_create.argtypes = [C.POINTER(Feeder), _P, C.c_int32, C.c_int32, C.POINTER(Options), C.POINTER(H)]
+    lib.opf_shard_precompute.argtypes = [H]
+    lib.opf_shard_sizes.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.opf_shard_maps.argtypes = [H, _P, _P]
+    lib.opf_shard_partial.argtypes = [H, C.c_double, _P]
+    lib.opf_shard_step.argtypes = [H, C.c_double, _P, _P]
+    lib.opf_shard_get_x.argtypes = [H, _P]
+    lib.opf_shard_get_locals.argtypes = [H, _P, _P, C.c_size_t]
+    lib.opf_shard_stream.argtypes = [H]
+    lib.opf_shard_stream.restype = C.c_void_p
+    lib.opf_shard_destroy.argtypes = [H]
+    lib.opf_shard_destroy.restype = None
+    lib.opf_test_rule.argtypes = [_P, C.c_double, C.c_double, C.c_double, _P]
     for name in ("opf_create", "opf_create_generic", "opf_precompute", "opf_solve", "opf_solve_ex",
                  "opf_step", "opf_reset", "opf_get_solution", "opf_get_residuals", "opf_get_locals",
                  "opf_set_locals", "opf_get_sizes", "opf_get_timing", "opf_global_update_static",
@@ -152,7 +167,10 @@ def load(path: str = LIB_PATH):
                  "opf_server_submit", "opf_server_step", "opf_server_poll", "opf_server_take_solution",
                  "opf_server_stats", "opf_stream_create_partition", "opf_stream_destroy_partition",
                  "opf_probe_fma", "opf_server_poll_ex", "opf_server_set_admission", "opf_server_model_stats",
-                 "opf_batch_set_start", "opf_server_set_model_start"):
+                 "opf_batch_set_start", "opf_server_set_model_start", "opf_batch_set_tmem", "opf_partition",
+                 "opf_shard_create", "opf_shard_precompute", "opf_shard_sizes", "opf_shard_maps",
+                 "opf_shard_partial", "opf_shard_step", "opf_shard_get_x", "opf_shard_get_locals",
+                 "opf_test_rule"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
