@@ -69,7 +69,7 @@ FP32_LANES = 128
 # DRAM bytes per launch of the dominant kernels, copied from the ncu captures
 # summarised in profiles/ (a copied constant, labelled so in the line; None
 # once the kernel has changed since the capture).
-BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 83461632 + 33740800
+BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 69220096 + 2185728
 BATCH_ENGINE_TRAFFIC_SOURCE = "profiles/k_batch_engine_123bus_x1024.md"
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 516864 + 768
 PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8708352 + 313088

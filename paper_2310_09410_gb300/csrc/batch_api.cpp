@@ -329,6 +329,7 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
 }
 
 constexpr int kBatchRecenter = 2000;
+constexpr int kPolishCheck = 2;     // test interval of a mixed solve's FP64 polish
 
 int plan_set_rho(opf_batch *b, BPlan *p, double rho) {
     if (p->rho == rho) return OPF_OK;
@@ -785,8 +786,13 @@ int opf_batch_solve(opf_batch *b, const opf_solve_opts *opts) {
         long long least = 0;
         for (size_t i = 0; i < b->h_st.size(); ++i) least = i ? std::min(least, b->h_st[i].iter) : b->h_st[i].iter;
         b->iter_base[1] = least;
+        // the polish of a mixed solve starts from iterates that already met the
+        // test in FP32: it tests every kPolishCheck iterations (at most 2 k of
+        // them), so an instance whose FP64 iterates meet the test at once stops
+        // after kPolishCheck FP64 iterations instead of k
+        const int kp = o.precision == OPF_PREC_MIXED ? std::min(k, kPolishCheck) : k;
         if (o.precision == OPF_PREC_MIXED) launch_brestart(b->n, b->d_st, 2LL * k, h->stream);
-        BTRY(run_loop(b, b->p64, o.rho, R, k, hl));
+        BTRY(run_loop(b, b->p64, o.rho, std::max(kp, (R / kp) * kp), kp, hl));
     }
     launch_bobjective(b->n, b->G, h->d_c64, b->d_x, b->d_obj, h->stream);
     BCUDA(cudaEventRecord(b->ev[2], h->stream));

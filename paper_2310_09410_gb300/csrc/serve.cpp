@@ -297,9 +297,11 @@ int step_batched_enqueue(opf_server *s, Model &m) {
                          (m.n32 + b->p32.K - 1) / b->p32.K);
     }
     if (m.n64) {
+        // slots in the polish met the test in FP32 already: tested every 2
+        // FP64 iterations, so most leave after the first test
         STRY(plan_set_rho(b, &b->p64, s->o.rho));
-        enqueue_body_any(b, b->p64, s->o.rho, R64, k, cudaGraphConditionalHandle{}, 0, nullptr, nullptr,
-                         (m.n64 + b->p64.K - 1) / b->p64.K, m.s64);
+        enqueue_body_any(b, b->p64, s->o.rho, R64, std::min(k, 2), cudaGraphConditionalHandle{}, 0, nullptr,
+                         nullptr, (m.n64 + b->p64.K - 1) / b->p64.K, m.s64);
     }
     SCUDA(cudaEventRecord(m.ev64, m.s64));
     SCUDA(cudaStreamWaitEvent(b->h->stream, m.ev64, 0));
