@@ -464,6 +464,44 @@ def count_launches_batch(t):
     return 3 + 1 + 4 + 6 * (t["fp32_passes"] + t["fp64_passes"]) + 2 + 1
 
 
+# Single-instance configurations reported beside the batch: (feeder, precision,
+# timed solves); one untimed solve first (graph and engine plans).
+SINGLE_RECORDS = (("13", "fp64", 20), ("13", "mixed", 20), ("123", "fp64", 3), ("123", "mixed", 5),
+                  ("8500", "mixed", 1))
+
+
+def single_records(opf, synth, device, stream):
+    """Plain FP64 and FP32 + FP64-polish solves of single instances (the
+    13-, 123- and 8500-bus configurations), each timed with CUDA events on the
+    library's stream around precompute + solve + read-back."""
+    import torch
+    out = {}
+    for name, prec, n in SINGLE_RECORDS:
+        f = synth.preset_feeder(name, SINGLE_SEEDS[name])
+        s = opf.Solver.from_feeder(f, device=device, stream=stream.cuda_stream)
+        p = opf.PREC_FP64 if prec == "fp64" else opf.PREC_MIXED
+        kw = dict(rho=RHO, eps_rel=SINGLE_EPS_REL[name], eps_abs_pres=EPS_ABS, max_iter=6_000_000, precision=p)
+        s.precompute()
+        s.solve(**dict(kw, max_iter=2000) if name == "8500" else kw)       # plans, graphs
+        times, ok = [], True
+        for _ in range(n):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.precompute()
+            ok &= s.solve(**kw)
+            x, obj = s.solution()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        r = s.residuals()
+        out[f"{name}_{prec}"] = {"solves_per_s": 1e3 * n / sum(times), "ms_per_solve": sum(times) / n,
+                                 "iterations": int(r["iters"]), "objective": obj, "pres": r["pres"],
+                                 "converged": bool(ok), "solves_timed": n}
+        s.close()
+    return out
+
+
 def plain_fp64_reference(opf, f, device, stream, n=2):
     """Solves/s of the plain single-instance FP64 GPU path on the feeder."""
     import torch
@@ -494,7 +532,7 @@ def run_batch(args, rank, world, local):
     import torch.distributed as dist
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2310_09410_gb300 import opf
+    from paper_2310_09410_gb300 import opf, synth
 
     n = args.instances
     f = feeder()
@@ -611,6 +649,7 @@ def run_batch(args, rank, world, local):
                     "so achieved is over-stated by about that much" % th["fp64_passes"]}
 
     plain = None if args.no_plain_fp64 else plain_fp64_reference(opf, f, local, stream)
+    singles = single_records(opf, synth, local, stream) if args.single_records else None
     serve = None
     if args.serve_requests > 0:
         # the serving workload, short: the metric's p50/p99 latency per feeder class
@@ -640,9 +679,19 @@ def run_batch(args, rank, world, local):
                 "roofline": roof, "clocks": clocks, "gpu_launches": int(launches)}
         if serve is not None:
             line["serve"] = serve
+        if singles is not None:
+            line["single"] = singles
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(fs)
             line["oracle_error"] = oracle_error(fs, obj_h, st_h["pres"], x=x_h, locals_of=batch.locals)
+            if singles is not None:
+                # the single-instance objectives against the oracle's LP optimum
+                # (the 8500-bus LP takes the host about half a minute: not here)
+                for key, rec in singles.items():
+                    name = key.split("_")[0]
+                    if name != "8500":
+                        star = _lp_optimum(synth.preset_feeder(name, SINGLE_SEEDS[name]))
+                        rec["obj_rel_err"] = abs(rec["objective"] - star) / abs(star)
         print(json.dumps(line), flush=True)
     batch.close()
     solver.close()
@@ -973,6 +1022,8 @@ def main():
                     help="serve: bound on an 8500-bus request's run time once admitted")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="batch workload: measured requests of the serving sub-record (0: none)")
+    ap.add_argument("--no-single-records", dest="single_records", action="store_false",
+                    help="batch workload: skip the single-instance sub-records (13/123/8500 buses)")
     ap.add_argument("--big-handles", type=int, default=2, help="serve: 8500-bus worker handles")
     ap.add_argument("--max-iter", type=int, default=1_000_000, help="serve: iteration cap per request")
     ap.add_argument("--mix", default="0.4,0.3,0.2,0.1", help="serve: weights of the 13/34/123/8500-bus requests")
