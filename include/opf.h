@@ -332,7 +332,8 @@ int opf_batch_step(opf_batch *b, double rho, int32_t n_iters);
 int opf_batch_set_shape(opf_batch *b, int32_t precision, int32_t k_inst, int32_t warps);
 int opf_batch_get_shape(opf_batch *b, int32_t precision, int32_t *out, int32_t n_out);
 
-/* FP32 engine storage (default 1): with 1, a plan whose warp count is a
+/* FP32 engine storage, an implementation choice with no counterpart in the
+ * paper (default 1): with 1, a plan whose warp count is a
  * multiple of 4 keeps lambda and bbar~ of its CTA's instances in tensor
  * memory (tcgen05 TMEM, allocated per CTA for each launch) when they fit in
  * 512 columns per lane quadrant, instead of streaming them from L2 every
@@ -428,7 +429,8 @@ int opf_server_set_model_tolerance(opf_server *s, int32_t model, double eps_rel,
  * the other requests.  NULL, NULL returns to the Sec. V-A start. */
 int opf_server_set_model_start(opf_server *s, int32_t model, const double *xs, const double *lam);
 
-/* Admission policy of one model (default: no bounds; 0 = no bound).
+/* Admission policy of one model (default: no bounds; 0 = no bound); the
+ * paper has no serving layer, so no passage defines it.
  * max_queue bounds the requests waiting for a slot.  max_wait_s bounds the
  * seconds a request may wait for one: at submit the wait is predicted from
  * the requests ahead (queued and running, served `slots` at a time) and the
@@ -474,7 +476,8 @@ int opf_server_take_solution(opf_server *s, int64_t tag, double *x, int32_t n);
 /* [0] submitted (refused ones included), [1] polled, [2] queued,
  * [3] running, [4] slots, [5] passes, [6] device bytes held for slots. */
 int opf_server_stats(opf_server *s, int64_t *out, int32_t n);
-/* Per model: [0] submitted, [1] served (finished after running, stopped
+/* Serving statistics (no counterpart in the paper).  Per model: [0]
+ * submitted, [1] served (finished after running, stopped
  * ones included), [2] of those converged, [3] refused at submit, [4] shed
  * from the queue, [5] queued, [6] running, [7] slots, [8] mean service time
  * in microseconds, [9] stopped by the service bound (part of [1]).

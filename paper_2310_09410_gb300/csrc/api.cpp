@@ -813,6 +813,14 @@ static int build_persist_plan(opf_handle *h, PersistPlan *pp, int P, int n_sm) {
     take(&c.off_misc, 16 + ((sizeof(DevStatus) + 15) & ~(size_t)15) + 32 * 6 * sizeof(double));
     c.bytes = (unsigned)off;
     c.threads = (int)std::min<long long>(kPersistMaxThreads, std::max<long long>(64, (std::max(mk, mj) + 31) / 32 * 32));
+    // plans of small CTAs (one or a few subsystems each: the 123-bus feeder)
+    // run phase B with each factor column on 4 lanes, given threads for it;
+    // large ones keep one lane per column (the split measured slower there)
+    c.split = 0;
+    if (c.threads <= 128) {
+        c.split = 1;
+        c.threads = (int)std::min<long long>(kPersistMaxThreads, std::max<long long>(c.threads, (4 * mj + 31) / 32 * 32));
+    }
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if ((long long)c.bytes > optin) return OPF_OK;

@@ -153,6 +153,7 @@ struct ClusterLayout {
 constexpr int kPersistMaxThreads = 512;
 struct PersistLayout {
     int P, L, threads;
+    int split;                     // phase B: a factor column on 4 lanes (plans of small CTAs)
     unsigned off_F, off_srec, off_items, off_meta, off_segp, off_pk, off_bt, off_ds, off_mu;
     unsigned off_ct, off_lbt, off_ubt, off_vbx, off_vbw, off_tb, off_recip, off_xrs, off_lrs, off_cobj;
     unsigned off_misc;

@@ -25,6 +25,7 @@
 // CTAs spread along the chains of neighbours.)
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "opf_internal.h"
@@ -113,6 +114,43 @@ __device__ __forceinline__ double dot_fv<double>(const double *__restrict__ f, c
     return a0 + a1;
 }
 
+// Part `part` (0..3) of <f, v> over the zero-padded column: 4-row vectors at
+// rows 4 part, 4 part + 16, ...
+template <typename T>
+__device__ __forceinline__ T dot_fv_part(const T *__restrict__ f, const T *__restrict__ v, int npad, int part);
+
+template <>
+__device__ __forceinline__ float dot_fv_part<float>(const float *__restrict__ f, const float *__restrict__ v,
+                                                    int npad, int part) {
+    float a0 = 0.0f, a1 = 0.0f;
+    for (int r = 4 * part; r < npad; r += 16) {
+        const float4 a = *reinterpret_cast<const float4 *>(f + r);
+        const float4 b = *reinterpret_cast<const float4 *>(v + r);
+        a0 = fmaf(a.x, b.x, a0);
+        a1 = fmaf(a.y, b.y, a1);
+        a0 = fmaf(a.z, b.z, a0);
+        a1 = fmaf(a.w, b.w, a1);
+    }
+    return a0 + a1;
+}
+
+template <>
+__device__ __forceinline__ double dot_fv_part<double>(const double *__restrict__ f, const double *__restrict__ v,
+                                                      int npad, int part) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int r = 4 * part; r < npad; r += 16) {
+        const double2 a = *reinterpret_cast<const double2 *>(f + r);
+        const double2 b = *reinterpret_cast<const double2 *>(v + r);
+        const double2 c = *reinterpret_cast<const double2 *>(f + r + 2);
+        const double2 d = *reinterpret_cast<const double2 *>(v + r + 2);
+        a0 = fma(a.x, b.x, a0);
+        a1 = fma(a.y, b.y, a1);
+        a0 = fma(c.x, d.x, a0);
+        a1 = fma(c.y, d.y, a1);
+    }
+    return a0 + a1;
+}
+
 // Column stride of a staged factor with npad rows: npad, plus 4 words when
 // npad is a multiple of 8, so that the 16-byte column reads of 8 consecutive
 // threads (consecutive columns) fall in distinct bank groups.
@@ -121,7 +159,7 @@ __host__ __device__ __forceinline__ int fstride(int npad) { return npad + ((npad
 // Part ranges: pr[field * (P + 1) + rank].
 enum { GR_K = 0, GR_S, GR_J, GR_F, GR_V, GR_NFIELDS };
 
-template <typename T>
+template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<T> g, PersistLayout lay, PersistPtrs pp, T *U,
                                                          int bar_extra, int n_iters, int check_every, DevStatus *st,
                                                          double rho_d, cudaGraphConditionalHandle cond,
@@ -240,12 +278,34 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
             }
         }
         __syncthreads();
-        // B: t = F^T v per own factor column
-        for (int j = threadIdx.x; j < nj; j += blockDim.x) {
-            const int itm = items[j];
-            const int4 r = srec[itm >> 8];
-            const int c = itm & 255, npad = (r.w >> 1) & 0x1ff;
-            tb[r.z + c] = dot_fv<T>(F + r.x + c * fstride(npad), vbw + r.y, npad);
+        // B: t = F^T v per own factor column.  SPLIT plans (small CTAs, given
+        // threads for it): each column on a group of 4 lanes (rows r, r + 16,
+        // .. of a lane in 4-row vectors, then a shuffle sum), so the longest
+        // column is no longer one lane's dependent chain; otherwise one lane
+        // per column.  The split loop's bound is rounded to whole warps.
+        if (!SPLIT || 4 * nj > (int)blockDim.x) {
+            for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+                const int itm = items[j];
+                const int4 r = srec[itm >> 8];
+                const int c = itm & 255, npad = (r.w >> 1) & 0x1ff;
+                tb[r.z + c] = dot_fv<T>(F + r.x + c * fstride(npad), vbw + r.y, npad);
+            }
+        } else {
+            const int nj4 = ((4 * nj + 31) >> 5) << 5;
+            for (int jj = threadIdx.x; jj < nj4; jj += blockDim.x) {
+                const int j = jj >> 2, part = jj & 3;
+                T acc = (T)0;
+                int itm = 0;
+                if (j < nj) {
+                    itm = items[j];
+                    const int4 r = srec[itm >> 8];
+                    const int c = itm & 255, npad = (r.w >> 1) & 0x1ff;
+                    acc = dot_fv_part<T>(F + r.x + c * fstride(npad), vbw + r.y, npad, part);
+                }
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                if (j < nj && part == 0) tb[srec[itm >> 8].z + (itm & 255)] = acc;
+            }
         }
         __syncthreads();
         // C: projection, dual update, u to the next iteration's buffer
@@ -350,18 +410,21 @@ __global__ void __launch_bounds__(kPersistMaxThreads) k_persist_engine(IterArgs<
 
 template <typename T>
 int prepare_persist_engine(unsigned bytes) {
-    return cudaFuncSetAttribute(k_persist_engine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-                   cudaSuccess
-               ? 0
-               : -1;
+    for (const void *fn : {(const void *)k_persist_engine<T, false>, (const void *)k_persist_engine<T, true>})
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+            return -1;
+    return 0;
 }
 
-// CTAs of `threads` threads and `bytes` of shared memory resident per SM.
+// CTAs per SM that both variants reach.
 template <typename T>
 int persist_occupancy(int threads, unsigned bytes) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist_engine<T>, threads, bytes) != cudaSuccess)
-        return 0;
+    int n = 1 << 30;
+    for (const void *fn : {(const void *)k_persist_engine<T, false>, (const void *)k_persist_engine<T, true>}) {
+        int m = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, fn, threads, bytes) != cudaSuccess) return 0;
+        n = std::min(n, m);
+    }
     return n;
 }
 
@@ -382,8 +445,11 @@ int launch_persist_engine(const IterArgs<T> &g, const PersistLayout &lay, const 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_persist_engine<T>, g, lay, pp, U, bar_extra, n_iters,
-                                             check_every, st, rho, cond, use_cond);
+    const cudaError_t e =
+        lay.split ? cudaLaunchKernelEx(&cfg, k_persist_engine<T, true>, g, lay, pp, U, bar_extra, n_iters, check_every,
+                                       st, rho, cond, use_cond)
+                  : cudaLaunchKernelEx(&cfg, k_persist_engine<T, false>, g, lay, pp, U, bar_extra, n_iters,
+                                       check_every, st, rho, cond, use_cond);
     return e == cudaSuccess ? 0 : -1;
 }
 

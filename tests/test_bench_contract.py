@@ -46,3 +46,25 @@ def test_fp64_engine_rule_and_launch_counts():
     assert bench.count_launches_single(st, "fp64", warp64=True) == 3 + 1 + 1 + 1
     st = {"main_iters": 26000, "polish_iters": 0}
     assert bench.count_launches_single(st, "fp64", persistent=True) == 3 + 1 + 1 + 2
+
+
+def test_oracle_error_of_the_bench_line():
+    """The per-result error the bench line reports: objectives of oracle
+    solves give errors at the solver's accuracy, a planted offset shows up,
+    and pres recomputed from x and x_s matches the recorded one."""
+    import numpy as np
+    from oracle import admm as oracle_admm, lindist
+    from paper_2310_09410_gb300 import synth
+    f = synth.preset_feeder("13", 1001)
+    fs = [synth.load_scenario(f, 4000 + j) for j in range(3)]
+    res = [oracle_admm.admm(oracle_admm.Prepared(lindist.build(g)), rho=100.0, eps_rel=1e-8, eps_abs_pres=1e-4,
+                            max_iter=200_000, check_every=50) for g in fs]
+    objs = np.array([r.objective for r in res])
+    pres = np.array([r.pres for r in res])
+    x = np.stack([r.x for r in res])
+    out = bench.oracle_error(fs, objs, pres, x=x, locals_of=lambda j: (res[j].xs, res[j].lam), sample=3)
+    assert out["instances"] == 3 and out["pres_host_sample"] == 3
+    assert out["max_obj_rel"] < 1e-6
+    assert out["pres_host_vs_gpu_max_rel_diff"] < 1e-9
+    bad = bench.oracle_error(fs, objs * (1 + 1e-3), pres)
+    assert 0.9e-3 < bad["max_obj_rel"] < 1.1e-3

@@ -114,3 +114,37 @@ def test_server_options_and_handles_checked_on_host(lib):
     lib.opf_server_set_model_tolerance.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double]
     assert lib.opf_server_set_model_tolerance(out, 0, 1e-9, 1e-4) == opf.OPF_E_INVALID   # no model 0
     lib.opf_server_destroy(out)
+
+
+def test_fma_probe_rejects_bad_sizes_on_host(lib):
+    from paper_2310_09410_gb300 import opf
+    for blocks, threads, iters in ((0, 256, 1), (1, 48, 1), (1, 2048, 1), (1, 256, 0)):
+        with pytest.raises(opf.OPFError) as e:
+            opf.probe_fma(blocks, threads, iters, 1)
+        assert e.value.code == opf.OPF_E_INVALID
+
+
+@pytest.mark.gpu
+def test_fma_probe_measures_a_plausible_fp32_rate():
+    """The roofline's denominator: the probe's flop count is the one its
+    kernel performs (8 chains x 16 x iters FMAs per thread, 2 flops each) and
+    its timed rate lies between a tenth of and the nominal FP32 peak."""
+    torch = pytest.importorskip("torch")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2310_09410_gb300 import opf
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = torch.empty(2 * sms * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        opf.probe_fma(2 * sms, 1024, 512, out.data_ptr(), stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fl = opf.probe_fma(2 * sms, 1024, 512, out.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    assert fl == 2.0 * 8 * 16 * 512 * 1024 * 2 * sms
+    tflops = fl / (e0.elapsed_time(e1) / 1e3) / 1e12
+    nominal = sms * 128 * 2 * 2.1e9 / 1e12
+    assert 0.1 * nominal < tflops < 1.05 * nominal, (tflops, nominal)
+    assert torch.isfinite(out).all()
