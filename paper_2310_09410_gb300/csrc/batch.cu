@@ -230,6 +230,10 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
     const int mode1 = (tk.modes >> (jpos >> tk.lp)) & 1;
     T v[4 * NQT], y[4 * NQT];
     double c0 = 0.0, c1 = 0.0, c3 = 0.0, c4 = 0.0;
+    // FP32 plans: a lane's test terms (FP32 already) summed over the task's
+    // chunks in FP32 and added to the FP64 sums once per task (FP64 adds
+    // cost this part 64 FP32 ones)
+    float f0 = 0.f, f1 = 0.f, f3 = 0.f, f4 = 0.f;
     const int ch0 = tk.ch0 + jpos;
     const unsigned tcol = tl + (unsigned)(tk.tm >> 2);
 #pragma unroll
@@ -316,10 +320,17 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
                 t3 += xa * xa;
                 t4 += la * la;
             }
-            c0 += (double)t0;
-            c1 += (double)t1;
-            c3 += (double)t3;
-            c4 += (double)t4;
+            if constexpr (sizeof(T) == 4) {
+                f0 += t0;
+                f1 += t1;
+                f3 += t3;
+                f4 += t4;
+            } else {
+                c0 += (double)t0;
+                c1 += (double)t1;
+                c3 += (double)t3;
+                c4 += (double)t4;
+            }
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) us[upos<K>(ch, e, sc)] = u4.v[e];
@@ -334,6 +345,12 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
         }
     }
     if (check) {
+        if constexpr (sizeof(T) == 4) {
+            c0 = (double)f0;
+            c1 = (double)f1;
+            c3 = (double)f3;
+            c4 = (double)f4;
+        }
         // per instance column: sum over the J member positions, in lane order
         for (int o = K; o < 32; o <<= 1) {
             c0 += __shfl_xor_sync(0xffffffffu, c0, o);
@@ -544,17 +561,30 @@ __global__ void __launch_bounds__(512, 1)
             // x of each global (at its first copy): objective and ||B x||^2 per
             // column on test iterations, and x~ of the running instances for
             // their results (thread column sc = tid % K)
+            // (FP32 plans: x_ref + x~ and the thread's partial sums in FP32,
+            // FP64 from the warp sums on; FP64 plans: FP64 throughout)
             double c2 = 0.0, c5 = 0.0;
+            T p2 = T(0), p5 = T(0);
             for (int item = tid; item < GK; item += nthr) {
                 const int i = item >> KS;
                 const int2 gt = gts[i];
                 const T xv = us[usg[gt.x & 0xffffff] + sc];
                 if (flags[sc]) a.xo[gb + item] = xv;
                 if (check) {
-                    const double xa = (double)xv + (double)__ldcg(a.xrf + gb + item);
-                    c2 += (double)((unsigned)gt.x >> 24) * xa * xa;
-                    c5 += (double)__ldg(a.cost + i) * xa;
+                    if constexpr (sizeof(T) == 4) {
+                        const T xa = xv + __ldcg(a.xrf + gb + item);
+                        p2 += (T)((unsigned)gt.x >> 24) * xa * xa;
+                        p5 += __ldg(a.cost + i) * xa;
+                    } else {
+                        const double xa = (double)xv + (double)__ldcg(a.xrf + gb + item);
+                        c2 += (double)((unsigned)gt.x >> 24) * xa * xa;
+                        c5 += (double)__ldg(a.cost + i) * xa;
+                    }
                 }
+            }
+            if constexpr (sizeof(T) == 4) {
+                c2 = (double)p2;
+                c5 = (double)p5;
             }
             if (check) {
                 for (int o = K; o < 32; o <<= 1) {
@@ -607,14 +637,22 @@ __global__ void __launch_bounds__(512, 1)
         if (check) {
             __syncthreads();
             if constexpr (TM) tm_fence_after();
+            // one thread per (column, quantity) sums the warps' parts in warp
+            // order into warp 0's slot, then one thread per column tests
+            if (tid < 6 * K) {
+                const int col = tid / 6, q = tid - 6 * col;
+                double sum = 0.0;
+                for (int ww = 0; ww < n_warps; ++ww) sum += red[((size_t)ww * K + col) * 6 + q];
+                red[col * 6 + q] = sum;
+            }
+            __syncthreads();
             if (tid < K) {
                 flags[K + tid] = 0;
                 if (flags[tid]) {
                     const int in = a.inst[c * K + tid];
-                    double s6[6] = {0, 0, 0, 0, 0, 0};
-                    for (int ww = 0; ww < n_warps; ++ww)
+                    double s6[6];
 #pragma unroll
-                        for (int q = 0; q < 6; ++q) s6[q] += red[((size_t)ww * K + tid) * 6 + q];
+                    for (int q = 0; q < 6; ++q) s6[q] = red[tid * 6 + q];
                     apply_test(&a.st[in], s6, a.rho_d, check_every);
                     if (a.st[in].done) {
                         flags[tid] = 0;
