@@ -257,9 +257,10 @@ int opf_get_timing(opf_handle *h, double *ms, int n);
  * Scratch is a fixed device array of OPF_STATIC_MAX_BLOCKS doubles, one per
  * block of 256 globals, held by every device that loads the library until
  * the process exits.  The first call in a CUDA context (the stream's; a
- * stream of an SM partition has its own) looks up the array's address in
- * that context, which needs no allocation; make that first call before any
- * stream capture.  Every call in a context shares the array: calls that may
+ * stream of an SM partition has its own) is the set-up: it looks up the
+ * array's address in that context, and the CUDA driver may load the
+ * library's device code into the context then; later calls in the context
+ * allocate nothing.  Make that first call before any stream capture.  Every call in a context shares the array: calls that may
  * overlap on the GPU (different streams without ordering) race and must be
  * serialised by the caller.  Each call writes every entry it reads, so stale
  * contents from an earlier call are never used.
