@@ -69,7 +69,7 @@ FP32_LANES = 128
 # DRAM bytes per launch of the dominant kernels, copied from the ncu captures
 # summarised in profiles/ (a copied constant, labelled so in the line; None
 # once the kernel has changed since the capture).
-BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 69220096 + 2185728
+BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 69075968 + 2099712
 BATCH_ENGINE_TRAFFIC_SOURCE = "profiles/k_batch_engine_123bus_x1024.md"
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 516864 + 768
 PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8708352 + 313088
@@ -217,6 +217,26 @@ def fp32_fma_peak(opf, torch, device, stream, reps=10):
     med, best = statistics.median(times), min(times)
     return {"tflops": fl / (med / 1e3) / 1e12, "tflops_best": fl / (best / 1e3) / 1e12, "sms": sms,
             "flops_per_launch": fl, "ms_median": med, "launches": reps}
+
+
+def fp64_fma_peak(opf, torch, device, stream, reps=5):
+    """FP64 FMA throughput of the device measured now (`opf_probe_dfma`), for
+    the FP64 iterations' ALU fraction; median of `reps` launches."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks, threads, iters = 2 * sms, 1024, 32
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=torch.device("cuda", device))
+    torch.cuda.synchronize()
+    opf.probe_dfma(blocks, threads, iters, out.data_ptr(), stream.cuda_stream)
+    times, fl = [], 0.0
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = opf.probe_dfma(blocks, threads, iters, out.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return fl / (statistics.median(times) / 1e3) / 1e12
 
 
 def _lp_optimum(g):
@@ -521,8 +541,16 @@ def plain_fp64_reference(opf, f, device, stream, n=2):
         if not ok:
             raise SystemExit("the plain FP64 solve did not converge")
     iters = s.residuals()["iters"]
+    t = s.timing()
+    fpi = algorithmic_flops_per_iter(s.sizes())
     s.close()
+    peak64 = fp64_fma_peak(opf, torch, device, stream)
+    ach = fpi * iters / (t["iterate_ms"] / 1e3) / 1e12 if t["iterate_ms"] > 0 else None
     return {"value": 1e3 * len(times) / sum(times), "unit": UNIT, "iterations": int(iters),
+            "fp64_alu": {"achieved_tflops": ach, "peak_tflops": peak64, "frac": ach / peak64 if ach else None,
+                         "peak_source": "measured in this run: FP64 FMA probe (opf_probe_dfma)",
+                         "note": "latency-bound: one instance's iteration is a chain of small dependent "
+                                 "products and a grid barrier"},
             "path": "single instance, FP64 iterations on the engine opf_solve_ex picks (warp engine up to 64 "
                     "subsystems, else the persistent grid engine)"}
 
@@ -803,6 +831,12 @@ def run_single(args, rank, world, local):
             "algorithmic_bytes_per_launch": bpi * ITERS_PER_LAUNCH if mixed else None,
             "kernel": kern,
             "bytes_per_iter": bpi, "iters_timed": n_it, "peak_source": peak_kind + " hbm_gbs"}
+    if not mixed:
+        # FP64 iterations: the FP64 FMA rate measured now is the other ceiling
+        peak64 = fp64_fma_peak(opf, torch, local, stream)
+        ach64 = algorithmic_flops_per_iter(sizes) * n_it / (sum(iter_ms) / 1e3) / 1e12
+        roof["fp64_alu"] = {"achieved_tflops": ach64, "peak_tflops": peak64, "frac": ach64 / peak64,
+                            "peak_source": "measured in this run: FP64 FMA probe (opf_probe_dfma)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -560,6 +560,9 @@ int opf_test_rule(const double *sums, double rho, double eps_rel, double eps_abs
  * FMA throughput of the device at its current clocks, the denominator of the
  * batched engine's roofline.  OPF_E_INVALID for bad sizes, OPF_E_CUDA. */
 int opf_probe_fma(int32_t blocks, int32_t threads, int32_t iters, float *out, void *stream, double *flops);
+/* The same with FP64 chains (out: blocks * threads doubles), for the FP64
+ * FMA rate, the denominator of FP64 iterations. */
+int opf_probe_dfma(int32_t blocks, int32_t threads, int32_t iters, double *out, void *stream, double *flops);
 
 /* A CUDA stream whose kernels run only on a partition of the device's SMs
  * (a green context), e.g. to keep the long single-instance solves of large

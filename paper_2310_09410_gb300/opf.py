@@ -141,6 +141,7 @@ def load(path: str = LIB_PATH):
                                                 C.POINTER(C.c_int32)]
     lib.opf_stream_destroy_partition.argtypes = [C.c_void_p]
     lib.opf_probe_fma.argtypes = [C.c_int32, C.c_int32, C.c_int32, _P, _P, C.POINTER(C.c_double)]
+    lib.opf_probe_dfma.argtypes = [C.c_int32, C.c_int32, C.c_int32, _P, _P, C.POINTER(C.c_double)]
     lib.opf_batch_set_tmem.argtypes = [H, C.c_int32]
     lib.opf_partition.argtypes = [C.POINTER(Feeder), C.c_int32, _P, C.c_int32]
     lib.opf_shard_create.argtypes = [C.POINTER(Feeder), _P, C.c_int32, C.c_int32, C.POINTER(Options), C.POINTER(H)]
@@ -170,7 +171,7 @@ def load(path: str = LIB_PATH):
                  "opf_batch_set_start", "opf_server_set_model_start", "opf_batch_set_tmem", "opf_partition",
                  "opf_shard_create", "opf_shard_precompute", "opf_shard_sizes", "opf_shard_maps",
                  "opf_shard_partial", "opf_shard_step", "opf_shard_get_x", "opf_shard_get_locals",
-                 "opf_test_rule"):
+                 "opf_test_rule", "opf_probe_dfma"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -257,6 +258,14 @@ def _feeder_struct(f):
     fd.gen_qmax = arr("gen_qmax", np.float64, (ng * 3,))
     fd.gen_cost = arr("gen_cost", np.float64)
     return fd, keep
+
+
+def probe_dfma(blocks, threads, iters, out_ptr, stream=None):
+    """Enqueue the FP64 FMA throughput probe (see include/opf.h); returns its flop count."""
+    fl = C.c_double()
+    _check(load().opf_probe_dfma(int(blocks), int(threads), int(iters), out_ptr, stream, C.byref(fl)),
+           "opf_probe_dfma")
+    return fl.value
 
 
 class Solver:

@@ -148,3 +148,26 @@ def test_fma_probe_measures_a_plausible_fp32_rate():
     nominal = sms * 128 * 2 * 2.1e9 / 1e12
     assert 0.1 * nominal < tflops < 1.05 * nominal, (tflops, nominal)
     assert torch.isfinite(out).all()
+
+
+@pytest.mark.gpu
+def test_fp64_fma_probe_counts_its_flops():
+    """The FP64 probe (the denominator of FP64 iterations): its flop count and
+    a rate of the order of this part's FP64 FMA throughput."""
+    torch = pytest.importorskip("torch")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2310_09410_gb300 import opf
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = torch.empty(sms * 1024, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    opf.probe_dfma(sms, 1024, 8, out.data_ptr(), stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fl = opf.probe_dfma(sms, 1024, 8, out.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    assert fl == 2.0 * 8 * 16 * 8 * 1024 * sms
+    tflops = fl / (e0.elapsed_time(e1) / 1e3) / 1e12
+    assert 0.05 < tflops < 10.0, tflops
+    assert torch.isfinite(out).all()
