@@ -327,9 +327,15 @@ int opf_batch_step(opf_batch *b, double rho, int32_t n_iters);
 /* Engine shape for one precision (OPF_PREC_FP32 or OPF_PREC_FP64): k_inst
  * instances per CTA (power of two <= 32) and warps per CTA (<= 16); 0 = pick
  * (FP32: the fastest of the candidate shapes timed on the batch; FP64: the
- * largest k_inst <= 4 that fits).  out (get): ok, k_inst, warps, chunks per
- * lane, tasks, chunks per CTA, shared bytes, CTAs, lambda and bbar~ in
- * tensor memory (1/0), tensor-memory columns per CTA. */
+ * largest k_inst <= 4 that fits).  FP32 k_inst = 128 selects the lane engine
+ * (never picked automatically; several times slower than the other shapes on
+ * the feeders measured): one instance per lane, tiles of 128 instances, each
+ * on a cluster of up to 16 CTAs that split the subsystems; warps 4, 8, 12 or
+ * 16 per CTA (OPF_E_CAPACITY at the solve when the model needs more than 16
+ * parts of at most 256 slots).  out (get): ok, k_inst, warps, chunks per lane, tasks,
+ * chunks per CTA (lane engine: per tile), shared bytes, CTAs (lane engine:
+ * tiles), lambda and bbar~ in tensor memory (1/0), tensor-memory columns per
+ * CTA, CTAs per cluster (lane engine, else 0). */
 int opf_batch_set_shape(opf_batch *b, int32_t precision, int32_t k_inst, int32_t warps);
 int opf_batch_get_shape(opf_batch *b, int32_t precision, int32_t *out, int32_t n_out);
 

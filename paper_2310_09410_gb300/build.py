@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libopf.so")
-SOURCES = ["kernels.cu", "api.cpp", "model.cpp", "static_update.cu", "batch.cu", "batch_api.cpp", "serve.cpp", "partition.cpp", "persist.cu", "probe.cu", "shard.cu"]
+SOURCES = ["kernels.cu", "api.cpp", "model.cpp", "static_update.cu", "batch.cu", "batch_api.cpp", "serve.cpp", "partition.cpp", "persist.cu", "probe.cu", "shard.cu", "lane.cu", "lane_plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fPIC,-O2,-fno-strict-aliasing", "-I" + os.path.join(ROOT, "include")]

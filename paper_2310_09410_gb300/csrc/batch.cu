@@ -31,6 +31,7 @@
 
 #include "opf_internal.h"
 #include "test_rule.cuh"
+#include "tmem.cuh"
 
 namespace opf {
 
@@ -141,21 +142,8 @@ __device__ __forceinline__ int upos(int ch, int e, int sc) {
     return (ch * 4 + (e ^ (ch & 3))) * K + sc;
 }
 
-// ---- tensor memory (tcgen05): lambda and bbar~ of the tasks, 32-bit columns.
-// A warp w reaches the 32 lanes of quadrant w % 4; a lane of the warp reads
-// and writes its own tensor-memory lane.  Address = (lane << 16) | column.
-__device__ __forceinline__ void tm_alloc(unsigned *dst_smem, int cols) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(dst_smem);
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(a), "r"(cols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tm_dealloc(unsigned taddr, int cols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
-}
-__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// ---- tensor memory (tcgen05, tmem.cuh): lambda and bbar~ of the tasks,
+// 32-bit columns.
 // 8 consecutive columns of the lane: lambda (4) then bbar~ (4) of one chunk
 __device__ __forceinline__ void tm_ld8(unsigned taddr, Q4<float> &m, Q4<float> &b) {
     unsigned r[8];

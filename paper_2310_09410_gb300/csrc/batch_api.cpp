@@ -61,43 +61,9 @@ void launch_bpack(int n_tasks, int J, const BatchTask *tasks, const int *memb, c
                   const double *F64, T *dst, cudaStream_t s);
 }  // namespace opf
 
-#define BCUDA(call)                                                                      \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess) {                                                         \
-            set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
-            return e_ == cudaErrorMemoryAllocation ? OPF_E_OOM : OPF_E_CUDA;             \
-        }                                                                                \
-    } while (0)
-#define BTRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
-
-static constexpr unsigned kMaxSmem = 227u * 1024u;
-
 namespace opf {
 namespace bx {
 
-template <typename T>
-int balloc(std::vector<void *> &list, T **p, size_t n) {
-    if (n == 0) n = 1;
-    void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, n * sizeof(T));
-    if (e != cudaSuccess) {
-        set_last_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        return OPF_E_OOM;
-    }
-    list.push_back(q);
-    *p = reinterpret_cast<T *>(q);
-    return OPF_OK;
-}
-
-template <typename T>
-int bupload(std::vector<void *> &list, T **p, const std::vector<T> &v, cudaStream_t s) {
-    BTRY(balloc(list, p, v.size()));
-    if (!v.empty()) BCUDA(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-    return OPF_OK;
-}
-
-unsigned a16(size_t x) { return (unsigned)((x + 15) & ~(size_t)15); }
 
 int ilog2(int x) {
     int l = 0;
@@ -387,10 +353,16 @@ void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_eve
                    h->d_c64, h->d_lb64, h->d_ub64, rho, b->d_xs, b->d_lam, b->d_st, b->d_xref, (T *)p.ct,
                    (T *)p.xrf, (T *)p.lbt, (T *)p.ubt, h->d_sub, h->d_sub2, h->d_F64, h->d_gk, p.d_sch,
                    b->d_bbar, (T *)p.bt, (T *)p.ds, (T *)p.mu, (T *)p.lref, s);
-    BatchArgs<T> a = engine_args<T>(b, p, rho);
     if (e0) cudaEventRecord(e0, s);
     const int grid = ctas >= 0 ? std::min(ctas, p.C) : p.C;
-    if (grid > 0) batch_engine_launch<T>(a, p.nq, p.fg, grid, p.threads, p.bytes, n_iters, check_every, s);
+    if (p.lane) {
+        // tiles of kLaneInst instances, one cluster each
+        if (grid > 0)
+            lane_engine_launch(lane_args(b, p, rho), grid, p.threads, p.bytes, n_iters, check_every, s);
+    } else if (grid > 0) {
+        BatchArgs<T> a = engine_args<T>(b, p, rho);
+        batch_engine_launch<T>(a, p.nq, p.fg, grid, p.threads, p.bytes, n_iters, check_every, s);
+    }
     if (e1) cudaEventRecord(e1, s);
     launch_bunshift<T>(b->n, b->G, b->L, p.K, p.ks, p.NCH, p.d_ipos, h->d_gk, p.d_sch, b->d_xref,
                        (const T *)p.ds, (const T *)p.mu, (const T *)p.xo, b->d_st, b->d_xs, b->d_lam, b->d_x, s);
@@ -491,6 +463,9 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
         set_last_error("batch: no FP64 engine shape fits");
         return OPF_E_CAPACITY;
     }
+    // candidates (K, W); K = kLaneInst (the lane engine, W / 4 warps per lane
+    // quadrant) only when asked for: it measured several times slower than
+    // these shapes on the feeders it holds
     std::vector<std::pair<int, int>> cand;
     if (b->force_k32) cand.push_back({b->force_k32, b->force_w32 > 0 ? b->force_w32 : 16});
     else {
@@ -498,9 +473,13 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
         const int Ws[] = {16, 12, 8};
         for (int K : Ks) for (int W : Ws) cand.push_back({K, W});
     }
+    auto build = [&](int K, int W) -> int {
+        if (K == kLaneInst) return build_lane_plan(b, &p, W / 4, 16);
+        return build_plan(b, &p, false, K, W, 4, false);
+    };
     b->tune_log.clear();
     if (cand.size() == 1) {
-        BTRY(build_plan(b, &p, false, cand[0].first, cand[0].second, 4, false));
+        BTRY(build(cand[0].first, cand[0].second));
         return OPF_OK;
     }
     // timing runs on a copy of the status; the FP64 state is not touched by
@@ -510,17 +489,21 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
     int bk = 0, bw = 0;
     const int iters = 2 * std::max(k, 2);
     for (auto &c : cand) {
-        if (build_plan(b, &p, false, c.first, c.second, 4, false) != OPF_OK) continue;
+        if (build(c.first, c.second) != OPF_OK) continue;
         BTRY(plan_set_rho(b, &p, rho));
         launch_bref<float>(b->n, h->S, b->G, b->L, p.K, p.ks, p.NCH, p.NB, p.d_ipos, h->d_gseg, h->d_uslot,
                            b->d_bidx, h->d_c64, h->d_lb64, h->d_ub64, rho, b->d_xs, b->d_lam, b->d_st, b->d_xref,
                            (float *)p.ct, (float *)p.xrf, (float *)p.lbt, (float *)p.ubt, h->d_sub, h->d_sub2,
                            h->d_F64, h->d_gk, p.d_sch, b->d_bbar, (float *)p.bt, (float *)p.ds, (float *)p.mu,
                            (float *)p.lref, h->stream);
-        BatchArgs<float> a = engine_args<float>(b, p, rho);
-        batch_engine_launch<float>(a, p.nq, false, p.C, p.threads, p.bytes, 4, 0, h->stream);   // warm-up
+        auto run = [&](int n_it) {
+            if (p.lane) lane_engine_launch(lane_args(b, p, rho), p.C, p.threads, p.bytes, n_it, 0, h->stream);
+            else batch_engine_launch<float>(engine_args<float>(b, p, rho), p.nq, false, p.C, p.threads, p.bytes,
+                                            n_it, 0, h->stream);
+        };
+        run(4);   // warm-up
         BCUDA(cudaEventRecord(b->ev[0], h->stream));
-        batch_engine_launch<float>(a, p.nq, false, p.C, p.threads, p.bytes, iters, 0, h->stream);
+        run(iters);
         BCUDA(cudaEventRecord(b->ev[1], h->stream));
         BCUDA(cudaEventSynchronize(b->ev[1]));
         BCUDA(cudaGetLastError());
@@ -535,7 +518,7 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
     // the status copies carry the pad (shifted) marks of the timing runs: clear them
     BCUDA(cudaMemcpyAsync(b->d_st, b->d_st_save, b->n * sizeof(DevStatus), cudaMemcpyDeviceToDevice, h->stream));
     if (!bk) { p.release(); set_last_error("batch: no FP32 engine shape fits"); return OPF_E_CAPACITY; }
-    BTRY(build_plan(b, &p, false, bk, bw, 4, false));
+    BTRY(build(bk, bw));
     return OPF_OK;
 }
 
@@ -706,9 +689,12 @@ int opf_batch_set_loads_device(opf_batch *b, int32_t first, int32_t count, const
 
 int opf_batch_set_shape(opf_batch *b, int32_t precision, int32_t k_inst, int32_t warps) {
     const int wmax = 16;
-    if (!b || (precision != OPF_PREC_FP32 && precision != OPF_PREC_FP64) || k_inst < 0 || k_inst > 32 ||
-        (k_inst & (k_inst - 1)) || warps < 0 || warps > wmax) {
-        set_last_error("batch shape: precision FP32 or FP64, K a power of two <= 32 (0: auto), warps <= 16");
+    const bool lane = precision == OPF_PREC_FP32 && k_inst == kLaneInst;
+    if (!b || (precision != OPF_PREC_FP32 && precision != OPF_PREC_FP64) || k_inst < 0 ||
+        (!lane && (k_inst > 32 || (k_inst & (k_inst - 1)) || warps < 0 || warps > wmax)) ||
+        (lane && (warps < 0 || warps > wmax || warps % 4 != 0))) {
+        set_last_error("batch shape: precision FP32 or FP64, K a power of two <= 32 (0: auto), warps <= 16; "
+                       "FP32 K = 128: the lane engine, warps 4, 8, 12 or 16");
         return OPF_E_INVALID;
     }
     if (precision == OPF_PREC_FP32) { b->force_k32 = k_inst; b->force_w32 = warps; b->p32.release(); }
@@ -726,9 +712,9 @@ int opf_batch_set_tmem(opf_batch *b, int32_t enable) {
 int opf_batch_get_shape(opf_batch *b, int32_t precision, int32_t *out, int32_t n_out) {
     if (!b || !out || n_out < 1) return OPF_E_INVALID;
     const BPlan &p = precision == OPF_PREC_FP64 ? b->p64 : b->p32;
-    const int32_t v[10] = {p.ok ? 1 : 0, p.K, p.W, p.nq, p.n_tasks, p.NCH, (int32_t)p.bytes, p.C, p.tm ? 1 : 0,
-                           p.tm_cols};
-    for (int i = 0; i < n_out && i < 10; ++i) out[i] = v[i];
+    const int32_t v[11] = {p.ok ? 1 : 0, p.K, p.W, p.nq, p.n_tasks, p.NCH, (int32_t)p.bytes, p.C, p.tm ? 1 : 0,
+                           p.tm_cols, p.lane ? p.lane_C : 0};
+    for (int i = 0; i < n_out && i < 11; ++i) out[i] = v[i];
     return OPF_OK;
 }
 

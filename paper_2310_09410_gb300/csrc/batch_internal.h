@@ -2,6 +2,7 @@
 // request server).
 #pragma once
 
+#include <string>
 #include <vector>
 
 #include "handle.h"
@@ -24,12 +25,20 @@ struct BPlan {
     void *d_F = nullptr, *d_recip = nullptr, *d_cost = nullptr;
     void *mu = nullptr, *ds = nullptr, *xo = nullptr, *bt = nullptr, *lref = nullptr;
     void *ct = nullptr, *xrf = nullptr, *lbt = nullptr, *ubt = nullptr;
+    // lane-engine plans (K = kLaneInst, C = tiles of K instances)
+    bool lane = false;
+    int lane_C = 0, lane_nslm = 0, lane_maxux = 0;
+    unsigned loff[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    LanePart *d_lparts = nullptr;
+    int4 *d_lsub = nullptr, *d_lgi = nullptr;
+    int *d_lcp = nullptr, *d_lux = nullptr, *d_lgk = nullptr;
     GraphCache graph;
     void release() {
         graph.reset();
         for (void *p : allocs) cudaFree(p);
         allocs.clear();
         ok = false;
+        lane = false;
     }
 };
 
@@ -64,8 +73,62 @@ struct opf_batch {
     std::vector<double> tune_log;   // (K, W, ms) triples of the last autotune
 };
 
+#define BCUDA(call)                                                                      \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+            return e_ == cudaErrorMemoryAllocation ? OPF_E_OOM : OPF_E_CUDA;             \
+        }                                                                                \
+    } while (0)
+#define BTRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+
+constexpr unsigned kMaxSmem = 227u * 1024u;   // dynamic shared memory of one CTA
+
 namespace opf {
+
+// Lane engine (lane.cu): kernel attributes for clusters of C CTAs, clusters
+// the device holds at once, a launch of `tiles` clusters, factor packing.
+int lane_engine_prepare(int C, unsigned bytes);
+int lane_engine_max_clusters(int C, int threads, unsigned bytes);
+int lane_engine_ctas_per_sm(int threads, unsigned bytes);
+int lane_engine_launch(const LaneArgs &a, int tiles, int threads, unsigned bytes, int n_iters, int check_every,
+                       cudaStream_t s);
+void launch_lpack(int nrec, const int4 *desc, const int4 *sub, const int4 *sub2, const double *F64, float *dst,
+                  cudaStream_t s);
+
 namespace bx {
+
+// Device allocation recorded in `list` (freed with the plan or batch).
+template <typename T>
+inline int balloc(std::vector<void *> &list, T **p, size_t n) {
+    if (n == 0) n = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+    if (e != cudaSuccess) {
+        set_last_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return OPF_E_OOM;
+    }
+    list.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return OPF_OK;
+}
+
+// Allocation filled from v on stream s.
+template <typename T>
+inline int bupload(std::vector<void *> &list, T **p, const std::vector<T> &v, cudaStream_t s) {
+    BTRY(balloc(list, p, v.size()));
+    if (!v.empty()) BCUDA(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return OPF_OK;
+}
+
+inline unsigned a16(size_t x) { return (unsigned)((x + 15) & ~(size_t)15); }
+
+// Lane-engine plan (FP32): K = kLaneInst instances per tile, C tiles, clusters
+// of lane_C <= maxC CTAs, WG warps per lane quadrant; OPF_E_CAPACITY when the
+// model does not fit (a part above the tensor-memory or shared-memory budget).
+int build_lane_plan(opf_batch *b, BPlan *p, int WG, int maxC);
+LaneArgs lane_args(opf_batch *b, const BPlan &p, double rho);
 
 // Engine plan for one arithmetic type (built on first use; FP32 autotuned).
 int ensure_plan(opf_batch *b, bool dbl, double rho, int k);

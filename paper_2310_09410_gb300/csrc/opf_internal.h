@@ -227,4 +227,49 @@ struct BatchArgs {
     double rho_d;
 };
 
+// Lane engine (FP32 batches): a tile of kLaneInst instances, one instance per
+// lane (warp w serves instances 32 (w % 4) .. + 31, which are also the
+// tensor-memory lanes it reaches), runs on a cluster of C CTAs; CTA r of the
+// cluster holds part r of the subsystems for all the tile's instances.  The
+// engine arrays are those of the batched engine with K = kLaneInst columns
+// per tile and the tile's slot positions grouped by part (part r owns chunks
+// [cb, cb + nslot / 4)).
+constexpr int kLaneInst = 128;
+constexpr int kLaneMaxGroups = 8;     // item groups (warps per lane quadrant)
+constexpr int kLaneMaxF4 = 6;         // factor vectors per subsystem <= 4 kLaneMaxF4
+
+struct LanePart {
+    int nsub, sub0;       // subsystem records [sub0, sub0 + nsub)
+    int nslot, cb;        // local slot positions (a multiple of 4); first chunk in the tile
+    int nF, F0;           // packed factor floats (multiples of 4)
+    int ng, g0;           // global items, the part's own (interior) globals first
+    int ncp, cp0;         // copy entries
+    int nux, pad;         // exchange rows (slots whose global has copies in other parts)
+    // per item group g: subsystems [gsub[g], gsub[g + 1]), interior globals
+    // [gint[g], gint[g + 1]) and the others [gcut[g], gcut[g + 1]) (local indices)
+    int gsub[kLaneMaxGroups + 1], gint[kLaneMaxGroups + 1], gcut[kLaneMaxGroups + 1];
+};
+
+struct LaneArgs {
+    int C, WG, G, NB, NCH;
+    int nslm;             // tensor-memory column of bbar~ of local slot 0 (lambda of slot p at column p)
+    int tm_cols, maxux;
+    unsigned off_U, off_X, off_F, off_sub, off_gi, off_cp, off_ux, off_gk, off_rc, off_red, off_part, off_flag;
+    const LanePart *parts;   // [C]
+    const int4 *sub;      // (first local slot, rows n, factor offset, mode | has-exchange-rows << 1 | F4 << 8)
+    const int4 *gi;       // (global, bounded index or -1, first copy entry, copies N | owner << 16)
+    const int *cp;        // (part << 24) | row: local slot position in the own part, else exchange row
+    const int *ux;        // per tile slot position: exchange row or -1
+    const int *gk;        // per tile slot position: global or -1
+    const float *F;       // factors: per subsystem n rows of 4 F4 floats, F[k][c] at k * 4 F4 + c
+    const float *recip;   // [kBatchRecip] 1 / (rho N)
+    const float *cost;    // [G]
+    float *mu, *ds, *xo;
+    const float *bt, *lref, *ct, *xrf, *lbt, *ubt;
+    const int *inst;      // [tiles * kLaneInst]
+    DevStatus *st;
+    float rho, inv_rho;
+    double rho_d;
+};
+
 }  // namespace opf

@@ -428,10 +428,10 @@ class Batch:
         _check(load().opf_batch_set_shape(self._b, int(precision), int(k_inst), int(warps)), "opf_batch_set_shape")
 
     def shape(self, precision=PREC_FP32):
-        out = np.zeros(10, np.int32)
-        _check(load().opf_batch_get_shape(self._b, int(precision), _ptr(out), 10), "opf_batch_get_shape")
+        out = np.zeros(11, np.int32)
+        _check(load().opf_batch_get_shape(self._b, int(precision), _ptr(out), 11), "opf_batch_get_shape")
         keys = ("ok", "k_inst", "warps", "chunks_per_lane", "tasks", "chunks", "smem_bytes", "ctas", "tmem",
-                "tmem_cols")
+                "tmem_cols", "cluster")
         return {k: int(v) for k, v in zip(keys, out)}
 
     def set_tmem(self, enable):
