@@ -441,7 +441,9 @@ int opf_server_set_model_start(opf_server *s, int32_t model, const double *xs, c
  * max_queue bounds the requests waiting for a slot.  max_wait_s bounds the
  * seconds a request may wait for one: at submit the wait is predicted from
  * the requests ahead (queued and running, served `slots` at a time) and the
- * model's mean service time so far, and a queued request that has waited
+ * model's mean service time so far (before any of its requests finished:
+ * the longest time a running one has run, a lower bound on the service
+ * time), and a queued request that has waited
  * longer is shed by opf_server_step.  max_service_s bounds the seconds a
  * request may run once admitted: a batched slot past it is retired at the
  * end of a pass, a worker's solve stops at its next chunk.  Shed and stopped

@@ -1186,6 +1186,7 @@ static int run_graph(opf_handle *h, GraphCache *gc, Fn fn) {
         if (h->h_st->done) return OPF_OK;
         if (h->cancel.load() || (h->deadline > 0.0 && opf::steady_seconds() > h->deadline)) {
             g_last_error = "solve stopped by its deadline or a cancel request";
+            h->total_iters = h->h_st->iter;      // iterations run so far (opf_get_residuals)
             return OPF_E_TIMEOUT;
         }
     }

@@ -26,6 +26,7 @@
 // the bound is shed; both are counted, and a shed request is reported by
 // opf_server_poll_ex with status OPF_E_TIMEOUT, so no request stays pending
 // without a status when a model cannot keep up with its arrivals.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -71,6 +72,7 @@ struct Worker {                      // single-instance slot
     opf_handle *h = nullptr;
     std::thread th;
     std::atomic<bool> busy{false}, finished{false};
+    double t_admit = 0.0;                 // start of the request it runs (set by the stepping thread)
     Done result;
 };
 
@@ -247,8 +249,8 @@ void single_worker(opf_server *s, Model *m, Worker *w, Request req, double t_adm
         std::lock_guard<std::mutex> g(s->mu);
         if (o.keep_solutions) s->kept.emplace_back(d.tag, std::move(d.x));
         finish_locked(s, *m, std::move(d));
+        w->finished = true;       // with the result queued: a worker counts as running until then
     }
-    w->finished = true;
 }
 
 int step_single(opf_server *s, Model &m) {
@@ -264,7 +266,8 @@ int step_single(opf_server *s, Model &m) {
             m.queue.pop_front();
             w.busy = true;
             w.finished = false;
-            w.th = std::thread(single_worker, s, &m, &w, std::move(r), now_s());
+            w.t_admit = now_s();
+            w.th = std::thread(single_worker, s, &m, &w, std::move(r), w.t_admit);
         }
     }
     return OPF_OK;
@@ -545,16 +548,29 @@ int opf_server_submit(opf_server *s, int32_t model, const double *load_p, const 
     }
     if (m.max_wait_s > 0.0) {
         // predicted wait for a slot: the requests ahead (queued and running)
-        // served cap at a time, each taking the model's mean service time
+        // served cap at a time, each taking the model's mean service time;
+        // before any request of the model finished, the longest time a
+        // running one has run so far (its service time is at least that)
         double svc;
         {
             std::lock_guard<std::mutex> g(s->mu);
             svc = m.n_svc ? m.svc_s : 0.0;
         }
+        const bool no_history = svc == 0.0;
+        const double t = now_s();
         int busy = 0;
-        if (m.batched) busy = m.running();
-        else
-            for (auto &w : m.workers) busy += w->busy ? 1 : 0;
+        if (m.batched) {
+            busy = m.running();
+            if (no_history)
+                for (int i = 0; i < m.cap; ++i)
+                    if (m.state[i]) svc = std::max(svc, t - m.t_admit[i]);
+        } else {
+            for (auto &w : m.workers) {
+                if (!w->busy || w->finished) continue;
+                ++busy;
+                if (no_history) svc = std::max(svc, t - w->t_admit);
+            }
+        }
         const int ahead = (int)m.queue.size() + busy;
         const double wait = ahead < m.cap ? 0.0 : (double)((ahead - m.cap) / m.cap + 1) * svc;
         if (wait > m.max_wait_s) {
@@ -640,7 +656,7 @@ int opf_server_stats(opf_server *s, int64_t *out, int32_t n) {
         slots += m->cap;
         if (m->batched) running += m->running();
         else
-            for (auto &w : m->workers) running += w->busy ? 1 : 0;
+            for (auto &w : m->workers) running += (w->busy && !w->finished) ? 1 : 0;
     }
     const int64_t v[7] = {s->n_submitted, s->n_completed, queued, running, slots, s->n_passes, s->mem_used};
     for (int i = 0; i < n && i < 7; ++i) out[i] = v[i];
@@ -653,7 +669,7 @@ int opf_server_model_stats(opf_server *s, int32_t model, int64_t *out, int32_t n
     int64_t running = 0;
     if (m.batched) running = m.running();
     else
-        for (auto &w : m.workers) running += w->busy ? 1 : 0;
+        for (auto &w : m.workers) running += (w->busy && !w->finished) ? 1 : 0;
     double svc;
     {
         std::lock_guard<std::mutex> g(s->mu);

@@ -244,3 +244,29 @@ def test_service_bound_stops_running_requests_with_a_status():
         assert st["queued"] == 0 and st["running"] == 0
     hz.close()
     h13.close()
+
+
+def test_no_history_wait_predicted_from_running_requests():
+    """Before any request of a model has finished, the predicted wait uses
+    the time the running request has run so far (a lower bound on its
+    service time): a request that would have to wait longer than max_wait_s
+    is refused at submit instead of queued and shed later."""
+    import time
+    fz = synth.with_zip_delta(synth.preset_feeder("123", 5123), seed=14)
+    h = solver(fz)
+    with opf.Server() as srv:
+        m = srv.add_model([h], capacity=1)
+        srv.set_model_tolerance(m, 1e-15, 1e-15)       # runs until stopped
+        srv.set_admission(m, max_wait_s=0.1, max_service_s=0.6)
+        g = synth.load_scenario(fz, 7000)
+        assert srv.submit(m, g["load_a"], g["load_b"], tag=0, refusable=True)
+        srv.step()                                     # the worker takes request 0
+        time.sleep(0.2)
+        g = synth.load_scenario(fz, 7001)
+        assert not srv.submit(m, g["load_a"], g["load_b"], tag=1, refusable=True)
+        got = drain(srv, [0])
+        st = srv.model_stats(m)
+    assert got[0]["status"] == opf.OPF_E_TIMEOUT and got[0]["iters"] > 0
+    assert st["submitted"] == 2 and st["refused"] == 1 and st["stopped"] == 1 and st["shed"] == 0
+    assert st["queued"] == 0 and st["running"] == 0
+    h.close()
