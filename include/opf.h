@@ -116,7 +116,8 @@ typedef struct opf_solve_opts {
     double rho;                     /* penalty (the paper's default is 100) */
     double eps_rel;                 /* epsilon_rel of the Sec. III-C test */
     double eps_abs_pres;            /* absolute gate: also require pres <= this */
-    int32_t max_iter;               /* iteration cap (counts every iteration) */
+    int32_t max_iter;               /* iteration cap (counts every iteration), applied at the
+                                       tests: rounded up to a multiple of check_every */
     int32_t check_every;            /* iterations between tests; even, >= 2 */
     int32_t precision;              /* OPF_PREC_* */
     int32_t recenter_every;         /* OPF_PREC_MIXED: iterations between FP64 re-centrings (0 = default) */
@@ -399,7 +400,7 @@ typedef struct opf_server opf_server;
 
 typedef struct opf_server_opts {
     double rho, eps_rel, eps_abs_pres;  /* the stopping test, as opf_solve_opts */
-    int32_t max_iter;               /* per request */
+    int32_t max_iter;               /* per request (rounded up to a multiple of check_every) */
     int32_t check_every;            /* iterations between tests; even, >= 2 */
     int32_t chunk_iters;            /* iterations per pass (a multiple of check_every) */
     int32_t keep_solutions;         /* 1: keep x of finished requests for opf_server_take_solution */

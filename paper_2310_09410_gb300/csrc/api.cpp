@@ -1403,6 +1403,7 @@ extern "C" int opf_solve_ex(opf_handle *h, const opf_solve_opts *opts) {
         g_last_error = "solve options: need rho > 0, max_iter >= 1, even check_every >= 2";
         return OPF_E_INVALID;
     }
+    o.max_iter = cap_at_tests(o.max_iter, o.check_every);
     CUDA_TRY(cudaSetDevice(h->device));
     h->last_rho = o.rho;
     TRY(set_status(h, o, false));

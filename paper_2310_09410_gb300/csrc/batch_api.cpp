@@ -731,6 +731,7 @@ int opf_batch_solve(opf_batch *b, const opf_solve_opts *opts) {
         set_last_error("batch solve options: need rho > 0, max_iter >= 1, even check_every >= 2");
         return OPF_E_INVALID;
     }
+    o.max_iter = cap_at_tests(o.max_iter, o.check_every);
     BCUDA(cudaSetDevice(h->device));
     const int k = o.check_every;
     // default interval: 2000 (a batch pays a re-centring pass over every

@@ -187,6 +187,15 @@ int stream_sm_count(cudaStream_t s, int device);
 // (part * nq + q), q < nq, of its member's slots, part = jpos % p, 4 slots
 // per chunk.  Chunk (q, jpos) of the task is chunk ch0 + q * J + jpos of the
 // CTA's chunk array.
+// The iteration cap is applied at the tests of the Sec. III-C rule, which
+// run every k iterations: max_iter rounded up to a multiple of k (at most the
+// largest multiple of k in an int32).
+inline int32_t cap_at_tests(int32_t max_iter, int32_t k) {
+    const long long r = ((long long)max_iter + k - 1) / k * k;
+    const long long top = (0x7fffffffLL / k) * k;
+    return (int32_t)(r < top ? r : top);
+}
+
 constexpr int kBatchRecip = 256;   // copy counts of a global are below this (the 8-bit count field)
 
 struct BatchTask {

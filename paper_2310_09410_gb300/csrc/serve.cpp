@@ -401,6 +401,7 @@ int opf_server_create(const opf_server_opts *o, opf_server **out) {
     }
     opf_server *s = new opf_server();
     s->o = *o;
+    s->o.max_iter = cap_at_tests(o->max_iter, o->check_every);
     if (s->o.polish_chunk_iters == 0) s->o.polish_chunk_iters = 2 * o->check_every;
     *out = s;
     return OPF_OK;
