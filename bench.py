@@ -71,9 +71,32 @@ FP32_LANES = 128
 # once the kernel has changed since the capture).
 BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 69075968 + 2099712
 BATCH_ENGINE_TRAFFIC_SOURCE = "profiles/k_batch_engine_123bus_x1024.md"
+# Warp instructions per instance-iteration of the batched engine in the
+# shape the autotune picks for the 1024 x 123-bus batch (8 instances per CTA,
+# 16 warps, tensor memory): smsp__inst_executed.sum of the same capture over
+# its 2000 iterations x 1024 instances (copied; None for other shapes).
+BATCH_ENGINE_INST_PER_INSTANCE_ITER = 11.01e9 / (2000 * 1024)
+BATCH_ENGINE_INST_SHAPE = {"k_inst": 8, "warps": 16, "tmem": 1}
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 516864 + 768
 PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8708352 + 313088
 ITERS_PER_LAUNCH = 1000
+
+
+def issue_roofline(shape, inst_iters, engine_ms, sm_mhz):
+    """Instruction-issue figure of the batched engine (its bound): warp
+    instructions issued per cycle on each SM of its grid against the 4 an SM
+    issues at most, from the instructions per instance-iteration of the ncu
+    capture and this run's instance-iterations, engine time and SM clock."""
+    if any(shape.get(k) != v for k, v in BATCH_ENGINE_INST_SHAPE.items()) or not engine_ms:
+        return None
+    inst = BATCH_ENGINE_INST_PER_INSTANCE_ITER * inst_iters
+    ipc = inst / (engine_ms / 1e3 * sm_mhz * 1e6 * shape["ctas"])
+    return {"achieved_ipc_per_sm": ipc, "peak_ipc_per_sm": 4.0, "frac": ipc / 4.0, "sms": shape["ctas"],
+            "sm_mhz": sm_mhz,
+            "warp_instructions_per_instance_iteration": BATCH_ENGINE_INST_PER_INSTANCE_ITER,
+            "source": "instructions per instance-iteration copied from the ncu capture in "
+                      + BATCH_ENGINE_TRAFFIC_SOURCE + " (smsp__inst_executed.sum, not measured in this run); "
+                      "instance-iterations, engine time and SM clock measured in this run"}
 
 
 def batch_config(n):
@@ -669,6 +692,7 @@ def run_batch(args, rank, world, local):
                       % (shape["k_inst"], shape["warps"], shape["ctas"],
                          "in tensor memory (%d TMEM columns per CTA)" % shape["tmem_cols"] if shape["tmem"]
                          else "streamed from L2"),
+            "issue": issue_roofline(shape, inst_iters, th["engine_ms"], clocks.get("sm_mhz") or max_mhz),
             "flops_per_instance_iteration": fpi,
             "instance_iterations_timed": inst_iters,
             "launches_timed": passes,
