@@ -906,7 +906,10 @@ def serve_config(args):
         "admission": f"every model: a request whose predicted wait for a slot exceeds {args.max_wait_s:g} s is "
                      f"refused at submit, one that has waited longer is shed; 8500-bus requests stop after "
                      f"{args.max_service_s:g} s of service; each outcome is counted per class",
-        "models": f"13/34/123-bus: continuous batching in the batched engine, passes of {args.chunk} FP32 iterations "
+        "models": f"13/34/123-bus: continuous batching in the batched engine ("
+                  + (f"FP32 shape {args.serve_k} instances per CTA, {args.serve_warps} warps: latency first"
+                     if args.serve_k else "FP32 shape autotuned on a full batch") +
+                  f"), passes of {args.chunk} FP32 iterations "
                   f"(slots in the FP64 polish: {args.polish_chunk or 100} FP64 iterations per pass); "
                   f"8500-bus: {args.big_handles} "
                   f"single-instance handles on worker threads, each on an SM partition of {args.big_sms} SMs "
@@ -958,6 +961,8 @@ def serve_measure(args, local, requests, warm_requests, drain_s):
             hs.append(sv)
         solvers[k] = hs
         mid[k] = srv.add_model(hs, caps.get(k, 1))
+        if k != "8500" and args.serve_k:
+            srv.set_model_shape(mid[k], args.serve_k, args.serve_warps)
         if SINGLE_EPS_REL[k] != EPS_REL:
             srv.set_model_tolerance(mid[k], SINGLE_EPS_REL[k], EPS_ABS)   # the large feeder's stopping rule
         srv.set_admission(mid[k], max_wait_s=args.max_wait_s,
@@ -1083,6 +1088,9 @@ def main():
     ap.add_argument("--no-single-records", dest="single_records", action="store_false",
                     help="batch workload: skip the single-instance sub-records (13/123/8500 buses)")
     ap.add_argument("--big-handles", type=int, default=2, help="serve: 8500-bus worker handles")
+    ap.add_argument("--serve-k", type=int, default=2,
+                    help="serve: FP32 instances per CTA of the batched models (0: autotuned on a full batch)")
+    ap.add_argument("--serve-warps", type=int, default=16, help="serve: warps per CTA of the batched models")
     ap.add_argument("--max-iter", type=int, default=1_000_000, help="serve: iteration cap per request")
     ap.add_argument("--mix", default="0.4,0.3,0.2,0.1", help="serve: weights of the 13/34/123/8500-bus requests")
     ap.add_argument("--big-sms", type=int, default=16, help="serve: SMs of the 8500-bus workers' partition (0: none)")

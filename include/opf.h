@@ -430,6 +430,21 @@ int opf_server_add_model(opf_server *s, opf_handle *const *handles, int32_t n_ha
  * for an unknown model or a negative or NaN tolerance. */
 int opf_server_set_model_tolerance(opf_server *s, int32_t model, double eps_rel, double eps_abs_pres);
 
+/* FP32 engine shape of a batched model (as opf_batch_set_shape: k_inst
+ * instances per CTA, warps per CTA; 0, 0 = the shape timed fastest on a full
+ * batch of the model's slots), for passes started after the call.  The
+ * default favours throughput when every slot runs; a model whose requests
+ * keep only part of its slots busy is served with lower latency by a smaller
+ * k_inst (more CTAs, less work each, on otherwise idle SMs): on the 123-bus
+ * feeder an iteration takes about 8.4 us with 8 instances per CTA and 6 us
+ * with 2.  The shape stays fixed until the next call, so a request's result
+ * does not depend on the other requests.  The paper has no serving layer, so
+ * no passage defines this.  OPF_E_INVALID for an unknown model, a model
+ * served by worker threads or an invalid shape; OPF_E_STATE while a pass of
+ * the model is in flight; OPF_E_CAPACITY when the shape does not hold the
+ * model. */
+int opf_server_set_model_shape(opf_server *s, int32_t model, int32_t k_inst, int32_t warps);
+
 /* Warm start of one model's requests (opt-in, as opf_batch_set_start): every
  * request admitted after the call starts from x_s = xs, lambda = lam
  * (n_slots doubles each, canonical slot order) instead of the Sec. V-A

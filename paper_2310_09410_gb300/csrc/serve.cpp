@@ -509,6 +509,22 @@ int opf_server_set_model_tolerance(opf_server *s, int32_t model, double eps_rel,
     return OPF_OK;
 }
 
+int opf_server_set_model_shape(opf_server *s, int32_t model, int32_t k_inst, int32_t warps) {
+    if (!s || model < 0 || model >= (int)s->models.size()) return OPF_E_INVALID;
+    Model &m = *s->models[model];
+    if (!m.batched) {
+        set_last_error("server: the model is served by worker threads (no batched engine)");
+        return OPF_E_INVALID;
+    }
+    if (m.inflight) {
+        set_last_error("server: a pass of the model is in flight (set the shape between steps)");
+        return OPF_E_STATE;
+    }
+    STRY(opf_batch_set_shape(m.b, OPF_PREC_FP32, k_inst, warps));
+    // the plan for the next pass (each pass re-centres from the FP64 state)
+    return ensure_plan(m.b, false, s->o.rho, s->o.check_every);
+}
+
 int opf_server_set_model_start(opf_server *s, int32_t model, const double *xs, const double *lam) {
     if (!s || model < 0 || model >= (int)s->models.size() || (!xs) != (!lam)) return OPF_E_INVALID;
     Model &m = *s->models[model];

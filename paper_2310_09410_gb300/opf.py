@@ -126,6 +126,7 @@ def load(path: str = LIB_PATH):
     lib.opf_server_add_model.argtypes = [H, _P, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
     lib.opf_server_submit.argtypes = [H, C.c_int32, _P, _P, C.c_int64]
     lib.opf_server_set_model_tolerance.argtypes = [H, C.c_int32, C.c_double, C.c_double]
+    lib.opf_server_set_model_shape.argtypes = [H, C.c_int32, C.c_int32, C.c_int32]
     lib.opf_server_step.argtypes = [H]
     lib.opf_server_poll.argtypes = [H, _P, _P, _P, _P, _P, C.c_int32]
     lib.opf_server_poll_ex.argtypes = [H, _P, _P, _P, _P, _P, _P, C.c_int32]
@@ -171,7 +172,7 @@ def load(path: str = LIB_PATH):
                  "opf_batch_set_start", "opf_server_set_model_start", "opf_batch_set_tmem", "opf_partition",
                  "opf_shard_create", "opf_shard_precompute", "opf_shard_sizes", "opf_shard_maps",
                  "opf_shard_partial", "opf_shard_step", "opf_shard_get_x", "opf_shard_get_locals",
-                 "opf_test_rule", "opf_probe_dfma"):
+                 "opf_test_rule", "opf_probe_dfma", "opf_server_set_model_tolerance", "opf_server_set_model_shape"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -545,6 +546,10 @@ class Server:
         self._solvers.extend(solvers)
         self._n_global[mid.value] = solvers[0].sizes()["n_global"]
         return mid.value
+
+    def set_model_shape(self, model, k_inst=0, warps=0):
+        _check(load().opf_server_set_model_shape(self._s, int(model), int(k_inst), int(warps)),
+               "opf_server_set_model_shape")
 
     def set_model_tolerance(self, model, eps_rel, eps_abs_pres=1e-4):
         _check(load().opf_server_set_model_tolerance(self._s, int(model), float(eps_rel), float(eps_abs_pres)),

@@ -270,3 +270,42 @@ def test_no_history_wait_predicted_from_running_requests():
     assert st["submitted"] == 2 and st["refused"] == 1 and st["stopped"] == 1 and st["shed"] == 0
     assert st["queued"] == 0 and st["running"] == 0
     h.close()
+
+
+def test_model_shape_fixed_for_latency():
+    """A batched model served with a fixed small shape (2 instances per CTA):
+    its requests converge to the LP optimum and a request's result is the
+    same alone and among others; worker models and bad shapes are refused."""
+    f = synth.preset_feeder("34", 5034)
+    h = solver(f)
+    fz = synth.with_zip_delta(synth.preset_feeder("34", 5034), seed=15)
+    hz = solver(fz)
+    target = synth.load_scenario(f, 7100)
+    with opf.Server() as srv:
+        m = srv.add_model([h], capacity=64)
+        mz = srv.add_model([hz], capacity=2)
+        srv.set_model_shape(m, 2, 16)
+        for bad in ((3, 16), (2, 17)):
+            with pytest.raises(opf.OPFError) as e:
+                srv.set_model_shape(m, *bad)
+            assert e.value.code == opf.OPF_E_INVALID
+        srv.set_model_shape(m, 2, 16)
+        with pytest.raises(opf.OPFError) as e:
+            srv.set_model_shape(mz, 2, 16)
+        assert e.value.code == opf.OPF_E_INVALID
+        srv.submit(m, target["load_a"], target["load_b"], tag=0)
+        alone = drain(srv, [0])[0]
+        for r in range(1, 13):
+            g = synth.load_scenario(f, 7100 + r)
+            srv.submit(m, g["load_a"], g["load_b"], tag=r)
+        srv.step()
+        srv.submit(m, target["load_a"], target["load_b"], tag=99)
+        got = drain(srv, list(range(1, 13)) + [99])
+    assert alone["converged"] and got[99]["converged"]
+    assert alone["iters"] == got[99]["iters"] and alone["objective"] == got[99]["objective"]
+    star, _ = oracle_admm.lp_optimum(lindist.build(target))
+    assert abs(alone["objective"] - star) <= TOL_OBJ * abs(star)
+    for r in range(1, 13):
+        assert got[r]["converged"]
+    h.close()
+    hz.close()
