@@ -69,13 +69,13 @@ FP32_LANES = 128
 # DRAM bytes per launch of the dominant kernels, copied from the ncu captures
 # summarised in profiles/ (a copied constant, labelled so in the line; None
 # once the kernel has changed since the capture).
-BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 69075968 + 2099712
+BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 68959488 + 1522688
 BATCH_ENGINE_TRAFFIC_SOURCE = "profiles/k_batch_engine_123bus_x1024.md"
 # Warp instructions per instance-iteration of the batched engine in the
 # shape the autotune picks for the 1024 x 123-bus batch (8 instances per CTA,
 # 16 warps, tensor memory): smsp__inst_executed.sum of the same capture over
 # its 2000 iterations x 1024 instances (copied; None for other shapes).
-BATCH_ENGINE_INST_PER_INSTANCE_ITER = 11.01e9 / (2000 * 1024)
+BATCH_ENGINE_INST_PER_INSTANCE_ITER = 10.1726e9 / (2000 * 1024)
 BATCH_ENGINE_INST_SHAPE = {"k_inst": 8, "warps": 16, "tmem": 1}
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 516864 + 768
 PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8708352 + 313088

@@ -369,8 +369,12 @@ __global__ void __launch_bounds__(512, 1)
     constexpr int KQ = K < 4 ? K : 4;          // columns per global-update item
     constexpr int NQD = K / KQ;                  // items per global
     constexpr int QS = NQD == 1 ? 0 : NQD == 2 ? 1 : NQD == 4 ? 2 : 3;
-    // global-update items per thread with loads in flight (fewer for FP64 rows of 4: registers)
-    constexpr int GB = (sizeof(T) == 8 && KQ == 4) ? 4 : 8;
+    // global-update items per thread taken together (their loads in flight
+    // together): 2 in FP32 (measured on the 1024 x 123-bus batch: 1 to 8
+    // items gave 211.9, 209.9, 214.1, 216.9, 226.3, 235.0, 230.3 and 231.4 ms
+    // per launch; more items cost predicated instructions and registers that
+    // the rest of the iteration needs), 4 for FP64 rows of 4
+    constexpr int GB = (sizeof(T) == 8 && KQ == 4) ? 4 : 2;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *Fsm = reinterpret_cast<T *>(smraw);
     const T *Fs = FG ? a.Fpk : Fsm;
