@@ -7,13 +7,16 @@
 //                  in shared memory; lambda, bbar~ and the test data streamed
 //                  from L2 as 16-byte vectors.  Per iteration:
 //                    G. per (global, instance): Eq. closed_1 as a fixed-order
-//                       sum over the global's copies of u;
+//                       sum over the global's copies of u (globals with one
+//                       copy and no bounds: done by the local update below);
 //                    -- CTA barrier --
 //                    L. per warp task: J member subsystems x K instances;
 //                       v = x_g + lambda / rho, x_s = M v + bbar~ as one pass
 //                       over the factor rows (w_r = <F_r, v>, y += w_r F_r),
 //                       lambda <- rho (v - x_s) (Eq. ADMM-3 with
-//                       x_g = v - lambda / rho), u = rho x_s - lambda;
+//                       x_g = v - lambda / rho), u = rho x_s - lambda, or
+//                       at a one-copy unbounded global its next x = u / rho
+//                       (Eq. closed_1 with N = 1 and c~ = 0);
 //                    -- CTA barrier --
 //                  and every check_every iterations the Sec. III-C sums per
 //                  instance in FP64 and the test; finished instances freeze.
@@ -209,11 +212,14 @@ __device__ __forceinline__ void tm_stage_out(const BatchTask &tk, unsigned tl, f
     }
 }
 
+// skc: per chunk, bit e set when slot e holds the only copy of an unbounded
+// global: with c~ = 0 Eq. closed_1 gives that global x = u / rho, which the
+// task writes into the slot in place of u (the global update skips it).
 template <typename T, int K, int NQT, bool TM>
 __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *us, T *mu_c, const T *bt_c,
-                                           T *ds_c, const T *lr_c, const T *xr_c, const int4 *chg, int jpos,
-                                           int sc, T rho, T inv_rho, bool check, bool act, bool wds,
-                                           double *redw, unsigned tl) {
+                                           T *ds_c, const T *lr_c, const T *xr_c, const int4 *chg,
+                                           const unsigned char *skc, int jpos, int sc, T rho, T inv_rho,
+                                           bool check, bool act, bool wds, double *redw, unsigned tl) {
     constexpr int J = 32 / K;
     const int mode1 = (tk.modes >> (jpos >> tk.lp)) & 1;
     T v[4 * NQT], y[4 * NQT];
@@ -224,6 +230,9 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
     float f0 = 0.f, f1 = 0.f, f3 = 0.f, f4 = 0.f;
     const int ch0 = tk.ch0 + jpos;
     const unsigned tcol = tl + (unsigned)(tk.tm >> 2);
+    unsigned skb = 0;     // 4 bits per chunk
+#pragma unroll
+    for (int q = 0; q < NQT; ++q) skb |= (unsigned)__ldg(skc + ch0 + q * J) << (4 * q);
 #pragma unroll
     for (int q = 0; q < NQT; ++q) {
         const int ch = ch0 + q * J;
@@ -287,9 +296,10 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
             const T vv = v[4 * q + e];
             const T xsv = mode1 ? y[4 * q + e] : vv - y[4 * q + e];
             const T mun = rho * (vv - xsv);
+            const T uu = rho * xsv - mun;
             x4.v[e] = xsv;
             m4.v[e] = mun;
-            u4.v[e] = rho * xsv - mun;
+            u4.v[e] = (skb >> (4 * q + e)) & 1u ? uu * inv_rho : uu;
         }
         if (check) {
             const int4 g4 = __ldg(chg + ch);
@@ -422,12 +432,17 @@ __global__ void __launch_bounds__(512, 1)
     }
     T *mu_c = a.mu + sb, *ds_c = a.ds + sb;
     const T *bt_c = a.bt + sb, *lr_c = a.lref + sb;
-    // u = rho d - mu into the swizzled slot array
+    // u = rho d - mu into the swizzled slot array (x = u / rho at the slots
+    // of one-copy unbounded globals, which the global update skips)
     for (int idx = tid; idx < a.NCH * K; idx += nthr) {
         const int ch = idx >> KS, col = idx & (K - 1);
         const Q4<T> d = ld4cg(ds_c + (size_t)idx * 4), m = ld4cg(mu_c + (size_t)idx * 4);
+        const unsigned sk = __ldg(a.skc + ch);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) us[upos<K>(ch, e, col)] = a.rho * d.v[e] - m.v[e];
+        for (int e = 0; e < 4; ++e) {
+            const T uu = a.rho * d.v[e] - m.v[e];
+            us[upos<K>(ch, e, col)] = (sk >> e) & 1u ? uu * a.inv_rho : uu;
+        }
     }
     const int sc = tid & (K - 1);
     const int jpos = lane >> KS;
@@ -460,7 +475,8 @@ __global__ void __launch_bounds__(512, 1)
     int last_check = 0;
     bool all_done = false;
     const int GK = a.G * K;
-    const int GQ = a.G * NQD;
+    const int GQ = a.Gs * NQD;       // the globals the global update computes come first,
+    const int GBQ = a.NB * NQD;      // the bounded ones (table entry = bounded index) first of all
     for (int it = 0; it < n_iters; ++it) {
         const bool check = check_every > 0 && ((it + 1) % check_every == 0);
         const bool last = it == n_iters - 1;
@@ -475,13 +491,14 @@ __global__ void __launch_bounds__(512, 1)
             *tnext = n_warps;
         }
         // ---- G: global update (Eq. closed_1).  An item is one global and KQ of
-        // its columns: sum of u over the copies, shift, scale, clip, and x
-        // stored into every copy's slot; GB items per thread with c~ in flight
+        // its columns: sum of u over the copies, shift (bounded globals: the
+        // first NB table entries, c~ from L2; elsewhere c~ = 0), scale, clip,
+        // and x stored into every copy's slot; GB items per thread
         for (int b0 = tid; b0 < GQ; b0 += GB * nthr) {
             // the GB items of this thread advance stage by stage, so that the
-            // loads of one stage are in flight together: c~ (L2) and the
-            // table entries, the first two copies' rows, their u; further
-            // copies (vertices of degree > 1) one by one; then the update
+            // loads of one stage are in flight together: c~ and the table
+            // entries, the first two copies' rows, their u; further copies
+            // (vertices of degree > 1) one by one; then the update
             RowK<T, KQ> cr[GB], sum[GB];
             int2 gtj[GB];
             int row0[GB], row1[GB];
@@ -489,10 +506,9 @@ __global__ void __launch_bounds__(512, 1)
             for (int j = 0; j < GB; ++j) {
                 const int item = b0 + j * nthr;
                 gtj[j] = make_int2(0, -1);
-                if (item < GQ) {
-                    load_row<T, KQ, true>(cr[j], a.ct + gb + (size_t)(item >> QS) * K + (item & (NQD - 1)) * KQ);
-                    gtj[j] = gts[item >> QS];
-                }
+                if (item < GBQ)
+                    load_row<T, KQ, true>(cr[j], a.cbt + bb + (size_t)(item >> QS) * K + (item & (NQD - 1)) * KQ);
+                if (item < GQ) gtj[j] = gts[item >> QS];
             }
 #pragma unroll
             for (int j = 0; j < GB; ++j) {
@@ -534,14 +550,17 @@ __global__ void __launch_bounds__(512, 1)
                     for (int k = 0; k < KQ; ++k) sum[j].v[k] += uq.v[k];
                 }
                 const T rcp = rcs[cnt];
-#pragma unroll
-                for (int k = 0; k < KQ; ++k) sum[j].v[k] = (sum[j].v[k] - cr[j].v[k]) * rcp;
                 if (gt.y >= 0) {
+#pragma unroll
+                    for (int k = 0; k < KQ; ++k) sum[j].v[k] = (sum[j].v[k] - cr[j].v[k]) * rcp;
                     RowK<T, KQ> lo, hi;
                     load_row<T, KQ, false>(lo, bnd + (gt.y * 2) * K + h * KQ);
                     load_row<T, KQ, false>(hi, bnd + (gt.y * 2 + 1) * K + h * KQ);
 #pragma unroll
                     for (int k = 0; k < KQ; ++k) sum[j].v[k] = clampT(sum[j].v[k], lo.v[k], hi.v[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < KQ; ++k) sum[j].v[k] *= rcp;
                 }
                 if (cnt > 0) store_row<T, KQ>(us + row0[j], sum[j]);
                 if (cnt > 1) store_row<T, KQ>(us + row1[j], sum[j]);
@@ -558,17 +577,19 @@ __global__ void __launch_bounds__(512, 1)
             double c2 = 0.0, c5 = 0.0;
             T p2 = T(0), p5 = T(0);
             for (int item = tid; item < GK; item += nthr) {
-                const int i = item >> KS;
-                const int2 gt = gts[i];
+                const int j = item >> KS;
+                const int2 gt = gts[j];
+                const int i = __ldg(a.gperm + j);
+                const size_t gi = gb + (size_t)i * K + sc;
                 const T xv = us[usg[gt.x & 0xffffff] + sc];
-                if (flags[sc]) a.xo[gb + item] = xv;
+                if (flags[sc]) a.xo[gi] = xv;
                 if (check) {
                     if constexpr (sizeof(T) == 4) {
-                        const T xa = xv + __ldcg(a.xrf + gb + item);
+                        const T xa = xv + __ldcg(a.xrf + gi);
                         p2 += (T)((unsigned)gt.x >> 24) * xa * xa;
                         p5 += __ldg(a.cost + i) * xa;
                     } else {
-                        const double xa = (double)xv + (double)__ldcg(a.xrf + gb + item);
+                        const double xa = (double)xv + (double)__ldcg(a.xrf + gi);
                         c2 += (double)((unsigned)gt.x >> 24) * xa * xa;
                         c5 += (double)__ldg(a.cost + i) * xa;
                     }
@@ -607,16 +628,16 @@ __global__ void __launch_bounds__(512, 1)
                 if (!check && lane == 0) claim = atomicAdd(cnt, 1);
                 const BatchTask tk = tks[t];
                 switch (tk.nq) {
-                    case 1: batch_task<T, K, 1, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
+                    case 1: batch_task<T, K, 1, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, a.skc, jpos, sc, rho,
                                                     inv_rho, check, act, wds, redw, tl); break;
                     case 2: if constexpr (NQ >= 2) batch_task<T, K, 2, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                           a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                           a.chg, a.skc, jpos, sc, rho, inv_rho, check, act,
                                                                            wds, redw, tl); break;
                     case 3: if constexpr (NQ >= 3) batch_task<T, K, 3, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                           a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                           a.chg, a.skc, jpos, sc, rho, inv_rho, check, act,
                                                                            wds, redw, tl); break;
                     default: if constexpr (NQ >= 4) batch_task<T, K, 4, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                            a.chg, jpos, sc, rho, inv_rho, check, act,
+                                                                            a.chg, a.skc, jpos, sc, rho, inv_rho, check, act,
                                                                             wds, redw, tl); break;
                 }
                 t = check ? t + t_step : __shfl_sync(0xffffffffu, claim, 0);
@@ -807,12 +828,21 @@ __global__ void k_bconsistent(int i0, int cnt, int S, const int *sm, const int *
 // Per (instance, global), instances still running: x_ref = clip((sum over the
 // copies of rho x_s - lambda) - c) / (rho N)) in FP64 (the next global
 // update), c~ = c + sum lambda_ref, bounds - x_ref, all in the engine layout.
+// The change of variables is exact for any reference dual; at an unbounded
+// global i it is lambda_ref_k = lambda_k - delta_i with delta_i = (c_i + sum
+// over the copies of lambda) / N_i (FP64, kept in dref), which makes c~_i
+// zero (up to rounding), and delta_i is itself small near a solution (the
+// stationarity of Eq. closed_1 makes c_i + sum lambda = rho sum (x_k - x_i)).
+// At a bounded global lambda_ref = lambda (delta = 0): there c~ is the bound's
+// multiplier, which the clip of the global update removes, and a copy of it in
+// every lambda~ would cost the FP32 iterations their small values.  c~ of the
+// bounded globals also goes to cbt, in the layout of the bounds.
 template <typename T>
 __global__ void k_bref_globals(int n_inst, int G, int L, int K, int kshift, int NB, const int *ipos,
                                const int2 *gseg, const int *uslot, const int *bidx, const double *c64,
                                const double *lb, const double *ub, double rho, const double *xsv,
-                               const double *lam, DevStatus *st, double *xref, T *ct, T *xrf, T *lbt,
-                               T *ubt) {
+                               const double *lam, DevStatus *st, double *xref, double *dref, T *ct, T *xrf,
+                               T *lbt, T *ubt, T *cbt) {
     const long long n = (long long)n_inst * G;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int in = (int)(t / G), i = (int)(t % G);
@@ -828,38 +858,44 @@ __global__ void k_bref_globals(int n_inst, int G, int L, int K, int kshift, int 
         double x = (s - c64[i]) / (rho * sg.y);
         x = fmin(fmax(x, lb[i]), ub[i]);
         xref[(size_t)in * G + i] = x;
+        const int b = bidx[i];
+        const double delta = b >= 0 ? 0.0 : (c64[i] + ls) / sg.y;
+        dref[(size_t)in * G + i] = delta;
         const int pos = ipos[in], cc = pos >> kshift, sc = pos & (K - 1);
         const size_t e = ((size_t)cc * G + i) * K + sc;
-        ct[e] = (T)(c64[i] + ls);
+        const double cs = c64[i] + (ls - sg.y * delta);
+        ct[e] = (T)cs;
         xrf[e] = (T)x;
-        const int b = bidx[i];
         if (b >= 0) {
             const size_t eb = ((size_t)cc * NB + b) * K + sc;
             lbt[eb] = (T)(lb[i] - x);
             ubt[eb] = (T)(ub[i] - x);
+            cbt[eb] = (T)cs;
         }
         if (i == 0) st[in].pad = 1;     // shifted: unshift after the engine
     }
 }
 
 // Per (subsystem, instance), one warp: bbar~ = M (x_ref[g] + lambda_ref / rho)
-// + bbar - x_ref[g], d = x_s - x_ref[g], mu = 0, lambda_ref, in the engine layout.
+// + bbar - x_ref[g], d = x_s - x_ref[g], mu = lambda - lambda_ref, lambda_ref,
+// in the engine layout (lambda_ref = lambda - delta[g]).
 // One subsystem of one instance by `nl` lanes starting at lane `l0` of the
 // warp (v and t staged in v[], tt[]): the two FP64 products of the shifted
 // bbar, written in the engine layout.
 template <typename T>
 __device__ __forceinline__ void bref_one(int in, bool valid, int d, int l0, int nl, int lane, const int4 h,
                                          const int4 q2, const double *F64, const int *ipos, const int *gk,
-                                         const int *sch, double rho, const double *xref, const double *xsv,
-                                         const double *lam, const double *bbar, int G, int L, int K, int kshift,
-                                         int NCH, double *v, double *tt, T *bt, T *ds, T *mu, T *lref) {
+                                         const int *sch, double rho, const double *xref, const double *dref,
+                                         const double *xsv, const double *lam, const double *bbar, int G, int L,
+                                         int K, int kshift, int NCH, double *v, double *tt, T *bt, T *ds, T *mu,
+                                         T *lref) {
     const int so = h.x, n = h.y, f = h.z, mode = h.w, npad = q2.y;
     const double *Fs = F64 + q2.x;
     const int ll = lane - l0;
-    const double *xr = xref + (size_t)in * G;
+    const double *xr = xref + (size_t)in * G, *dr = dref + (size_t)in * G;
     const double *xi = xsv + (size_t)in * L, *li = lam + (size_t)in * L, *bi = bbar + (size_t)in * L;
     if (valid)
-        for (int r = ll; r < n; r += nl) v[r] = xr[gk[so + r]] + li[so + r] / rho;
+        for (int r = ll; r < n; r += nl) v[r] = xr[gk[so + r]] + (li[so + r] - dr[gk[so + r]]) / rho;
     __syncwarp();
     if (valid)
         for (int cc = ll; cc < f; cc += nl) {
@@ -879,10 +915,11 @@ __device__ __forceinline__ void bref_one(int in, bool valid, int d, int l0, int 
         const int p = sch[k];
         const size_t e = (((size_t)cta * NCH + (p >> 2)) * K + sc) * 4 + (p & 3);
         const double btv = mv + bi[k] - xg;
+        const double dg = dr[gk[k]];
         bt[e] = (T)(mode ? btv : -btv);      // the engine starts y at this value
         ds[e] = (T)(xi[k] - xg);
-        mu[e] = T(0);
-        lref[e] = (T)li[k];
+        mu[e] = (T)dg;
+        lref[e] = (T)(li[k] - dg);
     }
 }
 
@@ -896,8 +933,8 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_bref_slots(int S, int n_inst, int G, int L, int K, int kshift, int NCH,
                                                     const int *ipos, const int4 *sub, const int4 *sub2,
                                                     const double *F64, const int *gk, const int *sch,
-                                                    double rho, const double *xref, const double *xsv,
-                                                    const double *lam, const double *bbar,
+                                                    double rho, const double *xref, const double *dref,
+                                                    const double *xsv, const double *lam, const double *bbar,
                                                     const DevStatus *st, T *bt, T *ds, T *mu, T *lref) {
     __shared__ double buf[4][2][OPF_MAX_NS];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -909,25 +946,26 @@ __global__ void __launch_bounds__(128) k_bref_slots(int S, int n_inst, int G, in
     if (h.y <= 16 && h.z <= 16) {
         const int half = lane >> 4, in = 2 * pair + half;
         const bool valid = in < n_inst && !st[in].done && ipos[in] >= 0;
-        bref_one<T>(in, valid, d, half * 16, 16, lane, h, q2, F64, ipos, gk, sch, rho, xref, xsv, lam, bbar, G, L,
-                    K, kshift, NCH, buf[wl][0] + half * 128, buf[wl][1] + half * 128, bt, ds, mu, lref);
+        bref_one<T>(in, valid, d, half * 16, 16, lane, h, q2, F64, ipos, gk, sch, rho, xref, dref, xsv, lam, bbar,
+                    G, L, K, kshift, NCH, buf[wl][0] + half * 128, buf[wl][1] + half * 128, bt, ds, mu, lref);
     } else {
         for (int q = 0; q < 2; ++q) {
             const int in = 2 * pair + q;
             if (in >= n_inst) break;
             const bool valid = !st[in].done && ipos[in] >= 0;
-            bref_one<T>(in, valid, d, 0, 32, lane, h, q2, F64, ipos, gk, sch, rho, xref, xsv, lam, bbar, G, L, K,
-                        kshift, NCH, buf[wl][0], buf[wl][1], bt, ds, mu, lref);
+            bref_one<T>(in, valid, d, 0, 32, lane, h, q2, F64, ipos, gk, sch, rho, xref, dref, xsv, lam, bbar, G,
+                        L, K, kshift, NCH, buf[wl][0], buf[wl][1], bt, ds, mu, lref);
             __syncwarp();
         }
     }
 }
 
-// Back to the unshifted FP64 state for instances that ran (status pad = 1).
+// Back to the unshifted FP64 state for instances that ran (status pad = 1):
+// x_s = x_ref[g] + d, lambda = lambda_ref + mu = lambda - delta[g] + mu.
 template <typename T>
 __global__ void k_bunshift_slots(int n_inst, int G, int L, int K, int kshift, int NCH, const int *ipos,
-                                 const int *gk, const int *sch, const double *xref, const T *ds, const T *mu,
-                                 const DevStatus *st, double *xsv, double *lam) {
+                                 const int *gk, const int *sch, const double *xref, const double *dref,
+                                 const T *ds, const T *mu, const DevStatus *st, double *xsv, double *lam) {
     const long long n = (long long)n_inst * L;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int in = (int)(t / L), k = (int)(t % L);
@@ -935,8 +973,9 @@ __global__ void k_bunshift_slots(int n_inst, int G, int L, int K, int kshift, in
         const int pos = ipos[in], cta = pos >> kshift, sc = pos & (K - 1);
         const int p = sch[k];
         const size_t e = (((size_t)cta * NCH + (p >> 2)) * K + sc) * 4 + (p & 3);
-        xsv[(size_t)in * L + k] = xref[(size_t)in * G + gk[k]] + (double)ds[e];
-        lam[(size_t)in * L + k] += (double)mu[e];
+        const size_t gi = (size_t)in * G + gk[k];
+        xsv[(size_t)in * L + k] = xref[gi] + (double)ds[e];
+        lam[(size_t)in * L + k] = (lam[(size_t)in * L + k] - dref[gi]) + (double)mu[e];
     }
 }
 
@@ -1120,43 +1159,46 @@ template <typename T>
 void launch_bref(int n_inst, int S, int G, int L, int K, int kshift, int NCH, int NB, const int *ipos,
                  const int2 *gseg, const int *uslot, const int *bidx, const double *c64, const double *lb,
                  const double *ub, double rho, const double *xsv, const double *lam, DevStatus *st,
-                 double *xref, T *ct, T *xrf, T *lbt, T *ubt, const int4 *sub, const int4 *sub2,
-                 const double *F64, const int *gk, const int *sch, const double *bbar, T *bt, T *ds, T *mu,
-                 T *lref, cudaStream_t s) {
+                 double *xref, double *dref, T *ct, T *xrf, T *lbt, T *ubt, T *cbt, const int4 *sub,
+                 const int4 *sub2, const double *F64, const int *gk, const int *sch, const double *bbar, T *bt,
+                 T *ds, T *mu, T *lref, cudaStream_t s) {
     k_bref_globals<T><<<bl((long long)n_inst * G, 256), 256, 0, s>>>(n_inst, G, L, K, kshift, NB, ipos, gseg, uslot,
                                                                     bidx, c64, lb, ub, rho, xsv, lam, st, xref,
-                                                                    ct, xrf, lbt, ubt);
+                                                                    dref, ct, xrf, lbt, ubt, cbt);
     const long long warps = (long long)S * ((n_inst + 1) / 2);
     k_bref_slots<T><<<(int)((warps + 3) / 4), 128, 0, s>>>(S, n_inst, G, L, K, kshift, NCH, ipos, sub, sub2, F64,
-                                                           gk, sch, rho, xref, xsv, lam, bbar, st, bt, ds, mu, lref);
+                                                           gk, sch, rho, xref, dref, xsv, lam, bbar, st, bt, ds, mu,
+                                                           lref);
 }
 
 template <typename T>
 void launch_bunshift(int n_inst, int G, int L, int K, int kshift, int NCH, const int *ipos, const int *gk,
-                     const int *sch, const double *xref, const T *ds, const T *mu, const T *xo,
+                     const int *sch, const double *xref, const double *dref, const T *ds, const T *mu, const T *xo,
                      const DevStatus *st, double *xsv, double *lam, double *x, cudaStream_t s) {
     k_bunshift_slots<T><<<bl((long long)n_inst * L, 256), 256, 0, s>>>(n_inst, G, L, K, kshift, NCH, ipos, gk, sch,
-                                                                      xref, ds, mu, st, xsv, lam);
+                                                                      xref, dref, ds, mu, st, xsv, lam);
     k_bunshift_globals<T><<<bl((long long)n_inst * G, 256), 256, 0, s>>>(n_inst, G, K, kshift, ipos, xref, xo, st, x);
 }
 
 template void launch_bref<float>(int, int, int, int, int, int, int, int, const int *, const int2 *, const int *,
                                  const int *, const double *, const double *, const double *, double,
-                                 const double *, const double *, DevStatus *, double *, float *, float *,
-                                 float *, float *, const int4 *, const int4 *, const double *, const int *,
-                                 const int *, const double *, float *, float *, float *, float *, cudaStream_t);
+                                 const double *, const double *, DevStatus *, double *, double *, float *,
+                                 float *, float *, float *, float *, const int4 *, const int4 *, const double *,
+                                 const int *, const int *, const double *, float *, float *, float *, float *,
+                                 cudaStream_t);
 template void launch_bref<double>(int, int, int, int, int, int, int, int, const int *, const int2 *, const int *,
                                   const int *, const double *, const double *, const double *, double,
                                   const double *, const double *, DevStatus *, double *, double *, double *,
-                                  double *, double *, const int4 *, const int4 *, const double *, const int *,
-                                  const int *, const double *, double *, double *, double *, double *,
-                                  cudaStream_t);
+                                  double *, double *, double *, double *, const int4 *, const int4 *, const double *,
+                                  const int *, const int *, const double *, double *, double *, double *,
+                                  double *, cudaStream_t);
 template void launch_bunshift<float>(int, int, int, int, int, int, const int *, const int *, const int *,
-                                     const double *, const float *, const float *, const float *,
+                                     const double *, const double *, const float *, const float *, const float *,
                                      const DevStatus *, double *, double *, double *, cudaStream_t);
 template void launch_bunshift<double>(int, int, int, int, int, int, const int *, const int *, const int *,
                                       const double *, const double *, const double *, const double *,
-                                      const DevStatus *, double *, double *, double *, cudaStream_t);
+                                      const double *, const DevStatus *, double *, double *, double *,
+                                      cudaStream_t);
 
 void launch_bany(int n_inst, const int *ipos, DevStatus *st, int *flag, cudaGraphConditionalHandle cond,
                  int use_cond, cudaStream_t s) {

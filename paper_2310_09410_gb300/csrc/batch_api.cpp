@@ -45,12 +45,12 @@ template <typename T>
 void launch_bref(int n_inst, int S, int G, int L, int K, int kshift, int NCH, int NB, const int *ipos,
                  const int2 *gseg, const int *uslot, const int *bidx, const double *c64, const double *lb,
                  const double *ub, double rho, const double *xsv, const double *lam, DevStatus *st,
-                 double *xref, T *ct, T *xrf, T *lbt, T *ubt, const int4 *sub, const int4 *sub2,
-                 const double *F64, const int *gk, const int *sch, const double *bbar, T *bt, T *ds, T *mu,
-                 T *lref, cudaStream_t s);
+                 double *xref, double *dref, T *ct, T *xrf, T *lbt, T *ubt, T *cbt, const int4 *sub,
+                 const int4 *sub2, const double *F64, const int *gk, const int *sch, const double *bbar, T *bt,
+                 T *ds, T *mu, T *lref, cudaStream_t s);
 template <typename T>
 void launch_bunshift(int n_inst, int G, int L, int K, int kshift, int NCH, const int *ipos, const int *gk,
-                     const int *sch, const double *xref, const T *ds, const T *mu, const T *xo,
+                     const int *sch, const double *xref, const double *dref, const T *ds, const T *mu, const T *xo,
                      const DevStatus *st, double *xsv, double *lam, double *x, cudaStream_t s);
 void launch_bany(int n_inst, const int *ipos, DevStatus *st, int *flag, cudaGraphConditionalHandle cond,
                  int use_cond, cudaStream_t s);
@@ -219,15 +219,39 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     p->NB = b->NB;
     // copies of each global in u order, as offsets into the CTA's u array
     std::vector<int> useg(L);
-    std::vector<int4> gtab(G);
     for (int i = 0; i < G; ++i) {
         const int s0 = h->h_gstart[i], cnt = h->h_gstart[i + 1] - s0;
-        gtab[i] = make_int4(s0, cnt, b->h_bidx[i], 0);
         for (int q = 0; q < cnt; ++q) {
             const int pos = sch[h->h_uslot[s0 + q]];
             const int ch = pos >> 2, e = pos & 3;
             useg[s0 + q] = (ch * 4 + (e ^ (ch & 3))) * K;
         }
+    }
+    // global table: the bounded globals (in bounded-index order, so entry j
+    // is bounded global j), the other globals the global update computes (Gs
+    // entries up to here), then those with one copy and no bounds, whose next
+    // x the local update of that copy writes (flagged per chunk in skc)
+    std::vector<int> gperm;
+    gperm.reserve(G);
+    std::vector<unsigned char> skc(p->NCH, 0);
+    auto by_slot = [&](int i) {
+        return h->h_gstart[i + 1] - h->h_gstart[i] == 1 && b->h_bidx[i] < 0;
+    };
+    for (int i = 0; i < G; ++i) if (b->h_bidx[i] >= 0) gperm.push_back(i);
+    for (int j = 0; j < (int)gperm.size(); ++j)
+        if (b->h_bidx[gperm[j]] != j) { set_last_error("batch plan: bounded-global order"); return OPF_E_INVALID; }
+    for (int i = 0; i < G; ++i) if (b->h_bidx[i] < 0 && !by_slot(i)) gperm.push_back(i);
+    p->Gs = (int)gperm.size();
+    for (int i = 0; i < G; ++i) {
+        if (!by_slot(i)) continue;
+        gperm.push_back(i);
+        const int pos = sch[h->h_uslot[h->h_gstart[i]]];
+        skc[pos >> 2] |= (unsigned char)(1u << (pos & 3));
+    }
+    std::vector<int4> gtab(G);
+    for (int j = 0; j < G; ++j) {
+        const int i = gperm[j], s0 = h->h_gstart[i];
+        gtab[j] = make_int4(s0, h->h_gstart[i + 1] - s0, b->h_bidx[i], 0);
     }
     // shared memory
     p->off_u = fg ? 0u : a16((size_t)p->nF * sz);
@@ -258,6 +282,8 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     BTRY(bupload(A, &p->d_useg, useg, st));
     BTRY(bupload(A, &p->d_chg, chg, st));
     BTRY(bupload(A, &p->d_gtab, gtab, st));
+    BTRY(bupload(A, &p->d_gperm, gperm, st));
+    BTRY(bupload(A, &p->d_skc, skc, st));
     BTRY(bupload(A, &p->d_inst, inst, st));
     BTRY(bupload(A, &p->d_ipos, ipos, st));
     const size_t nslot = (size_t)p->C * p->NCH * K * 4, nglob = (size_t)p->C * G * K;
@@ -273,7 +299,7 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     BTRY(arr(&p->d_cost, (size_t)G));
     BTRY(arr(&p->mu, nslot)); BTRY(arr(&p->ds, nslot)); BTRY(arr(&p->bt, nslot)); BTRY(arr(&p->lref, nslot));
     BTRY(arr(&p->xo, nglob)); BTRY(arr(&p->ct, nglob)); BTRY(arr(&p->xrf, nglob));
-    BTRY(arr(&p->lbt, nbnd)); BTRY(arr(&p->ubt, nbnd));
+    BTRY(arr(&p->lbt, nbnd)); BTRY(arr(&p->ubt, nbnd)); BTRY(arr(&p->cbt, nbnd));
     if (dbl) launch_bpack<double>(p->n_tasks, J, p->d_tasks, p->d_memb, h->d_sub, h->d_sub2, h->d_F64,
                                   (double *)p->d_F, st);
     else launch_bpack<float>(p->n_tasks, J, p->d_tasks, p->d_memb, h->d_sub, h->d_sub2, h->d_F64,
@@ -327,12 +353,12 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
     a.off_u = p.off_u; a.off_gt = p.off_gt; a.off_rc = p.off_rc; a.off_task = p.off_task; a.off_useg = p.off_useg;
     a.off_bnd = p.off_bnd;
     a.off_red = p.off_red; a.off_flag = p.off_flag;
-    a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab;
+    a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab; a.gperm = p.d_gperm; a.skc = p.d_skc; a.Gs = p.Gs;
     a.useg = p.d_useg;
     a.Fpk = (const T *)p.d_F; a.recip = (const T *)p.d_recip; a.cost = (const T *)p.d_cost;
     a.mu = (T *)p.mu; a.ds = (T *)p.ds; a.xo = (T *)p.xo;
     a.bt = (const T *)p.bt; a.lref = (const T *)p.lref; a.ct = (const T *)p.ct; a.xrf = (const T *)p.xrf;
-    a.lbt = (const T *)p.lbt; a.ubt = (const T *)p.ubt;
+    a.lbt = (const T *)p.lbt; a.ubt = (const T *)p.ubt; a.cbt = (const T *)p.cbt;
     a.inst = p.d_inst; a.st = b->d_st;
     a.rho = (T)rho; a.inv_rho = (T)(1.0 / rho); a.rho_d = rho;
     a.tm = p.tm ? 1 : 0;
@@ -350,8 +376,8 @@ void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_eve
     opf_handle *h = b->h;
     cudaStream_t s = stream ? stream : h->stream;
     launch_bref<T>(b->n, h->S, b->G, b->L, p.K, p.ks, p.NCH, p.NB, p.d_ipos, h->d_gseg, h->d_uslot, b->d_bidx,
-                   h->d_c64, h->d_lb64, h->d_ub64, rho, b->d_xs, b->d_lam, b->d_st, b->d_xref, (T *)p.ct,
-                   (T *)p.xrf, (T *)p.lbt, (T *)p.ubt, h->d_sub, h->d_sub2, h->d_F64, h->d_gk, p.d_sch,
+                   h->d_c64, h->d_lb64, h->d_ub64, rho, b->d_xs, b->d_lam, b->d_st, b->d_xref, b->d_dref, (T *)p.ct,
+                   (T *)p.xrf, (T *)p.lbt, (T *)p.ubt, (T *)p.cbt, h->d_sub, h->d_sub2, h->d_F64, h->d_gk, p.d_sch,
                    b->d_bbar, (T *)p.bt, (T *)p.ds, (T *)p.mu, (T *)p.lref, s);
     if (e0) cudaEventRecord(e0, s);
     const int grid = ctas >= 0 ? std::min(ctas, p.C) : p.C;
@@ -364,7 +390,7 @@ void enqueue_body(opf_batch *b, BPlan &p, double rho, int n_iters, int check_eve
         batch_engine_launch<T>(a, p.nq, p.fg, grid, p.threads, p.bytes, n_iters, check_every, s);
     }
     if (e1) cudaEventRecord(e1, s);
-    launch_bunshift<T>(b->n, b->G, b->L, p.K, p.ks, p.NCH, p.d_ipos, h->d_gk, p.d_sch, b->d_xref,
+    launch_bunshift<T>(b->n, b->G, b->L, p.K, p.ks, p.NCH, p.d_ipos, h->d_gk, p.d_sch, b->d_xref, b->d_dref,
                        (const T *)p.ds, (const T *)p.mu, (const T *)p.xo, b->d_st, b->d_xs, b->d_lam, b->d_x, s);
     launch_bany(b->n, p.d_ipos, b->d_st, p.dbl ? b->d_flag + 1 : b->d_flag, cond, use_cond, s);
 }
@@ -493,7 +519,8 @@ int ensure_plan(opf_batch *b, bool dbl, double rho, int k) {
         BTRY(plan_set_rho(b, &p, rho));
         launch_bref<float>(b->n, h->S, b->G, b->L, p.K, p.ks, p.NCH, p.NB, p.d_ipos, h->d_gseg, h->d_uslot,
                            b->d_bidx, h->d_c64, h->d_lb64, h->d_ub64, rho, b->d_xs, b->d_lam, b->d_st, b->d_xref,
-                           (float *)p.ct, (float *)p.xrf, (float *)p.lbt, (float *)p.ubt, h->d_sub, h->d_sub2,
+                           b->d_dref, (float *)p.ct, (float *)p.xrf, (float *)p.lbt, (float *)p.ubt, (float *)p.cbt,
+                           h->d_sub, h->d_sub2,
                            h->d_F64, h->d_gk, p.d_sch, b->d_bbar, (float *)p.bt, (float *)p.ds, (float *)p.mu,
                            (float *)p.lref, h->stream);
         auto run = [&](int n_it) {
@@ -628,7 +655,8 @@ int opf_batch_create(opf_handle *h, int32_t n_inst, opf_batch **out) {
     std::vector<void *> &A = b->allocs;
     int rc = OPF_OK;
     if ((rc = balloc(A, &b->d_rhs, n * R)) || (rc = balloc(A, &b->d_bbar, n * L)) || (rc = balloc(A, &b->d_xs, n * L)) ||
-        (rc = balloc(A, &b->d_lam, n * L)) || (rc = balloc(A, &b->d_xref, n * G)) || (rc = balloc(A, &b->d_x, n * G)) ||
+        (rc = balloc(A, &b->d_lam, n * L)) || (rc = balloc(A, &b->d_xref, n * G)) ||
+        (rc = balloc(A, &b->d_dref, n * G)) || (rc = balloc(A, &b->d_x, n * G)) ||
         (rc = balloc(A, &b->d_obj, n)) || (rc = balloc(A, &b->d_st, n)) || (rc = balloc(A, &b->d_st_save, n)) ||
         (rc = balloc(A, &b->d_flag, 2)) || (rc = balloc(A, &b->d_bad, n)))
         return fail(rc);

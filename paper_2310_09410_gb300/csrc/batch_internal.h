@@ -11,7 +11,7 @@
 struct BPlan {
     bool ok = false, dbl = false, fg = false;   // fg: factors read from global memory
     int K = 0, ks = 0, J = 0, W = 0, nq = 0, threads = 0;
-    int NCH = 0, NB = 0, nF = 0, n_tasks = 0, C = 0;
+    int NCH = 0, NB = 0, nF = 0, n_tasks = 0, C = 0, Gs = 0;
     bool tm = false;                  // lambda and bbar~ in tensor memory (FP32 plans)
     int tm_cols = 0, qstart[5] = {0, 0, 0, 0, 0};
     unsigned off_u = 0, off_gt = 0, off_rc = 0, off_task = 0, off_useg = 0, off_bnd = 0, off_red = 0, off_flag = 0;
@@ -20,11 +20,12 @@ struct BPlan {
     std::vector<void *> allocs;
     BatchTask *d_tasks = nullptr;
     int *d_memb = nullptr, *d_sch = nullptr, *d_useg = nullptr;
-    int *d_inst = nullptr, *d_ipos = nullptr;
+    int *d_inst = nullptr, *d_ipos = nullptr, *d_gperm = nullptr;
+    unsigned char *d_skc = nullptr;
     int4 *d_chg = nullptr, *d_gtab = nullptr;
     void *d_F = nullptr, *d_recip = nullptr, *d_cost = nullptr;
     void *mu = nullptr, *ds = nullptr, *xo = nullptr, *bt = nullptr, *lref = nullptr;
-    void *ct = nullptr, *xrf = nullptr, *lbt = nullptr, *ubt = nullptr;
+    void *ct = nullptr, *xrf = nullptr, *lbt = nullptr, *ubt = nullptr, *cbt = nullptr;
     // lane-engine plans (K = kLaneInst, C = tiles of K instances)
     bool lane = false;
     int lane_C = 0, lane_nslm = 0, lane_maxux = 0;
@@ -48,6 +49,7 @@ struct opf_batch {
     int G = 0, L = 0, S = 0, nrows = 0;
     std::vector<void *> allocs;
     double *d_rhs = nullptr, *d_bbar = nullptr, *d_xs = nullptr, *d_lam = nullptr, *d_xref = nullptr;
+    double *d_dref = nullptr;            // per (instance, global): lambda - lambda_ref of its copies
     double *d_x = nullptr, *d_obj = nullptr, *d_b0 = nullptr, *d_rcoef = nullptr, *d_stage = nullptr;
     double *d_start = nullptr;           // warm start (x_s then lambda, device slot order), or none
     size_t stage_len = 0;

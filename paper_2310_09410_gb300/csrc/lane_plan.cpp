@@ -369,7 +369,7 @@ int build_lane_plan(opf_batch *b, BPlan *p, int WG, int maxC) {
     BTRY(arr(&p->d_cost, (size_t)G));
     BTRY(arr(&p->mu, nslot)); BTRY(arr(&p->ds, nslot)); BTRY(arr(&p->bt, nslot)); BTRY(arr(&p->lref, nslot));
     BTRY(arr(&p->xo, nglob)); BTRY(arr(&p->ct, nglob)); BTRY(arr(&p->xrf, nglob));
-    BTRY(arr(&p->lbt, nbnd)); BTRY(arr(&p->ubt, nbnd));
+    BTRY(arr(&p->lbt, nbnd)); BTRY(arr(&p->ubt, nbnd)); BTRY(arr(&p->cbt, nbnd));
     launch_lpack((int)fdesc.size(), d_fdesc, h->d_sub, h->d_sub2, h->d_F64, (float *)p->d_F, st);
     BCUDA(cudaGetLastError());
     {

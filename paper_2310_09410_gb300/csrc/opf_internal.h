@@ -213,9 +213,17 @@ struct BatchTask {
 //   per slot      [c][NCH][K][4]   mu, ds, bt (+bbar~ if M = F^T F, else -bbar~), lref (lambda_ref)
 //   per global    [c][G][K]        ct (c~), xrf (x_ref), xo (x~ at the end)
 //   per bounded   [c][NB][K]       lbt, ubt (bounds - x_ref)
+//   per bounded   [c][NB][K]       cbt (c~ of the bounded globals)
+// The reference lambda_ref of the shifted frame makes c~ = c + sum lambda_ref
+// zero at every unbounded global, so this engine reads c~ of the bounded ones
+// only (cbt; the lane engine reads ct).  The global table is permuted: the NB
+// bounded globals (entry j = bounded index j), the other globals the global
+// update computes (Gs entries in all), then those with one copy and no
+// bounds, whose next x = u / rho the local update of their only slot writes
+// (skc).
 template <typename T>
 struct BatchArgs {
-    int K, kshift, J, NCH, G, L, NB, n_tasks, nF;
+    int K, kshift, J, NCH, G, L, NB, n_tasks, nF, Gs;
     unsigned off_u, off_gt, off_rc, off_task, off_useg, off_bnd, off_red, off_flag;   // shared-memory byte offsets
     // Tensor-memory plans (FP32): lambda and bbar~ of every task stay in
     // tensor memory for the launch; the tasks of lane quadrant q are
@@ -223,13 +231,15 @@ struct BatchArgs {
     int tm, tm_cols, qstart[5];
     const BatchTask *tasks;    // [n_tasks] in decreasing cost
     const int4 *chg;           // [NCH] g * K of each chunk's 4 slots (-1: padding)
-    const int4 *gtab;          // [G] (first copy in useg, copies, bounded index or -1, 0)
+    const int4 *gtab;          // [G] permuted: (first copy in useg, copies, bounded index or -1, 0)
+    const int *gperm;          // [G] global of table entry j
+    const unsigned char *skc;  // [NCH] bit e: slot e of the chunk holds a global the local update computes
     const int *useg;           // copies of each global: slot-array row (ch * 4 + (e ^ (ch & 3))) * K
     const T *Fpk;              // [nF] factors, task-interleaved
     const T *recip;            // [kBatchRecip] 1 / (rho N) by copy count N
     const T *cost;             // [G] c_i
     T *mu, *ds, *xo;
-    const T *bt, *lref, *ct, *xrf, *lbt, *ubt;
+    const T *bt, *lref, *ct, *xrf, *lbt, *ubt, *cbt;
     const int *inst;
     DevStatus *st;             // per instance
     T rho, inv_rho;

@@ -175,7 +175,7 @@ void shed_expired(opf_server *s, Model &m) {
 // share of both engines' per-column arrays.
 size_t batch_slot_bytes(opf_handle *h) {
     const size_t L = h->L, G = h->G, R = h->n_rows;
-    size_t fp64 = 8 * (R + 4 * L + 2 * G) + sizeof(DevStatus) * 2 + 16;
+    size_t fp64 = 8 * (R + 4 * L + 3 * G) + sizeof(DevStatus) * 2 + 16;
     size_t eng = (size_t)(1.6 * L) * (4 * 4 + 4 * 8) + G * (3 * 4 + 3 * 8);
     return fp64 + eng;
 }
