@@ -57,6 +57,13 @@ SINGLE_SEEDS = {"13": 1001, "34": 5034, "123": 2001, "8500": 3001}
 SINGLE_EPS_REL = {"13": 1e-8, "34": 1e-8, "123": 1e-8, "8500": 2e-9}
 N_SCEN, SCEN_SEED0 = 1024, 4000
 RHO, EPS_REL, EPS_ABS = 100.0, 1e-8, 1e-4
+# Iterations between stopping tests of the batched workload.  A test
+# iteration of the batched engine costs about two ordinary ones; on the 1024 x
+# 123-bus batch 50 and 100 gave the same stopping iterations for every
+# instance (the FP32 phase met the test only at multiples of 100), with the
+# FP32 phase 207.5 and 202.2 ms; 20 / 200 gave 220.6 / 199.6 ms with 22 fewer
+# / 24 more iterations on average.
+BATCH_CHECK_EVERY = 100
 METRIC = "OPF solves/s to 1e-4 residual (batched/served vs plain FP64); p50/p99 latency"
 UNIT = "solves/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -69,13 +76,13 @@ FP32_LANES = 128
 # DRAM bytes per launch of the dominant kernels, copied from the ncu captures
 # summarised in profiles/ (a copied constant, labelled so in the line; None
 # once the kernel has changed since the capture).
-BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 68959488 + 1522688
+BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 63068672 + 857344
 BATCH_ENGINE_TRAFFIC_SOURCE = "profiles/k_batch_engine_123bus_x1024.md"
 # Warp instructions per instance-iteration of the batched engine in the
 # shape the autotune picks for the 1024 x 123-bus batch (8 instances per CTA,
 # 16 warps, tensor memory): smsp__inst_executed.sum of the same capture over
 # its 2000 iterations x 1024 instances (copied; None for other shapes).
-BATCH_ENGINE_INST_PER_INSTANCE_ITER = 10.1726e9 / (2000 * 1024)
+BATCH_ENGINE_INST_PER_INSTANCE_ITER = 9.8699e9 / (2000 * 1024)
 BATCH_ENGINE_INST_SHAPE = {"k_inst": 8, "warps": 16, "tmem": 1}
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 516864 + 768
 PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8708352 + 313088
@@ -103,7 +110,8 @@ def batch_config(n):
     return {
         "workload": f"{n} load scenarios of the 123-bus synthetic radial 3-phase feeder (seed 2001; "
                     "85 loads scaled by U[0.6,1.2] x N(1,0.05) per scenario, seeds 4000+j), 10 DERs, "
-                    "rho=100, each instance stopped at eps_rel=1e-8 and pres<=1e-4",
+                    f"rho=100, each instance stopped at eps_rel=1e-8 and pres<=1e-4 (Sec. III-C test every "
+                    f"{BATCH_CHECK_EVERY} iterations)",
         "buses": 123, "instances": n, "precision": "FP32 iterations re-centred in FP64 + FP64 polish",
         "step": "factorization of the feeder (FP64) + per-scenario bbar = A_s^+ b + ADMM to the test "
                 "for every instance + objectives read back",
@@ -602,7 +610,8 @@ def run_batch(args, rank, world, local):
     def step():
         solver.precompute()
         batch.set_loads_device(0, n, dlp.data_ptr(), dlq.data_ptr())
-        ok = batch.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=opf.PREC_MIXED, flags=flags)
+        ok = batch.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, check_every=BATCH_CHECK_EVERY,
+                         precision=opf.PREC_MIXED, flags=flags)
         _, obj = batch.solution()
         return ok, obj
 
@@ -650,7 +659,8 @@ def run_batch(args, rank, world, local):
         t0 = time.perf_counter()
         solver.precompute()
         batch.set_loads(0, lp_pin.numpy(), lq_pin.numpy())
-        batch.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=opf.PREC_MIXED, flags=flags)
+        batch.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, check_every=BATCH_CHECK_EVERY,
+                    precision=opf.PREC_MIXED, flags=flags)
         x, _ = batch.solution(out=(x_pin.numpy(), obj_pin.numpy()))
         e2e_times.append(time.perf_counter() - t0)
     e2e_total = max_over_ranks(sum(e2e_times), world, f"cuda:{local}")
@@ -661,8 +671,8 @@ def run_batch(args, rank, world, local):
     # dominant kernel: the FP32 engine, timed alone on direct launches
     solver.precompute()
     batch.set_loads_device(0, n, dlp.data_ptr(), dlq.data_ptr())
-    batch.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, precision=opf.PREC_MIXED,
-                flags=opf.SOLVE_HOST_LOOP)
+    batch.solve(rho=RHO, eps_rel=EPS_REL, eps_abs_pres=EPS_ABS, check_every=BATCH_CHECK_EVERY,
+                precision=opf.PREC_MIXED, flags=opf.SOLVE_HOST_LOOP)
     th = batch.timing()
     sizes = solver.sizes()
     fpi = algorithmic_flops_per_iter(sizes)
