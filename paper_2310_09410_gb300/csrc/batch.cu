@@ -7,16 +7,17 @@
 //                  in shared memory; lambda, bbar~ and the test data streamed
 //                  from L2 as 16-byte vectors.  Per iteration:
 //                    G. per (global, instance): Eq. closed_1 as a fixed-order
-//                       sum over the global's copies of u (globals with one
-//                       copy and no bounds: done by the local update below);
+//                       sum over the global's copies of u, rho x stored into
+//                       the copies' slots (a global with one copy and no
+//                       bounds needs none: with c~ = 0 its rho x is the u of
+//                       its slot);
 //                    -- CTA barrier --
-//                    L. per warp task: J member subsystems x K instances;
-//                       v = x_g + lambda / rho, x_s = M v + bbar~ as one pass
-//                       over the factor rows (w_r = <F_r, v>, y += w_r F_r),
-//                       lambda <- rho (v - x_s) (Eq. ADMM-3 with
-//                       x_g = v - lambda / rho), u = rho x_s - lambda, or
-//                       at a one-copy unbounded global its next x = u / rho
-//                       (Eq. closed_1 with N = 1 and c~ = 0);
+//                    L. per warp task: J member subsystems x K instances,
+//                       in units of rho (no multiplies): V = rho x_g + lambda
+//                       (= rho v), rho x_s = M V + rho bbar~ as one pass over
+//                       the factor rows (w_r = <F_r, V>, y += w_r F_r),
+//                       lambda <- V - rho x_s (Eq. ADMM-3 with
+//                       rho x_g = V - lambda), u = rho x_s - lambda;
 //                    -- CTA barrier --
 //                  and every check_every iterations the Sec. III-C sums per
 //                  instance in FP64 and the test; finished instances freeze.
@@ -189,13 +190,16 @@ __device__ __forceinline__ void tm_ld4(unsigned taddr, Q4<float> &m) {
 // in `wcols` (bit sc), after the lanes' own loads.
 template <int K, int NQT>
 __device__ __forceinline__ void tm_stage_in(const BatchTask &tk, unsigned tl, const float *mu_c, const float *bt_c,
-                                            int jpos, int sc) {
+                                            int jpos, int sc, float rho) {
     constexpr int J = 32 / K;
     const unsigned col = (unsigned)(tk.tm >> 2);
 #pragma unroll
     for (int q = 0; q < NQT; ++q) {
         const int off = ((tk.ch0 + jpos + q * J) * K + sc) * 4;
-        tm_st8(tl + col + 8 * q, ld4cg(mu_c + off), ld4cg(bt_c + off));
+        Q4<float> b = ld4cg(bt_c + off);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) b.v[e] *= rho;     // rho bbar~
+        tm_st8(tl + col + 8 * q, ld4cg(mu_c + off), b);
     }
 }
 template <int K, int NQT>
@@ -212,14 +216,15 @@ __device__ __forceinline__ void tm_stage_out(const BatchTask &tk, unsigned tl, f
     }
 }
 
-// skc: per chunk, bit e set when slot e holds the only copy of an unbounded
-// global: with c~ = 0 Eq. closed_1 gives that global x = u / rho, which the
-// task writes into the slot in place of u (the global update skips it).
+// The slot array holds rho x_g at every slot when the task starts (the global
+// update wrote it; a one-copy unbounded global's slot holds its u, which is
+// that value) and gets u at the end; y starts at +-rho bbar~ (tensor-memory
+// plans stage it scaled, the others scale it on load).
 template <typename T, int K, int NQT, bool TM>
 __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *us, T *mu_c, const T *bt_c,
-                                           T *ds_c, const T *lr_c, const T *xr_c, const int4 *chg,
-                                           const unsigned char *skc, int jpos, int sc, T rho, T inv_rho,
-                                           bool check, bool act, bool wds, double *redw, unsigned tl) {
+                                           T *ds_c, const T *lr_c, const T *xr_c, const int4 *chg, int jpos,
+                                           int sc, T rho, T inv_rho, bool check, bool act, bool wds,
+                                           double *redw, unsigned tl) {
     constexpr int J = 32 / K;
     const int mode1 = (tk.modes >> (jpos >> tk.lp)) & 1;
     T v[4 * NQT], y[4 * NQT];
@@ -230,9 +235,6 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
     float f0 = 0.f, f1 = 0.f, f3 = 0.f, f4 = 0.f;
     const int ch0 = tk.ch0 + jpos;
     const unsigned tcol = tl + (unsigned)(tk.tm >> 2);
-    unsigned skb = 0;     // 4 bits per chunk
-#pragma unroll
-    for (int q = 0; q < NQT; ++q) skb |= (unsigned)__ldg(skc + ch0 + q * J) << (4 * q);
 #pragma unroll
     for (int q = 0; q < NQT; ++q) {
         const int ch = ch0 + q * J;
@@ -247,11 +249,11 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            y[4 * q + e] = b4.v[e];
-            v[4 * q + e] = us[upos<K>(ch, e, sc)] + m4.v[e] * inv_rho;
+            y[4 * q + e] = TM ? b4.v[e] : rho * b4.v[e];
+            v[4 * q + e] = us[upos<K>(ch, e, sc)] + m4.v[e];
         }
     }
-    // x_s = M v + bbar~ over the factor rows, two rows per step
+    // rho x_s = M V + rho bbar~ over the factor rows, two rows per step
     const int rstride = NQT * J * 4;
     const T *F0 = Fs + tk.foff + jpos * 4;
     const int red_top = tk.p * K;
@@ -290,17 +292,20 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
     for (int q = 0; q < NQT; ++q) {
         const int ch = ch0 + q * J;
         const int off = (ch * K + sc) * 4;
-        Q4<T> x4, m4, u4;
+        Q4<T> x4, m4, u4, r4;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const T vv = v[4 * q + e];
-            const T xsv = mode1 ? y[4 * q + e] : vv - y[4 * q + e];
-            const T mun = rho * (vv - xsv);
-            const T uu = rho * xsv - mun;
-            x4.v[e] = xsv;
+            const T rx = mode1 ? y[4 * q + e] : vv - y[4 * q + e];     // rho x_s
+            const T mun = vv - rx;
+            r4.v[e] = rx;
             m4.v[e] = mun;
-            u4.v[e] = (skb >> (4 * q + e)) & 1u ? uu * inv_rho : uu;
+            u4.v[e] = rx - mun;
         }
+        // x_s~ (written on wds iterations, test terms); computed on every
+        // iteration: a branch here measured 6 % slower per launch
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x4.v[e] = r4.v[e] * inv_rho;
         if (check) {
             const int4 g4 = __ldg(chg + ch);
             const int gg[4] = {g4.x, g4.y, g4.z, g4.w};
@@ -310,7 +315,7 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (gg[e] < 0) continue;
-                const T d0 = us[upos<K>(ch, e, sc)] - x4.v[e], d1 = x4.v[e] - o4.v[e];
+                const T d0 = (us[upos<K>(ch, e, sc)] - r4.v[e]) * inv_rho, d1 = x4.v[e] - o4.v[e];
                 const T xa = x4.v[e] + __ldcg(xr_c + gg[e]);
                 const T la = m4.v[e] + l4.v[e];
                 t0 += d0 * d0;
@@ -419,7 +424,8 @@ __global__ void __launch_bounds__(512, 1)
         const int4 gt = __ldg(a.gtab + i);
         gts[i] = make_int2((int)((unsigned)gt.x | ((unsigned)gt.y << 24)), gt.z);
     }
-    for (int i = tid; i < kBatchRecip; i += nthr) rcs[i] = __ldg(a.recip + i);
+    // 1 / N by copy count N: the global update stores rho x = (sum u - c~) / N
+    for (int i = tid; i < kBatchRecip; i += nthr) rcs[i] = i ? (T)(1.0 / (double)i) : T(0);
     for (int i = tid; i < a.n_tasks; i += nthr) tks[i] = a.tasks[i];
     for (int k = tid; k < a.L; k += nthr) usg[k] = __ldg(a.useg + k);
     const size_t sb = (size_t)c * a.NCH * K * 4;     // this CTA's slot arrays
@@ -427,22 +433,17 @@ __global__ void __launch_bounds__(512, 1)
     const size_t bb = (size_t)c * a.NB * K;          // bounded-global arrays
     for (int idx = tid; idx < a.NB * K; idx += nthr) {
         const int b = idx >> KS, col = idx & (K - 1);
-        bnd[(b * 2) * K + col] = __ldcg(a.lbt + bb + idx);
-        bnd[(b * 2 + 1) * K + col] = __ldcg(a.ubt + bb + idx);
+        bnd[(b * 2) * K + col] = a.rho * __ldcg(a.lbt + bb + idx);         // rho (bounds - x_ref)
+        bnd[(b * 2 + 1) * K + col] = a.rho * __ldcg(a.ubt + bb + idx);
     }
     T *mu_c = a.mu + sb, *ds_c = a.ds + sb;
     const T *bt_c = a.bt + sb, *lr_c = a.lref + sb;
-    // u = rho d - mu into the swizzled slot array (x = u / rho at the slots
-    // of one-copy unbounded globals, which the global update skips)
+    // u = rho d - mu into the swizzled slot array
     for (int idx = tid; idx < a.NCH * K; idx += nthr) {
         const int ch = idx >> KS, col = idx & (K - 1);
         const Q4<T> d = ld4cg(ds_c + (size_t)idx * 4), m = ld4cg(mu_c + (size_t)idx * 4);
-        const unsigned sk = __ldg(a.skc + ch);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const T uu = a.rho * d.v[e] - m.v[e];
-            us[upos<K>(ch, e, col)] = (sk >> e) & 1u ? uu * a.inv_rho : uu;
-        }
+        for (int e = 0; e < 4; ++e) us[upos<K>(ch, e, col)] = a.rho * d.v[e] - m.v[e];
     }
     const int sc = tid & (K - 1);
     const int jpos = lane >> KS;
@@ -458,10 +459,10 @@ __global__ void __launch_bounds__(512, 1)
         for (int t = a.qstart[qd] + wq; t < a.qstart[qd + 1]; t += nwq) {
             const BatchTask tk = a.tasks[t];
             switch (tk.nq) {
-                case 1: tm_stage_in<K, 1>(tk, tl, mu_c, bt_c, jpos, sc); break;
-                case 2: tm_stage_in<K, 2>(tk, tl, mu_c, bt_c, jpos, sc); break;
-                case 3: tm_stage_in<K, 3>(tk, tl, mu_c, bt_c, jpos, sc); break;
-                default: tm_stage_in<K, 4>(tk, tl, mu_c, bt_c, jpos, sc); break;
+                case 1: tm_stage_in<K, 1>(tk, tl, mu_c, bt_c, jpos, sc, a.rho); break;
+                case 2: tm_stage_in<K, 2>(tk, tl, mu_c, bt_c, jpos, sc, a.rho); break;
+                case 3: tm_stage_in<K, 3>(tk, tl, mu_c, bt_c, jpos, sc, a.rho); break;
+                default: tm_stage_in<K, 4>(tk, tl, mu_c, bt_c, jpos, sc, a.rho); break;
             }
         }
         tm_wait_st();
@@ -492,8 +493,9 @@ __global__ void __launch_bounds__(512, 1)
         }
         // ---- G: global update (Eq. closed_1).  An item is one global and KQ of
         // its columns: sum of u over the copies, shift (bounded globals: the
-        // first NB table entries, c~ from L2; elsewhere c~ = 0), scale, clip,
-        // and x stored into every copy's slot; GB items per thread
+        // first NB table entries, c~ from L2; elsewhere c~ = 0), 1 / N, clip
+        // to rho (bounds - x_ref), and rho x stored into every copy's slot;
+        // GB items per thread
         for (int b0 = tid; b0 < GQ; b0 += GB * nthr) {
             // the GB items of this thread advance stage by stage, so that the
             // loads of one stage are in flight together: c~ and the table
@@ -569,9 +571,9 @@ __global__ void __launch_bounds__(512, 1)
         }
         __syncthreads();
         if (check || last) {
-            // x of each global (at its first copy): objective and ||B x||^2 per
-            // column on test iterations, and x~ of the running instances for
-            // their results (thread column sc = tid % K)
+            // x of each global (rho x at its first copy): objective and
+            // ||B x||^2 per column on test iterations, and x~ of the running
+            // instances for their results (thread column sc = tid % K)
             // (FP32 plans: x_ref + x~ and the thread's partial sums in FP32,
             // FP64 from the warp sums on; FP64 plans: FP64 throughout)
             double c2 = 0.0, c5 = 0.0;
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(512, 1)
                 const int2 gt = gts[j];
                 const int i = __ldg(a.gperm + j);
                 const size_t gi = gb + (size_t)i * K + sc;
-                const T xv = us[usg[gt.x & 0xffffff] + sc];
+                const T xv = us[usg[gt.x & 0xffffff] + sc] * a.inv_rho;
                 if (flags[sc]) a.xo[gi] = xv;
                 if (check) {
                     if constexpr (sizeof(T) == 4) {
@@ -628,16 +630,16 @@ __global__ void __launch_bounds__(512, 1)
                 if (!check && lane == 0) claim = atomicAdd(cnt, 1);
                 const BatchTask tk = tks[t];
                 switch (tk.nq) {
-                    case 1: batch_task<T, K, 1, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, a.skc, jpos, sc, rho,
+                    case 1: batch_task<T, K, 1, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c, a.chg, jpos, sc, rho,
                                                     inv_rho, check, act, wds, redw, tl); break;
                     case 2: if constexpr (NQ >= 2) batch_task<T, K, 2, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                           a.chg, a.skc, jpos, sc, rho, inv_rho, check, act,
+                                                                           a.chg, jpos, sc, rho, inv_rho, check, act,
                                                                            wds, redw, tl); break;
                     case 3: if constexpr (NQ >= 3) batch_task<T, K, 3, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                           a.chg, a.skc, jpos, sc, rho, inv_rho, check, act,
+                                                                           a.chg, jpos, sc, rho, inv_rho, check, act,
                                                                            wds, redw, tl); break;
                     default: if constexpr (NQ >= 4) batch_task<T, K, 4, TM>(tk, Fs, us, mu_c, bt_c, ds_c, lr_c, xr_c,
-                                                                            a.chg, a.skc, jpos, sc, rho, inv_rho, check, act,
+                                                                            a.chg, jpos, sc, rho, inv_rho, check, act,
                                                                             wds, redw, tl); break;
                 }
                 t = check ? t + t_step : __shfl_sync(0xffffffffu, claim, 0);

@@ -229,11 +229,10 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     }
     // global table: the bounded globals (in bounded-index order, so entry j
     // is bounded global j), the other globals the global update computes (Gs
-    // entries up to here), then those with one copy and no bounds, whose next
-    // x the local update of that copy writes (flagged per chunk in skc)
+    // entries up to here), then those with one copy and no bounds, which need
+    // no global update (the u of their slot is rho x)
     std::vector<int> gperm;
     gperm.reserve(G);
-    std::vector<unsigned char> skc(p->NCH, 0);
     auto by_slot = [&](int i) {
         return h->h_gstart[i + 1] - h->h_gstart[i] == 1 && b->h_bidx[i] < 0;
     };
@@ -242,12 +241,7 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
         if (b->h_bidx[gperm[j]] != j) { set_last_error("batch plan: bounded-global order"); return OPF_E_INVALID; }
     for (int i = 0; i < G; ++i) if (b->h_bidx[i] < 0 && !by_slot(i)) gperm.push_back(i);
     p->Gs = (int)gperm.size();
-    for (int i = 0; i < G; ++i) {
-        if (!by_slot(i)) continue;
-        gperm.push_back(i);
-        const int pos = sch[h->h_uslot[h->h_gstart[i]]];
-        skc[pos >> 2] |= (unsigned char)(1u << (pos & 3));
-    }
+    for (int i = 0; i < G; ++i) if (by_slot(i)) gperm.push_back(i);
     std::vector<int4> gtab(G);
     for (int j = 0; j < G; ++j) {
         const int i = gperm[j], s0 = h->h_gstart[i];
@@ -283,7 +277,6 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     BTRY(bupload(A, &p->d_chg, chg, st));
     BTRY(bupload(A, &p->d_gtab, gtab, st));
     BTRY(bupload(A, &p->d_gperm, gperm, st));
-    BTRY(bupload(A, &p->d_skc, skc, st));
     BTRY(bupload(A, &p->d_inst, inst, st));
     BTRY(bupload(A, &p->d_ipos, ipos, st));
     const size_t nslot = (size_t)p->C * p->NCH * K * 4, nglob = (size_t)p->C * G * K;
@@ -353,7 +346,7 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
     a.off_u = p.off_u; a.off_gt = p.off_gt; a.off_rc = p.off_rc; a.off_task = p.off_task; a.off_useg = p.off_useg;
     a.off_bnd = p.off_bnd;
     a.off_red = p.off_red; a.off_flag = p.off_flag;
-    a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab; a.gperm = p.d_gperm; a.skc = p.d_skc; a.Gs = p.Gs;
+    a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab; a.gperm = p.d_gperm; a.Gs = p.Gs;
     a.useg = p.d_useg;
     a.Fpk = (const T *)p.d_F; a.recip = (const T *)p.d_recip; a.cost = (const T *)p.d_cost;
     a.mu = (T *)p.mu; a.ds = (T *)p.ds; a.xo = (T *)p.xo;

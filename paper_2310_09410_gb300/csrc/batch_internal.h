@@ -21,7 +21,6 @@ struct BPlan {
     BatchTask *d_tasks = nullptr;
     int *d_memb = nullptr, *d_sch = nullptr, *d_useg = nullptr;
     int *d_inst = nullptr, *d_ipos = nullptr, *d_gperm = nullptr;
-    unsigned char *d_skc = nullptr;
     int4 *d_chg = nullptr, *d_gtab = nullptr;
     void *d_F = nullptr, *d_recip = nullptr, *d_cost = nullptr;
     void *mu = nullptr, *ds = nullptr, *xo = nullptr, *bt = nullptr, *lref = nullptr;

@@ -216,11 +216,11 @@ struct BatchTask {
 //   per bounded   [c][NB][K]       cbt (c~ of the bounded globals)
 // The reference lambda_ref of the shifted frame makes c~ = c + sum lambda_ref
 // zero at every unbounded global, so this engine reads c~ of the bounded ones
-// only (cbt; the lane engine reads ct).  The global table is permuted: the NB
+// only (cbt; the lane engine reads ct).  Its slot array holds rho x between
+// the phases, so a global with one copy and no bounds needs no global update:
+// the u of its slot is that value.  The global table is permuted: the NB
 // bounded globals (entry j = bounded index j), the other globals the global
-// update computes (Gs entries in all), then those with one copy and no
-// bounds, whose next x = u / rho the local update of their only slot writes
-// (skc).
+// update computes (Gs entries in all), then the one-copy unbounded ones.
 template <typename T>
 struct BatchArgs {
     int K, kshift, J, NCH, G, L, NB, n_tasks, nF, Gs;
@@ -233,7 +233,6 @@ struct BatchArgs {
     const int4 *chg;           // [NCH] g * K of each chunk's 4 slots (-1: padding)
     const int4 *gtab;          // [G] permuted: (first copy in useg, copies, bounded index or -1, 0)
     const int *gperm;          // [G] global of table entry j
-    const unsigned char *skc;  // [NCH] bit e: slot e of the chunk holds a global the local update computes
     const int *useg;           // copies of each global: slot-array row (ch * 4 + (e ^ (ch & 3))) * K
     const T *Fpk;              // [nF] factors, task-interleaved
     const T *recip;            // [kBatchRecip] 1 / (rho N) by copy count N
