@@ -385,20 +385,22 @@ __global__ void __launch_bounds__(512, 1)
     constexpr int NQD = K / KQ;                  // items per global
     constexpr int QS = NQD == 1 ? 0 : NQD == 2 ? 1 : NQD == 4 ? 2 : 3;
     // global-update items per thread taken together (their loads in flight
-    // together): 2 in FP32 (measured on the 1024 x 123-bus batch: 1 to 8
-    // items gave 211.9, 209.9, 214.1, 216.9, 226.3, 235.0, 230.3 and 231.4 ms
-    // per launch; more items cost predicated instructions and registers that
-    // the rest of the iteration needs), 4 for FP64 rows of 4
-    constexpr int GB = (sizeof(T) == 8 && KQ == 4) ? 4 : 2;
+    // together): 1 in FP32 (on the 1024 x 123-bus batch, with the first two
+    // copies' rows in the table entry and c~ in shared memory, 1 to 4 items
+    // gave 12.89, 12.97, 13.30 and 12.98 ms per launch of 2000 iterations;
+    // with the copy rows looked up in a second table and c~ read from L2, 2
+    // had been fastest: more items cost predicated instructions and
+    // registers the rest of the iteration needs), 4 for FP64 rows of 4
+    constexpr int GB = (sizeof(T) == 8 && KQ == 4) ? 4 : 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *Fsm = reinterpret_cast<T *>(smraw);
     const T *Fs = FG ? a.Fpk : Fsm;
     T *us = reinterpret_cast<T *>(smraw + a.off_u);
-    int2 *gts = reinterpret_cast<int2 *>(smraw + a.off_gt);      // (first copy | copies << 24, bounded index)
+    int4 *gts = reinterpret_cast<int4 *>(smraw + a.off_gt);      // [Gs] (row0, row1, copies | first extra << 8, bounded index)
     T *rcs = reinterpret_cast<T *>(smraw + a.off_rc);            // 1 / (rho N) by copy count N
     BatchTask *tks = reinterpret_cast<BatchTask *>(smraw + a.off_task);   // the warp tasks
-    int *usg = reinterpret_cast<int *>(smraw + a.off_useg);      // slot-array row of every copy
-    T *bnd = reinterpret_cast<T *>(smraw + a.off_bnd);           // [NB][2][K]: bounds - x_ref
+    int *usg = reinterpret_cast<int *>(smraw + a.off_useg);      // slot-array rows of the third and later copies
+    T *bnd = reinterpret_cast<T *>(smraw + a.off_bnd);           // [NB][3][K]: rho (bounds - x_ref), c~
     double *red = reinterpret_cast<double *>(smraw + a.off_red);
     int *flags = reinterpret_cast<int *>(smraw + a.off_flag);    // [0,K) running, [K,2K) just finished
     int *tnext = flags + 2 * K;                                    // next task of the dynamic schedule (per quadrant)
@@ -420,21 +422,19 @@ __global__ void __launch_bounds__(512, 1)
     // factors and the global-update tables into shared memory (nF is a multiple of 4)
     if (!FG)
         for (int i = tid * 4; i < a.nF; i += nthr * 4) st4(Fsm + i, ld4(a.Fpk + i));
-    for (int i = tid; i < a.G; i += nthr) {
-        const int4 gt = __ldg(a.gtab + i);
-        gts[i] = make_int2((int)((unsigned)gt.x | ((unsigned)gt.y << 24)), gt.z);
-    }
+    for (int j = tid; j < a.Gs; j += nthr) gts[j] = __ldg(a.gtab + j);
     // 1 / N by copy count N: the global update stores rho x = (sum u - c~) / N
     for (int i = tid; i < kBatchRecip; i += nthr) rcs[i] = i ? (T)(1.0 / (double)i) : T(0);
     for (int i = tid; i < a.n_tasks; i += nthr) tks[i] = a.tasks[i];
-    for (int k = tid; k < a.L; k += nthr) usg[k] = __ldg(a.useg + k);
+    for (int k = tid; k < a.n_uxt; k += nthr) usg[k] = __ldg(a.uxt + k);
     const size_t sb = (size_t)c * a.NCH * K * 4;     // this CTA's slot arrays
     const size_t gb = (size_t)c * a.G * K;           // global arrays
     const size_t bb = (size_t)c * a.NB * K;          // bounded-global arrays
     for (int idx = tid; idx < a.NB * K; idx += nthr) {
         const int b = idx >> KS, col = idx & (K - 1);
-        bnd[(b * 2) * K + col] = a.rho * __ldcg(a.lbt + bb + idx);         // rho (bounds - x_ref)
-        bnd[(b * 2 + 1) * K + col] = a.rho * __ldcg(a.ubt + bb + idx);
+        bnd[(b * 3) * K + col] = a.rho * __ldcg(a.lbt + bb + idx);         // rho (bounds - x_ref)
+        bnd[(b * 3 + 1) * K + col] = a.rho * __ldcg(a.ubt + bb + idx);
+        bnd[(b * 3 + 2) * K + col] = __ldcg(a.cbt + bb + idx);              // c~
     }
     T *mu_c = a.mu + sb, *ds_c = a.ds + sb;
     const T *bt_c = a.bt + sb, *lr_c = a.lref + sb;
@@ -476,8 +476,7 @@ __global__ void __launch_bounds__(512, 1)
     int last_check = 0;
     bool all_done = false;
     const int GK = a.G * K;
-    const int GQ = a.Gs * NQD;       // the globals the global update computes come first,
-    const int GBQ = a.NB * NQD;      // the bounded ones (table entry = bounded index) first of all
+    const int GQ = a.Gs * NQD;       // the globals the global update computes (the table's first Gs)
     for (int it = 0; it < n_iters; ++it) {
         const bool check = check_every > 0 && ((it + 1) % check_every == 0);
         const bool last = it == n_iters - 1;
@@ -492,37 +491,30 @@ __global__ void __launch_bounds__(512, 1)
             *tnext = n_warps;
         }
         // ---- G: global update (Eq. closed_1).  An item is one global and KQ of
-        // its columns: sum of u over the copies, shift (bounded globals: the
-        // first NB table entries, c~ from L2; elsewhere c~ = 0), 1 / N, clip
-        // to rho (bounds - x_ref), and rho x stored into every copy's slot;
-        // GB items per thread
+        // its columns: sum of u over the copies, shift (bounded globals, the
+        // first NB table entries: c~; elsewhere c~ = 0), 1 / N, clip to
+        // rho (bounds - x_ref), and rho x stored into every copy's slot; GB
+        // items per thread
         for (int b0 = tid; b0 < GQ; b0 += GB * nthr) {
             // the GB items of this thread advance stage by stage, so that the
-            // loads of one stage are in flight together: c~ and the table
-            // entries, the first two copies' rows, their u; further copies
+            // loads of one stage are in flight together: the table entries
+            // (with the first two copies' rows), their u; further copies
             // (vertices of degree > 1) one by one; then the update
-            RowK<T, KQ> cr[GB], sum[GB];
-            int2 gtj[GB];
+            RowK<T, KQ> sum[GB];
+            int4 gtj[GB];
             int row0[GB], row1[GB];
 #pragma unroll
             for (int j = 0; j < GB; ++j) {
                 const int item = b0 + j * nthr;
-                gtj[j] = make_int2(0, -1);
-                if (item < GBQ)
-                    load_row<T, KQ, true>(cr[j], a.cbt + bb + (size_t)(item >> QS) * K + (item & (NQD - 1)) * KQ);
+                gtj[j] = make_int4(0, 0, 0, -1);
                 if (item < GQ) gtj[j] = gts[item >> QS];
-            }
-#pragma unroll
-            for (int j = 0; j < GB; ++j) {
-                const int item = b0 + j * nthr;
-                const int st0 = gtj[j].x & 0xffffff, cnt = (int)((unsigned)gtj[j].x >> 24);
                 const int hq = (item & (NQD - 1)) * KQ;
-                row0[j] = cnt > 0 ? usg[st0] + hq : 0;
-                row1[j] = cnt > 1 ? usg[st0 + 1] + hq : 0;
+                row0[j] = gtj[j].x + hq;
+                row1[j] = gtj[j].y + hq;
             }
 #pragma unroll
             for (int j = 0; j < GB; ++j) {
-                const int cnt = (int)((unsigned)gtj[j].x >> 24);
+                const int cnt = gtj[j].z & 0xff;
 #pragma unroll
                 for (int k = 0; k < KQ; ++k) sum[j].v[k] = T(0);
                 if (cnt > 0) {
@@ -543,8 +535,8 @@ __global__ void __launch_bounds__(512, 1)
                 const int item = b0 + j * nthr;
                 if (item >= GQ) continue;
                 const int h = item & (NQD - 1);
-                const int2 gt = gtj[j];
-                const int st0 = gt.x & 0xffffff, cnt = (int)((unsigned)gt.x >> 24);
+                const int4 gt = gtj[j];
+                const int cnt = gt.z & 0xff, st0 = (gt.z >> 8) - 2;    // usg[st0 + q]: copy q >= 2
                 for (int q = 2; q < cnt; ++q) {
                     RowK<T, KQ> uq;
                     load_row<T, KQ, false>(uq, us + usg[st0 + q] + h * KQ);
@@ -552,12 +544,13 @@ __global__ void __launch_bounds__(512, 1)
                     for (int k = 0; k < KQ; ++k) sum[j].v[k] += uq.v[k];
                 }
                 const T rcp = rcs[cnt];
-                if (gt.y >= 0) {
+                if (gt.w >= 0) {
+                    RowK<T, KQ> lo, hi, cr;
+                    load_row<T, KQ, false>(cr, bnd + (gt.w * 3 + 2) * K + h * KQ);
+                    load_row<T, KQ, false>(lo, bnd + (gt.w * 3) * K + h * KQ);
+                    load_row<T, KQ, false>(hi, bnd + (gt.w * 3 + 1) * K + h * KQ);
 #pragma unroll
-                    for (int k = 0; k < KQ; ++k) sum[j].v[k] = (sum[j].v[k] - cr[j].v[k]) * rcp;
-                    RowK<T, KQ> lo, hi;
-                    load_row<T, KQ, false>(lo, bnd + (gt.y * 2) * K + h * KQ);
-                    load_row<T, KQ, false>(hi, bnd + (gt.y * 2 + 1) * K + h * KQ);
+                    for (int k = 0; k < KQ; ++k) sum[j].v[k] = (sum[j].v[k] - cr.v[k]) * rcp;
 #pragma unroll
                     for (int k = 0; k < KQ; ++k) sum[j].v[k] = clampT(sum[j].v[k], lo.v[k], hi.v[k]);
                 } else {
@@ -580,10 +573,10 @@ __global__ void __launch_bounds__(512, 1)
             T p2 = T(0), p5 = T(0);
             for (int item = tid; item < GK; item += nthr) {
                 const int j = item >> KS;
-                const int2 gt = gts[j];
+                const int2 gt = make_int2(__ldg(a.gx + j), 0);   // first copy's row | copies << 24
                 const int i = __ldg(a.gperm + j);
                 const size_t gi = gb + (size_t)i * K + sc;
-                const T xv = us[usg[gt.x & 0xffffff] + sc] * a.inv_rho;
+                const T xv = us[(gt.x & 0xffffff) + sc] * a.inv_rho;
                 if (flags[sc]) a.xo[gi] = xv;
                 if (check) {
                     if constexpr (sizeof(T) == 4) {

@@ -217,14 +217,14 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     p->nF = (fo + 3) & ~3;
     p->n_tasks = (int)tasks.size();
     p->NB = b->NB;
-    // copies of each global in u order, as offsets into the CTA's u array
-    std::vector<int> useg(L);
+    // slot-array row of every copy (global-major copy order)
+    std::vector<int> crow(L);
     for (int i = 0; i < G; ++i) {
         const int s0 = h->h_gstart[i], cnt = h->h_gstart[i + 1] - s0;
         for (int q = 0; q < cnt; ++q) {
             const int pos = sch[h->h_uslot[s0 + q]];
             const int ch = pos >> 2, e = pos & 3;
-            useg[s0 + q] = (ch * 4 + (e ^ (ch & 3))) * K;
+            crow[s0 + q] = (ch * 4 + (e ^ (ch & 3))) * K;
         }
     }
     // global table: the bounded globals (in bounded-index order, so entry j
@@ -242,19 +242,30 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     for (int i = 0; i < G; ++i) if (b->h_bidx[i] < 0 && !by_slot(i)) gperm.push_back(i);
     p->Gs = (int)gperm.size();
     for (int i = 0; i < G; ++i) if (by_slot(i)) gperm.push_back(i);
-    std::vector<int4> gtab(G);
+    // entries of the computed globals: the first two copies' rows inline,
+    // later copies in uxt; every entry's first row and copy count in gx
+    std::vector<int4> gtab(std::max(p->Gs, 1), make_int4(0, 0, 0, -1));
+    std::vector<int> uxt, gx(G);
     for (int j = 0; j < G; ++j) {
-        const int i = gperm[j], s0 = h->h_gstart[i];
-        gtab[j] = make_int4(s0, h->h_gstart[i + 1] - s0, b->h_bidx[i], 0);
+        const int i = gperm[j], s0 = h->h_gstart[i], cnt = h->h_gstart[i + 1] - s0;
+        if (cnt < 1 || cnt >= kBatchRecip || crow[s0] >= (1 << 24) || uxt.size() >= (1u << 22)) {
+            set_last_error("batch plan: global table");
+            return OPF_E_CAPACITY;
+        }
+        gx[j] = crow[s0] | (cnt << 24);
+        if (j >= p->Gs) continue;
+        gtab[j] = make_int4(crow[s0], cnt > 1 ? crow[s0 + 1] : 0, cnt | ((int)uxt.size() << 8), b->h_bidx[i]);
+        for (int q = 2; q < cnt; ++q) uxt.push_back(crow[s0 + q]);
     }
+    p->n_uxt = (int)uxt.size();
     // shared memory
     p->off_u = fg ? 0u : a16((size_t)p->nF * sz);
     p->off_gt = p->off_u + a16((size_t)p->NCH * K * 4 * sz);
-    p->off_rc = p->off_gt + a16((size_t)G * sizeof(int2));
+    p->off_rc = p->off_gt + a16((size_t)p->Gs * sizeof(int4));
     p->off_task = p->off_rc + a16((size_t)kBatchRecip * sz);
     p->off_useg = p->off_task + a16((size_t)p->n_tasks * sizeof(BatchTask));
-    p->off_bnd = p->off_useg + a16((size_t)L * sizeof(int));
-    p->off_red = p->off_bnd + a16((size_t)b->NB * 2 * K * sz);
+    p->off_bnd = p->off_useg + a16((size_t)p->n_uxt * sizeof(int));
+    p->off_red = p->off_bnd + a16((size_t)b->NB * 3 * K * sz);
     p->off_flag = p->off_red + a16((size_t)W * K * 6 * sizeof(double));
     p->bytes = p->off_flag + a16((size_t)(2 * K + 4) * sizeof(int));
     if (p->bytes > kMaxSmem) { set_last_error("batch plan: shared memory"); return OPF_E_CAPACITY; }
@@ -273,7 +284,8 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     BTRY(bupload(A, &p->d_tasks, tasks, st));
     BTRY(bupload(A, &p->d_memb, memb, st));
     BTRY(bupload(A, &p->d_sch, sch, st));
-    BTRY(bupload(A, &p->d_useg, useg, st));
+    BTRY(bupload(A, &p->d_uxt, uxt, st));
+    BTRY(bupload(A, &p->d_gx, gx, st));
     BTRY(bupload(A, &p->d_chg, chg, st));
     BTRY(bupload(A, &p->d_gtab, gtab, st));
     BTRY(bupload(A, &p->d_gperm, gperm, st));
@@ -347,7 +359,7 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
     a.off_bnd = p.off_bnd;
     a.off_red = p.off_red; a.off_flag = p.off_flag;
     a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab; a.gperm = p.d_gperm; a.Gs = p.Gs;
-    a.useg = p.d_useg;
+    a.uxt = p.d_uxt; a.gx = p.d_gx; a.n_uxt = p.n_uxt;
     a.Fpk = (const T *)p.d_F; a.recip = (const T *)p.d_recip; a.cost = (const T *)p.d_cost;
     a.mu = (T *)p.mu; a.ds = (T *)p.ds; a.xo = (T *)p.xo;
     a.bt = (const T *)p.bt; a.lref = (const T *)p.lref; a.ct = (const T *)p.ct; a.xrf = (const T *)p.xrf;

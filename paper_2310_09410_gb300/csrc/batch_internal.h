@@ -19,7 +19,8 @@ struct BPlan {
     double rho = -1.0;
     std::vector<void *> allocs;
     BatchTask *d_tasks = nullptr;
-    int *d_memb = nullptr, *d_sch = nullptr, *d_useg = nullptr;
+    int *d_memb = nullptr, *d_sch = nullptr, *d_uxt = nullptr, *d_gx = nullptr;
+    int n_uxt = 0;
     int *d_inst = nullptr, *d_ipos = nullptr, *d_gperm = nullptr;
     int4 *d_chg = nullptr, *d_gtab = nullptr;
     void *d_F = nullptr, *d_recip = nullptr, *d_cost = nullptr;

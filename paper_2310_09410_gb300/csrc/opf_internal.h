@@ -231,9 +231,13 @@ struct BatchArgs {
     int tm, tm_cols, qstart[5];
     const BatchTask *tasks;    // [n_tasks] in decreasing cost
     const int4 *chg;           // [NCH] g * K of each chunk's 4 slots (-1: padding)
-    const int4 *gtab;          // [G] permuted: (first copy in useg, copies, bounded index or -1, 0)
+    // slot-array row of a copy: (ch * 4 + (e ^ (ch & 3))) * K
+    const int4 *gtab;          // [Gs] (row of copy 0, row of copy 1, copies | first later copy in uxt << 8,
+                               //       bounded index or -1)
+    const int *uxt;            // [n_uxt] rows of the third and later copies
+    const int *gx;             // [G] row of copy 0 | copies << 24, every table entry
     const int *gperm;          // [G] global of table entry j
-    const int *useg;           // copies of each global: slot-array row (ch * 4 + (e ^ (ch & 3))) * K
+    int n_uxt;
     const T *Fpk;              // [nF] factors, task-interleaved
     const T *recip;            // [kBatchRecip] 1 / (rho N) by copy count N
     const T *cost;             // [G] c_i
