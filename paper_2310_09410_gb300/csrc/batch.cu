@@ -260,19 +260,19 @@ __device__ __forceinline__ void batch_task(const BatchTask &tk, const T *Fs, T *
     // (the task's row count is even: a member's missing rows are zero)
     for (int r = 0; r < tk.f; r += 2, F0 += 2 * rstride) {
         const T *F1 = F0 + rstride;
-        T p0[4] = {T(0), T(0), T(0), T(0)}, p1[4] = {T(0), T(0), T(0), T(0)};
+        // one accumulation chain per row (four partial sums and their adds
+        // measured 4.5 % slower per launch: more instructions)
+        T s0 = T(0), s1 = T(0);
 #pragma unroll
         for (int q = 0; q < NQT; ++q) {
             const Q4<T> f0 = ld4(F0 + q * J * 4);
             const Q4<T> f1 = ld4(F1 + q * J * 4);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                p0[e] += f0.v[e] * v[4 * q + e];
-                p1[e] += f1.v[e] * v[4 * q + e];
+                s0 += f0.v[e] * v[4 * q + e];
+                s1 += f1.v[e] * v[4 * q + e];
             }
         }
-        T s0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
-        T s1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
         for (int o = K; o < red_top; o <<= 1) {
             s0 += __shfl_xor_sync(0xffffffffu, s0, o);
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
