@@ -76,13 +76,13 @@ FP32_LANES = 128
 # DRAM bytes per launch of the dominant kernels, copied from the ncu captures
 # summarised in profiles/ (a copied constant, labelled so in the line; None
 # once the kernel has changed since the capture).
-BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 63068672 + 857344
+BATCH_ENGINE_TRAFFIC_PER_LAUNCH = 63054592 + 893184
 BATCH_ENGINE_TRAFFIC_SOURCE = "profiles/k_batch_engine_123bus_x1024.md"
 # Warp instructions per instance-iteration of the batched engine in the
 # shape the autotune picks for the 1024 x 123-bus batch (8 instances per CTA,
 # 16 warps, tensor memory): smsp__inst_executed.sum of the same capture over
-# its 2000 iterations x 1024 instances (copied; None for other shapes).
-BATCH_ENGINE_INST_PER_INSTANCE_ITER = 9.8699e9 / (2000 * 1024)
+# its 4000 iterations x 1024 instances (copied; None for other shapes).
+BATCH_ENGINE_INST_PER_INSTANCE_ITER = 16.7984e9 / (4000 * 1024)
 BATCH_ENGINE_INST_SHAPE = {"k_inst": 8, "warps": 16, "tmem": 1}
 WARP_ENGINE_TRAFFIC_PER_LAUNCH = 516864 + 768
 PERSIST_ENGINE_TRAFFIC_PER_LAUNCH = 8708352 + 313088
@@ -695,7 +695,7 @@ def run_batch(args, rank, world, local):
                               FP32_LANES, max_mhz, nominal),
             "frac_of_nominal": achieved / nominal if achieved else None,
             "traffic": BATCH_ENGINE_TRAFFIC_PER_LAUNCH,
-            "traffic_unit": "DRAM bytes per engine launch of 2000 iterations, copied from the ncu capture in "
+            "traffic_unit": "DRAM bytes per engine launch of 4000 iterations, copied from the ncu capture in "
                             + BATCH_ENGINE_TRAFFIC_SOURCE + " (not measured in this run)",
             "kernel": "k_batch_engine<float> (FP32; %d instances per CTA, %d warps, %d CTAs; factors, u and x "
                       "in shared memory, lambda and bbar~ %s)"

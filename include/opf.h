@@ -314,7 +314,7 @@ int opf_batch_set_loads_device(opf_batch *b, int32_t first, int32_t count, const
 
 /* Runs every instance to its own stopping test (options as opf_solve_ex;
  * engine and cluster ignored).  OPF_PREC_MIXED: FP32 iterations re-centred
- * every recenter_every iterations (0: 2000) on an FP64 reference, then FP64 iterations
+ * every recenter_every iterations (0: 4000) on an FP64 reference, then FP64 iterations
  * until the test holds in FP64 (this polish tests every 2 iterations, for at
  * most 2 check_every iterations).  Returns OPF_OK when every instance
  * converged, OPF_NOT_CONVERGED when some hit max_iter (per-instance results in

@@ -72,12 +72,12 @@ def test_oracle_error_of_the_bench_line():
 
 def test_issue_roofline_of_the_batched_engine():
     """The issue figure: warp instructions per SM-cycle of the engine's grid
-    against 4; one launch of the captured kernel (2000 iterations x 1024
-    instances, 9.87 G warp instructions, 14.70 ms single-pass at 2070 MHz on
-    128 SMs) gives 2.53 per cycle; other engine shapes get none."""
+    against 4; one launch of the captured kernel (4000 iterations x 1024
+    instances, 16.80 G warp instructions, 25.42 ms single-pass at 2070 MHz on
+    128 SMs) gives 2.49 per cycle; other engine shapes get none."""
     shape = {"k_inst": 8, "warps": 16, "tmem": 1, "ctas": 128}
-    r = bench.issue_roofline(shape, 2000 * 1024, 14.70, 2070.0)
-    assert abs(r["achieved_ipc_per_sm"] - 9.8699e9 / (14.70e-3 * 2070e6 * 128)) < 1e-9
-    assert 0.6 < r["frac"] < 0.67 and r["peak_ipc_per_sm"] == 4.0 and r["sms"] == 128
+    r = bench.issue_roofline(shape, 4000 * 1024, 25.42, 2070.0)
+    assert abs(r["achieved_ipc_per_sm"] - 16.7984e9 / (25.42e-3 * 2070e6 * 128)) < 1e-9
+    assert 0.6 < r["frac"] < 0.65 and r["peak_ipc_per_sm"] == 4.0 and r["sms"] == 128
     assert bench.issue_roofline(dict(shape, k_inst=4), 2000 * 1024, 17.59, 2070.0) is None
     assert bench.issue_roofline(shape, 2000 * 1024, 0.0, 2070.0) is None
