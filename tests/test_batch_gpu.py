@@ -100,6 +100,47 @@ def test_fp64_batch_generic_rank_deficient_rhs():
     assert M.n == len(g["c"])
 
 
+@pytest.mark.parametrize("seed", [11, 12])
+def test_batch_generic_free_globals(seed):
+    """Globals without bounds, with one copy (which the batched engine leaves
+    out of its global update: with the shifted cost zero there, rho x is the
+    u of the copy's slot) and with several, beside bounded ones, each with a
+    cost: FP64 iterates to 1e-10 and FP32 iterates to 1e-4 of the oracle's
+    after 100 iterations, on several right-hand sides."""
+    g = synth.random_generic(seed, n_global=150, n_sub=14, max_n=30, p_free=0.6)
+    copies = np.zeros(len(g["c"]), int)
+    for sub in g["subs"]:
+        copies[np.asarray(sub["idx"])] += 1
+    free = ~np.isfinite(g["lb"]) & ~np.isfinite(g["ub"])
+    assert np.any(free & (copies == 1)) and np.any(free & (copies > 1)) and np.any(~free)
+    rng = np.random.default_rng(seed)
+    subs_j, rhs = [], []
+    for j in range(3):
+        subs = []
+        for sub in g["subs"]:
+            A = np.asarray(sub["A"], float)
+            subs.append(dict(sub, b=A @ rng.uniform(-0.4, 0.4, A.shape[1])))
+        subs_j.append(subs)
+        rhs.append(np.concatenate([sb["b"] for sb in subs]))
+    refs = [oracle_iterates(lindist.from_generic(dict(g, subs=subs)), 100, rho=3.0) for subs in subs_j]
+    with opf.Solver.from_generic(g["c"], g["lb"], g["ub"], g["subs"]) as s:
+        s.precompute()
+        with opf.Batch(s, 3) as b:
+            b.set_rhs(0, np.stack(rhs))
+            b.step(100, rho=3.0)
+            for j in range(3):
+                xs, lam = b.locals(j)
+                assert rel_err(xs, refs[j].xs) <= TOL_ITER
+                assert rel_err(lam, refs[j].lam) <= TOL_ITER
+            b.set_rhs(0, np.stack(rhs))
+            b.solve(rho=3.0, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP32)
+            assert np.all(b.status()["iters"] == 100)
+            for j in range(3):
+                xs, lam = b.locals(j)
+                assert rel_err(xs, refs[j].xs) <= 1e-4
+                assert rel_err(lam, refs[j].lam) <= 1e-4
+
+
 @pytest.mark.parametrize("k32", [8, 4])
 def test_fp32_batch_tracks_oracle(k32):
     f = synth.preset_feeder("123", 2001)
