@@ -227,18 +227,15 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
             crow[s0 + q] = (ch * 4 + (e ^ (ch & 3))) * K;
         }
     }
-    // global table: the bounded globals (in bounded-index order, so entry j
-    // is bounded global j), the other globals the global update computes (Gs
-    // entries up to here), then those with one copy and no bounds, which need
-    // no global update (the u of their slot is rho x)
+    // global order of the tables: the bounded globals, the other globals the
+    // global update computes (Gs up to here), then those with one copy and no
+    // bounds, which need no global update (the u of their slot is rho x)
     std::vector<int> gperm;
     gperm.reserve(G);
     auto by_slot = [&](int i) {
         return h->h_gstart[i + 1] - h->h_gstart[i] == 1 && b->h_bidx[i] < 0;
     };
     for (int i = 0; i < G; ++i) if (b->h_bidx[i] >= 0) gperm.push_back(i);
-    for (int j = 0; j < (int)gperm.size(); ++j)
-        if (b->h_bidx[gperm[j]] != j) { set_last_error("batch plan: bounded-global order"); return OPF_E_INVALID; }
     for (int i = 0; i < G; ++i) if (b->h_bidx[i] < 0 && !by_slot(i)) gperm.push_back(i);
     p->Gs = (int)gperm.size();
     for (int i = 0; i < G; ++i) if (by_slot(i)) gperm.push_back(i);
@@ -360,9 +357,9 @@ BatchArgs<T> engine_args(opf_batch *b, const BPlan &p, double rho) {
     a.off_red = p.off_red; a.off_flag = p.off_flag;
     a.tasks = p.d_tasks; a.chg = p.d_chg; a.gtab = p.d_gtab; a.gperm = p.d_gperm; a.Gs = p.Gs;
     a.uxt = p.d_uxt; a.gx = p.d_gx; a.n_uxt = p.n_uxt;
-    a.Fpk = (const T *)p.d_F; a.recip = (const T *)p.d_recip; a.cost = (const T *)p.d_cost;
+    a.Fpk = (const T *)p.d_F; a.cost = (const T *)p.d_cost;
     a.mu = (T *)p.mu; a.ds = (T *)p.ds; a.xo = (T *)p.xo;
-    a.bt = (const T *)p.bt; a.lref = (const T *)p.lref; a.ct = (const T *)p.ct; a.xrf = (const T *)p.xrf;
+    a.bt = (const T *)p.bt; a.lref = (const T *)p.lref; a.xrf = (const T *)p.xrf;
     a.lbt = (const T *)p.lbt; a.ubt = (const T *)p.ubt; a.cbt = (const T *)p.cbt;
     a.inst = p.d_inst; a.st = b->d_st;
     a.rho = (T)rho; a.inv_rho = (T)(1.0 / rho); a.rho_d = rho;

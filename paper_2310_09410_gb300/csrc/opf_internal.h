@@ -211,16 +211,15 @@ struct BatchTask {
 // Arguments of one batched-engine launch.  Instance column sc of CTA c holds
 // instance inst[c * K + sc] (-1: empty).  Engine arrays (type T):
 //   per slot      [c][NCH][K][4]   mu, ds, bt (+bbar~ if M = F^T F, else -bbar~), lref (lambda_ref)
-//   per global    [c][G][K]        ct (c~), xrf (x_ref), xo (x~ at the end)
-//   per bounded   [c][NB][K]       lbt, ubt (bounds - x_ref)
-//   per bounded   [c][NB][K]       cbt (c~ of the bounded globals)
+//   per global    [c][G][K]        xrf (x_ref), xo (x~ at the end)
+//   per bounded   [c][NB][K]       lbt, ubt (bounds - x_ref), cbt (c~)
 // The reference lambda_ref of the shifted frame makes c~ = c + sum lambda_ref
 // zero at every unbounded global, so this engine reads c~ of the bounded ones
-// only (cbt; the lane engine reads ct).  Its slot array holds rho x between
-// the phases, so a global with one copy and no bounds needs no global update:
-// the u of its slot is that value.  The global table is permuted: the NB
-// bounded globals (entry j = bounded index j), the other globals the global
-// update computes (Gs entries in all), then the one-copy unbounded ones.
+// only (cbt; the lane engine reads the per-global c~).  Its slot array holds
+// rho x between the phases, so a global with one copy and no bounds needs no
+// global update: the u of its slot is that value.  The global update's table
+// (gtab, Gs entries) holds the globals it computes, the bounded ones first;
+// gx and gperm list every global for the test iterations' x output.
 template <typename T>
 struct BatchArgs {
     int K, kshift, J, NCH, G, L, NB, n_tasks, nF, Gs;
@@ -239,10 +238,9 @@ struct BatchArgs {
     const int *gperm;          // [G] global of table entry j
     int n_uxt;
     const T *Fpk;              // [nF] factors, task-interleaved
-    const T *recip;            // [kBatchRecip] 1 / (rho N) by copy count N
     const T *cost;             // [G] c_i
     T *mu, *ds, *xo;
-    const T *bt, *lref, *ct, *xrf, *lbt, *ubt, *cbt;
+    const T *bt, *lref, *xrf, *lbt, *ubt, *cbt;
     const int *inst;
     DevStatus *st;             // per instance
     T rho, inv_rho;
