@@ -141,6 +141,38 @@ def test_batch_generic_free_globals(seed):
                 assert rel_err(lam, refs[j].lam) <= 1e-4
 
 
+def test_batch_without_global_update_items():
+    """One subsystem holding every global, none bounded: every global has one
+    copy and no bounds, so the batched engine's global update has no item at
+    all (each slot's u is rho x of its global).  FP64 iterates to 1e-10 and
+    FP32 iterates to 1e-4 of the oracle's after 100 iterations."""
+    g = synth.random_generic(21, n_global=60, n_sub=1, max_n=60, p_free=1.0)
+    assert len(g["subs"]) == 1 and not np.any(np.isfinite(g["lb"])) and not np.any(np.isfinite(g["ub"]))
+    rng = np.random.default_rng(21)
+    subs_j, rhs = [], []
+    for j in range(2):
+        A = np.asarray(g["subs"][0]["A"], float)
+        subs = [dict(g["subs"][0], b=A @ rng.uniform(-0.4, 0.4, A.shape[1]))]
+        subs_j.append(subs)
+        rhs.append(subs[0]["b"])
+    refs = [oracle_iterates(lindist.from_generic(dict(g, subs=subs)), 100, rho=3.0) for subs in subs_j]
+    with opf.Solver.from_generic(g["c"], g["lb"], g["ub"], g["subs"]) as s:
+        s.precompute()
+        with opf.Batch(s, 2) as b:
+            b.set_rhs(0, np.stack(rhs))
+            b.step(100, rho=3.0)
+            for j in range(2):
+                xs, lam = b.locals(j)
+                assert rel_err(xs, refs[j].xs) <= TOL_ITER
+                assert rel_err(lam, refs[j].lam) <= TOL_ITER
+            b.set_rhs(0, np.stack(rhs))
+            b.solve(rho=3.0, eps_rel=0.0, max_iter=100, check_every=50, precision=opf.PREC_FP32)
+            for j in range(2):
+                xs, lam = b.locals(j)
+                assert rel_err(xs, refs[j].xs) <= 1e-4
+                assert rel_err(lam, refs[j].lam) <= 1e-4
+
+
 @pytest.mark.parametrize("k32", [8, 4])
 def test_fp32_batch_tracks_oracle(k32):
     f = synth.preset_feeder("123", 2001)
