@@ -3,9 +3,10 @@
 // own right-hand side b, hence its own bbar = A_s^+ b.
 //
 //  k_batch_engine  n_iters iterations of Algorithm 1 for the K instances of
-//                  one CTA, all resident: factors, u = rho x_s - lambda and x
-//                  in shared memory; lambda, bbar~ and the test data streamed
-//                  from L2 as 16-byte vectors.  Per iteration:
+//                  one CTA, all resident: factors, u = rho x_s - lambda and
+//                  rho x in shared memory; lambda and bbar~ in tensor memory
+//                  (FP32 plans) or streamed from L2 as 16-byte vectors, the
+//                  test data from L2.  Per iteration:
 //                    G. per (global, instance): Eq. closed_1 as a fixed-order
 //                       sum over the global's copies of u, rho x stored into
 //                       the copies' slots (a global with one copy and no
@@ -22,10 +23,11 @@
 //                  and every check_every iterations the Sec. III-C sums per
 //                  instance in FP64 and the test; finished instances freeze.
 //  k_bref_*        FP64 re-centring: x_ref = next global update of the FP64
-//                  state, lambda_ref = lambda, shifted data written in the
-//                  engine layout (the engine iterates on x_s - x_ref[g] and
-//                  lambda - lambda_ref, the change of variables of the
-//                  single-instance engines).
+//                  state, lambda_ref = lambda (less delta at unbounded
+//                  globals, so that their shifted cost is zero), shifted data
+//                  written in the engine layout (the engine iterates on
+//                  x_s - x_ref[g] and lambda - lambda_ref, the change of
+//                  variables of the single-instance engines).
 //  k_bunshift_*    back to the unshifted FP64 state.
 //  k_bbar          bbar = A_s^+ b per instance and subsystem (Sec. III-B).
 #include <cuda_runtime.h>
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__(512, 1)
     const T *Fs = FG ? a.Fpk : Fsm;
     T *us = reinterpret_cast<T *>(smraw + a.off_u);
     int4 *gts = reinterpret_cast<int4 *>(smraw + a.off_gt);      // [Gs] (row0, row1, copies | first extra << 8, bounded index)
-    T *rcs = reinterpret_cast<T *>(smraw + a.off_rc);            // 1 / (rho N) by copy count N
+    T *rcs = reinterpret_cast<T *>(smraw + a.off_rc);            // 1 / N by copy count N
     BatchTask *tks = reinterpret_cast<BatchTask *>(smraw + a.off_task);   // the warp tasks
     int *usg = reinterpret_cast<int *>(smraw + a.off_useg);      // slot-array rows of the third and later copies
     T *bnd = reinterpret_cast<T *>(smraw + a.off_bnd);           // [NB][3][K]: rho (bounds - x_ref), c~
@@ -491,10 +493,10 @@ __global__ void __launch_bounds__(512, 1)
             *tnext = n_warps;
         }
         // ---- G: global update (Eq. closed_1).  An item is one global and KQ of
-        // its columns: sum of u over the copies, shift (bounded globals, the
-        // first NB table entries: c~; elsewhere c~ = 0), 1 / N, clip to
-        // rho (bounds - x_ref), and rho x stored into every copy's slot; GB
-        // items per thread
+        // its columns: sum of u over the copies, shift by c~ (bounded globals,
+        // whose table entry names their bounded index; elsewhere c~ = 0),
+        // 1 / N, clip to rho (bounds - x_ref), and rho x stored into every
+        // copy's slot; GB items per thread
         for (int b0 = tid; b0 < GQ; b0 += GB * nthr) {
             // the GB items of this thread advance stage by stage, so that the
             // loads of one stage are in flight together: the table entries
