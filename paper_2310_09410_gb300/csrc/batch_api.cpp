@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "batch_internal.h"
+#include "batch_tables.h"
 
 namespace opf {
 template <typename T> int batch_engine_prepare(int K, int nq, bool fg, bool tm, unsigned bytes);
@@ -227,33 +228,18 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
             crow[s0 + q] = (ch * 4 + (e ^ (ch & 3))) * K;
         }
     }
-    // global order of the tables: the bounded globals, the other globals the
-    // global update computes (Gs up to here), then those with one copy and no
-    // bounds, which need no global update (the u of their slot is rho x)
-    std::vector<int> gperm;
-    gperm.reserve(G);
-    auto by_slot = [&](int i) {
-        return h->h_gstart[i + 1] - h->h_gstart[i] == 1 && b->h_bidx[i] < 0;
-    };
-    for (int i = 0; i < G; ++i) if (b->h_bidx[i] >= 0) gperm.push_back(i);
-    for (int i = 0; i < G; ++i) if (b->h_bidx[i] < 0 && !by_slot(i)) gperm.push_back(i);
-    p->Gs = (int)gperm.size();
-    for (int i = 0; i < G; ++i) if (by_slot(i)) gperm.push_back(i);
-    // entries of the computed globals: the first two copies' rows inline,
-    // later copies in uxt; every entry's first row and copy count in gx
-    std::vector<int4> gtab(std::max(p->Gs, 1), make_int4(0, 0, 0, -1));
-    std::vector<int> uxt, gx(G);
-    for (int j = 0; j < G; ++j) {
-        const int i = gperm[j], s0 = h->h_gstart[i], cnt = h->h_gstart[i + 1] - s0;
-        if (cnt < 1 || cnt >= kBatchRecip || crow[s0] >= (1 << 24) || uxt.size() >= (1u << 22)) {
-            set_last_error("batch plan: global table");
-            return OPF_E_CAPACITY;
-        }
-        gx[j] = crow[s0] | (cnt << 24);
-        if (j >= p->Gs) continue;
-        gtab[j] = make_int4(crow[s0], cnt > 1 ? crow[s0 + 1] : 0, cnt | ((int)uxt.size() << 8), b->h_bidx[i]);
-        for (int q = 2; q < cnt; ++q) uxt.push_back(crow[s0 + q]);
+    // global-update tables (batch_tables.h): gperm, the computed globals'
+    // entries, later-copy rows and every global's first row
+    GlobalTables gt;
+    if (!build_global_tables(G, h->h_gstart, crow, b->h_bidx, &gt)) {
+        set_last_error("batch plan: global table");
+        return OPF_E_CAPACITY;
     }
+    p->Gs = gt.Gs;
+    std::vector<int4> gtab(std::max(p->Gs, 1), make_int4(0, 0, 0, -1));
+    for (int j = 0; j < p->Gs; ++j)
+        gtab[j] = make_int4(gt.gtab[4 * j], gt.gtab[4 * j + 1], gt.gtab[4 * j + 2], gt.gtab[4 * j + 3]);
+    const std::vector<int> &gperm = gt.gperm, &uxt = gt.uxt, &gx = gt.gx;
     p->n_uxt = (int)uxt.size();
     // shared memory
     p->off_u = fg ? 0u : a16((size_t)p->nF * sz);
