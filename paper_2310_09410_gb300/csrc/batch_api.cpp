@@ -81,141 +81,24 @@ int build_plan(opf_batch *b, BPlan *p, bool dbl, int K, int W, int nq, bool fg) 
     p->dbl = dbl;
     p->fg = fg;
     p->K = K; p->ks = ilog2(K); p->J = 32 / K; p->W = W; p->nq = nq; p->threads = 32 * W;
-    const int J = p->J, NPL = 4 * nq, S = h->S, L = h->L, G = h->G;
+    const int J = p->J, S = h->S, L = h->L, G = h->G;
     const size_t sz = dbl ? sizeof(double) : sizeof(float);
-    // per subsystem: positions p_d and chunks per position
-    std::vector<int> pd(S), nqd(S);
-    for (int d = 0; d < S; ++d) {
-        const int npad = h->h_npad[d];
-        int q = 1;
-        while (q * NPL < npad) q <<= 1;
-        if (q > J) { set_last_error("batch plan: a subsystem needs more lanes than a task has"); return OPF_E_CAPACITY; }
-        pd[d] = q;
-        nqd[d] = std::max(1, (npad + 4 * q - 1) / (4 * q));
-    }
-    // tasks: per class p, J / p members of similar shape
-    std::vector<BatchTask> tasks;
-    std::vector<int> memb;
-    for (int q = 1; q <= J; q <<= 1) {
-        std::vector<int> cls;
-        for (int d = 0; d < S; ++d) if (pd[d] == q) cls.push_back(d);
-        std::stable_sort(cls.begin(), cls.end(), [&](int x, int y) {
-            if (nqd[x] != nqd[y]) return nqd[x] > nqd[y];
-            return h->h_sf[x] > h->h_sf[y];
-        });
-        const int per = J / q;
-        for (size_t i = 0; i < cls.size(); i += per) {
-            BatchTask t;
-            memset(&t, 0, sizeof(t));
-            t.p = q; t.lp = ilog2(q);
-            for (int mb = 0; mb < per; ++mb) {
-                const int d = i + mb < cls.size() ? cls[i + mb] : -1;
-                memb.push_back(d);
-                if (d < 0) continue;
-                t.nq = std::max(t.nq, nqd[d]);
-                t.f = std::max(t.f, h->h_sf[d]);
-                if (h->h_mode[d]) t.modes |= 1 << mb;
-            }
-            for (int mb = per; mb < J; ++mb) memb.push_back(-1);
-            t.f += t.f & 1;        // rows in pairs (the packed extra row is zero)
-            tasks.push_back(t);
-        }
-    }
-    // decreasing cost (the engine hands tasks out in this order)
-    {
-        std::vector<double> cost(tasks.size());
-        for (size_t t = 0; t < tasks.size(); ++t)
-            cost[t] = tasks[t].nq * (tasks[t].f * (6.0 * 4 + 4 + 2 * tasks[t].lp) + 40.0) + 30.0;
-        std::vector<int> ord(tasks.size());
-        std::iota(ord.begin(), ord.end(), 0);
-        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-        std::vector<BatchTask> t2;
-        std::vector<int> m2;
-        for (int t : ord) {
-            t2.push_back(tasks[t]);
-            m2.insert(m2.end(), memb.begin() + (size_t)t * J, memb.begin() + (size_t)(t + 1) * J);
-        }
-        tasks.swap(t2);
-        memb.swap(m2);
-    }
-    // FP32 plans with a warp count divisible by 4: lambda and bbar~ of each
-    // task in tensor memory, in the lane quadrant of the warps that run it
-    // (a warp w reaches lanes 32 (w % 4) .. + 31 only).  Longest-first list
-    // scheduling of the tasks over the 4 quadrants by cost, 8 nq columns per
-    // task (per chunk 4 of lambda then 4 of bbar~), at most 512 per quadrant.
-    p->tm = false;
-    if (!dbl && b->allow_tmem && W % 4 == 0) {
-        std::vector<double> load(4, 0.0);
-        std::vector<int> used(4, 0), quad(tasks.size(), -1);
-        bool fits = true;
-        for (size_t t = 0; t < tasks.size() && fits; ++t) {
-            const double cost = tasks[t].nq * (tasks[t].f * (6.0 * 4 + 4 + 2 * tasks[t].lp) + 40.0) + 30.0;
-            int best = -1;
-            for (int q = 0; q < 4; ++q)
-                if (used[q] + 8 * tasks[t].nq <= 512 && (best < 0 || load[q] < load[best])) best = q;
-            if (best < 0) { fits = false; break; }
-            quad[t] = best;
-            load[best] += cost;
-            used[best] += 8 * tasks[t].nq;
-        }
-        if (fits) {
-            std::vector<BatchTask> t2;
-            std::vector<int> m2;
-            int cols[4] = {0, 0, 0, 0};
-            for (int q = 0; q < 4; ++q) {
-                p->qstart[q] = (int)t2.size();
-                for (size_t t = 0; t < tasks.size(); ++t) {
-                    if (quad[t] != q) continue;
-                    BatchTask tk = tasks[t];
-                    tk.tm = (cols[q] << 2) | q;
-                    cols[q] += 8 * tk.nq;
-                    t2.push_back(tk);
-                    m2.insert(m2.end(), memb.begin() + t * J, memb.begin() + (t + 1) * J);
-                }
-            }
-            p->qstart[4] = (int)t2.size();
-            tasks.swap(t2);
-            memb.swap(m2);
-            int mx = std::max(std::max(cols[0], cols[1]), std::max(cols[2], cols[3]));
-            p->tm_cols = 32;
-            while (p->tm_cols < mx) p->tm_cols <<= 1;
-            p->tm = true;
-        }
-    }
-    // chunk / factor offsets and slot tables
-    int ch = 0, fo = 0;
-    std::vector<int4> chg;
-    std::vector<int> sch(L, -1);
-    for (size_t t = 0; t < tasks.size(); ++t) {
-        BatchTask &tk = tasks[t];
-        tk.ch0 = ch;
-        tk.foff = fo;
-        chg.resize((size_t)ch + (size_t)tk.nq * J, make_int4(-1, -1, -1, -1));
-        for (int jpos = 0; jpos < J; ++jpos) {
-            const int mb = jpos >> tk.lp, part = jpos & (tk.p - 1);
-            const int d = memb[t * J + mb];
-            if (d < 0) continue;
-            const int so = h->h_soff[d], n = h->h_sn[d];
-            for (int q = 0; q < tk.nq; ++q) {
-                int g[4];
-                for (int e = 0; e < 4; ++e) {
-                    const int c = (part * tk.nq + q) * 4 + e;
-                    g[e] = -1;
-                    if (c < n) {
-                        g[e] = h->h_gk[so + c] * K;      // shared-memory row of the global
-                        sch[so + c] = (ch + q * J + jpos) * 4 + e;
-                    }
-                }
-                chg[(size_t)ch + q * J + jpos] = make_int4(g[0], g[1], g[2], g[3]);
-            }
-        }
-        ch += tk.nq * J;
-        fo += tk.f * tk.nq * J * 4;
-    }
-    for (int k = 0; k < L; ++k)
-        if (sch[k] < 0) { set_last_error("batch plan: slot without a chunk"); return OPF_E_INVALID; }
-    p->NCH = ch;
-    p->nF = (fo + 3) & ~3;
+    // warp tasks, tensor-memory quadrants, chunk and slot tables (batch_tables.h)
+    TaskPlan tp;
+    const int trc = build_task_plan(S, L, h->h_npad, h->h_sf, h->h_mode, h->h_soff, h->h_sn, h->h_gk, K, nq,
+                                    !dbl && b->allow_tmem && W % 4 == 0, &tp);
+    if (trc == 1) { set_last_error("batch plan: a subsystem needs more lanes than a task has"); return OPF_E_CAPACITY; }
+    if (trc) { set_last_error("batch plan: slot without a chunk"); return OPF_E_INVALID; }
+    std::vector<BatchTask> &tasks = tp.tasks;
+    std::vector<int> &memb = tp.memb, &sch = tp.sch;
+    std::vector<int4> chg(tp.chg.size() / 4);
+    for (size_t c = 0; c < chg.size(); ++c)
+        chg[c] = make_int4(tp.chg[4 * c], tp.chg[4 * c + 1], tp.chg[4 * c + 2], tp.chg[4 * c + 3]);
+    p->tm = tp.tm;
+    p->tm_cols = tp.tm_cols;
+    for (int q = 0; q < 5; ++q) p->qstart[q] = tp.qstart[q];
+    p->NCH = tp.NCH;
+    p->nF = tp.nF;
     p->n_tasks = (int)tasks.size();
     p->NB = b->NB;
     // slot-array row of every copy (global-major copy order)

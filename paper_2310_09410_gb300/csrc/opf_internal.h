@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/opf.h"
+#include "batch_tables.h"
 
 namespace opf {
 
@@ -198,15 +199,6 @@ inline int32_t cap_at_tests(int32_t max_iter, int32_t k) {
 
 constexpr int kBatchRecip = 256;   // copy counts of a global are below this (the 8-bit count field)
 
-struct BatchTask {
-    int ch0;     // first chunk
-    int nq;      // chunks per position
-    int f;       // factor rows (maximum over the members; absent rows are zero)
-    int foff;    // factor element (r, q, jpos, e) at foff + ((r * nq + q) * J + jpos) * 4 + e
-    int p, lp;   // positions per member and log2(p)
-    int modes;   // bit mb: member mb uses M = F^T F (1) or M = I - F^T F (0)
-    int tm;      // tensor-memory plans: (first column << 2) | lane quadrant of the task's lambda / bbar~
-};
 
 // Arguments of one batched-engine launch.  Instance column sc of CTA c holds
 // instance inst[c * K + sc] (-1: empty).  Engine arrays (type T):
