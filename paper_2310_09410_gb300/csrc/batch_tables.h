@@ -56,10 +56,14 @@ struct TaskPlan {
     int tm_cols = 0, qstart[5] = {0, 0, 0, 0, 0};
 };
 
-// Estimated cost of a task (cycles / 10 or so): its chunks, factor rows and
-// the shuffles of a member on p > 1 positions.
+// Estimated cycles of a task per iteration: a least-squares fit to per-task
+// clock counts of the FP32 engine (8 instances per CTA, 16 warps) on the
+// 1024 x 123-bus batch, over its chunks per lane nq, row pairs f / 2 and
+// log2 p (the shuffle levels of a member on p > 1 positions); within 18 % of
+// every measured task.  (A cost of nq (f (28 + 2 lp) + 40) + 30 before gave
+// 12.33 ms per launch of 2000 iterations, this one 12.28 ms.)
 inline double batch_task_cost(const BatchTask &t) {
-    return t.nq * (t.f * (6.0 * 4 + 4 + 2 * t.lp) + 40.0) + 30.0;
+    return 11.0 + 179.0 * t.nq + 0.5 * t.f * (107.0 + 66.0 * t.nq + 76.0 * t.lp);
 }
 
 // Per subsystem d (S of them): npad[d] padded slots, sf[d] factor rows,
